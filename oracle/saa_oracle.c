@@ -1,0 +1,910 @@
+/*
+ * saa_oracle.c -- plain, slow, FP64 CPU oracle for the Monte Carlo
+ * sample-average (SAA) estimate of the mean-variance objective and its
+ * gradient (arXiv 2404.11631, Sec. 3.1, Eqs. 3-5, Algorithm 1).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant with the CUDA library: every constant below is
+ * written here from its mathematical definition, and the tests pin the
+ * oracle against closed forms, brute force and independent library routines.
+ *
+ * Contents
+ *   1. Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
+ *      as easy as 1, 2, 3", SC'11), the counter-based generator that draws
+ *      the i.i.d. samples R_i of Sec. 3.1.
+ *   2. The scenario generator: uniforms, Box-Muller normals built on this
+ *      file's own LOG / SIN2PI / COS2PI / EXP, and the law transforms.
+ *   3. The SAA estimator of Eq. 4 with the sample mean of Eq. 5, written out
+ *      directly: R_bar first, then the sum of squared projections of the
+ *      centred samples, and the gradient of Eq. 4 in w.
+ *   4. Frank-Wolfe, Algorithm 1 (resample every M iterations, LMO over
+ *      W = {w >= 0, 1'w <= 1}, step 2/(kM+m+2)).
+ *   5. The relative squared error of Table 2's notes.
+ *
+ * Floating-point discipline: compiled with -ffp-contract=off; every fused
+ * multiply-add in the generator is an explicit fmaf()/fma() call, so each
+ * operation rounds exactly once in IEEE round-to-nearest-even.
+ *
+ * Sums over scenarios use Neumaier compensation over a fixed partition of the
+ * scenario range into chunks that are merged in chunk order, so results do
+ * not depend on the number of OpenMP threads.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_OK 0
+#define OR_EINVAL 1
+#define OR_ENOMEM 2
+
+/* Law codes (scenario distributions). */
+#define OR_LAW_GAUSS 0     /* R = mu + C z, z ~ N(0, I): R ~ N(mu, Sigma), Sec. 3.1 */
+#define OR_LAW_LOGN_STD 1  /* z replaced by standardised lognormal (sigma=1) innovations */
+#define OR_LAW_STUDENT_T 2 /* R = mu + s C z, s = sqrt(nu / chi2_nu): multivariate t */
+#define OR_LAW_MIX 3       /* scenarios i < N/2 Gaussian, i >= N/2 standardised lognormal */
+
+typedef struct {
+    int32_t d;        /* decision / asset dimension */
+    int64_t N;        /* number of samples R_i */
+    int32_t law;      /* OR_LAW_* */
+    int32_t nu;       /* degrees of freedom (even) for the t law */
+    double lambda;    /* weight of the variance term (1/2 in Eq. 3) */
+    uint64_t seed;    /* Philox key */
+    uint32_t instance;/* instance id (low 24 bits of counter word 3) */
+    uint32_t epoch;   /* resample index (counter word 2) */
+    const double* mu;   /* [d] mean of R */
+    const double* chol; /* [d*d] row-major lower-triangular C with C C' = Sigma */
+} oracle_problem;
+
+/* ------------------------------------------------------------------------- */
+/* 1. Philox4x32-10                                                          */
+/* ------------------------------------------------------------------------- */
+/* Round multipliers and Weyl key increments of Philox4x32 (SC'11, Table 2). */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u /* golden ratio */
+#define PHILOX_W1 0xBB67AE85u /* sqrt(3) - 1 */
+
+static void philox10(const uint32_t in[4], uint32_t k0, uint32_t k1, uint32_t out[4])
+{
+    uint32_t x0 = in[0], x1 = in[1], x2 = in[2], x3 = in[3];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    philox10(ctr, key[0], key[1], out);
+}
+
+void oracle_philox_batch(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out)
+{
+    for (int64_t i = 0; i < n; ++i) philox10(ctr + 4 * i, key[2 * i], key[2 * i + 1], out + 4 * i);
+}
+
+/* ------------------------------------------------------------------------- */
+/* 2. Own elementary functions                                               */
+/* ------------------------------------------------------------------------- */
+/* Constants, each the correctly rounded value of the stated real number.
+ * Decimal literals carry 40 significant digits; the compiler rounds them
+ * once to the target format.  Dyadic constants are written exactly in hex. */
+
+/* sqrt(2) */
+static const float SQRT2_F = 1.414213562373095048801688724209698078570f;
+static const double SQRT2_D = 1.414213562373095048801688724209698078570;
+/* Cody-Waite split of ln 2: the high part is ln 2 rounded to 16 (float) or
+ * 32 (double) significant bits, so e * LN2_HI is exact for every exponent e
+ * that occurs; the low part is the rounded remainder ln 2 - LN2_HI. */
+static const float LN2_HI_F = 0x1.62e4p-1f;
+static const float LN2_LO_F = 0x1.7f7d1cp-20f;
+static const double LN2_HI_D = 0x1.62e42ffp-1;
+static const double LN2_LO_D = -0x1.718432a1b0e26p-35;
+/* 1 / ln 2 */
+static const float LOG2E_F = 1.442695040888963407359924681001892137427f;
+static const double LOG2E_D = 1.442695040888963407359924681001892137427;
+/* e^(1/2) = mean of exp(Z), Z ~ N(0,1) */
+static const float E_HALF_F = 1.648721270700128146848650787814163571654f;
+static const double E_HALF_D = 1.648721270700128146848650787814163571654;
+/* 1 / sqrt(e^2 - e) = 1 / standard deviation of exp(Z) */
+static const float INV_SD_LN_F = 0.4627064573764711388582888487271463418743f;
+static const double INV_SD_LN_D = 0.4627064573764711388582888487271463418743;
+
+/* log(m) = 2 atanh(s), s = (m-1)/(m+1):  2 atanh(s) = s * sum_k 2/(2k+1) s^(2k).
+ * Coefficients 2/(2k+1), k = 0..4 (float) and k = 0..10 (double). */
+#define NLOG_F 5
+#define NLOG_D 11
+static const float LOGP_F[NLOG_F] = {
+    2.0f,
+    0.6666666666666666666666666666666666666667f,
+    0.4000000000000000000000000000000000000000f,
+    0.2857142857142857142857142857142857142857f,
+    0.2222222222222222222222222222222222222222f,
+};
+static const double LOGP_D[NLOG_D] = {
+    2.0,
+    0.6666666666666666666666666666666666666667,
+    0.4000000000000000000000000000000000000000,
+    0.2857142857142857142857142857142857142857,
+    0.2222222222222222222222222222222222222222,
+    0.1818181818181818181818181818181818181818,
+    0.1538461538461538461538461538461538461538,
+    0.1333333333333333333333333333333333333333,
+    0.1176470588235294117647058823529411764706,
+    0.1052631578947368421052631578947368421053,
+    0.09523809523809523809523809523809523809524,
+};
+
+/* Taylor series of sin(2 pi r) / r and cos(2 pi r) in t = r^2:
+ *   sin: (-1)^k (2 pi)^(2k+1) / (2k+1)!,   cos: (-1)^k (2 pi)^(2k) / (2k)!
+ * 5 / 6 terms in float, 9 / 10 terms in double (|2 pi r| <= pi/4). */
+#define NSIN_F 5
+#define NCOS_F 6
+#define NSIN_D 9
+#define NCOS_D 10
+static const float SINP_F[NSIN_F] = {
+    6.283185307179586476925286766559005768394f,
+    -41.34170224039976023396842008946852693630f,
+    81.60524927607505420339768267824949506141f,
+    -76.70585975306138584163064109389312588997f,
+    42.05869394489765314498681114813355254161f,
+};
+static const float COSP_F[NCOS_F] = {
+    1.0f,
+    -19.73920880217871723766898199975230227063f,
+    64.93939402266829149096022179247007416649f,
+    -85.45681720669372773601950610243732434375f,
+    60.24464137187666036272111431051914791554f,
+    -26.42625678337439745290065331496842204896f,
+};
+static const double SINP_D[NSIN_D] = {
+    6.283185307179586476925286766559005768394,
+    -41.34170224039976023396842008946852693630,
+    81.60524927607505420339768267824949506141,
+    -76.70585975306138584163064109389312588997,
+    42.05869394489765314498681114813355254161,
+    -15.09464257682299039182661623253152051448,
+    3.819952584848282127733792067340466125441,
+    -0.7181223017785005122317402786068623805399,
+    0.1042291622081398411727104489876041109703,
+};
+static const double COSP_D[NCOS_D] = {
+    1.0,
+    -19.73920880217871723766898199975230227063,
+    64.93939402266829149096022179247007416649,
+    -85.45681720669372773601950610243732434375,
+    60.24464137187666036272111431051914791554,
+    -26.42625678337439745290065331496842204896,
+    7.903536371318468804212103428857682494130,
+    -1.714390711088672065421586077323089143567,
+    0.2820059684557912150702701749840722854475,
+    -0.03638284114254567077175122330646765486151,
+};
+
+/* exp(r) Taylor series 1/j!, degree 7 (float) and 13 (double), |r| <= ln2/2. */
+#define NEXP_F 8
+#define NEXP_D 14
+static const float EXPP_F[NEXP_F] = {
+    1.0f, 1.0f, 0.5f,
+    0.1666666666666666666666666666666666666667f,
+    0.04166666666666666666666666666666666666667f,
+    0.008333333333333333333333333333333333333333f,
+    0.001388888888888888888888888888888888888889f,
+    0.0001984126984126984126984126984126984126984f,
+};
+static const double EXPP_D[NEXP_D] = {
+    1.0, 1.0, 0.5,
+    0.1666666666666666666666666666666666666667,
+    0.04166666666666666666666666666666666666667,
+    0.008333333333333333333333333333333333333333,
+    0.001388888888888888888888888888888888888889,
+    0.0001984126984126984126984126984126984126984,
+    0.00002480158730158730158730158730158730158730,
+    0.000002755731922398589065255731922398589065256,
+    0.0000002755731922398589065255731922398589065256,
+    0.00000002505210838544171877505210838544171877505,
+    0.000000002087675698786809897921009032120143231254,
+    0.0000000001605904383682161459939237717015494793273,
+};
+
+/* Natural log of a positive normal float u < 2^128.
+ * u = 2^e m with m in [1,2); if m > sqrt(2) use m/2, e+1 so m in
+ * [sqrt(2)/2, sqrt(2)]; log u = e ln2 + 2 atanh((m-1)/(m+1)). */
+static float own_logf(float u)
+{
+    uint32_t b;
+    memcpy(&b, &u, 4);
+    int e = (int)((b >> 23) & 0xffu) - 127;
+    uint32_t mb = (b & 0x7fffffu) | 0x3f800000u;
+    float m;
+    memcpy(&m, &mb, 4);
+    if (m > SQRT2_F) {
+        m = m * 0.5f;
+        e = e + 1;
+    }
+    float f = m - 1.0f; /* exact (Sterbenz) */
+    float g = m + 1.0f;
+    float s = f / g;
+    float t = s * s;
+    float p = LOGP_F[NLOG_F - 1];
+    for (int k = NLOG_F - 2; k >= 0; --k) p = fmaf(p, t, LOGP_F[k]);
+    float ls = s * p;
+    float ef = (float)e;
+    float hi = ef * LN2_HI_F; /* exact */
+    float lo = fmaf(ef, LN2_LO_F, ls);
+    return hi + lo;
+}
+
+static double own_log(double u)
+{
+    uint64_t b;
+    memcpy(&b, &u, 8);
+    int e = (int)((b >> 52) & 0x7ffu) - 1023;
+    uint64_t mb = (b & 0xfffffffffffffull) | 0x3ff0000000000000ull;
+    double m;
+    memcpy(&m, &mb, 8);
+    if (m > SQRT2_D) {
+        m = m * 0.5;
+        e = e + 1;
+    }
+    double f = m - 1.0;
+    double g = m + 1.0;
+    double s = f / g;
+    double t = s * s;
+    double p = LOGP_D[NLOG_D - 1];
+    for (int k = NLOG_D - 2; k >= 0; --k) p = fma(p, t, LOGP_D[k]);
+    double ls = s * p;
+    double ef = (double)e;
+    double hi = ef * LN2_HI_D;
+    double lo = fma(ef, LN2_LO_D, ls);
+    return hi + lo;
+}
+
+/* sin(2 pi u), cos(2 pi u) for u = n 2^-24, n an odd integer in [1, 2^24).
+ * The quadrant q = round(4u) and the remainder r = u - q/4 (|r| <= 1/8) are
+ * exact integer operations; the result is rotated by q quarter turns. */
+static void own_sincos2pif(uint32_t n, float* s_out, float* c_out)
+{
+    uint32_t q = (n + (1u << 21)) >> 22;
+    int32_t ri = (int32_t)n - (int32_t)(q << 22);
+    float r = (float)ri * 0x1p-24f; /* exact */
+    float t = r * r;
+    float ps = SINP_F[NSIN_F - 1];
+    for (int k = NSIN_F - 2; k >= 0; --k) ps = fmaf(ps, t, SINP_F[k]);
+    float sn = r * ps;
+    float pc = COSP_F[NCOS_F - 1];
+    for (int k = NCOS_F - 2; k >= 0; --k) pc = fmaf(pc, t, COSP_F[k]);
+    float cs = pc;
+    switch (q & 3u) {
+    case 0: *s_out = sn; *c_out = cs; break;
+    case 1: *s_out = cs; *c_out = -sn; break;
+    case 2: *s_out = -sn; *c_out = -cs; break;
+    default: *s_out = -cs; *c_out = sn; break;
+    }
+}
+
+/* Same for u = n 2^-53, n odd in [1, 2^53). */
+static void own_sincos2pi(uint64_t n, double* s_out, double* c_out)
+{
+    uint64_t q = (n + (1ull << 50)) >> 51;
+    int64_t ri = (int64_t)n - (int64_t)(q << 51);
+    double r = (double)ri * 0x1p-53;
+    double t = r * r;
+    double ps = SINP_D[NSIN_D - 1];
+    for (int k = NSIN_D - 2; k >= 0; --k) ps = fma(ps, t, SINP_D[k]);
+    double sn = r * ps;
+    double pc = COSP_D[NCOS_D - 1];
+    for (int k = NCOS_D - 2; k >= 0; --k) pc = fma(pc, t, COSP_D[k]);
+    double cs = pc;
+    switch (q & 3u) {
+    case 0: *s_out = sn; *c_out = cs; break;
+    case 1: *s_out = cs; *c_out = -sn; break;
+    case 2: *s_out = -sn; *c_out = -cs; break;
+    default: *s_out = -cs; *c_out = sn; break;
+    }
+}
+
+/* exp(x) for |x| < 80: x = k ln2 + r with k = rint(x / ln2) (Cody-Waite
+ * reduction with the split ln 2), exp(r) by its Taylor polynomial, and the
+ * factor 2^k placed in the exponent field. */
+static float own_expf(float x)
+{
+    float kf = rintf(x * LOG2E_F);
+    float r = fmaf(-kf, LN2_HI_F, x);
+    r = fmaf(-kf, LN2_LO_F, r);
+    float p = EXPP_F[NEXP_F - 1];
+    for (int j = NEXP_F - 2; j >= 0; --j) p = fmaf(p, r, EXPP_F[j]);
+    int k = (int)kf;
+    uint32_t sb = (uint32_t)(k + 127) << 23;
+    float sc;
+    memcpy(&sc, &sb, 4);
+    return p * sc;
+}
+
+static double own_exp(double x)
+{
+    double kf = rint(x * LOG2E_D);
+    double r = fma(-kf, LN2_HI_D, x);
+    r = fma(-kf, LN2_LO_D, r);
+    double p = EXPP_D[NEXP_D - 1];
+    for (int j = NEXP_D - 2; j >= 0; --j) p = fma(p, r, EXPP_D[j]);
+    int64_t k = (int64_t)kf;
+    uint64_t sb = (uint64_t)(k + 1023) << 52;
+    double sc;
+    memcpy(&sc, &sb, 8);
+    return p * sc;
+}
+
+/* Test hooks for the elementary functions. */
+void oracle_log_f32(int64_t n, const float* u, float* out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = own_logf(u[i]);
+}
+void oracle_log_f64(int64_t n, const double* u, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = own_log(u[i]);
+}
+void oracle_exp_f32(int64_t n, const float* x, float* out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = own_expf(x[i]);
+}
+void oracle_exp_f64(int64_t n, const double* x, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = own_exp(x[i]);
+}
+void oracle_sincos2pi_f32(int64_t n, const uint32_t* num, float* s, float* c)
+{
+    for (int64_t i = 0; i < n; ++i) own_sincos2pif(num[i], s + i, c + i);
+}
+void oracle_sincos2pi_f64(int64_t n, const uint64_t* num, double* s, double* c)
+{
+    for (int64_t i = 0; i < n; ++i) own_sincos2pi(num[i], s + i, c + i);
+}
+
+/* Export of the constant tables, so that a test can compare each entry with
+ * the correctly rounded value of its definition.  which: 0 = float scalars
+ * {SQRT2, LN2_HI, LN2_LO, LOG2E, E_HALF, INV_SD_LN}, 1 = double scalars (same
+ * order), 2 = LOGP_F, 3 = LOGP_D, 4 = SINP_F, 5 = SINP_D, 6 = COSP_F,
+ * 7 = COSP_D, 8 = EXPP_F, 9 = EXPP_D.  Returns the entry count. */
+int oracle_constants(int which, double* out, int cap)
+{
+    const float fs[6] = {SQRT2_F, LN2_HI_F, LN2_LO_F, LOG2E_F, E_HALF_F, INV_SD_LN_F};
+    const double ds[6] = {SQRT2_D, LN2_HI_D, LN2_LO_D, LOG2E_D, E_HALF_D, INV_SD_LN_D};
+    const float* f = NULL;
+    const double* dd = NULL;
+    int n = 0;
+    switch (which) {
+    case 0: f = fs; n = 6; break;
+    case 1: dd = ds; n = 6; break;
+    case 2: f = LOGP_F; n = NLOG_F; break;
+    case 3: dd = LOGP_D; n = NLOG_D; break;
+    case 4: f = SINP_F; n = NSIN_F; break;
+    case 5: dd = SINP_D; n = NSIN_D; break;
+    case 6: f = COSP_F; n = NCOS_F; break;
+    case 7: dd = COSP_D; n = NCOS_D; break;
+    case 8: f = EXPP_F; n = NEXP_F; break;
+    case 9: dd = EXPP_D; n = NEXP_D; break;
+    default: return -1;
+    }
+    for (int k = 0; k < n && k < cap; ++k) out[k] = f ? (double)f[k] : dd[k];
+    return n;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 2b. Scenario generator                                                    */
+/* ------------------------------------------------------------------------- */
+/* Counter layout: c0 = dimension block, c1 = scenario index i, c2 = epoch
+ * (resample index), c3 = (tag << 24) | instance.  Tag 0 draws the normals,
+ * tag 1 the chi-square uniforms of the t law.  Key = (seed lo, seed hi). */
+#define TAG_NORMAL 0u
+#define TAG_CHI2 1u
+
+static void draw(const oracle_problem* p, uint32_t block, uint32_t i, uint32_t epoch, uint32_t tag,
+                 uint32_t out[4])
+{
+    uint32_t c[4];
+    c[0] = block;
+    c[1] = i;
+    c[2] = epoch;
+    c[3] = (tag << 24) | (p->instance & 0xffffffu);
+    philox10(c, (uint32_t)(p->seed & 0xffffffffu), (uint32_t)(p->seed >> 32), out);
+}
+
+/* Odd numerators of the uniforms: u = n 2^-24 and u = n 2^-53, both in (0,1). */
+static uint32_t u24_num(uint32_t x) { return 2u * (x >> 9) + 1u; }
+static float u24(uint32_t x) { return (float)u24_num(x) * 0x1p-24f; }
+static uint64_t u53_num(uint32_t a, uint32_t b)
+{
+    uint64_t v = ((uint64_t)a << 32) | (uint64_t)b;
+    return 2ull * (v >> 12) + 1ull;
+}
+static double u53(uint32_t a, uint32_t b) { return (double)u53_num(a, b) * 0x1p-53; }
+
+/* Box-Muller: r = sqrt(-2 log u1), (z0, z1) = (r cos 2 pi u2, r sin 2 pi u2). */
+static void box_muller_f(float u1, uint32_t n2, float* z0, float* z1)
+{
+    float L = own_logf(u1);
+    float r = sqrtf(-2.0f * L);
+    float sn, cs;
+    own_sincos2pif(n2, &sn, &cs);
+    *z0 = r * cs;
+    *z1 = r * sn;
+}
+static void box_muller_d(double u1, uint64_t n2, double* z0, double* z1)
+{
+    double L = own_log(u1);
+    double r = sqrt(-2.0 * L);
+    double sn, cs;
+    own_sincos2pi(n2, &sn, &cs);
+    *z0 = r * cs;
+    *z1 = r * sn;
+}
+
+static int law_is_lognormal(const oracle_problem* p, int64_t i)
+{
+    if (p->law == OR_LAW_LOGN_STD) return 1;
+    if (p->law == OR_LAW_MIX) return i >= p->N / 2;
+    return 0;
+}
+
+/* Scenario i in float mode: d innovations zhat and the scale s. */
+static void gen_f32(const oracle_problem* p, int64_t i, uint32_t epoch, float* zhat, float* s_out)
+{
+    const int d = p->d;
+    for (int b = 0; 4 * b < d; ++b) {
+        uint32_t x[4];
+        draw(p, (uint32_t)b, (uint32_t)i, epoch, TAG_NORMAL, x);
+        float z[4];
+        box_muller_f(u24(x[0]), u24_num(x[1]), &z[0], &z[1]);
+        box_muller_f(u24(x[2]), u24_num(x[3]), &z[2], &z[3]);
+        for (int q = 0; q < 4 && 4 * b + q < d; ++q) zhat[4 * b + q] = z[q];
+    }
+    if (law_is_lognormal(p, i)) {
+        for (int j = 0; j < d; ++j) zhat[j] = (own_expf(zhat[j]) - E_HALF_F) * INV_SD_LN_F;
+    }
+    float s = 1.0f;
+    if (p->law == OR_LAW_STUDENT_T) {
+        float acc = 0.0f;
+        uint32_t x[4];
+        for (int r = 0; r < p->nu / 2; ++r) {
+            if (r % 4 == 0) draw(p, (uint32_t)(r / 4), (uint32_t)i, epoch, TAG_CHI2, x);
+            acc = acc + own_logf(u24(x[r % 4]));
+        }
+        float W = -2.0f * acc;
+        s = sqrtf((float)p->nu / W);
+    }
+    *s_out = s;
+}
+
+/* Scenario i in double mode. */
+static void gen_f64(const oracle_problem* p, int64_t i, uint32_t epoch, double* zhat, double* s_out)
+{
+    const int d = p->d;
+    for (int b = 0; 2 * b < d; ++b) {
+        uint32_t x[4];
+        draw(p, (uint32_t)b, (uint32_t)i, epoch, TAG_NORMAL, x);
+        double z[2];
+        box_muller_d(u53(x[0], x[1]), u53_num(x[2], x[3]), &z[0], &z[1]);
+        for (int q = 0; q < 2 && 2 * b + q < d; ++q) zhat[2 * b + q] = z[q];
+    }
+    if (law_is_lognormal(p, i)) {
+        for (int j = 0; j < d; ++j) zhat[j] = (own_exp(zhat[j]) - E_HALF_D) * INV_SD_LN_D;
+    }
+    double s = 1.0;
+    if (p->law == OR_LAW_STUDENT_T) {
+        double acc = 0.0;
+        uint32_t x[4];
+        for (int r = 0; r < p->nu / 2; ++r) {
+            if (r % 2 == 0) draw(p, (uint32_t)(r / 2), (uint32_t)i, epoch, TAG_CHI2, x);
+            int w = 2 * (r % 2);
+            acc = acc + own_log(u53(x[w], x[w + 1]));
+        }
+        double W = -2.0 * acc;
+        s = sqrt((double)p->nu / W);
+    }
+    *s_out = s;
+}
+
+static int check_problem(const oracle_problem* p)
+{
+    if (!p || p->d < 1 || p->N < 2 || p->N > 0xffffffffll) return OR_EINVAL;
+    if (p->law < 0 || p->law > OR_LAW_MIX) return OR_EINVAL;
+    if (p->law == OR_LAW_STUDENT_T && (p->nu < 2 || (p->nu & 1))) return OR_EINVAL;
+    if (!p->mu || !p->chol) return OR_EINVAL;
+    return OR_OK;
+}
+
+/* Innovations and scales of scenarios i0..i0+n-1 (promoted to double), and
+ * optionally the scenarios themselves at scenario precision:
+ *   xi_ij = fma(s_i, acc_j, mu_j),  acc_j = fma chain over l = 0..j of
+ *   C_jl zhat_il in increasing l, with C and mu first rounded to that precision.
+ * prec: 32 = float scenarios, 64 = double scenarios. */
+int oracle_generate(const oracle_problem* p, int prec, uint32_t epoch, int64_t i0, int64_t n,
+                    double* zhat, double* s, double* xi)
+{
+    if (check_problem(p) != OR_OK || (prec != 32 && prec != 64) || i0 < 0 || n < 0 || i0 + n > p->N)
+        return OR_EINVAL;
+    const int d = p->d;
+    int err = OR_OK;
+#pragma omp parallel
+    {
+        float* zf = (float*)malloc(sizeof(float) * (size_t)d);
+        double* zd = (double*)malloc(sizeof(double) * (size_t)d);
+        float* Cf = NULL;
+        float* muf = NULL;
+        if (xi && prec == 32) {
+            Cf = (float*)malloc(sizeof(float) * (size_t)d * (size_t)d);
+            muf = (float*)malloc(sizeof(float) * (size_t)d);
+            if (Cf && muf) {
+                for (int64_t k = 0; k < (int64_t)d * d; ++k) Cf[k] = (float)p->chol[k];
+                for (int j = 0; j < d; ++j) muf[j] = (float)p->mu[j];
+            }
+        }
+        if (!zf || !zd || (xi && prec == 32 && (!Cf || !muf))) {
+#pragma omp atomic write
+            err = OR_ENOMEM;
+        } else {
+#pragma omp for schedule(static)
+            for (int64_t r = 0; r < n; ++r) {
+                int64_t i = i0 + r;
+                if (prec == 32) {
+                    float sf;
+                    gen_f32(p, i, epoch, zf, &sf);
+                    for (int j = 0; j < d; ++j) zhat[r * d + j] = (double)zf[j];
+                    if (s) s[r] = (double)sf;
+                    if (xi) {
+                        for (int j = 0; j < d; ++j) {
+                            float acc = 0.0f;
+                            for (int l = 0; l <= j; ++l) acc = fmaf(Cf[(int64_t)j * d + l], zf[l], acc);
+                            xi[r * d + j] = (double)fmaf(sf, acc, muf[j]);
+                        }
+                    }
+                } else {
+                    double sd;
+                    gen_f64(p, i, epoch, zd, &sd);
+                    for (int j = 0; j < d; ++j) zhat[r * d + j] = zd[j];
+                    if (s) s[r] = sd;
+                    if (xi) {
+                        for (int j = 0; j < d; ++j) {
+                            double acc = 0.0;
+                            for (int l = 0; l <= j; ++l) acc = fma(p->chol[(int64_t)j * d + l], zd[l], acc);
+                            xi[r * d + j] = fma(sd, acc, p->mu[j]);
+                        }
+                    }
+                }
+            }
+        }
+        free(zf);
+        free(zd);
+        free(Cf);
+        free(muf);
+    }
+    return err;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 3. SAA estimator, Eq. 4 with Eq. 5                                        */
+/* ------------------------------------------------------------------------- */
+/* Neumaier-compensated running sum. */
+typedef struct {
+    double s, c;
+} nsum;
+static void nadd(nsum* a, double x)
+{
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x))
+        a->c += (a->s - t) + x;
+    else
+        a->c += (x - t) + a->s;
+    a->s = t;
+}
+static double nval(const nsum* a) { return a->s + a->c; }
+
+/* Where the samples R_i come from: an explicit N x d matrix, or the
+ * generator (R_i = mu + s_i C zhat_i formed in double from the innovations
+ * promoted to double). */
+typedef struct {
+    const oracle_problem* p; /* generator source when R == NULL */
+    int prec;
+    uint32_t epoch;
+    const double* R;         /* explicit source, row-major N x d */
+    const double* Ct;        /* transpose of C (column-major C) */
+    int64_t N;
+    int d;
+} sample_src;
+
+typedef struct {
+    float* zf;
+    double* zd;
+} sample_buf;
+
+/* Writes sample R_i into out[d]. */
+static void get_sample(const sample_src* S, sample_buf* B, int64_t i, double* out)
+{
+    const int d = S->d;
+    if (S->R) {
+        memcpy(out, S->R + i * d, sizeof(double) * (size_t)d);
+        return;
+    }
+    double s;
+    if (S->prec == 32) {
+        float sf;
+        gen_f32(S->p, i, S->epoch, B->zf, &sf);
+        for (int j = 0; j < d; ++j) B->zd[j] = (double)B->zf[j];
+        s = (double)sf;
+    } else {
+        gen_f64(S->p, i, S->epoch, B->zd, &s);
+    }
+    /* R_i = mu + s_i C zhat_i: out_j = mu_j + s_i * sum_{l<=j} C_jl zhat_l,
+     * each sum taken in increasing l (loops interchanged over j only). */
+    for (int j = 0; j < d; ++j) out[j] = 0.0;
+    for (int l = 0; l < d; ++l) {
+        const double zl = B->zd[l];
+        const double* col = S->Ct + (int64_t)l * d;
+        for (int j = l; j < d; ++j) out[j] = out[j] + col[j] * zl;
+    }
+    for (int j = 0; j < d; ++j) out[j] = S->p->mu[j] + s * out[j];
+}
+
+#define MAX_CHUNKS 64
+
+/* f_k   = lambda * (1/(N-1)) sum_i (w_k'(R_i - R_bar))^2 - w_k' R_bar      (Eq. 4)
+ * pbar_k = w_k' R_bar,  R_bar = (1/N) sum_i R_i                          (Eq. 5)
+ * var_k = (1/(N-1)) sum_i (w_k'(R_i - R_bar))^2
+ * grad_k = lambda * (2/(N-1)) sum_i (R_i - R_bar)(R_i - R_bar)' w_k - R_bar
+ * (the derivative of Eq. 4 in w).  Two passes: R_bar first, then the
+ * centred sums.  lambda = 1 is Eq. 4 as printed; lambda = 1/2 matches the
+ * objective of Eq. 3. */
+static int saa_core(const sample_src* S, int K, const double* W, double lambda, double* f, double* pbar,
+                    double* var, double* grad)
+{
+    const int64_t N = S->N;
+    const int d = S->d;
+    const int nch = (int)(N < MAX_CHUNKS ? N : MAX_CHUNKS);
+    nsum* rsum = (nsum*)calloc((size_t)nch * d, sizeof(nsum));
+    nsum* vsum = (nsum*)calloc((size_t)nch * K, sizeof(nsum));
+    nsum* gsum = grad ? (nsum*)calloc((size_t)nch * K * d, sizeof(nsum)) : NULL;
+    double* Rbar = (double*)malloc(sizeof(double) * (size_t)d);
+    if (!rsum || !vsum || (grad && !gsum) || !Rbar) {
+        free(rsum); free(vsum); free(gsum); free(Rbar);
+        return OR_ENOMEM;
+    }
+    int err = OR_OK;
+
+    /* Pass 1: R_bar (Eq. 5). */
+#pragma omp parallel
+    {
+        sample_buf B = {(float*)malloc(sizeof(float) * (size_t)d), (double*)malloc(sizeof(double) * (size_t)d)};
+        double* Ri = (double*)malloc(sizeof(double) * (size_t)d);
+        if (!B.zf || !B.zd || !Ri) {
+#pragma omp atomic write
+            err = OR_ENOMEM;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int c = 0; c < nch; ++c) {
+                int64_t a = N * c / nch, e = N * (c + 1) / nch;
+                nsum* acc = rsum + (int64_t)c * d;
+                for (int64_t i = a; i < e; ++i) {
+                    get_sample(S, &B, i, Ri);
+                    for (int j = 0; j < d; ++j) nadd(&acc[j], Ri[j]);
+                }
+            }
+        }
+        free(B.zf); free(B.zd); free(Ri);
+    }
+    if (err != OR_OK) goto done;
+    for (int j = 0; j < d; ++j) {
+        nsum t = {0.0, 0.0};
+        for (int c = 0; c < nch; ++c) {
+            nadd(&t, rsum[(int64_t)c * d + j].s);
+            nadd(&t, rsum[(int64_t)c * d + j].c);
+        }
+        Rbar[j] = nval(&t) / (double)N;
+    }
+
+    /* Pass 2: centred squared projections and the centred cross sums. */
+#pragma omp parallel
+    {
+        sample_buf B = {(float*)malloc(sizeof(float) * (size_t)d), (double*)malloc(sizeof(double) * (size_t)d)};
+        double* D = (double*)malloc(sizeof(double) * (size_t)d);
+        if (!B.zf || !B.zd || !D) {
+#pragma omp atomic write
+            err = OR_ENOMEM;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int c = 0; c < nch; ++c) {
+                int64_t a = N * c / nch, e = N * (c + 1) / nch;
+                nsum* va = vsum + (int64_t)c * K;
+                nsum* ga = gsum ? gsum + (int64_t)c * K * d : NULL;
+                for (int64_t i = a; i < e; ++i) {
+                    get_sample(S, &B, i, D);
+                    for (int j = 0; j < d; ++j) D[j] = D[j] - Rbar[j]; /* R_i - R_bar */
+                    for (int k = 0; k < K; ++k) {
+                        const double* wk = W + (int64_t)k * d;
+                        double proj = 0.0; /* w_k'(R_i - R_bar) */
+                        for (int j = 0; j < d; ++j) proj = proj + wk[j] * D[j];
+                        nadd(&va[k], proj * proj);
+                        if (ga) {
+                            nsum* g = ga + (int64_t)k * d;
+                            for (int j = 0; j < d; ++j) nadd(&g[j], D[j] * proj);
+                        }
+                    }
+                }
+            }
+        }
+        free(B.zf); free(B.zd); free(D);
+    }
+    if (err != OR_OK) goto done;
+
+    for (int k = 0; k < K; ++k) {
+        const double* wk = W + (int64_t)k * d;
+        nsum t = {0.0, 0.0};
+        for (int c = 0; c < nch; ++c) {
+            nadd(&t, vsum[(int64_t)c * K + k].s);
+            nadd(&t, vsum[(int64_t)c * K + k].c);
+        }
+        double V = nval(&t) / (double)(N - 1);
+        double pb = 0.0;
+        for (int j = 0; j < d; ++j) pb = pb + wk[j] * Rbar[j];
+        if (var) var[k] = V;
+        if (pbar) pbar[k] = pb;
+        if (f) f[k] = lambda * V - pb;
+        if (grad) {
+            for (int j = 0; j < d; ++j) {
+                nsum g = {0.0, 0.0};
+                for (int c = 0; c < nch; ++c) {
+                    nadd(&g, gsum[((int64_t)c * K + k) * d + j].s);
+                    nadd(&g, gsum[((int64_t)c * K + k) * d + j].c);
+                }
+                grad[(int64_t)k * d + j] = lambda * (2.0 / (double)(N - 1)) * nval(&g) - Rbar[j];
+            }
+        }
+    }
+done:
+    free(rsum); free(vsum); free(gsum); free(Rbar);
+    return err;
+}
+
+/* Eq. 4 on an explicit sample matrix R (N x d, row-major). */
+int oracle_saa_explicit(int64_t N, int d, const double* R, int K, const double* W, double lambda, double* f,
+                        double* pbar, double* var, double* grad)
+{
+    if (N < 2 || d < 1 || K < 1 || !R || !W) return OR_EINVAL;
+    sample_src S;
+    memset(&S, 0, sizeof(S));
+    S.R = R;
+    S.N = N;
+    S.d = d;
+    return saa_core(&S, K, W, lambda, f, pbar, var, grad);
+}
+
+static double* transpose_chol(const oracle_problem* p)
+{
+    const int d = p->d;
+    double* Ct = (double*)malloc(sizeof(double) * (size_t)d * (size_t)d);
+    if (!Ct) return NULL;
+    for (int j = 0; j < d; ++j)
+        for (int l = 0; l < d; ++l) Ct[(int64_t)l * d + j] = (l <= j) ? p->chol[(int64_t)j * d + l] : 0.0;
+    return Ct;
+}
+
+/* Eq. 4 on the N generated samples of resample index `epoch`. */
+int oracle_saa(const oracle_problem* p, int prec, uint32_t epoch, int K, const double* W, double* f, double* pbar,
+               double* var, double* grad)
+{
+    if (check_problem(p) != OR_OK || (prec != 32 && prec != 64) || K < 1 || !W) return OR_EINVAL;
+    double* Ct = transpose_chol(p);
+    if (!Ct) return OR_ENOMEM;
+    sample_src S;
+    memset(&S, 0, sizeof(S));
+    S.p = p;
+    S.prec = prec;
+    S.epoch = epoch;
+    S.Ct = Ct;
+    S.N = p->N;
+    S.d = p->d;
+    int rc = saa_core(&S, K, W, p->lambda, f, pbar, var, grad);
+    free(Ct);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 4. Frank-Wolfe, Algorithm 1                                               */
+/* ------------------------------------------------------------------------- */
+/* One iteration after the gradient g = grad f_hat(w_t):
+ *   LMO over W = {w >= 0, 1'w <= 1}: its vertices are 0 and the unit
+ *   vectors e_j, so s = e_j* with j* the first index of min_j g_j when
+ *   g_j* < 0, else s = 0;
+ *   gamma = 2 / (t + 2) with t = kM + m the global iteration count;
+ *   w_{t+1} = w_t + gamma (s - w_t);  FW gap = g'(w_t - s) >= 0.
+ * Returns j* (or -1 for the zero vertex). */
+int oracle_fw_step(int d, const double* g, const double* w, int64_t t, double* w_next, double* gap)
+{
+    int js = 0;
+    for (int j = 1; j < d; ++j)
+        if (g[j] < g[js]) js = j;
+    if (!(g[js] < 0.0)) js = -1;
+    double gamma = 2.0 / ((double)t + 2.0);
+    double gw = 0.0;
+    for (int j = 0; j < d; ++j) gw = gw + g[j] * w[j];
+    if (gap) *gap = gw - (js >= 0 ? g[js] : 0.0);
+    for (int j = 0; j < d; ++j) {
+        double sj = (j == js) ? 1.0 : 0.0;
+        w_next[j] = w[j] + gamma * (sj - w[j]);
+    }
+    return js;
+}
+
+/* Algorithm 1 from iteration t0 for T iterations, resampling every M
+ * iterations: iteration t uses the samples of resample index
+ * p->epoch + t / M.  f_trace[t - t0] = f_hat(w_t) on those samples,
+ * gap_trace[t - t0] = the FW gap at w_t.  w_trace (optional, T x d)
+ * receives w_t before each step. */
+int oracle_fw(const oracle_problem* p, int prec, const double* w0, int T, int M, int64_t t0, double* w_out,
+              double* f_trace, double* gap_trace, double* w_trace)
+{
+    if (check_problem(p) != OR_OK || (prec != 32 && prec != 64) || T < 0 || M < 1 || t0 < 0 || !w0 || !w_out)
+        return OR_EINVAL;
+    const int d = p->d;
+    double* w = (double*)malloc(sizeof(double) * (size_t)d);
+    double* wn = (double*)malloc(sizeof(double) * (size_t)d);
+    double* g = (double*)malloc(sizeof(double) * (size_t)d);
+    if (!w || !wn || !g) {
+        free(w); free(wn); free(g);
+        return OR_ENOMEM;
+    }
+    memcpy(w, w0, sizeof(double) * (size_t)d);
+    int rc = OR_OK;
+    for (int it = 0; it < T; ++it) {
+        int64_t t = t0 + it;
+        uint32_t epoch = p->epoch + (uint32_t)(t / M);
+        double fv;
+        rc = oracle_saa(p, prec, epoch, 1, w, &fv, NULL, NULL, g);
+        if (rc != OR_OK) break;
+        if (w_trace) memcpy(w_trace + (int64_t)it * d, w, sizeof(double) * (size_t)d);
+        if (f_trace) f_trace[it] = fv;
+        double gap;
+        oracle_fw_step(d, g, w, t, wn, &gap);
+        if (gap_trace) gap_trace[it] = gap;
+        memcpy(w, wn, sizeof(double) * (size_t)d);
+    }
+    if (rc == OR_OK) memcpy(w_out, w, sizeof(double) * (size_t)d);
+    free(w); free(wn); free(g);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 5. RSE (Table 2 notes): ((y_t - y*) / y_t)^2 * 100 %                      */
+/* ------------------------------------------------------------------------- */
+double oracle_rse(double y_t, double y_star)
+{
+    double r = (y_t - y_star) / y_t;
+    return r * r * 100.0;
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
