@@ -1,0 +1,327 @@
+"""Throughput of the SAA hot path on GB300: scenario-decision evals/s.
+
+One step = one saa_eval of the mean-variance SAA estimate (Eq. 4, Sec. 3.1 of
+arXiv 2404.11631) over the whole workload: prologue (y_k = C'w_k), in-kernel
+Philox scenario generation, the scenario x decision contraction, the fused
+S1/S2 epilogue, the FP64 cross-block reduction and the finalize.
+
+Workload (default): d = 128 assets, N = 2^20 scenarios (first half Gaussian,
+second half standardised lognormal sigma = 1), K = 256 candidate decisions
+x ~ U[0,1]^d, mu ~ U[-1,1]^d, Sigma = LL' + 0.1 I, Philox seed 0.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec P]
+       python bench.py --impl reference ...   (the CPU oracle, bounded sample)
+Under torchrun each rank evaluates its own independent instance (instance id
+= rank): the work is partitioned with no data-path collective (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="batched_d128_N1M_K256_mix", d=128, N=1 << 20, K=256, law=3)
+METRIC = "scenario-decision evals/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                for line in out.stdout.strip().splitlines():
+                    self.rows.append([c.strip() for c in line.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(d, K, law, n_target_s=12.0, N_full=1 << 20, rank=0):
+    """Times the CPU oracle on a bounded sample of the workload (scenarios
+    N' < N, all K decisions); returns (evals/s, sample description, cores)."""
+    import oracle
+    from paper_2404_11631_gb300 import inputs
+    inst = inputs.instance(d, 0)
+    X = inputs.decisions(K, d, 0)
+    n = 1 << 12
+    while True:
+        prob = oracle.make_problem(d, n, inst.mu, inst.chol, law=law, seed=0, instance=rank)
+        t0 = time.perf_counter()
+        oracle.saa(prob, 32, X)
+        dt = time.perf_counter() - t0
+        if dt >= n_target_s / 4 or n * 2 > N_full:
+            break
+        n *= 2
+    if dt < n_target_s and n * 2 <= N_full:
+        scale = max(1, int(n_target_s / max(dt, 1e-3)))
+        n2 = min(N_full, n * min(scale, 8))
+        prob = oracle.make_problem(d, n2, inst.mu, inst.chol, law=law, seed=0, instance=rank)
+        t0 = time.perf_counter()
+        oracle.saa(prob, 32, X)
+        dt = time.perf_counter() - t0
+        n = n2
+    return n * K / dt, dt, n, oracle.max_threads()
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    d, N, K, law = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["K"], WORKLOAD["law"]
+    import oracle
+    from paper_2404_11631_gb300 import inputs
+    inst = inputs.instance(d, 0)
+    X = inputs.decisions(K, d, 0)
+    # per-step sample sized so that warmup + steps stay within a few minutes
+    n = 1 << 13
+    prob = oracle.make_problem(d, n, inst.mu, inst.chol, law=law, seed=0)
+    t0 = time.perf_counter()
+    oracle.saa(prob, 32, X)
+    one = time.perf_counter() - t0
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    while one * 2 < budget and n * 2 <= N:
+        n *= 2
+        one *= 2
+    prob = oracle.make_problem(d, n, inst.mu, inst.chol, law=law, seed=0)
+    for _ in range(args.warmup):
+        oracle.saa(prob, 32, X)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.saa(prob, 32, X)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = n * K / (ms / 1e3)
+    cores = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "d": d, "N": N, "K": K, "law": "half Gaussian / half lognormal",
+                   "sample_N_per_step": n},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n} of {N} scenarios x all {K} decisions per step (FP64 oracle, OpenMP)"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2404_11631_gb300 import inputs, saa
+
+    world, rank, local = _dist()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    d, N, K, law = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["K"], WORKLOAD["law"]
+    prec = args.prec
+    inst = inputs.instance(d, 0)
+    Xn = inputs.decisions(K, d, 0)
+    mu = torch.tensor(inst.mu, device=dev)
+    ch = torch.tensor(inst.chol, device=dev)
+    X = torch.tensor(Xn, device=dev)
+    prob = saa.Problem(mu=mu, chol=ch, N=N, law=law, seed=0, instance=rank)
+    ws = torch.empty(saa.workspace_size(prob, K, prec, 0), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return saa.saa_eval(prob, X, prec, ws=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    saa.saa_profile_enable(True, dev.index)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else 0) as clk:
+        for i in range(args.steps):
+            flush.zero_()                       # L2 flushed between timed steps (outside the event pair)
+            ev[i][0].record(stream)
+            out = step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+    main_ms, main_n, launched = saa.saa_profile_read(dev.index)
+    saa.saa_profile_enable(False, dev.index)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        dist.barrier()
+    ms_per_step = 1e3 * total_s / args.steps
+    value = world * N * K * args.steps / total_s
+
+    # e2e through the public API with host buffers: H2D of the step's inputs
+    # (mu, C, X from pinned memory) and D2H of f inside the timed region.
+    mu_h = torch.tensor(inst.mu).pin_memory()
+    ch_h = torch.tensor(inst.chol).pin_memory()
+    X_h = torch.tensor(Xn).pin_memory()
+    f_h = torch.empty(K, dtype=torch.float64).pin_memory()
+    mu_d, ch_d, X_d = torch.empty_like(mu), torch.empty_like(ch), torch.empty_like(X)
+    prob_e = saa.Problem(mu=mu_d, chol=ch_d, N=N, law=law, seed=0, instance=rank)
+
+    def e2e_step():
+        mu_d.copy_(mu_h, non_blocking=True)
+        ch_d.copy_(ch_h, non_blocking=True)
+        X_d.copy_(X_h, non_blocking=True)
+        r = saa.saa_eval(prob_e, X_d, prec, pbar=False, var=False, ws=ws)
+        f_h.copy_(r["f"], non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        e2e_ev[i][0].record(stream)
+        e2e_step()
+        e2e_ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * N * K * args.steps / e2e_s
+    h2d = (mu_h.numel() + ch_h.numel() + X_h.numel()) * 8
+    d2h = K * 8
+
+    peaks, peak_src = _peaks()
+    kern_s = main_ms / 1e3 / max(1, main_n)
+    if prec == "bf16x3":
+        flops = 3 * 2.0 * N * d * K
+        peak = float(peaks["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": flops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / kern_s / 1e12 / peak, "traffic": None,
+                "peak_source": f"{peak_src} bf16 dense (burst)",
+                "note": "BF16x3 = three tensor products (hi*hi, hi*lo, lo*hi) per scenario-decision-dimension"}
+    else:
+        lanes = 128 if prec == "fp32" else 2   # FP32 FMA lanes / FP64 FMA units per SM per clock
+        flops = 2.0 * N * d * K
+        peak = 152 * lanes * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / kern_s / 1e12 / peak, "traffic": None,
+                "peak_source": f"derived: 152 SMs x {lanes} FMA/clk x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz",
+                "note": "achieved counts the contraction's 2Nd K flops only (the RNG ALU work is extra)"}
+    roof["kernel_ms"] = kern_s * 1e3
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3"}[prec],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "d": d, "N": N, "K": K,
+                   "law": "half Gaussian / half standardised lognormal", "prec": prec,
+                   "l2": "flushed (256 MB write) between timed steps", "instances": world},
+        "gpu_launches": int(launched),
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": roof,
+    }
+    if rank == 0:
+        line["clocks"] = clk.summary()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, n, cores = oracle_sample(d, K, law)
+        line["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{n} of {N} scenarios x all {K} decisions, {dt:.1f} s (FP64 oracle)"}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default=os.environ.get("SAA_BENCH_PREC", "fp32"), choices=["fp64", "fp32", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

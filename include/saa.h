@@ -1,0 +1,181 @@
+/*
+ * saa.h -- C ABI of libsaa: GPU Monte Carlo sample-average (SAA) estimation
+ * of the mean-variance objective, its gradient, and the Frank-Wolfe loop of
+ * arXiv 2404.11631 ("A Preliminary Study on Accelerating Simulation
+ * Optimization with GPU Implementation"), Sec. 3.1.
+ *
+ * Problem (Sec. 3.1, Eq. 3): minimise f(w) = (1/2) Var[w'R] - E[w'R] over
+ * W = {w >= 0, 1'w <= 1}, R ~ D(mu, Sigma).  The SAA estimate (Eq. 4, with
+ * the sample mean R_bar of Eq. 5) over N samples R_i is
+ *
+ *     f_hat(w) = lambda * (1/(N-1)) sum_i (w'(R_i - R_bar))^2 - w'R_bar,
+ *
+ * lambda = 1/2 reproducing Eq. 3 (Eq. 4 as printed has lambda = 1).  The
+ * library evaluates f_hat and grad_w f_hat for K candidate decisions at once
+ * and runs Algorithm 1 (Frank-Wolfe with resampling every M iterations).
+ *
+ * Samples.  R_i = mu + s_i C zhat_i, C the lower Cholesky factor of Sigma,
+ * zhat_i innovations drawn in-kernel from a counter-based Philox4x32-10
+ * stream (Salmon et al., SC'11) keyed by `seed`, with counter
+ * (dimension block, i, epoch, (tag << 24) | instance).  Nothing of size N
+ * is ever stored: every kernel regenerates the samples it needs.
+ *   law GAUSS        zhat ~ N(0, I), s = 1             (R ~ N(mu, Sigma), Sec. 3.1)
+ *   law LOGN_STD     zhat = standardised lognormal(sigma=1) innovations, s = 1
+ *                    (mean mu, covariance Sigma, heavy right tail)
+ *   law STUDENT_T    zhat ~ N(0, I), s = sqrt(nu / chi2_nu)  (multivariate t)
+ *   law MIX          i < N/2 GAUSS, i >= N/2 LOGN_STD
+ * Precision FP64 draws FP64 normals; every other precision draws FP32
+ * normals.  Both are bit-exact with the project's CPU oracle.
+ *
+ * Conventions.
+ *   - Array arguments are caller-owned DEVICE memory unless stated.  Dense
+ *     matrices are row-major.  The library allocates only inside saa_ctx.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream).  The returned status covers argument validation and
+ *     launch; device-side flags (bounds, timeouts) surface at the next call on
+ *     the same context or at saa_ctx_sync().
+ *   - Calls on one context must not run concurrently from several host
+ *     threads.  Results are deterministic: the same inputs and device give
+ *     bitwise-identical outputs.
+ *   - The workspace `ws` (device memory, 256-byte aligned, at least
+ *     saa_workspace_size() bytes) is scratch owned by the caller; it may be
+ *     reused after the call's work on `stream` has completed.
+ *   - On error the call returns a non-zero saa_status and saa_last_error()
+ *     gives a thread-local message.
+ */
+#ifndef SAA_H
+#define SAA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SAA_OK = 0,
+    SAA_EINVAL = 1,       /* invalid argument (message in saa_last_error) */
+    SAA_ENOMEM = 2,       /* workspace too small or host allocation failed */
+    SAA_ECUDA = 3,        /* CUDA runtime error */
+    SAA_ETIMEOUT = 4,     /* a bounded device wait gave up */
+    SAA_EDEVICE = 5,      /* a device-side check flagged an error */
+    SAA_EUNSUPPORTED = 6  /* size or precision outside what this build supports */
+} saa_status;
+
+typedef enum {
+    SAA_LAW_GAUSS = 0,
+    SAA_LAW_LOGN_STD = 1,
+    SAA_LAW_STUDENT_T = 2,
+    SAA_LAW_MIX = 3
+} saa_law;
+
+typedef enum {
+    SAA_FP64 = 0,   /* FP64 normals, FP64 contraction (DFMA): the plain FP64 GPU path */
+    SAA_FP32 = 1,   /* FP32 normals, FP32 contraction (FFMA), FP64 cross-block reduction */
+    SAA_BF16X3 = 2, /* FP32 normals, BF16 hi/lo split contraction on tcgen05 tensor cores
+                       (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM), FP64 reduction */
+    SAA_FP8X = 3    /* reserved: FP8 E4M3 scaled contraction with hi/lo refinement */
+} saa_prec;
+
+typedef struct saa_ctx saa_ctx;
+
+/* One SAA problem (Sec. 3.1).  A host struct holding device pointers. */
+typedef struct {
+    int32_t d;          /* dimension of w and R (number of assets), 1 <= d */
+    int32_t law;        /* saa_law */
+    int64_t N;          /* number of samples per resample, 2 <= N < 2^32 */
+    int32_t nu;         /* degrees of freedom of the t law: even, >= 2 (else ignored) */
+    int32_t reserved;   /* must be 0 */
+    double lambda;      /* variance weight; 0.5 gives Eq. 3 */
+    uint64_t seed;      /* Philox key */
+    uint32_t instance;  /* stream id, low 24 bits used (counter word 3) */
+    uint32_t epoch;     /* resample index (counter word 2) */
+    const double* mu;   /* device [d]: mean of R */
+    const double* chol; /* device [d*d] row-major lower-triangular C, C C' = Sigma;
+                           entries above the diagonal are ignored */
+} saa_problem;
+
+/* Context: device properties, tuned launch shapes, a device error word and
+ * cached CUDA graphs.  `device` is a CUDA ordinal; the call makes it current. */
+saa_status saa_ctx_create(saa_ctx** out, int device);
+void saa_ctx_destroy(saa_ctx* ctx);
+
+/* Waits for `stream`, then reads and clears the device error word:
+ * SAA_OK, SAA_EDEVICE or SAA_ETIMEOUT. */
+saa_status saa_ctx_sync(saa_ctx* ctx, void* stream);
+
+/* Workspace bytes needed by saa_eval (want_grad = 0), saa_grad (1) or
+ * saa_solve (2) for this problem, K decisions and precision; 0 if the
+ * arguments are invalid. */
+size_t saa_workspace_size(const saa_ctx* ctx, const saa_problem* prob, int32_t K, saa_prec prec, int want_grad);
+
+/* Eq. 4 for K decisions at once.
+ *   X     device [K*d]: row k is the decision w_k (need not lie in W)
+ *   f     device [K]: f_hat(w_k)
+ *   pbar  device [K] or NULL: w_k'R_bar (Eq. 5)
+ *   var   device [K] or NULL: (1/(N-1)) sum_i (w_k'(R_i - R_bar))^2
+ * Errors: SAA_EINVAL for d < 1, N < 2, N >= 2^32, K outside [1, 65535], a bad law/nu, NULL
+ * required pointers; SAA_ENOMEM if ws_bytes is too small; SAA_EUNSUPPORTED
+ * for d beyond the precision's limit (saa_max_dim). */
+saa_status saa_eval(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec,
+                    double* f, double* pbar, double* var, void* ws, size_t ws_bytes, void* stream);
+
+/* Eq. 4 and its gradient in w (the paper uses it in Algorithm 1 without
+ * writing it out; differentiating Eq. 4 gives
+ *   grad f_hat(w) = lambda (2/(N-1)) sum_i (R_i - R_bar)(R_i - R_bar)'w - R_bar).
+ *   f     device [K] or NULL
+ *   grad  device [K*d]: row k is grad f_hat(w_k)
+ * Errors as saa_eval. */
+saa_status saa_grad(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec,
+                    double* f, double* grad, void* ws, size_t ws_bytes, void* stream);
+
+/* Algorithm 1 (Frank-Wolfe for mean-variance optimisation) from global
+ * iteration t0 for T iterations.  Iteration t uses the samples of resample
+ * index prob->epoch + t / M (a fresh draw every M iterations), evaluates
+ * g = grad f_hat(w_t), takes the LMO vertex s_t over W (e_j for the first
+ * j minimising g_j if g_j < 0, else 0), gamma_t = 2/(t+2) and
+ * w_{t+1} = w_t + gamma_t (s_t - w_t).  Resuming with (t0, w_t0) continues
+ * a run bit for bit.
+ *   w0        device [d], in W
+ *   w_out     device [d]: w_{t0+T}
+ *   f_trace   device [T] or NULL: f_hat(w_t) on iteration t's samples
+ *   gap_trace device [T] or NULL: Frank-Wolfe gap g'(w_t - s_t) >= 0
+ * The T iterations run as replays of one captured CUDA graph. */
+saa_status saa_solve(saa_ctx* ctx, const saa_problem* prob, const double* w0, int32_t T, int32_t M, int64_t t0,
+                     saa_prec prec, double* w_out, double* f_trace, double* gap_trace, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* The scenario generator on its own (debugging, streamed mode, parity):
+ * scenarios i0 .. i0+n-1 of resample index prob->epoch.
+ *   prec     SAA_FP64 (double outputs) or SAA_FP32 (float outputs)
+ *   z_out    device [n*d]: innovations zhat_i after the law transform
+ *   s_out    device [n] or NULL: scales s_i
+ *   xi_out   device [n*d] or NULL: samples R_i = mu + s_i C zhat_i at the
+ *            same precision, xi_ij = fma(s_i, acc_j, mu_j) with acc_j the fma
+ *            chain over l = 0..j of C_jl zhat_il (C, mu rounded first). */
+saa_status saa_generate(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, saa_prec prec, void* z_out,
+                        void* s_out, void* xi_out, void* stream);
+
+/* Kernel timing (tracing).  While enabled, every saa_eval / saa_grad call
+ * records a CUDA event pair on its stream around its main sample kernel (the
+ * generation + contraction + epilogue kernel) and counts the kernels it
+ * launches.  saa_profile_read waits for the recorded events, returns the
+ * summed main-kernel time in milliseconds, the number of main-kernel
+ * launches timed and the total kernels launched since the last read, then
+ * resets the counters.  Not recorded inside saa_solve's captured graph. */
+saa_status saa_profile_enable(saa_ctx* ctx, int enable);
+saa_status saa_profile_read(saa_ctx* ctx, double* main_ms, int64_t* main_launches, int64_t* kernels_launched);
+
+/* Largest d supported by `prec` in this build. */
+int32_t saa_max_dim(saa_prec prec);
+
+const char* saa_status_string(saa_status s);
+/* Message of the last failed call on this host thread ("" if none). */
+const char* saa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAA_H */

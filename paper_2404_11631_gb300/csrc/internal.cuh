@@ -1,0 +1,114 @@
+// internal.cuh -- host/device declarations shared by the libsaa translation
+// units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/saa.h"
+
+namespace saa {
+
+constexpr int kThreads = 256;   // threads per CTA of the SIMT kernels
+constexpr int kBN = 64;         // decisions per K-chunk in the SIMT kernels
+constexpr int kDK = 32;         // dimensions per staged Y chunk
+constexpr int kMaxDimSimt = 1024;
+
+// Device error word bits (ctx->err).
+enum : uint32_t { kErrBounds = 1u, kErrTimeout = 2u, kErrInput = 4u };
+
+// Everything a sample-generating kernel needs to know about the law.
+struct LawArgs {
+  int d;
+  int law;
+  int nu;
+  uint32_t N;
+  uint64_t seed;
+  uint32_t instance;
+  uint32_t epoch;            // base resample index
+  const int64_t* t_dev;      // optional: device iteration counter (Frank-Wolfe)
+  int32_t M;                 // resample period when t_dev is set
+};
+
+// Per-call workspace carve-up.  Partials are per CTA ("grid" of them) and are
+// merged in CTA order by the finalize kernels, so results are deterministic.
+struct Workspace {
+  void* Y;            // [K][d] scalar (float or double): y_k = C' w_k
+  double* Y64;        // [K][d] double copy (tensor paths build operands from it)
+  double* c;          // [K] mu' w_k
+  double* part_s1;    // [grid][K] sum_i Q_ik
+  double* part_s2;    // [grid][K] sum_i Q_ik^2
+  double* part_m;     // [grid][d] sum_i s_i zhat_i
+  void* part_g;       // [grid][K][d] scalar: sum_i s_i zhat_i Q_ik  (grad)
+  void* part_gc;      // [grid][K][d] scalar: Kahan compensation of part_g
+  double* tot_s1;     // [K]
+  double* tot_s2;     // [K]
+  double* tot_m;      // [d]
+  double* grad_tmp;   // [K][d] u_k of the gradient finalize
+  double* grad_out;   // [K][d] (solve: gradient of the iterate)
+  double* f_tmp;      // [K]    (solve)
+  int64_t* t_dev;     // [1]    (solve: iteration counter)
+  void* tc;           // tensor-path operand area
+  size_t bytes;       // total
+};
+
+struct Plan {
+  int prec;       // saa_prec
+  int bm;         // scenarios per tile
+  int grid;       // CTAs of the main kernel
+  int smem;       // dynamic shared memory of the main kernel
+  int64_t tiles;  // scenario tiles
+  size_t tc_bytes;
+};
+
+}  // namespace saa
+
+struct saa_ctx {
+  int device;
+  int sm_count;
+  int smem_optin;
+  uint32_t* err;                 // device error word
+  // graph of the last saa_solve (kept until the next solve or destroy)
+  cudaGraphExec_t fw_exec;
+  // kernel timing (saa_profile_*)
+  int prof_on;
+  int prof_n;                    // recorded event pairs
+  cudaEvent_t prof_ev[2 * 256];  // (start, end) pairs, created on enable
+  int64_t kernels;               // kernels launched since the last read
+};
+
+namespace saa {
+
+void set_error(const std::string& msg);
+saa_status cuda_status(cudaError_t e, const char* what);
+
+// Plan and workspace for a problem (host).
+saa_status make_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec prec, int want_grad, Plan* plan);
+size_t carve(const saa_problem* p, int K, const Plan& plan, int want_grad, void* base, Workspace* ws);
+
+// Launchers (host, one per translation unit).
+cudaError_t launch_prologue(const saa_problem* p, int K, const double* X, int prec, const Workspace& ws,
+                            cudaStream_t st);
+cudaError_t launch_simt(const LawArgs& la, int K, int prec, int want_grad, const Plan& plan, const Workspace& ws,
+                        cudaStream_t st);
+cudaError_t launch_finalize(const saa_problem* p, int K, int prec, int want_grad, const Plan& plan,
+                            const Workspace& ws, double* f, double* pbar, double* var, double* grad,
+                            cudaStream_t st);
+cudaError_t launch_generate(const LawArgs& la, int64_t i0, int64_t n, int prec, const double* mu,
+                            const double* chol, void* z, void* s, void* xi, cudaStream_t st);
+cudaError_t launch_fw_step(int d, const double* g, const double* f, double* w, const int64_t* t_dev,
+                           int64_t t_base, double* f_trace, double* gap_trace, int64_t* t_next, cudaStream_t st);
+
+// SIMT tile shape for (prec, d).
+int simt_bm(int prec, int d);
+size_t simt_smem(int prec, int d, int bm);
+
+// Tensor-core (tcgen05, BF16 hi/lo) value path.
+bool tc_supported(const saa_problem* p, int K, int want_grad);
+saa_status tc_plan(const saa_ctx* ctx, const saa_problem* p, int K, Plan* plan);
+cudaError_t launch_tc(const LawArgs& la, int K, const Plan& plan, const Workspace& ws, uint32_t* err,
+                      cudaStream_t st);
+
+}  // namespace saa

@@ -1,0 +1,401 @@
+// saa_api.cu -- the C ABI declared in include/saa.h: argument validation,
+// launch planning, workspace carve-up and the launch sequences of
+// saa_eval / saa_grad / saa_solve / saa_generate.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.cuh"
+
+namespace saa {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+saa_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return SAA_OK;
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return SAA_ECUDA;
+}
+
+cudaError_t launch_set_i64(int64_t* p, int64_t v, cudaStream_t st);
+int simt_occupancy(int prec, int bm, int smem);
+
+static saa_status fail(saa_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+static saa_status check_problem(const saa_problem* p) {
+  if (!p) return fail(SAA_EINVAL, "problem is NULL");
+  if (p->d < 1) return fail(SAA_EINVAL, "d must be >= 1");
+  if (p->N < 2) return fail(SAA_EINVAL, "N must be >= 2 (the variance divides by N-1)");
+  if (p->N > 0xffffffffll) return fail(SAA_EINVAL, "N must be < 2^32 (scenario counter word)");
+  if (p->law < SAA_LAW_GAUSS || p->law > SAA_LAW_MIX) return fail(SAA_EINVAL, "unknown law");
+  if (p->law == SAA_LAW_STUDENT_T && (p->nu < 2 || (p->nu & 1) || p->nu > 64))
+    return fail(SAA_EINVAL, "t law needs an even nu in [2, 64]");
+  if (p->reserved != 0) return fail(SAA_EINVAL, "reserved field must be 0");
+  if (!p->mu || !p->chol) return fail(SAA_EINVAL, "mu and chol must be device pointers");
+  return SAA_OK;
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+saa_status make_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec prec, int want_grad, Plan* plan) {
+  std::memset(plan, 0, sizeof(*plan));
+  plan->prec = prec;
+  if (prec == SAA_BF16X3) {
+    if (!tc_supported(p, K, want_grad))
+      return fail(SAA_EUNSUPPORTED, "BF16X3 tensor-core path: this d/K/law/gradient combination is not built");
+    return tc_plan(ctx, p, K, plan);
+  }
+  if (prec != SAA_FP32 && prec != SAA_FP64) return fail(SAA_EUNSUPPORTED, "precision not built");
+  if (p->d > kMaxDimSimt) return fail(SAA_EUNSUPPORTED, "d exceeds saa_max_dim for this precision");
+  plan->bm = simt_bm(prec, p->d);
+  plan->smem = (int)simt_smem(prec, p->d, plan->bm);
+  if (plan->smem > ctx->smem_optin) return fail(SAA_EUNSUPPORTED, "tile does not fit in shared memory");
+  plan->tiles = (p->N + plan->bm - 1) / plan->bm;
+  const int occ = simt_occupancy(prec, plan->bm, plan->smem);
+  const int64_t cap = (int64_t)ctx->sm_count * occ;
+  plan->grid = (int)(plan->tiles < cap ? plan->tiles : cap);
+  return SAA_OK;
+}
+
+size_t carve(const saa_problem* p, int K, const Plan& plan, int want_grad, void* base, Workspace* ws) {
+  const size_t d = (size_t)p->d, k = (size_t)K, g = (size_t)plan.grid;
+  const size_t es = (plan.prec == SAA_FP64) ? 8 : 4;
+  char* b = (char*)base;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> void* {
+    void* r = b ? (void*)(b + off) : nullptr;
+    off = align_up(off + bytes);
+    return r;
+  };
+  Workspace w;
+  std::memset(&w, 0, sizeof(w));
+  w.Y = take(k * d * es);
+  w.Y64 = (double*)take(k * d * 8);
+  w.c = (double*)take(k * 8);
+  w.part_s1 = (double*)take(g * k * 8);
+  w.part_s2 = (double*)take(g * k * 8);
+  w.part_m = (double*)take(g * d * 8);
+  if (want_grad) {
+    w.part_g = take(g * k * d * es);
+    w.part_gc = take(g * k * d * es);
+    w.grad_tmp = (double*)take(k * d * 8);
+  }
+  w.tot_s1 = (double*)take(k * 8);
+  w.tot_s2 = (double*)take(k * 8);
+  w.tot_m = (double*)take(d * 8);
+  if (want_grad == 2) {
+    w.f_tmp = (double*)take(k * 8);
+    w.t_dev = (int64_t*)take(8);
+    w.grad_out = (double*)take(k * d * 8);
+  }
+  if (plan.tc_bytes) w.tc = take(plan.tc_bytes);
+  w.bytes = off;
+  if (ws) *ws = w;
+  return off;
+}
+
+// Makes ctx->device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+static LawArgs law_args(const saa_problem* p) {
+  LawArgs la;
+  la.d = p->d;
+  la.law = p->law;
+  la.nu = p->nu;
+  la.N = (uint32_t)p->N;
+  la.seed = p->seed;
+  la.instance = p->instance;
+  la.epoch = p->epoch;
+  la.t_dev = nullptr;
+  la.M = 1;
+  return la;
+}
+
+// prologue -> main kernel -> finalize, all on `st`.
+static saa_status run_estimator(saa_ctx* ctx, const saa_problem* p, int K, const double* X, saa_prec prec,
+                                int want_grad, const Plan& plan, const Workspace& ws, const LawArgs& la, double* f,
+                                double* pbar, double* var, double* grad, cudaStream_t st) {
+  saa_status s = cuda_status(launch_prologue(p, K, X, prec, ws, st), "prologue launch");
+  if (s != SAA_OK) return s;
+  const bool prof = ctx->prof_on && !la.t_dev && ctx->prof_n < 256;
+  if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], st);
+  if (prec == SAA_BF16X3)
+    s = cuda_status(launch_tc(la, K, plan, ws, ctx->err, st), "tensor-core kernel launch");
+  else
+    s = cuda_status(launch_simt(la, K, prec, want_grad, plan, ws, st), "sample kernel launch");
+  if (s != SAA_OK) return s;
+  if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n++ + 1], st);
+  s = cuda_status(launch_finalize(p, K, prec, want_grad, plan, ws, f, pbar, var, grad, st), "finalize launch");
+  // prologue, main, reduce, value outputs (if any), gradient (2)
+  ctx->kernels += 3 + ((f || pbar || var) ? 1 : 0) + ((want_grad && grad) ? 2 : 0);
+  return s;
+}
+
+}  // namespace saa
+
+using namespace saa;
+
+extern "C" {
+
+saa_status saa_ctx_create(saa_ctx** out, int device) {
+  if (!out) return fail(SAA_EINVAL, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n)
+    return fail(SAA_EINVAL, "no such CUDA device");
+  DeviceGuard g(device);
+  if (!g.ok) return fail(SAA_ECUDA, "cudaSetDevice failed");
+  saa_ctx* c = new (std::nothrow) saa_ctx();
+  if (!c) return fail(SAA_ENOMEM, "host allocation failed");
+  std::memset(c, 0, sizeof(*c));
+  c->device = device;
+  cudaDeviceProp prop;
+  saa_status s = cuda_status(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+  if (s == SAA_OK) {
+    c->sm_count = prop.multiProcessorCount;
+    c->smem_optin = (int)prop.sharedMemPerBlockOptin;
+    if (prop.major != 10) s = fail(SAA_EUNSUPPORTED, "libsaa is built for sm_103a (Blackwell) only");
+  }
+  if (s == SAA_OK) s = cuda_status(cudaMalloc((void**)&c->err, sizeof(uint32_t)), "cudaMalloc(error word)");
+  if (s == SAA_OK) s = cuda_status(cudaMemset(c->err, 0, sizeof(uint32_t)), "cudaMemset(error word)");
+  if (s != SAA_OK) {
+    if (c->err) cudaFree(c->err);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return SAA_OK;
+}
+
+void saa_ctx_destroy(saa_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  if (ctx->fw_exec) {
+    cudaDeviceSynchronize();
+    cudaGraphExecDestroy(ctx->fw_exec);
+  }
+  if (ctx->prof_on)
+    for (int i = 0; i < 2 * 256; ++i) cudaEventDestroy(ctx->prof_ev[i]);
+  if (ctx->err) cudaFree(ctx->err);
+  delete ctx;
+}
+
+saa_status saa_ctx_sync(saa_ctx* ctx, void* stream) {
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  saa_status s = cuda_status(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  if (s != SAA_OK) return s;
+  uint32_t w = 0;
+  s = cuda_status(cudaMemcpy(&w, ctx->err, sizeof(w), cudaMemcpyDeviceToHost), "read error word");
+  if (s != SAA_OK) return s;
+  if (w) {
+    cudaMemset(ctx->err, 0, sizeof(uint32_t));
+    if (w & kErrTimeout) return fail(SAA_ETIMEOUT, "a bounded device wait gave up");
+    return fail(SAA_EDEVICE, "a device-side check flagged an error");
+  }
+  return SAA_OK;
+}
+
+saa_status saa_profile_enable(saa_ctx* ctx, int enable) {
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  DeviceGuard g(ctx->device);
+  if (enable && !ctx->prof_on) {
+    for (int i = 0; i < 2 * 256; ++i) {
+      saa_status s = cuda_status(cudaEventCreate(&ctx->prof_ev[i]), "cudaEventCreate");
+      if (s != SAA_OK) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(ctx->prof_ev[j]);
+        return s;
+      }
+    }
+    ctx->prof_on = 1;
+  } else if (!enable && ctx->prof_on) {
+    for (int i = 0; i < 2 * 256; ++i) cudaEventDestroy(ctx->prof_ev[i]);
+    ctx->prof_on = 0;
+  }
+  ctx->prof_n = 0;
+  ctx->kernels = 0;
+  return SAA_OK;
+}
+
+saa_status saa_profile_read(saa_ctx* ctx, double* main_ms, int64_t* main_launches, int64_t* kernels_launched) {
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  DeviceGuard g(ctx->device);
+  double total = 0.0;
+  for (int i = 0; i < ctx->prof_n; ++i) {
+    saa_status s = cuda_status(cudaEventSynchronize(ctx->prof_ev[2 * i + 1]), "cudaEventSynchronize");
+    if (s != SAA_OK) return s;
+    float ms = 0.f;
+    s = cuda_status(cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]), "cudaEventElapsedTime");
+    if (s != SAA_OK) return s;
+    total += ms;
+  }
+  if (main_ms) *main_ms = total;
+  if (main_launches) *main_launches = ctx->prof_n;
+  if (kernels_launched) *kernels_launched = ctx->kernels;
+  ctx->prof_n = 0;
+  ctx->kernels = 0;
+  return SAA_OK;
+}
+
+int32_t saa_max_dim(saa_prec prec) {
+  switch (prec) {
+    case SAA_FP64:
+    case SAA_FP32: return kMaxDimSimt;
+    case SAA_BF16X3: return 256;
+    default: return 0;
+  }
+}
+
+size_t saa_workspace_size(const saa_ctx* ctx, const saa_problem* prob, int32_t K, saa_prec prec, int want_grad) {
+  if (!ctx || check_problem(prob) != SAA_OK || K < 1) return 0;
+  if (want_grad == 2) K = 1;
+  DeviceGuard g(ctx->device);
+  Plan plan;
+  if (make_plan(ctx, prob, K, prec, want_grad ? 1 : 0, &plan) != SAA_OK) return 0;
+  return carve(prob, K, plan, want_grad, nullptr, nullptr);
+}
+
+static saa_status eval_impl(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec,
+                            int want_grad, double* f, double* pbar, double* var, double* grad, void* ws,
+                            size_t ws_bytes, void* stream) {
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  saa_status s = check_problem(prob);
+  if (s != SAA_OK) return s;
+  if (K < 1 || K > 65535) return fail(SAA_EINVAL, "K must be in [1, 65535]");
+  if (!X) return fail(SAA_EINVAL, "X is NULL");
+  if (want_grad ? !grad : !f) return fail(SAA_EINVAL, "output pointer is NULL");
+  if (!ws) return fail(SAA_EINVAL, "workspace is NULL");
+  if (((uintptr_t)ws) & 255u) return fail(SAA_EINVAL, "workspace must be 256-byte aligned");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(SAA_ECUDA, "cudaSetDevice failed");
+  Plan plan;
+  s = make_plan(ctx, prob, K, prec, want_grad, &plan);
+  if (s != SAA_OK) return s;
+  Workspace w;
+  const size_t need = carve(prob, K, plan, want_grad, ws, &w);
+  if (ws_bytes < need) return fail(SAA_ENOMEM, "workspace smaller than saa_workspace_size()");
+  return run_estimator(ctx, prob, K, X, prec, want_grad, plan, w, law_args(prob), f, pbar, var, grad,
+                       (cudaStream_t)stream);
+}
+
+saa_status saa_eval(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec, double* f,
+                    double* pbar, double* var, void* ws, size_t ws_bytes, void* stream) {
+  return eval_impl(ctx, prob, K, X, prec, 0, f, pbar, var, nullptr, ws, ws_bytes, stream);
+}
+
+saa_status saa_grad(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec, double* f,
+                    double* grad, void* ws, size_t ws_bytes, void* stream) {
+  return eval_impl(ctx, prob, K, X, prec, 1, f, nullptr, nullptr, grad, ws, ws_bytes, stream);
+}
+
+saa_status saa_solve(saa_ctx* ctx, const saa_problem* prob, const double* w0, int32_t T, int32_t M, int64_t t0,
+                     saa_prec prec, double* w_out, double* f_trace, double* gap_trace, void* ws, size_t ws_bytes,
+                     void* stream) {
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  saa_status s = check_problem(prob);
+  if (s != SAA_OK) return s;
+  if (T < 0 || M < 1 || t0 < 0) return fail(SAA_EINVAL, "need T >= 0, M >= 1, t0 >= 0");
+  if (!w0 || !w_out) return fail(SAA_EINVAL, "w0 and w_out must be device pointers");
+  if (!ws || (((uintptr_t)ws) & 255u)) return fail(SAA_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if ((int64_t)prob->epoch + (t0 + T) / M > 0xffffffffll) return fail(SAA_EINVAL, "resample index overflows");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(SAA_ECUDA, "cudaSetDevice failed");
+  Plan plan;
+  s = make_plan(ctx, prob, 1, prec, 1, &plan);
+  if (s != SAA_OK) return s;
+  Workspace w;
+  const size_t need = carve(prob, 1, plan, 2, ws, &w);
+  if (ws_bytes < need) return fail(SAA_ENOMEM, "workspace smaller than saa_workspace_size(..., want_grad=2)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = prob->d;
+  s = cuda_status(cudaMemcpyAsync(w_out, w0, sizeof(double) * d, cudaMemcpyDeviceToDevice, st), "copy w0");
+  if (s != SAA_OK) return s;
+  s = cuda_status(launch_set_i64(w.t_dev, t0, st), "set iteration counter");
+  if (s != SAA_OK || T == 0) return s;
+
+  LawArgs la = law_args(prob);
+  la.t_dev = w.t_dev;
+  la.M = M;
+  // Capture one iteration on a private stream, replay it T times on `st`.
+  cudaStream_t cap;
+  s = cuda_status(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "create capture stream");
+  if (s != SAA_OK) return s;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  s = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (s == SAA_OK) {
+    saa_status r = run_estimator(ctx, prob, 1, w_out, prec, 1, plan, w, la, w.f_tmp, nullptr, nullptr, w.grad_out,
+                                 cap);
+    if (r == SAA_OK)
+      r = cuda_status(launch_fw_step(d, w.grad_out, w.f_tmp, w_out, w.t_dev, t0, f_trace, gap_trace, w.t_dev, cap),
+                      "Frank-Wolfe step launch");
+    cudaError_t e = cudaStreamEndCapture(cap, &graph);
+    s = (r != SAA_OK) ? r : cuda_status(e, "end capture");
+  }
+  if (s == SAA_OK) s = cuda_status(cudaGraphInstantiate(&exec, graph, 0), "instantiate graph");
+  for (int32_t it = 0; s == SAA_OK && it < T; ++it) s = cuda_status(cudaGraphLaunch(exec, st), "graph launch");
+  if (ctx->fw_exec) {
+    // the previous call's graph may still be queued on another stream
+    cudaDeviceSynchronize();
+    cudaGraphExecDestroy(ctx->fw_exec);
+    ctx->fw_exec = nullptr;
+  }
+  ctx->fw_exec = exec;  // destroyed by the next solve or by saa_ctx_destroy
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  return s;
+}
+
+saa_status saa_generate(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, saa_prec prec, void* z_out,
+                        void* s_out, void* xi_out, void* stream) {
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  saa_status s = check_problem(prob);
+  if (s != SAA_OK) return s;
+  if (prec != SAA_FP32 && prec != SAA_FP64) return fail(SAA_EINVAL, "saa_generate takes SAA_FP32 or SAA_FP64");
+  if (i0 < 0 || n < 0 || i0 + n > prob->N) return fail(SAA_EINVAL, "scenario range outside [0, N)");
+  if (!z_out) return fail(SAA_EINVAL, "z_out is NULL");
+  if (xi_out && !s_out) return fail(SAA_EINVAL, "xi_out needs s_out");
+  if (n == 0) return SAA_OK;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(SAA_ECUDA, "cudaSetDevice failed");
+  return cuda_status(launch_generate(law_args(prob), i0, n, prec, prob->mu, prob->chol, z_out, s_out, xi_out,
+                                     (cudaStream_t)stream),
+                     "generate launch");
+}
+
+const char* saa_status_string(saa_status s) {
+  switch (s) {
+    case SAA_OK: return "SAA_OK";
+    case SAA_EINVAL: return "SAA_EINVAL: invalid argument";
+    case SAA_ENOMEM: return "SAA_ENOMEM: workspace too small or allocation failed";
+    case SAA_ECUDA: return "SAA_ECUDA: CUDA runtime error";
+    case SAA_ETIMEOUT: return "SAA_ETIMEOUT: bounded device wait gave up";
+    case SAA_EDEVICE: return "SAA_EDEVICE: device-side check failed";
+    case SAA_EUNSUPPORTED: return "SAA_EUNSUPPORTED: not supported by this build";
+  }
+  return "unknown saa_status";
+}
+
+const char* saa_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

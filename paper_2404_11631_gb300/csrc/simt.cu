@@ -1,0 +1,488 @@
+// simt.cu -- CUDA-core (FFMA / DFMA) path of the SAA estimator, the
+// prologue that folds the law into the decisions, and the deterministic
+// finalize kernels shared by every precision.
+//
+// Algebra (exact in real arithmetic; the CPU oracle does NOT use it, it forms
+// R_i and evaluates Eq. 4 directly):
+//   R_i = mu + C a_i with a_i = s_i zhat_i, so for decision w_k
+//   w_k'R_i = c_k + Q_ik,  c_k = mu'w_k,  Q_ik = a_i'y_k,  y_k = C'w_k.
+//   With S1_k = sum_i Q_ik, S2_k = sum_i Q_ik^2, m~ = sum_i a_i and
+//   G_k = sum_i a_i Q_ik (the adjoint contraction A'Q):
+//     pbar_k = c_k + S1_k/N                                          (Eq. 5)
+//     V_k    = (S2_k - S1_k^2/N) / (N-1)
+//     f_k    = lambda V_k - pbar_k                                   (Eq. 4)
+//     grad_k = C [ lambda 2/(N-1) (G_k - S1_k m) - m ] - mu,  m = m~/N
+// The hot loop therefore never forms R_i: it regenerates the tile of a_i,
+// contracts it with Y, and reduces Q in the epilogue.
+#include <cuda_runtime.h>
+
+#include "gen.cuh"
+#include "internal.cuh"
+
+namespace saa {
+
+// ------------------------------------------------------------------------
+// Prologue: y_k = C' w_k (FP64, also rounded to the contraction precision
+// and stored transposed [d][K] for the SIMT kernel) and c_k = mu' w_k.
+// ------------------------------------------------------------------------
+template <typename T>
+__global__ void k_prologue(int d, int K, const double* __restrict__ X, const double* __restrict__ mu,
+                           const double* __restrict__ C, T* __restrict__ Yt, double* __restrict__ Y64,
+                           double* __restrict__ c) {
+  const int k = blockIdx.x;
+  const double* w = X + (size_t)k * d;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    double acc = 0.0;
+    for (int l = j; l < d; ++l) acc = fma(C[(size_t)l * d + j], w[l], acc);
+    if (Yt) Yt[(size_t)j * K + k] = (T)acc;
+    if (Y64) Y64[(size_t)k * d + j] = acc;
+  }
+  __shared__ double red[kThreads];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) s = fma(mu[j], w[j], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) c[k] = red[0];
+}
+
+cudaError_t launch_prologue(const saa_problem* p, int K, const double* X, int prec, const Workspace& ws,
+                            cudaStream_t st) {
+  if (prec == SAA_FP64)
+    k_prologue<double><<<K, kThreads, 0, st>>>(p->d, K, X, p->mu, p->chol, (double*)ws.Y, ws.Y64, ws.c);
+  else
+    k_prologue<float><<<K, kThreads, 0, st>>>(p->d, K, X, p->mu, p->chol, (float*)ws.Y, ws.Y64, ws.c);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// Main SIMT kernel.  Persistent over scenario tiles of BM rows; per tile:
+//   1. scales s_i (t law) and the tile A' = [s_i zhat_i]' into shared memory
+//      ([d][BMP], zero-filled past the ragged end of the scenario range);
+//   2. m~ partial sums per dimension (FP64 registers);
+//   3. per K-chunk of 64 decisions: Q = A Y by register tiling (TM x 4 per
+//      thread), the S1/S2 column sums by a 16-lane shuffle tree, and for the
+//      gradient the adjoint tile A'Q accumulated into the CTA's partial.
+// Every partial element is owned by exactly one thread of one CTA, which
+// writes it on the CTA's first tile and accumulates afterwards.
+// ------------------------------------------------------------------------
+template <typename T> struct Pad;
+template <> struct Pad<float> { static constexpr int v = 4; };
+template <> struct Pad<double> { static constexpr int v = 2; };
+
+template <typename T, int BM>
+__global__ void __launch_bounds__(kThreads) k_simt(LawArgs la, int K, int want_grad, const T* __restrict__ Yt,
+                                                   double* __restrict__ part_s1, double* __restrict__ part_s2,
+                                                   double* __restrict__ part_m, T* __restrict__ part_g,
+                                                   T* __restrict__ part_gc, int64_t tiles) {
+  constexpr int TM = BM / 16;
+  constexpr int TN = 4;
+  constexpr int BMP = BM + Pad<T>::v;
+  constexpr int PC = gen::Gen<T>::kPerCall;
+  constexpr int QP = kBN + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int d = la.d;
+  T* As = reinterpret_cast<T*>(smem_raw);  // [d][BMP]
+  T* Ys = As + (size_t)d * BMP;            // [kDK][kBN]
+  T* Qs = Ys + kDK * kBN;                  // [BM][QP]
+  T* ss = Qs + BM * QP;                    // [BM]
+
+  const int tid = threadIdx.x;
+  const int ty = tid & 15;  // scenario group
+  const int tx = tid >> 4;  // decision group
+  uint32_t epoch = la.epoch;
+  if (la.t_dev) epoch += (uint32_t)(*la.t_dev / la.M);
+  const gen::Stream st = gen::make_stream(la.seed, epoch, la.instance);
+  const uint32_t half = la.N / 2u;
+  const int nb = (d + PC - 1) / PC;
+
+  double macc[kMaxDimSimt / kThreads];
+#pragma unroll
+  for (int r = 0; r < kMaxDimSimt / kThreads; ++r) macc[r] = 0.0;
+
+  bool first = true;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const uint32_t i0 = (uint32_t)(tile * BM);
+    const int nrow = (int)min((int64_t)BM, (int64_t)la.N - (int64_t)i0);
+    __syncthreads();
+    if (tid < BM) ss[tid] = (tid < nrow) ? gen::Gen<T>::scale(st, i0 + tid, la.law, la.nu) : T(0);
+    __syncthreads();
+    for (int idx = tid; idx < nb * BM; idx += kThreads) {
+      const int i = idx % BM;
+      const int b = idx / BM;
+      T z[PC];
+      if (i < nrow) {
+        gen::Gen<T>::block(st, (uint32_t)b, i0 + i, gen::is_lognormal(la.law, i0 + i, half), z);
+        const T s = ss[i];
+#pragma unroll
+        for (int q = 0; q < PC; ++q) z[q] *= s;
+      } else {
+#pragma unroll
+        for (int q = 0; q < PC; ++q) z[q] = T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < PC; ++q) {
+        const int j = b * PC + q;
+        if (j < d) As[(size_t)j * BMP + i] = z[q];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kMaxDimSimt / kThreads; ++r) {
+      const int j = tid + r * kThreads;
+      if (j < d) {
+        T sum = T(0);
+        for (int i = 0; i < nrow; ++i) sum += As[(size_t)j * BMP + i];
+        macc[r] += (double)sum;
+      }
+    }
+
+    for (int k0 = 0; k0 < K; k0 += kBN) {
+      T acc[TM][TN];
+#pragma unroll
+      for (int m = 0; m < TM; ++m)
+#pragma unroll
+        for (int n = 0; n < TN; ++n) acc[m][n] = T(0);
+
+      for (int j0 = 0; j0 < d; j0 += kDK) {
+        __syncthreads();
+        for (int idx = tid; idx < kDK * kBN; idx += kThreads) {
+          const int jj = idx / kBN, kk = idx % kBN;
+          const int j = j0 + jj, k = k0 + kk;
+          Ys[idx] = (j < d && k < K) ? Yt[(size_t)j * K + k] : T(0);
+        }
+        __syncthreads();
+        const int jmax = min(kDK, d - j0);
+        for (int jj = 0; jj < jmax; ++jj) {
+          const T* arow = As + (size_t)(j0 + jj) * BMP + ty * TM;
+          const T* yrow = Ys + jj * kBN + tx * TN;
+          T a[TM], y[TN];
+#pragma unroll
+          for (int m = 0; m < TM; ++m) a[m] = arow[m];
+#pragma unroll
+          for (int n = 0; n < TN; ++n) y[n] = yrow[n];
+#pragma unroll
+          for (int m = 0; m < TM; ++m)
+#pragma unroll
+            for (int n = 0; n < TN; ++n) acc[m][n] = fma(a[m], y[n], acc[m][n]);
+        }
+      }
+
+      // S1 / S2 over the tile's rows: own rows, then the 16 lanes sharing tx.
+#pragma unroll
+      for (int n = 0; n < TN; ++n) {
+        T s1 = T(0), s2 = T(0);
+#pragma unroll
+        for (int m = 0; m < TM; ++m) {
+          s1 += acc[m][n];
+          s2 = fma(acc[m][n], acc[m][n], s2);
+        }
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1) {
+          s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+          s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+        }
+        const int k = k0 + tx * TN + n;
+        if (ty == 0 && k < K) {
+          double* p1 = part_s1 + (size_t)blockIdx.x * K + k;
+          double* p2 = part_s2 + (size_t)blockIdx.x * K + k;
+          *p1 = first ? (double)s1 : *p1 + (double)s1;
+          *p2 = first ? (double)s2 : *p2 + (double)s2;
+        }
+      }
+
+      if (want_grad) {
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < TM; ++m)
+#pragma unroll
+          for (int n = 0; n < TN; ++n) Qs[(ty * TM + m) * QP + tx * TN + n] = acc[m][n];
+        __syncthreads();
+        for (int jd0 = 0; jd0 < d; jd0 += 64) {
+          T g[4][TN];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int n = 0; n < TN; ++n) g[q][n] = T(0);
+          for (int i = 0; i < nrow; ++i) {
+            T a[4], qv[TN];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int j = jd0 + ty + 16 * q;
+              a[q] = (j < d) ? As[(size_t)j * BMP + i] : T(0);
+            }
+#pragma unroll
+            for (int n = 0; n < TN; ++n) qv[n] = Qs[i * QP + tx * TN + n];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+              for (int n = 0; n < TN; ++n) g[q][n] = fma(a[q], qv[n], g[q][n]);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = jd0 + ty + 16 * q;
+#pragma unroll
+            for (int n = 0; n < TN; ++n) {
+              const int k = k0 + tx * TN + n;
+              if (j < d && k < K) {
+                const size_t e = ((size_t)blockIdx.x * K + k) * d + j;
+                if (first) {
+                  part_g[e] = g[q][n];
+                  part_gc[e] = T(0);
+                } else {  // Kahan: the partial carries its lost low part in part_gc
+                  const T y = g[q][n] - part_gc[e];
+                  const T s = part_g[e];
+                  const T t = s + y;
+                  part_gc[e] = (t - s) - y;
+                  part_g[e] = t;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    first = false;
+  }
+  if (!first) {
+#pragma unroll
+    for (int r = 0; r < kMaxDimSimt / kThreads; ++r) {
+      const int j = tid + r * kThreads;
+      if (j < d) part_m[(size_t)blockIdx.x * d + j] = macc[r];
+    }
+  }
+}
+
+int simt_bm(int prec, int d) {
+  if (prec == SAA_FP64) return d <= 256 ? 64 : (d <= 512 ? 32 : 16);
+  return d <= 512 ? 64 : 32;
+}
+
+size_t simt_smem(int prec, int d, int bm) {
+  const size_t es = (prec == SAA_FP64) ? 8 : 4;
+  const int pad = (prec == SAA_FP64) ? 2 : 4;
+  return es * ((size_t)d * (bm + pad) + (size_t)kDK * kBN + (size_t)bm * (kBN + 1) + bm);
+}
+
+template <typename T, int BM>
+static cudaError_t launch_simt_t(const LawArgs& la, int K, int want_grad, const Plan& plan, const Workspace& ws,
+                                 cudaStream_t st) {
+  auto kern = k_simt<T, BM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
+  if (e != cudaSuccess) return e;
+  kern<<<plan.grid, kThreads, plan.smem, st>>>(la, K, want_grad, (const T*)ws.Y, ws.part_s1, ws.part_s2,
+                                               ws.part_m, (T*)ws.part_g, (T*)ws.part_gc, plan.tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_simt(const LawArgs& la, int K, int prec, int want_grad, const Plan& plan, const Workspace& ws,
+                        cudaStream_t st) {
+  if (prec == SAA_FP64) {
+    switch (plan.bm) {
+      case 64: return launch_simt_t<double, 64>(la, K, want_grad, plan, ws, st);
+      case 32: return launch_simt_t<double, 32>(la, K, want_grad, plan, ws, st);
+      default: return launch_simt_t<double, 16>(la, K, want_grad, plan, ws, st);
+    }
+  }
+  switch (plan.bm) {
+    case 64: return launch_simt_t<float, 64>(la, K, want_grad, plan, ws, st);
+    default: return launch_simt_t<float, 32>(la, K, want_grad, plan, ws, st);
+  }
+}
+
+int simt_occupancy(int prec, int bm, int smem) {
+  int n = 0;
+  const void* f = nullptr;
+  if (prec == SAA_FP64)
+    f = bm == 64 ? (const void*)k_simt<double, 64> : bm == 32 ? (const void*)k_simt<double, 32>
+                                                              : (const void*)k_simt<double, 16>;
+  else
+    f = bm == 64 ? (const void*)k_simt<float, 64> : (const void*)k_simt<float, 32>;
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kThreads, smem) != cudaSuccess || n < 1) return 1;
+  return n;
+}
+
+// ------------------------------------------------------------------------
+// Finalize.  All cross-CTA sums are Neumaier-compensated FP64 sums in a
+// fixed order (CTA index, then a fixed warp tree), so the result does not
+// depend on scheduling.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
+  const double t = s + x;
+  if (fabs(s) >= fabs(x))
+    c += (s - t) + x;
+  else
+    c += (x - t) + s;
+  s = t;
+}
+
+// Items 0..K-1: part_s1, K..2K-1: part_s2, 2K..2K+d-1: part_m; one warp each.
+__global__ void k_reduce_parts(const double* __restrict__ part_s1, const double* __restrict__ part_s2,
+                               const double* __restrict__ part_m, int grid, int K, int d, double* __restrict__ s1,
+                               double* __restrict__ s2, double* __restrict__ m) {
+  const int item = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (item >= 2 * K + d) return;
+  const double* src;
+  int stride, off;
+  double* dst;
+  if (item < K) {
+    src = part_s1; stride = K; off = item; dst = s1 + item;
+  } else if (item < 2 * K) {
+    src = part_s2; stride = K; off = item - K; dst = s2 + (item - K);
+  } else {
+    src = part_m; stride = d; off = item - 2 * K; dst = m + (item - 2 * K);
+  }
+  double s = 0.0, c = 0.0;
+  for (int g = lane; g < grid; g += 32) neumaier(s, c, src[(size_t)g * stride + off]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double s_o = __shfl_down_sync(0xffffffffu, s, o);
+    const double c_o = __shfl_down_sync(0xffffffffu, c, o);
+    if (lane < o) {
+      neumaier(s, c, s_o);
+      c += c_o;
+    }
+  }
+  if (lane == 0) *dst = s + c;
+}
+
+__global__ void k_value_out(int K, double N, double lambda, const double* __restrict__ c,
+                            const double* __restrict__ s1, const double* __restrict__ s2, double* __restrict__ f,
+                            double* __restrict__ pbar, double* __restrict__ var) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const double qbar = s1[k] / N;
+  const double pb = c[k] + qbar;
+  const double V = (s2[k] - s1[k] * qbar) / (N - 1.0);
+  if (f) f[k] = lambda * V - pb;
+  if (pbar) pbar[k] = pb;
+  if (var) var[k] = V;
+}
+
+// u_k = lambda 2/(N-1) (G_k - S1_k m) - m, with G_k the CTA-ordered sum of
+// the Kahan-carried partials.
+template <typename T>
+__global__ void k_grad_u(int grid, int K, int d, double N, double lambda, const T* __restrict__ part_g,
+                         const T* __restrict__ part_gc, const double* __restrict__ s1, const double* __restrict__ mt,
+                         double* __restrict__ u) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (j >= d) return;
+  double s = 0.0, c = 0.0;
+  for (int g = 0; g < grid; ++g) {
+    const size_t e = ((size_t)g * K + k) * d + j;
+    neumaier(s, c, (double)part_g[e]);
+    neumaier(s, c, -(double)part_gc[e]);
+  }
+  const double G = s + c;
+  const double mj = mt[j] / N;
+  u[(size_t)k * d + j] = lambda * (2.0 / (N - 1.0)) * (G - s1[k] * mj) - mj;
+}
+
+// grad_kj = sum_{l <= j} C_jl u_kl - mu_j: one warp per (k, j).
+__global__ void k_grad_out(int K, int d, const double* __restrict__ C, const double* __restrict__ mu,
+                           const double* __restrict__ u, double* __restrict__ grad) {
+  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= K * d) return;
+  const int k = row / d, j = row % d;
+  const double* cj = C + (size_t)j * d;
+  const double* uk = u + (size_t)k * d;
+  double s = 0.0;
+  for (int l = lane; l <= j; l += 32) s = fma(cj[l], uk[l], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) grad[(size_t)k * d + j] = s - mu[j];
+}
+
+cudaError_t launch_finalize(const saa_problem* p, int K, int prec, int want_grad, const Plan& plan,
+                            const Workspace& ws, double* f, double* pbar, double* var, double* grad,
+                            cudaStream_t st) {
+  const int d = p->d;
+  const int items = 2 * K + d;
+  k_reduce_parts<<<(items * 32 + 255) / 256, 256, 0, st>>>(ws.part_s1, ws.part_s2, ws.part_m, plan.grid, K, d,
+                                                            ws.tot_s1, ws.tot_s2, ws.tot_m);
+  const double N = (double)p->N;
+  if (f || pbar || var)
+    k_value_out<<<(K + 255) / 256, 256, 0, st>>>(K, N, p->lambda, ws.c, ws.tot_s1, ws.tot_s2, f, pbar, var);
+  if (want_grad && grad) {
+    dim3 gu((d + 255) / 256, K);
+    if (prec == SAA_FP64)
+      k_grad_u<double><<<gu, 256, 0, st>>>(plan.grid, K, d, N, p->lambda, (const double*)ws.part_g,
+                                           (const double*)ws.part_gc, ws.tot_s1, ws.tot_m, ws.grad_tmp);
+    else
+      k_grad_u<float><<<gu, 256, 0, st>>>(plan.grid, K, d, N, p->lambda, (const float*)ws.part_g,
+                                          (const float*)ws.part_gc, ws.tot_s1, ws.tot_m, ws.grad_tmp);
+    const int64_t warps = (int64_t)K * d;
+    k_grad_out<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(K, d, p->chol, p->mu, ws.grad_tmp, grad);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// saa_generate: innovations / scales (one thread per (scenario, block)),
+// then the samples xi (one thread per (scenario, dimension)).
+// ------------------------------------------------------------------------
+template <typename T>
+__global__ void k_gen_z(LawArgs la, int64_t i0, int64_t n, T* __restrict__ z, T* __restrict__ s) {
+  constexpr int PC = gen::Gen<T>::kPerCall;
+  const int d = la.d;
+  const int nb = (d + PC - 1) / PC;
+  const gen::Stream st = gen::make_stream(la.seed, la.epoch, la.instance);
+  const uint32_t half = la.N / 2u;
+  const int64_t total = n * nb;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / nb;
+    const int b = (int)(idx % nb);
+    const uint32_t i = (uint32_t)(i0 + r);
+    T v[PC];
+    gen::Gen<T>::block(st, (uint32_t)b, i, gen::is_lognormal(la.law, i, half), v);
+#pragma unroll
+    for (int q = 0; q < PC; ++q) {
+      const int j = b * PC + q;
+      if (j < d) z[r * d + j] = v[q];
+    }
+    if (b == 0 && s) s[r] = gen::Gen<T>::scale(st, i, la.law, la.nu);
+  }
+}
+
+__device__ __forceinline__ float fma_p(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_p(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename T>
+__global__ void k_gen_xi(int d, int64_t n, const double* __restrict__ mu, const double* __restrict__ C,
+                         const T* __restrict__ z, const T* __restrict__ s, T* __restrict__ xi) {
+  const int64_t total = n * d;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / d;
+    const int j = (int)(idx % d);
+    const T* zr = z + r * d;
+    T acc = T(0);
+    for (int l = 0; l <= j; ++l) acc = fma_p((T)C[(size_t)j * d + l], zr[l], acc);
+    xi[idx] = fma_p(s[r], acc, (T)mu[j]);
+  }
+}
+
+cudaError_t launch_generate(const LawArgs& la, int64_t i0, int64_t n, int prec, const double* mu,
+                            const double* chol, void* z, void* s, void* xi, cudaStream_t st) {
+  const int blocks = 1024;
+  if (prec == SAA_FP64) {
+    k_gen_z<double><<<blocks, 256, 0, st>>>(la, i0, n, (double*)z, (double*)s);
+    if (xi) k_gen_xi<double><<<blocks, 256, 0, st>>>(la.d, n, mu, chol, (const double*)z, (const double*)s,
+                                                     (double*)xi);
+  } else {
+    k_gen_z<float><<<blocks, 256, 0, st>>>(la, i0, n, (float*)z, (float*)s);
+    if (xi) k_gen_xi<float><<<blocks, 256, 0, st>>>(la.d, n, mu, chol, (const float*)z, (const float*)s,
+                                                    (float*)xi);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace saa

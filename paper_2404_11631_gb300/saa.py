@@ -1,0 +1,284 @@
+"""Thin ctypes binding of libsaa (include/saa.h).
+
+Argument marshalling only: tensors are passed as raw device pointers with
+torch's current CUDA stream; every step of the estimator runs in libsaa's
+kernels.  There is no CPU or eager-PyTorch fallback: if the library is not
+built, or no CUDA device is present, calls raise.
+
+Names follow the C ABI: :func:`saa_eval`, :func:`saa_grad`,
+:func:`saa_solve`, :func:`saa_generate`, plus :class:`Problem` for the
+``saa_problem`` struct (the law of the samples R_i of Sec. 3.1,
+arXiv 2404.11631).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+SAA_OK, SAA_EINVAL, SAA_ENOMEM, SAA_ECUDA, SAA_ETIMEOUT, SAA_EDEVICE, SAA_EUNSUPPORTED = range(7)
+LAW_GAUSS, LAW_LOGN_STD, LAW_STUDENT_T, LAW_MIX = range(4)
+PRECS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "fp8x": 3}
+
+
+class SAAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libsaa status {status}: {msg}")
+        self.status = status
+
+
+class _CProblem(C.Structure):
+    _fields_ = [
+        ("d", C.c_int32),
+        ("law", C.c_int32),
+        ("N", C.c_int64),
+        ("nu", C.c_int32),
+        ("reserved", C.c_int32),
+        ("lam", C.c_double),
+        ("seed", C.c_uint64),
+        ("instance", C.c_uint32),
+        ("epoch", C.c_uint32),
+        ("mu", C.c_void_p),
+        ("chol", C.c_void_p),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+_ctx: dict[int, C.c_void_p] = {}
+
+
+def lib():
+    """Loads libsaa.so (building it in-tree first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                path = _build.build()
+            L = C.CDLL(path)
+            vp, sz = C.c_void_p, C.c_size_t
+            pp = C.POINTER(_CProblem)
+            L.saa_ctx_create.argtypes = [C.POINTER(vp), C.c_int]
+            L.saa_ctx_create.restype = C.c_int
+            L.saa_ctx_destroy.argtypes = [vp]
+            L.saa_ctx_sync.argtypes = [vp, vp]
+            L.saa_ctx_sync.restype = C.c_int
+            L.saa_workspace_size.argtypes = [vp, pp, C.c_int32, C.c_int, C.c_int]
+            L.saa_workspace_size.restype = sz
+            L.saa_eval.argtypes = [vp, pp, C.c_int32, vp, C.c_int, vp, vp, vp, vp, sz, vp]
+            L.saa_eval.restype = C.c_int
+            L.saa_grad.argtypes = [vp, pp, C.c_int32, vp, C.c_int, vp, vp, vp, sz, vp]
+            L.saa_grad.restype = C.c_int
+            L.saa_solve.argtypes = [vp, pp, vp, C.c_int32, C.c_int32, C.c_int64, C.c_int, vp, vp, vp, vp, sz, vp]
+            L.saa_solve.restype = C.c_int
+            L.saa_generate.argtypes = [vp, pp, C.c_int64, C.c_int64, C.c_int, vp, vp, vp, vp]
+            L.saa_generate.restype = C.c_int
+            L.saa_profile_enable.argtypes = [vp, C.c_int]
+            L.saa_profile_enable.restype = C.c_int
+            L.saa_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+            L.saa_profile_read.restype = C.c_int
+            L.saa_max_dim.argtypes = [C.c_int]
+            L.saa_max_dim.restype = C.c_int32
+            L.saa_status_string.argtypes = [C.c_int]
+            L.saa_status_string.restype = C.c_char_p
+            L.saa_last_error.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != SAA_OK:
+        raise SAAError(status, lib().saa_last_error().decode())
+
+
+def context(device: int | None = None) -> C.c_void_p:
+    """The libsaa context of a CUDA device (created once per process)."""
+    if not torch.cuda.is_available():
+        raise RuntimeError("libsaa needs a CUDA device; there is no CPU path")
+    dev = torch.cuda.current_device() if device is None else int(device)
+    with _lock:
+        ctx = _ctx.get(dev)
+    if ctx is None:
+        ctx = C.c_void_p()
+        _check(lib().saa_ctx_create(C.byref(ctx), dev))
+        with _lock:
+            _ctx[dev] = ctx
+    return ctx
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(device) -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+@dataclass
+class Problem:
+    """Law of the samples R_i = mu + s_i C zhat_i (Sec. 3.1) and estimator options.
+
+    mu   -- [d] float64 CUDA tensor, the mean of R
+    chol -- [d, d] float64 CUDA tensor, lower Cholesky factor C of Sigma
+    N    -- samples per resample; law -- LAW_*; nu -- t-law degrees of freedom
+    lam  -- weight of the variance term (0.5 reproduces Eq. 3)
+    seed, instance, epoch -- Philox key and counter words
+    """
+
+    mu: torch.Tensor
+    chol: torch.Tensor
+    N: int
+    law: int = LAW_GAUSS
+    nu: int = 4
+    lam: float = 0.5
+    seed: int = 0
+    instance: int = 0
+    epoch: int = 0
+
+    @property
+    def d(self) -> int:
+        return int(self.mu.shape[0])
+
+    @property
+    def device(self):
+        return self.mu.device
+
+    def c_struct(self) -> _CProblem:
+        for name, t in (("mu", self.mu), ("chol", self.chol)):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+        if self.chol.shape != (self.d, self.d):
+            raise ValueError("chol must be [d, d]")
+        return _CProblem(self.d, self.law, self.N, self.nu, 0, self.lam, self.seed, self.instance, self.epoch,
+                         self.mu.data_ptr(), self.chol.data_ptr())
+
+
+def _prec(prec) -> int:
+    return PRECS[prec] if isinstance(prec, str) else int(prec)
+
+
+def _decisions(X: torch.Tensor, prob: Problem) -> torch.Tensor:
+    if X.dim() == 1:
+        X = X.unsqueeze(0)
+    if not (X.is_cuda and X.dtype == torch.float64 and X.is_contiguous() and X.shape[1] == prob.d):
+        raise ValueError("X must be a contiguous float64 CUDA tensor [K, d]")
+    return X
+
+
+def workspace_size(prob: Problem, K: int, prec="fp32", want_grad: int = 0) -> int:
+    cp = prob.c_struct()
+    n = lib().saa_workspace_size(context(prob.device.index), C.byref(cp), K, _prec(prec), want_grad)
+    if n == 0:
+        raise SAAError(SAA_EINVAL, "no workspace size for these arguments: " + lib().saa_last_error().decode())
+    return int(n)
+
+
+def _workspace(prob, K, prec, want_grad, ws):
+    need = workspace_size(prob, K, prec, want_grad)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=prob.device)
+    return ws
+
+
+def saa_eval(prob: Problem, X: torch.Tensor, prec="fp32", pbar: bool = True, var: bool = True,
+             ws: torch.Tensor | None = None) -> dict:
+    """Eq. 4 for the K decisions in X: {'f', 'pbar', 'var'} as float64 CUDA tensors."""
+    X = _decisions(X, prob)
+    K = X.shape[0]
+    dev = prob.device
+    f = torch.empty(K, dtype=torch.float64, device=dev)
+    pb = torch.empty(K, dtype=torch.float64, device=dev) if pbar else None
+    vr = torch.empty(K, dtype=torch.float64, device=dev) if var else None
+    ws = _workspace(prob, K, prec, 0, ws)
+    cp = prob.c_struct()
+    _check(lib().saa_eval(context(dev.index), C.byref(cp), K, _ptr(X), _prec(prec), _ptr(f), _ptr(pb), _ptr(vr),
+                          _ptr(ws), ws.numel(), _stream(dev)))
+    out = {"f": f}
+    if pbar:
+        out["pbar"] = pb
+    if var:
+        out["var"] = vr
+    return out
+
+
+def saa_grad(prob: Problem, X: torch.Tensor, prec="fp32", want_f: bool = True,
+             ws: torch.Tensor | None = None) -> dict:
+    """Eq. 4 and its gradient in w: {'f', 'grad' [K, d]}."""
+    X = _decisions(X, prob)
+    K = X.shape[0]
+    dev = prob.device
+    f = torch.empty(K, dtype=torch.float64, device=dev) if want_f else None
+    g = torch.empty(K, prob.d, dtype=torch.float64, device=dev)
+    ws = _workspace(prob, K, prec, 1, ws)
+    cp = prob.c_struct()
+    _check(lib().saa_grad(context(dev.index), C.byref(cp), K, _ptr(X), _prec(prec), _ptr(f), _ptr(g), _ptr(ws),
+                          ws.numel(), _stream(dev)))
+    out = {"grad": g}
+    if want_f:
+        out["f"] = f
+    return out
+
+
+def saa_solve(prob: Problem, w0: torch.Tensor, T: int, M: int = 1, t0: int = 0, prec="fp32",
+              ws: torch.Tensor | None = None) -> dict:
+    """Algorithm 1 for T iterations from t0: {'w', 'f_trace', 'gap_trace'}."""
+    dev = prob.device
+    if not (w0.is_cuda and w0.dtype == torch.float64 and w0.is_contiguous() and w0.shape == (prob.d,)):
+        raise ValueError("w0 must be a contiguous float64 CUDA tensor [d]")
+    w = torch.empty(prob.d, dtype=torch.float64, device=dev)
+    ft = torch.empty(max(T, 1), dtype=torch.float64, device=dev)
+    gt = torch.empty(max(T, 1), dtype=torch.float64, device=dev)
+    ws = _workspace(prob, 1, prec, 2, ws)
+    cp = prob.c_struct()
+    _check(lib().saa_solve(context(dev.index), C.byref(cp), _ptr(w0), T, M, t0, _prec(prec), _ptr(w), _ptr(ft),
+                           _ptr(gt), _ptr(ws), ws.numel(), _stream(dev)))
+    return {"w": w, "f_trace": ft[:T], "gap_trace": gt[:T]}
+
+
+def saa_generate(prob: Problem, i0: int, n: int, prec="fp32", want_xi: bool = False) -> dict:
+    """Innovations zhat [n, d], scales s [n] and optionally samples xi [n, d]."""
+    dev = prob.device
+    dt = torch.float64 if _prec(prec) == 0 else torch.float32
+    z = torch.empty(n, prob.d, dtype=dt, device=dev)
+    s = torch.empty(n, dtype=dt, device=dev)
+    xi = torch.empty(n, prob.d, dtype=dt, device=dev) if want_xi else None
+    cp = prob.c_struct()
+    _check(lib().saa_generate(context(dev.index), C.byref(cp), i0, n, _prec(prec), _ptr(z), _ptr(s), _ptr(xi),
+                              _stream(dev)))
+    out = {"z": z, "s": s}
+    if want_xi:
+        out["xi"] = xi
+    return out
+
+
+def saa_ctx_sync(device: int | None = None):
+    """Waits for the current stream and raises if a device-side check fired."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    _check(lib().saa_ctx_sync(context(dev.index), _stream(dev)))
+
+
+def saa_profile_enable(enable: bool = True, device: int | None = None):
+    """Starts / stops event timing of the main sample kernel (see saa.h)."""
+    _check(lib().saa_profile_enable(context(device), int(enable)))
+
+
+def saa_profile_read(device: int | None = None) -> tuple[float, int, int]:
+    """(summed main-kernel ms, main-kernel launches, kernels launched) since the last read."""
+    ms, n, k = C.c_double(), C.c_int64(), C.c_int64()
+    _check(lib().saa_profile_read(context(device), C.byref(ms), C.byref(n), C.byref(k)))
+    return ms.value, n.value, k.value
+
+
+def max_dim(prec) -> int:
+    return int(lib().saa_max_dim(_prec(prec)))
+
+
+EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_size", "saa_eval", "saa_grad",
+            "saa_solve", "saa_generate", "saa_max_dim", "saa_status_string", "saa_last_error",
+            "saa_profile_enable", "saa_profile_read"]
