@@ -310,14 +310,22 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default=os.environ.get("SAA_BENCH_PREC", "fp32"), choices=["fp64", "fp32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--N", type=int, default=None, help="override the scenario count (profiling small cases)")
+    ap.add_argument("--K", type=int, default=None, help="override the decision count (profiling small cases)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.N:
+        WORKLOAD["N"] = args.N
+        WORKLOAD["name"] += f"_N{args.N}"
+    if args.K:
+        WORKLOAD["K"] = args.K
+        WORKLOAD["name"] += f"_K{args.K}"
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
