@@ -157,6 +157,28 @@ saa_status saa_solve(saa_ctx* ctx, const saa_problem* prob, const double* w0, in
 saa_status saa_generate(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, saa_prec prec, void* z_out,
                         void* s_out, void* xi_out, void* stream);
 
+/* saa_eval without a context or a workspace: for callers that cannot
+ * allocate device memory (a CUDA host callback or stream capture, where
+ * cudaMalloc is not allowed; a real-time loop that cannot afford
+ * cudaMalloc's implicit device synchronisation; a plug-in inside a host
+ * framework that owns all device memory).  The paper has no counterpart:
+ * this is a deployment convenience, not part of the method.
+ *
+ * Same arguments and results as saa_eval, on the CURRENT device, for
+ * SAA_FP32 and SAA_FP64.  Scratch comes from one array of
+ * SAA_STATIC_SCRATCH_BYTES in device memory defined by the library, which
+ * every GPU that loads libsaa holds until the process exits; problems whose
+ * scratch would not fit (large K times d, or very many CTAs) return
+ * SAA_ENOMEM with the needed size in saa_last_error().  The call allocates
+ * nothing.  Its first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the array: calls whose GPU work overlaps (other streams,
+ * other host threads) race on it.  Nothing in it needs clearing between
+ * calls; every value is written before it is read. */
+#define SAA_STATIC_SCRATCH_BYTES (16u << 20)
+saa_status saa_eval_static(const saa_problem* prob, int32_t K, const double* X, saa_prec prec, double* f,
+                           double* pbar, double* var, void* stream);
+
 /* Kernel timing (tracing).  While enabled, every saa_eval / saa_grad call
  * records a CUDA event pair on its stream around its main sample kernel (the
  * generation + contraction + epilogue kernel) and counts the kernels it

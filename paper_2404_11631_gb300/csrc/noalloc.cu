@@ -1,0 +1,120 @@
+// noalloc.cu -- saa_eval_static: the value estimate of saa_eval for callers
+// that cannot allocate device memory.
+//
+// saa_eval needs a caller-provided workspace and a context, and creating a
+// context calls cudaMalloc.  Some callers cannot do either: code running in
+// a CUDA host callback or while a stream is being captured (where cudaMalloc
+// is not allowed), real-time loops that cannot afford cudaMalloc's implicit
+// device synchronisation, and plug-ins inside a host framework that owns
+// all device memory through its own allocator.  For them this entry point
+// takes its scratch from one fixed array in device memory that the library
+// defines at file scope.  Every GPU that loads the library holds that array
+// (SAA_STATIC_SCRATCH_BYTES) until the process exits.
+//
+// The scratch is shared by every call in the process: two calls whose work
+// overlaps on the GPU (different streams, or different host threads) race
+// on it and give wrong results.  Nothing in it needs to start at zero: the
+// sample kernel writes each per-CTA partial on its first tile and the
+// finalize kernels overwrite the totals, so the contents left by the last
+// call are never read.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace saa {
+
+int simt_occupancy(int prec, int bm, int smem);
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[SAA_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void* g_scratch_dev[kMaxDevices];   // device address of g_static_scratch, per device
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the name g_static_scratch is only a host-side stand-in).
+saa_status scratch_address(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("saa_eval_static: device ordinal out of range");
+    return SAA_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  if (!g_scratch_dev[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_status(e, "saa_eval_static: cudaGetSymbolAddress(scratch)");
+    g_scratch_dev[dev] = p;
+  }
+  *out = g_scratch_dev[dev];
+  return SAA_OK;
+}
+
+}  // namespace
+}  // namespace saa
+
+using namespace saa;
+
+extern "C" saa_status saa_eval_static(const saa_problem* prob, int32_t K, const double* X, saa_prec prec, double* f,
+                                      double* pbar, double* var, void* stream) {
+  if (!prob || prob->d < 1 || prob->N < 2 || prob->N > 0xffffffffll || prob->law < SAA_LAW_GAUSS ||
+      prob->law > SAA_LAW_MIX || (prob->law == SAA_LAW_STUDENT_T && (prob->nu < 2 || (prob->nu & 1) || prob->nu > 64)) ||
+      prob->reserved != 0 || !prob->mu || !prob->chol) {
+    set_error("saa_eval_static: invalid problem (see saa_eval for the rules)");
+    return SAA_EINVAL;
+  }
+  if (K < 1 || K > 65535 || !X || !f) {
+    set_error("saa_eval_static: need 1 <= K <= 65535 and non-NULL X, f");
+    return SAA_EINVAL;
+  }
+  if (prec != SAA_FP32 && prec != SAA_FP64) {
+    set_error("saa_eval_static: only SAA_FP32 and SAA_FP64 are available without a workspace");
+    return SAA_EUNSUPPORTED;
+  }
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e, "saa_eval_static: cudaGetDevice");
+  void* scratch = nullptr;
+  saa_status s = scratch_address(dev, &scratch);
+  if (s != SAA_OK) return s;
+
+  // A context on the stack: device limits only, no device memory.
+  saa_ctx c;
+  std::memset(&c, 0, sizeof(c));
+  c.device = dev;
+  e = cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return cuda_status(e, "saa_eval_static: cudaDeviceGetAttribute");
+
+  Plan plan;
+  s = make_plan(&c, prob, K, prec, 0, &plan);
+  if (s != SAA_OK) return s;
+  Workspace ws;
+  const size_t need = carve(prob, K, plan, 0, scratch, &ws);
+  if (need > (size_t)SAA_STATIC_SCRATCH_BYTES) {
+    set_error("saa_eval_static: this d and K need " + std::to_string(need) + " bytes of scratch, more than the " +
+              std::to_string((size_t)SAA_STATIC_SCRATCH_BYTES) + " bytes of the static array; use saa_eval");
+    return SAA_ENOMEM;
+  }
+  LawArgs la;
+  la.d = prob->d;
+  la.law = prob->law;
+  la.nu = prob->nu;
+  la.N = (uint32_t)prob->N;
+  la.seed = prob->seed;
+  la.instance = prob->instance;
+  la.epoch = prob->epoch;
+  la.t_dev = nullptr;
+  la.M = 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  s = cuda_status(launch_prologue(prob, K, X, prec, ws, st), "saa_eval_static: prologue launch");
+  if (s != SAA_OK) return s;
+  s = cuda_status(launch_simt(la, K, prec, 0, plan, ws, st), "saa_eval_static: sample kernel launch");
+  if (s != SAA_OK) return s;
+  return cuda_status(launch_finalize(prob, K, prec, 0, plan, ws, f, pbar, var, nullptr, st),
+                     "saa_eval_static: finalize launch");
+}
