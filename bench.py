@@ -264,13 +264,13 @@ def run_ours(args):
 
     peaks, peak_src = _peaks()
     kern_s = main_ms / 1e3 / max(1, main_n)
-    if prec == "bf16x3":
+    if prec in ("bf16x3", "f16x3"):
         flops = 3 * 2.0 * N * d * K
         peak = float(peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": flops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "frac": flops / kern_s / 1e12 / peak, "traffic": None,
-                "peak_source": f"{peak_src} bf16 dense (burst)",
-                "note": "BF16x3 = three tensor products (hi*hi, hi*lo, lo*hi) per scenario-decision-dimension"}
+                "peak_source": f"{peak_src} bf16 dense (burst); f16 has the same nominal rate",
+                "note": "three tensor products (hi*hi, hi*lo, lo*hi) per scenario-decision-dimension"}
     else:
         lanes = 128 if prec == "fp32" else 2   # FP32 FMA lanes / FP64 FMA units per SM per clock
         flops = 2.0 * N * d * K
@@ -284,7 +284,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3"}[prec],
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3", "f16x3": "f16x3"}[prec],
         "data": "synthetic",
         "config": {"workload": WORKLOAD["name"], "d": d, "N": N, "K": K,
                    "law": "half Gaussian / half standardised lognormal", "prec": prec,
@@ -313,7 +313,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default=os.environ.get("SAA_BENCH_PREC", "fp32"), choices=["fp64", "fp32", "bf16x3"])
+    ap.add_argument("--prec", default=os.environ.get("SAA_BENCH_PREC", "fp32"),
+                    choices=["fp64", "fp32", "bf16x3", "f16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--N", type=int, default=None, help="override the scenario count (profiling small cases)")
     ap.add_argument("--K", type=int, default=None, help="override the decision count (profiling small cases)")

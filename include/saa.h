@@ -74,8 +74,11 @@ typedef enum {
     SAA_FP64 = 0,   /* FP64 normals, FP64 contraction (DFMA): the plain FP64 GPU path */
     SAA_FP32 = 1,   /* FP32 normals, FP32 contraction (FFMA), FP64 cross-block reduction */
     SAA_BF16X3 = 2, /* FP32 normals, BF16 hi/lo split contraction on tcgen05 tensor cores
-                       (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM), FP64 reduction */
-    SAA_FP8X = 3    /* reserved: FP8 E4M3 scaled contraction with hi/lo refinement */
+                       (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM), FP64 reduction;
+                       relative error of the estimates within 5e-5 */
+    SAA_FP8X = 3,   /* reserved: FP8 E4M3 scaled contraction with hi/lo refinement */
+    SAA_F16X3 = 4   /* as SAA_BF16X3 with FP16 hi/lo operands and a power-of-two scale per
+                       decision: relative error of the estimates within 1e-6 */
 } saa_prec;
 
 typedef struct saa_ctx saa_ctx;

@@ -105,10 +105,11 @@ cudaError_t launch_fw_step(int d, const double* g, const double* f, double* w, c
 int simt_bm(int prec, int d);
 size_t simt_smem(int prec, int d, int bm);
 
-// Tensor-core (tcgen05, BF16 hi/lo) value path.
+// Tensor-core (tcgen05, BF16 or FP16 hi/lo) value path.
+inline bool is_tc(int prec) { return prec == SAA_BF16X3 || prec == SAA_F16X3; }
 bool tc_supported(const saa_problem* p, int K, int want_grad);
 saa_status tc_plan(const saa_ctx* ctx, const saa_problem* p, int K, Plan* plan);
-cudaError_t launch_tc(const LawArgs& la, int K, const Plan& plan, const Workspace& ws, uint32_t* err,
+cudaError_t launch_tc(const LawArgs& la, int K, int prec, const Plan& plan, const Workspace& ws, uint32_t* err,
                       cudaStream_t st);
 
 }  // namespace saa

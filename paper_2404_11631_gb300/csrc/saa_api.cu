@@ -48,9 +48,9 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 saa_status make_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec prec, int want_grad, Plan* plan) {
   std::memset(plan, 0, sizeof(*plan));
   plan->prec = prec;
-  if (prec == SAA_BF16X3) {
+  if (is_tc(prec)) {
     if (!tc_supported(p, K, want_grad))
-      return fail(SAA_EUNSUPPORTED, "BF16X3 tensor-core path: this d/K/law/gradient combination is not built");
+      return fail(SAA_EUNSUPPORTED, "tensor-core path: this d/K/gradient combination is not built");
     return tc_plan(ctx, p, K, plan);
   }
   if (prec != SAA_FP32 && prec != SAA_FP64) return fail(SAA_EUNSUPPORTED, "precision not built");
@@ -138,15 +138,16 @@ static saa_status run_estimator(saa_ctx* ctx, const saa_problem* p, int K, const
   if (s != SAA_OK) return s;
   const bool prof = ctx->prof_on && !la.t_dev && ctx->prof_n < 256;
   if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], st);
-  if (prec == SAA_BF16X3)
-    s = cuda_status(launch_tc(la, K, plan, ws, ctx->err, st), "tensor-core kernel launch");
+  if (is_tc(prec))
+    s = cuda_status(launch_tc(la, K, prec, plan, ws, ctx->err, st), "tensor-core kernel launch");
   else
     s = cuda_status(launch_simt(la, K, prec, want_grad, plan, ws, st), "sample kernel launch");
   if (s != SAA_OK) return s;
   if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n++ + 1], st);
   s = cuda_status(launch_finalize(p, K, prec, want_grad, plan, ws, f, pbar, var, grad, st), "finalize launch");
-  // prologue, main, reduce, value outputs (if any), gradient (2)
-  ctx->kernels += 3 + ((f || pbar || var) ? 1 : 0) + ((want_grad && grad) ? 2 : 0);
+  // prologue, main, reduce, value outputs (if any), gradient (2); tensor path:
+  // operand scale + operand image + S1 from m~
+  ctx->kernels += 3 + ((f || pbar || var) ? 1 : 0) + ((want_grad && grad) ? 2 : 0) + (is_tc(prec) ? 3 : 0);
   return s;
 }
 
@@ -261,7 +262,8 @@ int32_t saa_max_dim(saa_prec prec) {
   switch (prec) {
     case SAA_FP64:
     case SAA_FP32: return kMaxDimSimt;
-    case SAA_BF16X3: return 256;
+    case SAA_BF16X3:
+    case SAA_F16X3: return 256;
     default: return 0;
   }
 }

@@ -351,6 +351,20 @@ __global__ void k_reduce_parts(const double* __restrict__ part_s1, const double*
   if (lane == 0) *dst = s + c;
 }
 
+// S1_k = m~'y_k (FP64, fixed order): the tensor path recovers the row sums
+// of Q from the per-dimension sums of a_i, sum_i Q_ik = (sum_i a_i)'y_k.
+__global__ void k_s1_from_m(int K, int d, const double* __restrict__ m, const double* __restrict__ Y64,
+                            double* __restrict__ s1) {
+  const int k = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int j = lane; j < d; j += 32) s = fma(m[j], Y64[(size_t)k * d + j], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) s1[k] = s;
+}
+
 __global__ void k_value_out(int K, double N, double lambda, const double* __restrict__ c,
                             const double* __restrict__ s1, const double* __restrict__ s2, double* __restrict__ f,
                             double* __restrict__ pbar, double* __restrict__ var) {
@@ -407,6 +421,8 @@ cudaError_t launch_finalize(const saa_problem* p, int K, int prec, int want_grad
   const int items = 2 * K + d;
   k_reduce_parts<<<(items * 32 + 255) / 256, 256, 0, st>>>(ws.part_s1, ws.part_s2, ws.part_m, plan.grid, K, d,
                                                             ws.tot_s1, ws.tot_s2, ws.tot_m);
+  if (is_tc(prec))   // S1 from m~ (the tensor kernel keeps no row sums of Q)
+    k_s1_from_m<<<(K * 32 + 255) / 256, 256, 0, st>>>(K, d, ws.tot_m, ws.Y64, ws.tot_s1);
   const double N = (double)p->N;
   if (f || pbar || var)
     k_value_out<<<(K + 255) / 256, 256, 0, st>>>(K, N, p->lambda, ws.c, ws.tot_s1, ws.tot_s2, f, pbar, var);

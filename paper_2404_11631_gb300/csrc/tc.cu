@@ -1,24 +1,611 @@
-// tc.cu -- tcgen05 tensor-core path (BF16 hi/lo split contraction).
+// tc.cu -- tcgen05 tensor-core path of the SAA estimate (value): split
+// precision contraction Q = A Y (BF16 or FP16 hi/lo operands, FP32
+// accumulation in TMEM).  The decision operand is scaled per decision by a
+// power of two so that its largest entry lies in [1, 2): exact, undone in
+// the epilogue, and it keeps FP16 within range.  Systematic error: the
+// representation error of y (identical for every scenario) does not average
+// over N, so FP16 (2 x 11 bits, ~2^-22) is the 1e-6 variant and BF16
+// (2 x 8 bits, ~2^-16) the 1e-4 variant.
+//
+// Per CTA (one per SM, persistent over 128-scenario tiles):
+//   RNG warps   regenerate the tile of a_i = s_i zhat_i (Sec. 3.1 samples)
+//               64 dimensions at a time, split each value into bf16 hi + lo
+//               and write both straight into a shared-memory stage in the
+//               128-byte-swizzled K-major layout tcgen05.mma reads; they
+//               also keep the per-dimension sums m~ = sum_i a_i.
+//   MMA warp    one thread issues, per 16-wide k step, the three products
+//               hi*hi + hi*lo + lo*hi (M = 128 scenarios, N = K decisions)
+//               into a TMEM accumulator, and commits stage releases.
+//   epilogue    four warps (one per TMEM lane quadrant) read Q from TMEM,
+//               square it and reduce each 32-row slice per decision with a
+//               warp reduce-scatter, accumulating S2 in FP64 registers.
+// The three products go to two accumulators: hi*hi into D1, the small
+// corrections hi*lo + lo*hi into D2, added in FP32 round-to-nearest in the
+// epilogue.  The tensor core's accumulation rounds each update of a running
+// sum with a bias toward zero; keeping the large running sum to one update
+// per 16-wide k step (instead of three) cuts that bias threefold.
+// The decision operand (y_k = C'w_k as bf16 hi/lo, pre-swizzled in global
+// memory by k_tc_bimage) is loaded once per CTA by bulk TMA and stays
+// resident.  S1_k = sum_i Q_ik is recovered exactly as m~'y_k in the
+// finalize.  Every wait on an mbarrier is bounded by a clock budget: on
+// expiry the kernel raises the context's error word, drains its own MMAs
+// and copies, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "gen.cuh"
 #include "internal.cuh"
 
 namespace saa {
+namespace tc {
+
+constexpr int kM = 128;             // scenarios per tile = MMA M = TMEM lanes
+constexpr int kKB = 64;             // dimensions per K block (128 B of bf16)
+constexpr int kStages = 3;          // A stages in flight
+constexpr int kStageBytes = 2 * kM * 128;   // hi + lo, 32 KB
+constexpr int kEpiWarps = 4;
+constexpr int kMmaWarp = 4;         // warps 0..3 epilogue, 4 MMA, 5.. RNG
+#ifndef SAA_TC_RNG_WARPS
+#define SAA_TC_RNG_WARPS 8
+#endif
+constexpr int kRngWarps = SAA_TC_RNG_WARPS;
+constexpr int kThreadsTc = 32 * (5 + kRngWarps);
+constexpr int kRngThreads = 32 * kRngWarps;
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+constexpr int kMaxKp = 256;         // MMA N limit (cta_group::1, M = 128)
+constexpr int kMaxDim = 256;
+constexpr int kMaxBBytes = 128 * 1024;
+
+struct Args {
+  LawArgs la;
+  int K, Kp, nkb;             // decisions, padded to 32 (epilogue sweeps 32 columns), K blocks of 64 dims
+  int64_t tiles;
+  const uint8_t* bimage;      // [nkb][hi,lo][Kp][128 B], swizzled
+  const double* scale2;       // [K] 4^e_k: undoes the operand scaling of Q^2
+  double* part_s2;            // [grid][K]
+  double* part_m;             // [grid][d]
+  uint32_t* err;
+};
+
+// ---------------------------------------------------------------- PTX ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// Bounded wait: false if the clock budget ran out or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
+                                          uint32_t* err) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1u;
+      atomicOr(err, kErrTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (bf16 inputs, f32 accumulate).
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrives on `bar` once every previously issued MMA of this thread is complete.
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 B apart (SBO), descriptor version 1, no base offset.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B both bf16 (fmt 1) or
+// both f16 (fmt 0), both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool f16) {
+  return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+#define SAA_R32(r) \
+  "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), \
+      "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),   \
+      "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),  \
+      "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+#define SAA_W32(r) \
+  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), \
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), \
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]),           \
+      "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+
+// 32 lanes x 32 consecutive 32-bit columns (lane quadrant of the warp).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : SAA_R32(r)
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      SAA_W32(r)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Byte offset of 16-byte unit u of row r in a swizzled K block.
+__device__ __forceinline__ uint32_t sw_off(int r, int u) { return (uint32_t)(r * 128 + ((u ^ (r & 7)) << 4)); }
+
+// Two floats rounded to the operand type (round to nearest even), packed.
+template <bool F16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  if (F16) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+}
+// The two packed values back as floats (exact).
+template <bool F16>
+__device__ __forceinline__ float2 unpack2(uint32_t w) {
+  if (F16) {
+    __half2 h = *reinterpret_cast<__half2*>(&w);
+    return __half22float2(h);
+  } else {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+  }
+}
+
+// ------------------------------------------------------------- kernel ----
+constexpr int kSBufs = 4;   // t-law scale buffers (producers run at most kStages stages ahead)
+
+struct Smem {
+  uint64_t a_full[kStages];
+  uint64_t a_empty[kStages];
+  uint64_t s_ready[kSBufs];
+  uint64_t q_full, q_empty, b_full, drain;
+  uint32_t tmem_base;
+  uint32_t abort_flag;
+  float s_buf[kSBufs][kM];
+};
+
+// Warp-uniform bounded wait (tcgen05.ld/st are warp-collective).
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
+                                          uint32_t* err) {
+  const bool ok = mbar_wait(bar, parity, abort_flag, err);
+  return __all_sync(0xffffffffu, ok);
+}
+
+// Layout: [A stages][B image][Smem]; the base must be 1024-byte aligned.
+size_t smem_bytes(int Kp, int nkb) {
+  return (size_t)kStages * kStageBytes + (size_t)nkb * 2 * Kp * 128 + sizeof(Smem);
+}
+
+template <bool F16, int NKB>
+__global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // The 128-byte swizzle is address based: operands need a 1024-byte aligned base.
+  const uint32_t base = smem_u32(smem_raw);
+  if (base & 1023u) {
+    if (threadIdx.x == 0) atomicOr(a.err, kErrBounds);
+    return;
+  }
+  const int bbytes = a.nkb * 2 * a.Kp * 128;
+  uint8_t* As = smem_raw;
+  Smem* sm = reinterpret_cast<Smem*>(smem_raw + kStages * kStageBytes + bbytes);
+  const uint32_t sA = base, sB = base + (uint32_t)(kStages * kStageBytes);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const LawArgs& la = a.la;
+  const int d = la.d;
+  volatile uint32_t* abort_flag = &sm->abort_flag;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&sm->a_full[s]), kRngWarps);
+      mbar_init(smem_u32(&sm->a_empty[s]), 1);
+    }
+    for (int s = 0; s < kSBufs; ++s) mbar_init(smem_u32(&sm->s_ready[s]), kM / 32);
+    mbar_init(smem_u32(&sm->q_full), 1);
+    mbar_init(smem_u32(&sm->q_empty), kEpiWarps);
+    mbar_init(smem_u32(&sm->b_full), 1);
+    mbar_init(smem_u32(&sm->drain), 1);
+    sm->abort_flag = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const uint32_t ncols = (2 * a.Kp <= 32) ? 32u : (2 * a.Kp <= 64) ? 64u : (2 * a.Kp <= 128) ? 128u
+                       : (2 * a.Kp <= 256) ? 256u : 512u;
+  if (warp == kMmaWarp) tmem_alloc(smem_u32(&sm->tmem_base), ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm->tmem_base;
+  const uint32_t td1 = tmem;                    // hi*hi accumulator: columns [0, Kp)
+  const uint32_t td2 = tmem + (uint32_t)a.Kp;  // hi*lo + lo*hi accumulator: columns [Kp, 2 Kp)
+  const int my_tiles = (int)((a.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+  const int iters = my_tiles * a.nkb;
+  float macc[NKB][8];             // RNG warps: per-dimension sums of a_i (NKB >= a.nkb)
+  double s2acc[kMaxKp / 32];      // epilogue warps: S2 of column c0 + lane, c0 = 32 g
+
+  if (warp == kMmaWarp) {
+    // ------------------------------------------------------------ MMA ---
+    if (lane == 0) {
+      const uint32_t bb = smem_u32(&sm->b_full);
+      mbar_expect_tx(bb, (uint32_t)bbytes);
+      for (int off = 0; off < bbytes; off += 32768) {
+        const int n = min(32768, bbytes - off);
+        bulk_g2s(sB + (uint32_t)off, a.bimage + off, (uint32_t)n, bb);
+      }
+      bool ok = mbar_wait(bb, 0, abort_flag, a.err);
+      const bool b_landed = ok;
+      const uint32_t idesc = idesc_f16(kM, a.Kp, F16);
+      const uint32_t hl_b = (uint32_t)(a.Kp * 128);
+      int tt = 0, kb = 0, st = 0;
+      uint32_t ph = 0;
+      for (int it = 0; ok && it < iters; ++it) {
+        if (kb == 0 && tt > 0) {
+          ok = mbar_wait(smem_u32(&sm->q_empty), (uint32_t)((tt - 1) & 1), abort_flag, a.err);
+          if (!ok) break;
+        }
+        ok = mbar_wait(smem_u32(&sm->a_full[st]), ph, abort_flag, a.err);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t a_hi = sA + (uint32_t)(st * kStageBytes);
+        const uint32_t a_lo = a_hi + kM * 128;
+        const uint32_t b_hi = sB + (uint32_t)(kb * 2) * hl_b;
+        const uint32_t b_lo = b_hi + hl_b;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t o = (uint32_t)(kk * 32);
+          const uint32_t acc0 = (kb == 0 && kk == 0) ? 0u : 1u;
+          mma_bf16(td1, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idesc, acc0);
+          mma_bf16(td2, desc_sw128(a_hi + o), desc_sw128(b_lo + o), idesc, acc0);
+          mma_bf16(td2, desc_sw128(a_lo + o), desc_sw128(b_hi + o), idesc, 1u);
+        }
+        mma_commit(smem_u32(&sm->a_empty[st]));
+        if (kb == a.nkb - 1) mma_commit(smem_u32(&sm->q_full));
+        if (++kb == a.nkb) { kb = 0; ++tt; }
+        if (++st == kStages) { st = 0; ph ^= 1u; }
+      }
+      // every MMA issued above completes before TMEM is released; after an
+      // abort, wait (bounded) for the operand copies still in flight too
+      mma_commit(smem_u32(&sm->drain));
+      uint32_t never = 0u;
+      mbar_wait(smem_u32(&sm->drain), 0, &never, a.err);
+      if (!b_landed) mbar_wait(bb, 0, &never, a.err);
+    }
+    __syncwarp();
+  } else if (warp < kEpiWarps) {
+    // ------------------------------------------------------- epilogue ---
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+    for (int g = 0; g < kMaxKp / 32; ++g) s2acc[g] = 0.0;
+    for (int tt = 0; tt < my_tiles; ++tt) {
+      if (!warp_wait(smem_u32(&sm->q_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
+      tc_fence_after();
+#pragma unroll 1
+      for (int g = 0; g < kMaxKp / 32; ++g) {
+        if (32 * g >= a.Kp) break;
+        const uint32_t c0 = (uint32_t)(32 * g);
+        uint32_t r1[32], r2[32];
+        tmem_ld32(td1 + lane_base + c0, r1);
+        tmem_ld32(td2 + lane_base + c0, r2);
+        tmem_wait_ld();
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float q = __uint_as_float(r1[i]) + __uint_as_float(r2[i]);
+          v[i] = q * q;
+        }
+        // reduce-scatter over the warp's 32 rows: lane l ends with column c0 + l
+#pragma unroll
+        for (int w = 16; w >= 1; w >>= 1) {
+          const bool upper = (lane & w) != 0;
+#pragma unroll
+          for (int i = 0; i < w; ++i) {
+            const float send = upper ? v[i] : v[i + w];
+            const float keep = upper ? v[i + w] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < kMaxKp / 32; ++h)
+          if (h == g) s2acc[h] += (double)v[0];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty));
+    }
+  } else {
+    // ------------------------------------------------------------ RNG ---
+    const int rt = threadIdx.x - 32 * (kMmaWarp + 1);   // 0 .. kRngThreads-1
+    const int cu = rt & 7;                               // 16-byte unit (8 dims) within the K block
+    const gen::Stream gs = gen::make_stream(la.seed, la.epoch, la.instance);
+    const uint32_t half = la.N / 2u;
+    const bool tlaw = la.law == SAA_LAW_STUDENT_T;
+#pragma unroll
+    for (int b = 0; b < NKB; ++b)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) macc[b][e] = 0.0f;
+    int tt = 0, kb = 0, st = 0;
+    uint32_t ph = 0;
+    for (int it = 0; it < iters; ++it) {
+      const uint32_t tile = blockIdx.x + (uint32_t)tt * gridDim.x;
+      const uint32_t i0 = tile * (uint32_t)kM;
+      const int nrow = (int)min((uint32_t)kM, la.N - i0);
+      const int sb = tt & (kSBufs - 1);
+      const uint32_t s_bar = smem_u32(&sm->s_ready[sb]);
+      if (tlaw && kb == 0 && rt < kM) {   // RNG warps 0..3 draw the tile's scales
+        sm->s_buf[sb][rt] = (rt < nrow) ? gen::t_scale_f(gs, i0 + (uint32_t)rt, la.nu) : 0.0f;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(s_bar);
+      }
+      if (!warp_wait(smem_u32(&sm->a_empty[st]), ph ^ 1u, abort_flag, a.err)) break;
+      if (tlaw && !warp_wait(s_bar, (uint32_t)((tt >> 2) & 1), abort_flag, a.err)) break;
+      uint8_t* stage = As + st * kStageBytes;
+      const int j0 = kb * kKB + cu * 8;   // first dimension of this unit
+#pragma unroll 2
+      for (int r = rt >> 3; r < kM; r += kRngThreads / 8) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0.0f;
+        if (r < nrow && j0 < d) {
+          const uint32_t i = i0 + (uint32_t)r;
+          const bool logn = gen::is_lognormal(la.law, i, half);
+          float z[4];
+          gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2), i, logn, z);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[e] = (j0 + e < d) ? z[e] : 0.0f;
+          if (j0 + 4 < d) {
+            gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2) + 1u, i, logn, z);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[4 + e] = (j0 + 4 + e < d) ? z[e] : 0.0f;
+          }
+          if (tlaw) {
+            const float s = sm->s_buf[sb][r];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] *= s;
+          }
+        }
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+          hi[e / 2] = pack2<F16>(v[e], v[e + 1]);
+          const float2 h = unpack2<F16>(hi[e / 2]);
+          lo[e / 2] = pack2<F16>(v[e] - h.x, v[e + 1] - h.y);
+        }
+        const uint32_t off = sw_off(r, cu);
+        *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(stage + kM * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+#pragma unroll
+        for (int b = 0; b < NKB; ++b)
+          if (b == kb)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) macc[b][e] += v[e];
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&sm->a_full[st]));
+      if (++kb == a.nkb) { kb = 0; ++tt; }
+      if (++st == kStages) { st = 0; ph ^= 1u; }
+    }
+    // lanes with equal rt & 7 hold the same unit: fold them (lanes 0..7 keep the sums)
+#pragma unroll
+    for (int b = 0; b < NKB; ++b)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        float v = macc[b][e];
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        macc[b][e] = v;
+      }
+  }
+
+  // ----------------------------------------------------- CTA reductions ---
+  __syncthreads();   // MMAs drained: the A stages are free for the reductions
+  const int dpad = a.nkb * kKB;
+  double* red_s2 = reinterpret_cast<double*>(As);      // [kEpiWarps][Kp]
+  float* red_m = reinterpret_cast<float*>(red_s2 + kEpiWarps * a.Kp);   // [kRngWarps][dpad]
+  if (warp > kMmaWarp && lane < 8) {
+    const int rw = warp - (kMmaWarp + 1);
+#pragma unroll
+    for (int b = 0; b < NKB; ++b)
+      if (b < a.nkb)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) red_m[rw * dpad + b * kKB + lane * 8 + e] = macc[b][e];
+  }
+  if (warp < kEpiWarps) {
+#pragma unroll
+    for (int g = 0; g < kMaxKp / 32; ++g)
+      if (32 * g < a.Kp) red_s2[warp * a.Kp + 32 * g + lane] = s2acc[g];
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    double s = 0.0;
+    for (int rw = 0; rw < kRngWarps; ++rw) s += (double)red_m[rw * dpad + j];
+    a.part_m[(size_t)blockIdx.x * d + j] = s;
+  }
+  for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < kEpiWarps; ++w) s += red_s2[w * a.Kp + k];
+    a.part_s2[(size_t)blockIdx.x * a.K + k] = s * a.scale2[k];
+  }
+  if (warp == kMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
+// Per-decision operand scale: e_k with max_j |y_kj| 2^-e_k in [1, 2) (e_k = 0
+// for y_k = 0); scale[k] = 2^e_k, scale2[k] = 4^e_k.  One warp per decision.
+__global__ void k_tc_scale(int d, int K, const double* __restrict__ Y64, double* __restrict__ scale,
+                           double* __restrict__ scale2) {
+  const int k = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= K) return;
+  double m = 0.0;
+  for (int j = lane; j < d; j += 32) m = fmax(m, fabs(Y64[(size_t)k * d + j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) {
+    const int e = (m > 0.0) ? ilogb(m) : 0;
+    scale[k] = ldexp(1.0, e);
+    scale2[k] = ldexp(1.0, 2 * e);
+  }
+}
+
+// Decision operand image: y_k 2^-e_k (FP64) split into hi + lo of the
+// operand type, laid out as [K block][hi, lo][Kp rows][128 B] in the
+// 128-byte-swizzled K-major order; rows k >= K and dimensions j >= d are 0.
+template <bool F16>
+__global__ void k_tc_bimage(int d, int K, int Kp, int nkb, const double* __restrict__ Y64,
+                            const double* __restrict__ scale, uint8_t* __restrict__ img) {
+  const int units = nkb * Kp * 8;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < units; idx += gridDim.x * blockDim.x) {
+    const int u = idx & 7;
+    const int n = (idx >> 3) % Kp;
+    const int kb = (idx >> 3) / Kp;
+    const double inv = (n < K) ? 1.0 / scale[n] : 0.0;   // exact: a power of two
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      double y[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int j = kb * kKB + u * 8 + e + q;
+        y[q] = (n < K && j < d) ? Y64[(size_t)n * d + j] * inv : 0.0;
+      }
+      hi[e / 2] = pack2<F16>((float)y[0], (float)y[1]);
+      const float2 h = unpack2<F16>(hi[e / 2]);
+      lo[e / 2] = pack2<F16>((float)(y[0] - (double)h.x), (float)(y[1] - (double)h.y));
+    }
+    const size_t blk = (size_t)kb * 2 * Kp * 128;
+    const uint32_t off = (uint32_t)(n * 128 + ((u ^ (n & 7)) << 4));
+    *reinterpret_cast<uint4*>(img + blk + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(img + blk + (size_t)Kp * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
+}  // namespace tc
 
 bool tc_supported(const saa_problem* p, int K, int want_grad) {
-  (void)p; (void)K; (void)want_grad;
-  return false;
+  if (want_grad) return false;
+  const int Kp = (K + 31) / 32 * 32;
+  const int nkb = (p->d + tc::kKB - 1) / tc::kKB;
+  return p->d <= tc::kMaxDim && Kp <= tc::kMaxKp && (size_t)nkb * 2 * Kp * 128 <= (size_t)tc::kMaxBBytes;
+}
+
+static size_t bimage_bytes(int K, int d) {
+  const int Kp = (K + 31) / 32 * 32;
+  const int nkb = (d + tc::kKB - 1) / tc::kKB;
+  return (size_t)nkb * 2 * Kp * 128;
 }
 
 saa_status tc_plan(const saa_ctx* ctx, const saa_problem* p, int K, Plan* plan) {
-  (void)ctx; (void)p; (void)K; (void)plan;
-  return SAA_EUNSUPPORTED;
+  const int Kp = (K + 31) / 32 * 32;
+  const int nkb = (p->d + tc::kKB - 1) / tc::kKB;
+  plan->bm = tc::kM;
+  plan->tiles = (p->N + tc::kM - 1) / tc::kM;
+  plan->grid = (int)(plan->tiles < ctx->sm_count ? plan->tiles : ctx->sm_count);
+  plan->smem = (int)tc::smem_bytes(Kp, nkb);
+  // operand image, then scale[K] and scale2[K]
+  plan->tc_bytes = bimage_bytes(K, p->d) + (size_t)16 * K;
+  if (plan->smem > ctx->smem_optin) {
+    set_error("tensor-core tile does not fit in shared memory");
+    return SAA_EUNSUPPORTED;
+  }
+  return SAA_OK;
 }
 
-cudaError_t launch_tc(const LawArgs& la, int K, const Plan& plan, const Workspace& ws, uint32_t* err,
+cudaError_t launch_tc(const LawArgs& la, int K, int prec, const Plan& plan, const Workspace& ws, uint32_t* err,
                       cudaStream_t st) {
-  (void)la; (void)K; (void)plan; (void)ws; (void)err; (void)st;
-  return cudaErrorNotSupported;
+  const bool f16 = (prec == SAA_F16X3);
+  tc::Args a;
+  a.la = la;
+  a.K = K;
+  a.Kp = (K + 31) / 32 * 32;
+  a.nkb = (la.d + tc::kKB - 1) / tc::kKB;
+  a.tiles = plan.tiles;
+  uint8_t* img = (uint8_t*)ws.tc;
+  double* scale = (double*)(img + bimage_bytes(K, la.d));
+  double* scale2 = scale + K;
+  a.bimage = img;
+  a.scale2 = scale2;
+  a.part_s2 = ws.part_s2;
+  a.part_m = ws.part_m;
+  a.err = err;
+  const int units = a.nkb * a.Kp * 8;
+  tc::k_tc_scale<<<(K * 32 + 255) / 256, 256, 0, st>>>(la.d, K, ws.Y64, scale, scale2);
+  if (f16)
+    tc::k_tc_bimage<true><<<(units + 255) / 256, 256, 0, st>>>(la.d, K, a.Kp, a.nkb, ws.Y64, scale, img);
+  else
+    tc::k_tc_bimage<false><<<(units + 255) / 256, 256, 0, st>>>(la.d, K, a.Kp, a.nkb, ws.Y64, scale, img);
+  auto kern = f16 ? (a.nkb == 1 ? tc::k_tc_value<true, 1> : a.nkb == 2 ? tc::k_tc_value<true, 2>
+                                                                          : tc::k_tc_value<true, 4>)
+                  : (a.nkb == 1 ? tc::k_tc_value<false, 1> : a.nkb == 2 ? tc::k_tc_value<false, 2>
+                                                                           : tc::k_tc_value<false, 4>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
+  if (e != cudaSuccess) return e;
+  kern<<<plan.grid, tc::kThreadsTc, plan.smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace saa

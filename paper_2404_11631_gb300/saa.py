@@ -23,7 +23,7 @@ from . import build as _build
 
 SAA_OK, SAA_EINVAL, SAA_ENOMEM, SAA_ECUDA, SAA_ETIMEOUT, SAA_EDEVICE, SAA_EUNSUPPORTED = range(7)
 LAW_GAUSS, LAW_LOGN_STD, LAW_STUDENT_T, LAW_MIX = range(4)
-PRECS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "fp8x": 3}
+PRECS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "fp8x": 3, "f16x3": 4}
 
 
 class SAAError(RuntimeError):

@@ -1,0 +1,84 @@
+"""Parity of the tcgen05 split-precision paths (SAA_F16X3, SAA_BF16X3) with
+the oracle on the same FP32-mode samples (Eq. 4 and Eq. 5, Sec. 3.1).  Shapes cover a single
+K block, several K blocks with a ragged last one, decision counts that are
+not multiples of 32, ragged scenario tails and every law; the full d=128,
+N=2^20, K=256 workload is checked on sampled decisions."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import TOL, est_err, make
+from paper_2404_11631_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _tc(d, N, K, law=oracle.LAW_GAUSS, seed=3, nu=4, lam=0.5, prec="f16x3"):
+    from paper_2404_11631_gb300 import saa
+    gp, op, inst = make(d, N, law=law, seed=seed, nu=nu, lam=lam)
+    X = inputs.decisions(K, d, seed=seed)
+    out = saa.saa_eval(gp, torch.tensor(X, device="cuda"), prec)
+    saa.saa_ctx_sync()
+    ref = oracle.saa(op, 32, X)
+    return {k: v.cpu().numpy() for k, v in out.items()}, ref, X, inst
+
+
+@pytest.mark.parametrize("d,N,K", [(1, 4099, 1), (7, 5000, 3), (64, 20_000, 32), (100, 9_999, 33),
+                                   (128, 40_000, 256), (256, 12_345, 64), (200, 30_000, 100)])
+@pytest.mark.parametrize("law", [oracle.LAW_GAUSS, oracle.LAW_MIX, oracle.LAW_STUDENT_T])
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+def test_tc_value_parity(d, N, K, law, prec):
+    out, ref, X, inst = _tc(d, N, K, law=law, prec=prec)
+    e_f = est_err(out["f"], ref["f"], ref["var"], X, inst.mu, 0.5)
+    e_p = est_err(out["pbar"], ref["pbar"], ref["var"], X, inst.mu, 0.5)
+    e_v = np.max(np.abs(out["var"] - ref["var"]) / ref["var"])
+    print(f"{prec} d={d} N={N} K={K} law={law}: f {e_f:.2e} pbar {e_p:.2e} var {e_v:.2e}")
+    assert e_f <= TOL[prec] and e_p <= TOL[prec] and e_v <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+def test_tc_small_N_edge(prec):
+    # N = 2 (one partial tile, 126 zero rows) and a tile-exact N = 128
+    for N in (2, 128, 129):
+        out, ref, X, inst = _tc(16, N, 5, seed=N, prec=prec)
+        assert est_err(out["f"], ref["f"], ref["var"], X, inst.mu, 0.5) <= TOL[prec] * 10
+
+
+def test_tc_deterministic_and_close_to_fp32_path():
+    from paper_2404_11631_gb300 import saa
+    gp, op, inst = make(128, 100_000, law=oracle.LAW_MIX, seed=7)
+    X = torch.tensor(inputs.decisions(256, 128, seed=7), device="cuda")
+    a = saa.saa_eval(gp, X, "f16x3")
+    b = saa.saa_eval(gp, X, "f16x3")
+    saa.saa_ctx_sync()
+    assert torch.equal(a["f"], b["f"]) and torch.equal(a["var"], b["var"])
+    c = saa.saa_eval(gp, X, "fp32")
+    rel = ((a["f"] - c["f"]).abs() / (0.5 * c["var"] + (X @ gp.mu).abs())).max().item()
+    assert rel <= 2e-6
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+def test_tc_full_size_sampled_decisions(prec):
+    from paper_2404_11631_gb300 import saa
+    d, N, K = 128, 1 << 20, 256
+    gp, op, inst = make(d, N, law=oracle.LAW_MIX, seed=0)
+    X = inputs.decisions(K, d, seed=0)
+    out = saa.saa_eval(gp, torch.tensor(X, device="cuda"), prec)
+    saa.saa_ctx_sync()
+    pick = [0, 131, 255]
+    ref = oracle.saa(op, 32, X[pick])
+    f = out["f"].cpu().numpy()[pick]
+    v = out["var"].cpu().numpy()[pick]
+    assert est_err(f, ref["f"], ref["var"], X[pick], inst.mu, 0.5) <= TOL[prec]
+    assert np.max(np.abs(v - ref["var"]) / ref["var"]) <= TOL[prec]
+
+
+def test_tc_unsupported_shapes_are_rejected():
+    from paper_2404_11631_gb300 import saa
+    gp, op, inst = make(1024, 1000)
+    with pytest.raises(saa.SAAError):
+        saa.saa_eval(gp, torch.zeros(2, 1024, dtype=torch.float64, device="cuda"), "f16x3")
+    gp, op, inst = make(16, 1000)
+    with pytest.raises(saa.SAAError):
+        saa.saa_grad(gp, torch.zeros(2, 16, dtype=torch.float64, device="cuda"), "f16x3")
