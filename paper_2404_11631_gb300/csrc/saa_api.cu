@@ -145,9 +145,9 @@ static saa_status run_estimator(saa_ctx* ctx, const saa_problem* p, int K, const
   if (s != SAA_OK) return s;
   if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n++ + 1], st);
   s = cuda_status(launch_finalize(p, K, prec, want_grad, plan, ws, f, pbar, var, grad, st), "finalize launch");
-  // prologue, main, reduce, value outputs (if any), gradient (2); tensor path:
-  // operand scale + operand image + S1 from m~
-  ctx->kernels += 3 + ((f || pbar || var) ? 1 : 0) + ((want_grad && grad) ? 2 : 0) + (is_tc(prec) ? 3 : 0);
+  // prologue, main, reduce, value outputs, gradient (2); tensor path: operand
+  // image + value outputs with S1 from m~ (always launched)
+  ctx->kernels += 3 + ((want_grad && grad) ? 2 : 0) + (is_tc(prec) ? 2 : ((f || pbar || var) ? 1 : 0));
   return s;
 }
 

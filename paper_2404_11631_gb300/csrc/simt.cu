@@ -22,39 +22,78 @@
 namespace saa {
 
 // ------------------------------------------------------------------------
-// Prologue: y_k = C' w_k (FP64, also rounded to the contraction precision
-// and stored transposed [d][K] for the SIMT kernel) and c_k = mu' w_k.
+// Prologue: y_k = C' w_k (FP64), c_k = mu' w_k, and y rounded to the SIMT
+// contraction precision, stored transposed [d][K].  One block per (group of
+// 4 decisions, 32 consecutive j); the sum over l >= j is split over 8 warps
+// (l = jc + w + 8t) and merged in warp order, so the result is deterministic.
 // ------------------------------------------------------------------------
+constexpr int kPrepK = 4;
+
 template <typename T>
-__global__ void k_prologue(int d, int K, const double* __restrict__ X, const double* __restrict__ mu,
-                           const double* __restrict__ C, T* __restrict__ Yt, double* __restrict__ Y64,
-                           double* __restrict__ c) {
-  const int k = blockIdx.x;
-  const double* w = X + (size_t)k * d;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    double acc = 0.0;
-    for (int l = j; l < d; ++l) acc = fma(C[(size_t)l * d + j], w[l], acc);
-    if (Yt) Yt[(size_t)j * K + k] = (T)acc;
-    if (Y64) Y64[(size_t)k * d + j] = acc;
+__global__ void __launch_bounds__(256) k_prologue(int d, int K, const double* __restrict__ X,
+                                                  const double* __restrict__ mu, const double* __restrict__ C,
+                                                  T* __restrict__ Yt, double* __restrict__ Y64,
+                                                  double* __restrict__ c) {
+  extern __shared__ double wsm[];            // [kPrepK][d] decisions
+  __shared__ double red[8][kPrepK][32];
+  const int k0 = blockIdx.x * kPrepK;
+  const int jc = blockIdx.y * 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int idx = threadIdx.x; idx < kPrepK * d; idx += blockDim.x) {
+    const int kk = idx / d, l = idx % d;
+    wsm[idx] = (k0 + kk < K) ? X[(size_t)(k0 + kk) * d + l] : 0.0;
   }
-  __shared__ double red[kThreads];
-  double s = 0.0;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) s = fma(mu[j], w[j], s);
-  red[threadIdx.x] = s;
   __syncthreads();
-  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-    if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
-    __syncthreads();
+  const int j = jc + lane;
+  double acc[kPrepK];
+#pragma unroll
+  for (int kk = 0; kk < kPrepK; ++kk) acc[kk] = 0.0;
+  if (j < d) {
+#pragma unroll 4
+    for (int l = jc + warp; l < d; l += 8) {
+      const double cl = (l >= j) ? C[(size_t)l * d + j] : 0.0;
+#pragma unroll
+      for (int kk = 0; kk < kPrepK; ++kk) acc[kk] = fma(cl, wsm[kk * d + l], acc[kk]);
+    }
   }
-  if (threadIdx.x == 0) c[k] = red[0];
+#pragma unroll
+  for (int kk = 0; kk < kPrepK; ++kk) red[warp][kk][lane] = acc[kk];
+  __syncthreads();
+  if (threadIdx.x < kPrepK * 32) {
+    const int kk = threadIdx.x >> 5, jj = threadIdx.x & 31;
+    const int k = k0 + kk, jo = jc + jj;
+    if (k < K && jo < d) {
+      double y = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) y += red[w][kk][jj];
+      Y64[(size_t)k * d + jo] = y;
+      if (Yt) Yt[(size_t)jo * K + k] = (T)y;
+    }
+  }
+  if (blockIdx.y == 0 && warp < kPrepK && k0 + warp < K) {
+    double sdot = 0.0;
+    for (int l = lane; l < d; l += 32) sdot = fma(mu[l], wsm[warp * d + l], sdot);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sdot += __shfl_down_sync(0xffffffffu, sdot, o);
+    if (lane == 0) c[k0 + warp] = sdot;
+  }
 }
 
 cudaError_t launch_prologue(const saa_problem* p, int K, const double* X, int prec, const Workspace& ws,
                             cudaStream_t st) {
+  const dim3 grid((K + kPrepK - 1) / kPrepK, (p->d + 31) / 32);
+  const size_t smem = sizeof(double) * kPrepK * p->d;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(prec == SAA_FP64 ? (const void*)k_prologue<double>
+                                                          : (const void*)k_prologue<float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   if (prec == SAA_FP64)
-    k_prologue<double><<<K, kThreads, 0, st>>>(p->d, K, X, p->mu, p->chol, (double*)ws.Y, ws.Y64, ws.c);
+    k_prologue<double><<<grid, 256, smem, st>>>(p->d, K, X, p->mu, p->chol, (double*)ws.Y, ws.Y64, ws.c);
   else
-    k_prologue<float><<<K, kThreads, 0, st>>>(p->d, K, X, p->mu, p->chol, (float*)ws.Y, ws.Y64, ws.c);
+    k_prologue<float><<<grid, 256, smem, st>>>(p->d, K, X, p->mu, p->chol, is_tc(prec) ? nullptr : (float*)ws.Y,
+                                               ws.Y64, ws.c);
   return cudaGetLastError();
 }
 
@@ -322,9 +361,9 @@ __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
 
 // Items 0..K-1: part_s1, K..2K-1: part_s2, 2K..2K+d-1: part_m; one warp each.
 __global__ void k_reduce_parts(const double* __restrict__ part_s1, const double* __restrict__ part_s2,
-                               const double* __restrict__ part_m, int grid, int K, int d, double* __restrict__ s1,
-                               double* __restrict__ s2, double* __restrict__ m) {
-  const int item = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+                               const double* __restrict__ part_m, int grid, int K, int d, int first,
+                               double* __restrict__ s1, double* __restrict__ s2, double* __restrict__ m) {
+  const int item = first + (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (item >= 2 * K + d) return;
   const double* src;
@@ -351,10 +390,13 @@ __global__ void k_reduce_parts(const double* __restrict__ part_s1, const double*
   if (lane == 0) *dst = s + c;
 }
 
-// S1_k = m~'y_k (FP64, fixed order): the tensor path recovers the row sums
-// of Q from the per-dimension sums of a_i, sum_i Q_ik = (sum_i a_i)'y_k.
-__global__ void k_s1_from_m(int K, int d, const double* __restrict__ m, const double* __restrict__ Y64,
-                            double* __restrict__ s1) {
+// Tensor path: S1_k = m~'y_k (FP64, fixed order) -- the row sums of Q are
+// recovered from the per-dimension sums of a_i, sum_i Q_ik = (sum_i a_i)'y_k --
+// then the value outputs.  One warp per decision.
+__global__ void k_value_out_m(int K, int d, double N, double lambda, const double* __restrict__ m,
+                              const double* __restrict__ Y64, const double* __restrict__ c,
+                              const double* __restrict__ s2, double* __restrict__ s1_out, double* __restrict__ f,
+                              double* __restrict__ pbar, double* __restrict__ var) {
   const int k = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (k >= K) return;
@@ -362,7 +404,15 @@ __global__ void k_s1_from_m(int K, int d, const double* __restrict__ m, const do
   for (int j = lane; j < d; j += 32) s = fma(m[j], Y64[(size_t)k * d + j], s);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) s1[k] = s;
+  if (lane == 0) {
+    s1_out[k] = s;
+    const double qbar = s / N;
+    const double pb = c[k] + qbar;
+    const double V = (s2[k] - s * qbar) / (N - 1.0);
+    if (f) f[k] = lambda * V - pb;
+    if (pbar) pbar[k] = pb;
+    if (var) var[k] = V;
+  }
 }
 
 __global__ void k_value_out(int K, double N, double lambda, const double* __restrict__ c,
@@ -419,12 +469,15 @@ cudaError_t launch_finalize(const saa_problem* p, int K, int prec, int want_grad
                             cudaStream_t st) {
   const int d = p->d;
   const int items = 2 * K + d;
-  k_reduce_parts<<<(items * 32 + 255) / 256, 256, 0, st>>>(ws.part_s1, ws.part_s2, ws.part_m, plan.grid, K, d,
-                                                            ws.tot_s1, ws.tot_s2, ws.tot_m);
-  if (is_tc(prec))   // S1 from m~ (the tensor kernel keeps no row sums of Q)
-    k_s1_from_m<<<(K * 32 + 255) / 256, 256, 0, st>>>(K, d, ws.tot_m, ws.Y64, ws.tot_s1);
+  // the tensor path keeps no row sums of Q: items 0..K-1 (S1 partials) are skipped
+  const int first = is_tc(prec) ? K : 0;
+  k_reduce_parts<<<((items - first) * 32 + 255) / 256, 256, 0, st>>>(ws.part_s1, ws.part_s2, ws.part_m, plan.grid,
+                                                                      K, d, first, ws.tot_s1, ws.tot_s2, ws.tot_m);
   const double N = (double)p->N;
-  if (f || pbar || var)
+  if (is_tc(prec))
+    k_value_out_m<<<(K * 32 + 255) / 256, 256, 0, st>>>(K, d, N, p->lambda, ws.tot_m, ws.Y64, ws.c, ws.tot_s2,
+                                                         ws.tot_s1, f, pbar, var);
+  else if (f || pbar || var)
     k_value_out<<<(K + 255) / 256, 256, 0, st>>>(K, N, p->lambda, ws.c, ws.tot_s1, ws.tot_s2, f, pbar, var);
   if (want_grad && grad) {
     dim3 gu((d + 255) / 256, K);

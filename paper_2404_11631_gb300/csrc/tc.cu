@@ -25,7 +25,7 @@
 // sum with a bias toward zero; keeping the large running sum to one update
 // per 16-wide k step (instead of three) cuts that bias threefold.
 // The decision operand (y_k = C'w_k as bf16 hi/lo, pre-swizzled in global
-// memory by k_tc_bimage) is loaded once per CTA by bulk TMA and stays
+// memory by k_tc_image) is loaded once per CTA by bulk TMA and stays
 // resident.  S1_k = sum_i Q_ik is recovered exactly as m~'y_k in the
 // finalize.  Every wait on an mbarrier is bounded by a clock budget: on
 // expiry the kernel raises the context's error word, drains its own MMAs
@@ -47,7 +47,7 @@ constexpr int kStageBytes = 2 * kM * 128;   // hi + lo, 32 KB
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarp = 4;         // warps 0..3 epilogue, 4 MMA, 5.. RNG
 #ifndef SAA_TC_RNG_WARPS
-#define SAA_TC_RNG_WARPS 8
+#define SAA_TC_RNG_WARPS 16
 #endif
 constexpr int kRngWarps = SAA_TC_RNG_WARPS;
 constexpr int kThreadsTc = 32 * (5 + kRngWarps);
@@ -494,48 +494,42 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
   }
 }
 
-// Per-decision operand scale: e_k with max_j |y_kj| 2^-e_k in [1, 2) (e_k = 0
-// for y_k = 0); scale[k] = 2^e_k, scale2[k] = 4^e_k.  One warp per decision.
-__global__ void k_tc_scale(int d, int K, const double* __restrict__ Y64, double* __restrict__ scale,
-                           double* __restrict__ scale2) {
-  const int k = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+// Decision operand image, one block per padded decision row n: the scale
+// e_n with max_j |y_nj| 2^-e_n in [1, 2) (e_n = 0 for a zero row; scale2[n] =
+// 4^e_n undoes it on Q^2), then y_n 2^-e_n split into hi + lo of the operand
+// type, laid out as [K block][hi, lo][Kp rows][128 B] in the 128-byte-swizzled
+// K-major order; rows n >= K and dimensions j >= d are zero.
+template <bool F16>
+__global__ void __launch_bounds__(64) k_tc_image(int d, int K, int Kp, int nkb, const double* __restrict__ Y64,
+                                                 double* __restrict__ scale2, uint8_t* __restrict__ img) {
+  __shared__ double wmax[2];
+  const int n = blockIdx.x;
   const int lane = threadIdx.x & 31;
-  if (k >= K) return;
   double m = 0.0;
-  for (int j = lane; j < d; j += 32) m = fmax(m, fabs(Y64[(size_t)k * d + j]));
+  if (n < K)
+    for (int j = threadIdx.x; j < d; j += blockDim.x) m = fmax(m, fabs(Y64[(size_t)n * d + j]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) {
-    const int e = (m > 0.0) ? ilogb(m) : 0;
-    scale[k] = ldexp(1.0, e);
-    scale2[k] = ldexp(1.0, 2 * e);
-  }
-}
-
-// Decision operand image: y_k 2^-e_k (FP64) split into hi + lo of the
-// operand type, laid out as [K block][hi, lo][Kp rows][128 B] in the
-// 128-byte-swizzled K-major order; rows k >= K and dimensions j >= d are 0.
-template <bool F16>
-__global__ void k_tc_bimage(int d, int K, int Kp, int nkb, const double* __restrict__ Y64,
-                            const double* __restrict__ scale, uint8_t* __restrict__ img) {
-  const int units = nkb * Kp * 8;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < units; idx += gridDim.x * blockDim.x) {
-    const int u = idx & 7;
-    const int n = (idx >> 3) % Kp;
-    const int kb = (idx >> 3) / Kp;
-    const double inv = (n < K) ? 1.0 / scale[n] : 0.0;   // exact: a power of two
+  if (lane == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = fmax(wmax[0], wmax[1]);
+  const int e = (m > 0.0) ? ilogb(m) : 0;
+  const double inv = ldexp(1.0, -e);   // exact
+  if (threadIdx.x == 0 && n < K) scale2[n] = ldexp(1.0, 2 * e);
+  for (int unit = threadIdx.x; unit < nkb * 8; unit += blockDim.x) {
+    const int kb = unit >> 3, u = unit & 7;
     uint32_t hi[4], lo[4];
 #pragma unroll
-    for (int e = 0; e < 8; e += 2) {
+    for (int q = 0; q < 8; q += 2) {
       double y[2];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int j = kb * kKB + u * 8 + e + q;
-        y[q] = (n < K && j < d) ? Y64[(size_t)n * d + j] * inv : 0.0;
+      for (int t = 0; t < 2; ++t) {
+        const int j = kb * kKB + u * 8 + q + t;
+        y[t] = (n < K && j < d) ? Y64[(size_t)n * d + j] * inv : 0.0;
       }
-      hi[e / 2] = pack2<F16>((float)y[0], (float)y[1]);
-      const float2 h = unpack2<F16>(hi[e / 2]);
-      lo[e / 2] = pack2<F16>((float)(y[0] - (double)h.x), (float)(y[1] - (double)h.y));
+      hi[q / 2] = pack2<F16>((float)y[0], (float)y[1]);
+      const float2 h = unpack2<F16>(hi[q / 2]);
+      lo[q / 2] = pack2<F16>((float)(y[0] - (double)h.x), (float)(y[1] - (double)h.y));
     }
     const size_t blk = (size_t)kb * 2 * Kp * 128;
     const uint32_t off = (uint32_t)(n * 128 + ((u ^ (n & 7)) << 4));
@@ -566,8 +560,8 @@ saa_status tc_plan(const saa_ctx* ctx, const saa_problem* p, int K, Plan* plan) 
   plan->tiles = (p->N + tc::kM - 1) / tc::kM;
   plan->grid = (int)(plan->tiles < ctx->sm_count ? plan->tiles : ctx->sm_count);
   plan->smem = (int)tc::smem_bytes(Kp, nkb);
-  // operand image, then scale[K] and scale2[K]
-  plan->tc_bytes = bimage_bytes(K, p->d) + (size_t)16 * K;
+  // operand image, then scale2[K]
+  plan->tc_bytes = bimage_bytes(K, p->d) + (size_t)8 * K;
   if (plan->smem > ctx->smem_optin) {
     set_error("tensor-core tile does not fit in shared memory");
     return SAA_EUNSUPPORTED;
@@ -585,19 +579,16 @@ cudaError_t launch_tc(const LawArgs& la, int K, int prec, const Plan& plan, cons
   a.nkb = (la.d + tc::kKB - 1) / tc::kKB;
   a.tiles = plan.tiles;
   uint8_t* img = (uint8_t*)ws.tc;
-  double* scale = (double*)(img + bimage_bytes(K, la.d));
-  double* scale2 = scale + K;
+  double* scale2 = (double*)(img + bimage_bytes(K, la.d));
   a.bimage = img;
   a.scale2 = scale2;
   a.part_s2 = ws.part_s2;
   a.part_m = ws.part_m;
   a.err = err;
-  const int units = a.nkb * a.Kp * 8;
-  tc::k_tc_scale<<<(K * 32 + 255) / 256, 256, 0, st>>>(la.d, K, ws.Y64, scale, scale2);
   if (f16)
-    tc::k_tc_bimage<true><<<(units + 255) / 256, 256, 0, st>>>(la.d, K, a.Kp, a.nkb, ws.Y64, scale, img);
+    tc::k_tc_image<true><<<a.Kp, 64, 0, st>>>(la.d, K, a.Kp, a.nkb, ws.Y64, scale2, img);
   else
-    tc::k_tc_bimage<false><<<(units + 255) / 256, 256, 0, st>>>(la.d, K, a.Kp, a.nkb, ws.Y64, scale, img);
+    tc::k_tc_image<false><<<a.Kp, 64, 0, st>>>(la.d, K, a.Kp, a.nkb, ws.Y64, scale2, img);
   auto kern = f16 ? (a.nkb == 1 ? tc::k_tc_value<true, 1> : a.nkb == 2 ? tc::k_tc_value<true, 2>
                                                                           : tc::k_tc_value<true, 4>)
                   : (a.nkb == 1 ? tc::k_tc_value<false, 1> : a.nkb == 2 ? tc::k_tc_value<false, 2>
