@@ -149,6 +149,27 @@ saa_status saa_solve(saa_ctx* ctx, const saa_problem* prob, const double* w0, in
                      saa_prec prec, double* w_out, double* f_trace, double* gap_trace, void* ws, size_t ws_bytes,
                      void* stream);
 
+/* A ragged batch of B independent problems (Eq. 4 for each), in one
+ * persistent launch: problem b has its own d, N, law, stream, K[b]
+ * decisions X[b] and outputs f[b] (pbar[b], var[b] optional; pass NULL for
+ * the whole array or per entry).  SAA_FP32 or SAA_FP64, d <= 1024.
+ *   probs, K, X, f, pbar, var   HOST arrays of length B; X[b], f[b], ...
+ *                               are device pointers
+ * Each problem's scenarios are cut into chunks that a persistent grid takes
+ * from a queue; every chunk has its own partial slot, merged per problem in
+ * chunk order, so results are deterministic for a given tile shape.  On the
+ * first call for a batch shape the context's autotuner (on by default, see
+ * saa_ctx_set_autotune) times the candidate tile shapes on the batch itself
+ * and caches the fastest for the process; that first call must not be
+ * inside a stream capture (it synchronises).  The descriptor tables go
+ * through a pinned staging buffer owned by the context. */
+size_t saa_workspace_size_batched(const saa_ctx* ctx, int32_t B, const saa_problem* probs, const int32_t* K,
+                                  saa_prec prec);
+saa_status saa_eval_batched(saa_ctx* ctx, int32_t B, const saa_problem* probs, const int32_t* K,
+                            const double* const* X, saa_prec prec, double* const* f, double* const* pbar,
+                            double* const* var, void* ws, size_t ws_bytes, void* stream);
+saa_status saa_ctx_set_autotune(saa_ctx* ctx, int enable);
+
 /* The scenario generator on its own (debugging, streamed mode, parity):
  * scenarios i0 .. i0+n-1 of resample index prob->epoch.
  *   prec     SAA_FP64 (double outputs) or SAA_FP32 (float outputs)

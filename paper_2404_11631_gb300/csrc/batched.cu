@@ -1,0 +1,480 @@
+// batched.cu -- a ragged batch of independent SAA problems (Eq. 4 for each,
+// Sec. 3.1) in one persistent launch.
+//
+// Each problem b has its own dimension d_b, sample count N_b, decisions K_b,
+// law and Philox stream.  Its scenario range is cut into chunks ("items") of
+// a fixed number of tiles; a persistent grid pulls items from an atomic
+// counter (dynamic load balance across problems of very different sizes),
+// and every item writes its own partial slot (S1, S2 per decision and m~ per
+// dimension), so the result does not depend on which CTA took which item.
+// A batched prologue computes every y_k = C_b'w_k; a finalize block per
+// problem merges that problem's item partials in item order.  The tile work
+// itself is the CUDA-core tile of the single-problem kernel (simt_tile).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gen.cuh"
+#include "internal.cuh"
+#include "simt_tile.cuh"
+
+namespace saa {
+
+struct BInst {
+  int d, K, law, nu;
+  uint32_t N, instance, epoch, pad;
+  uint64_t seed;
+  double lambda;
+  const double* mu;
+  const double* chol;
+  const double* X;
+  double* f;
+  double* pbar;
+  double* var;
+  int64_t y_off;     // element offset of Yt ([d][K], contraction precision)
+  int64_t y64_off;   // double offset of Y64 ([K][d])
+  int64_t c_off;     // double offset of c ([K])
+  int64_t part_off;  // double offset of this problem's item partials
+  int item0, nitems;
+  int pblock0, pad2;  // first prologue block
+};
+
+struct BItem {
+  int inst;
+  uint32_t i0, n;
+  int slot;  // item index within its problem
+};
+
+static_assert(sizeof(BInst) % 8 == 0, "descriptor alignment");
+
+// ------------------------------------------------------------ prologue ---
+constexpr int kBK = 4;   // decisions per prologue block
+
+__device__ __forceinline__ int find_inst(const BInst* insts, int B, int blk) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (insts[mid].pblock0 <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_batched_prologue(const BInst* __restrict__ insts, int B, T* __restrict__ Yf,
+                                                          double* __restrict__ Y64, double* __restrict__ cbuf) {
+  extern __shared__ double wsm[];   // [kBK][d]
+  __shared__ double red[8][kBK][32];
+  const int b = find_inst(insts, B, blockIdx.x);
+  const BInst in = insts[b];
+  const int d = in.d, K = in.K;
+  const int nj = (d + 31) / 32;
+  const int local = blockIdx.x - in.pblock0;
+  const int k0 = (local / nj) * kBK;
+  const int jc = (local % nj) * 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int idx = threadIdx.x; idx < kBK * d; idx += blockDim.x) {
+    const int kk = idx / d, l = idx % d;
+    wsm[idx] = (k0 + kk < K) ? in.X[(size_t)(k0 + kk) * d + l] : 0.0;
+  }
+  __syncthreads();
+  const int j = jc + lane;
+  double acc[kBK];
+#pragma unroll
+  for (int kk = 0; kk < kBK; ++kk) acc[kk] = 0.0;
+  if (j < d) {
+#pragma unroll 4
+    for (int l = jc + warp; l < d; l += 8) {
+      const double cl = (l >= j) ? in.chol[(size_t)l * d + j] : 0.0;
+#pragma unroll
+      for (int kk = 0; kk < kBK; ++kk) acc[kk] = fma(cl, wsm[kk * d + l], acc[kk]);
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < kBK; ++kk) red[warp][kk][lane] = acc[kk];
+  __syncthreads();
+  if (threadIdx.x < kBK * 32) {
+    const int kk = threadIdx.x >> 5, jj = threadIdx.x & 31;
+    const int k = k0 + kk, jo = jc + jj;
+    if (k < K && jo < d) {
+      double y = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) y += red[w][kk][jj];
+      Y64[in.y64_off + (size_t)k * d + jo] = y;
+      Yf[in.y_off + (size_t)jo * K + k] = (T)y;
+    }
+  }
+  if (jc == 0 && warp < kBK && k0 + warp < K) {
+    double s = 0.0;
+    for (int l = lane; l < d; l += 32) s = fma(in.mu[l], wsm[warp * d + l], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) cbuf[in.c_off + k0 + warp] = s;
+  }
+}
+
+// ---------------------------------------------------------------- main ---
+template <typename T, int BM>
+__global__ void __launch_bounds__(kThreads, 2) k_batched_main(const BInst* __restrict__ insts,
+                                                              const BItem* __restrict__ items, int nitems,
+                                                              const T* __restrict__ Yf, double* __restrict__ parts,
+                                                              uint32_t* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();   // the previous item's readers of s_item are done
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    const BItem item = items[it];
+    const BInst& in = insts[item.inst];
+    const int d = in.d, K = in.K;
+    const SimtSmem<T, BM> sm(smem_raw, d);
+    const gen::Stream st = gen::make_stream(in.seed, in.epoch, in.instance);
+    double macc[kMaxDimSimt / kThreads];
+#pragma unroll
+    for (int r = 0; r < kMaxDimSimt / kThreads; ++r) macc[r] = 0.0;
+    double* slot = parts + in.part_off + (size_t)item.slot * (2 * K + d);
+    const T* Yt = Yf + in.y_off;
+    bool first = true;
+    for (uint32_t off = 0; off < item.n; off += BM) {
+      const int nrow = (int)min((uint32_t)BM, item.n - off);
+      simt_tile<T, BM>(st, d, in.law, in.nu, in.N / 2u, item.i0 + off, nrow, K, Yt, sm, macc, first, 0, slot,
+                       slot + K, nullptr, nullptr);
+      first = false;
+    }
+#pragma unroll
+    for (int r = 0; r < kMaxDimSimt / kThreads; ++r) {
+      const int j = threadIdx.x + r * kThreads;
+      if (j < d) slot[2 * K + j] = macc[r];
+    }
+  }
+}
+
+// ------------------------------------------------------------ finalize ---
+__device__ __forceinline__ void nsum_add(double& s, double& c, double x) {
+  const double t = s + x;
+  if (fabs(s) >= fabs(x))
+    c += (s - t) + x;
+  else
+    c += (x - t) + s;
+  s = t;
+}
+
+// One block per problem: merge its item partials in item order, then
+// pbar_k = c_k + S1_k/N, V_k = (S2_k - S1_k^2/N)/(N-1), f_k = lambda V_k - pbar_k.
+__global__ void k_batched_finalize(const BInst* __restrict__ insts, const double* __restrict__ parts,
+                                   const double* __restrict__ cbuf) {
+  const BInst in = insts[blockIdx.x];
+  const int K = in.K, d = in.d;
+  const int stride = 2 * K + d;
+  const double* p = parts + in.part_off;
+  const double N = (double)in.N;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0;
+    for (int t = 0; t < in.nitems; ++t) {
+      nsum_add(s1, c1, p[(size_t)t * stride + k]);
+      nsum_add(s2, c2, p[(size_t)t * stride + K + k]);
+    }
+    const double S1 = s1 + c1, S2 = s2 + c2;
+    const double qbar = S1 / N;
+    const double pb = cbuf[in.c_off + k] + qbar;
+    const double V = (S2 - S1 * qbar) / (N - 1.0);
+    in.f[k] = in.lambda * V - pb;
+    if (in.pbar) in.pbar[k] = pb;
+    if (in.var) in.var[k] = V;
+  }
+}
+
+// ------------------------------------------------------------------ host ---
+struct BatchLayout {
+  size_t insts, items, yf, y64, c, parts, counter, total;
+  int nitems, pblocks, dmax;
+};
+
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Fills the descriptor tables (host) and the workspace layout for a chunk of
+// `chunk_tiles` tiles of BM scenarios per item.
+static BatchLayout plan_batch(int B, const saa_problem* probs, const int32_t* K, const double* const* X,
+                              double* const* f, double* const* pbar, double* const* var, int es, int bm,
+                              int chunk_tiles, std::vector<BInst>* hi, std::vector<BItem>* hitems) {
+  BatchLayout L;
+  std::memset(&L, 0, sizeof(L));
+  int64_t yf = 0, y64 = 0, c = 0, parts = 0;
+  int nitems = 0, pblocks = 0, dmax = 1;
+  const uint32_t chunk = (uint32_t)(bm * chunk_tiles);
+  if (hi) hi->resize(B);
+  if (hitems) hitems->clear();
+  for (int b = 0; b < B; ++b) {
+    const saa_problem& p = probs[b];
+    const int d = p.d, k = K[b];
+    const int nit = (int)((p.N + chunk - 1) / chunk);
+    if (hi) {
+      BInst& in = (*hi)[b];
+      std::memset(&in, 0, sizeof(in));
+      in.d = d; in.K = k; in.law = p.law; in.nu = p.nu;
+      in.N = (uint32_t)p.N; in.instance = p.instance; in.epoch = p.epoch;
+      in.seed = p.seed; in.lambda = p.lambda;
+      in.mu = p.mu; in.chol = p.chol; in.X = X[b];
+      in.f = f[b]; in.pbar = pbar ? pbar[b] : nullptr; in.var = var ? var[b] : nullptr;
+      in.y_off = yf; in.y64_off = y64; in.c_off = c; in.part_off = parts;
+      in.item0 = nitems; in.nitems = nit; in.pblock0 = pblocks;
+    }
+    if (hitems)
+      for (int t = 0; t < nit; ++t) {
+        BItem it;
+        it.inst = b;
+        it.i0 = (uint32_t)t * chunk;
+        it.n = (uint32_t)std::min<int64_t>(chunk, p.N - (int64_t)t * chunk);
+        it.slot = t;
+        hitems->push_back(it);
+      }
+    yf += (int64_t)d * k;
+    y64 += (int64_t)d * k;
+    c += k;
+    parts += (int64_t)nit * (2 * k + d);
+    nitems += nit;
+    pblocks += ((k + kBK - 1) / kBK) * ((d + 31) / 32);
+    dmax = std::max(dmax, d);
+  }
+  size_t off = 0;
+  L.insts = off; off = al(off + sizeof(BInst) * (size_t)B);
+  L.items = off; off = al(off + sizeof(BItem) * (size_t)nitems);
+  L.yf = off; off = al(off + (size_t)es * yf);
+  L.y64 = off; off = al(off + 8 * (size_t)y64);
+  L.c = off; off = al(off + 8 * (size_t)c);
+  L.parts = off; off = al(off + 8 * (size_t)parts);
+  L.counter = off; off = al(off + 8);
+  L.total = off;
+  L.nitems = nitems;
+  L.pblocks = pblocks;
+  L.dmax = dmax;
+  return L;
+}
+
+template <typename T, int BM>
+static cudaError_t launch_main(const saa_ctx* ctx, const BatchLayout& L, char* ws, cudaStream_t st) {
+  const int prec = sizeof(T) == 8 ? SAA_FP64 : SAA_FP32;
+  const int smem = (int)simt_smem(prec, L.dmax, BM);
+  auto kern = k_batched_main<T, BM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(L.nitems, ctx->sm_count * std::max(occ, 1)));
+  e = cudaMemsetAsync(ws + L.counter, 0, 8, st);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, smem, st>>>((const BInst*)(ws + L.insts), (const BItem*)(ws + L.items), L.nitems,
+                                     (const T*)(ws + L.yf), (double*)(ws + L.parts), (uint32_t*)(ws + L.counter));
+  return cudaGetLastError();
+}
+
+}  // namespace saa
+
+using namespace saa;
+
+namespace {
+
+constexpr int kChunkChoices[3] = {16, 32, 64};   // tiles per item
+
+struct TuneEntry {
+  uint64_t key;
+  int bm, chunk;
+};
+std::vector<TuneEntry> g_tune;   // per process: (batch-shape key) -> chosen tile shape
+std::mutex g_tune_mu;
+
+uint64_t shape_key(int B, const saa_problem* probs, const int32_t* K, int prec, int device) {
+  uint64_t h = 1469598103934665603ull ^ (uint64_t)device ^ ((uint64_t)prec << 8) ^ ((uint64_t)B << 16);
+  for (int b = 0; b < B; ++b) {
+    h = (h ^ (uint64_t)probs[b].d) * 1099511628211ull;
+    h = (h ^ (uint64_t)probs[b].N) * 1099511628211ull;
+    h = (h ^ (uint64_t)K[b]) * 1099511628211ull;
+  }
+  return h;
+}
+
+saa_status validate(int B, const saa_problem* probs, const int32_t* K, const double* const* X, double* const* f,
+                    saa_prec prec) {
+  if (B < 1 || !probs || !K || !X || !f) {
+    set_error("saa_eval_batched: need B >= 1 and non-NULL descriptor arrays");
+    return SAA_EINVAL;
+  }
+  if (prec != SAA_FP32 && prec != SAA_FP64) {
+    set_error("saa_eval_batched: SAA_FP32 or SAA_FP64");
+    return SAA_EUNSUPPORTED;
+  }
+  for (int b = 0; b < B; ++b) {
+    const saa_problem& p = probs[b];
+    if (p.d < 1 || p.d > kMaxDimSimt || p.N < 2 || p.N > 0xffffffffll || p.law < 0 || p.law > 3 ||
+        (p.law == SAA_LAW_STUDENT_T && (p.nu < 2 || (p.nu & 1) || p.nu > 64)) || p.reserved != 0 || !p.mu ||
+        !p.chol || K[b] < 1 || K[b] > 65535 || !X[b] || !f[b]) {
+      set_error("saa_eval_batched: invalid problem " + std::to_string(b));
+      return SAA_EINVAL;
+    }
+  }
+  return SAA_OK;
+}
+
+int pick_bm(int prec, int dmax) { return (prec == SAA_FP64) ? (dmax <= 256 ? 64 : 32) : (dmax <= 512 ? 64 : 32); }
+
+}  // namespace
+
+static saa_status run_batch(saa_ctx* ctx, int B, const saa_problem* probs, const int32_t* K, const double* const* X,
+                            saa_prec prec, double* const* f, double* const* pbar, double* const* var, void* ws,
+                            size_t ws_bytes, cudaStream_t st, int bm, int chunk, bool upload) {
+  const int es = prec == SAA_FP64 ? 8 : 4;
+  std::vector<BInst> hi;
+  std::vector<BItem> hitems;
+  const BatchLayout L = plan_batch(B, probs, K, X, f, pbar, var, es, bm, chunk, &hi, &hitems);
+  if (ws_bytes < L.total) {
+    set_error("saa_eval_batched: workspace smaller than saa_workspace_size_batched()");
+    return SAA_ENOMEM;
+  }
+  char* w = (char*)ws;
+  if (upload) {
+    // descriptors go through a pinned staging buffer owned by the context
+    const size_t bytes = L.yf;
+    if (ctx->stage_bytes < bytes) {
+      if (ctx->stage) {
+        cudaEventSynchronize(ctx->stage_ready);
+        cudaFreeHost(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_bytes = 0;
+      }
+      saa_status s = cuda_status(cudaHostAlloc(&ctx->stage, bytes, cudaHostAllocDefault), "pinned staging buffer");
+      if (s != SAA_OK) return s;
+      ctx->stage_bytes = bytes;
+    } else {
+      cudaEventSynchronize(ctx->stage_ready);   // the previous upload has been consumed
+    }
+    char* h = (char*)ctx->stage;
+    std::memcpy(h + L.insts, hi.data(), sizeof(BInst) * hi.size());
+    std::memcpy(h + L.items, hitems.data(), sizeof(BItem) * hitems.size());
+    saa_status s = cuda_status(cudaMemcpyAsync(w, h, bytes, cudaMemcpyHostToDevice, st), "descriptor upload");
+    if (s != SAA_OK) return s;
+    s = cuda_status(cudaEventRecord(ctx->stage_ready, st), "stage event");
+    if (s != SAA_OK) return s;
+  }
+  const size_t psmem = sizeof(double) * kBK * L.dmax;
+  if (prec == SAA_FP64) {
+    if (psmem > 48 * 1024)
+      cudaFuncSetAttribute(k_batched_prologue<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    k_batched_prologue<double><<<L.pblocks, 256, psmem, st>>>((const BInst*)(w + L.insts), B, (double*)(w + L.yf),
+                                                              (double*)(w + L.y64), (double*)(w + L.c));
+  } else {
+    if (psmem > 48 * 1024)
+      cudaFuncSetAttribute(k_batched_prologue<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    k_batched_prologue<float><<<L.pblocks, 256, psmem, st>>>((const BInst*)(w + L.insts), B, (float*)(w + L.yf),
+                                                             (double*)(w + L.y64), (double*)(w + L.c));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "batched prologue launch");
+  if (prec == SAA_FP64)
+    e = (bm == 64) ? launch_main<double, 64>(ctx, L, w, st) : launch_main<double, 32>(ctx, L, w, st);
+  else
+    e = (bm == 64) ? launch_main<float, 64>(ctx, L, w, st) : launch_main<float, 32>(ctx, L, w, st);
+  if (e != cudaSuccess) return cuda_status(e, "batched sample kernel launch");
+  k_batched_finalize<<<B, 64, 0, st>>>((const BInst*)(w + L.insts), (const double*)(w + L.parts),
+                                       (const double*)(w + L.c));
+  ctx->kernels += 3;
+  return cuda_status(cudaGetLastError(), "batched finalize launch");
+}
+
+extern "C" size_t saa_workspace_size_batched(const saa_ctx* ctx, int32_t B, const saa_problem* probs,
+                                             const int32_t* K, saa_prec prec) {
+  if (!ctx || B < 1 || !probs || !K) return 0;
+  const int es = prec == SAA_FP64 ? 8 : 4;
+  int dmax = 1;
+  for (int b = 0; b < B; ++b) dmax = std::max(dmax, probs[b].d);
+  size_t need = 0;
+  // the largest layout over the tile shapes the autotuner may pick
+  for (int bm : {32, 64})
+    for (int ch : kChunkChoices)
+      need = std::max(need, plan_batch(B, probs, K, nullptr, nullptr, nullptr, nullptr, es, bm, ch, nullptr, nullptr)
+                                .total);
+  return need;
+}
+
+extern "C" saa_status saa_eval_batched(saa_ctx* ctx, int32_t B, const saa_problem* probs, const int32_t* K,
+                                       const double* const* X, saa_prec prec, double* const* f, double* const* pbar,
+                                       double* const* var, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return SAA_EINVAL;
+  }
+  saa_status s = validate(B, probs, K, X, f, prec);
+  if (s != SAA_OK) return s;
+  if (!ws || (((uintptr_t)ws) & 255u)) {
+    set_error("workspace must be non-NULL and 256-byte aligned");
+    return SAA_EINVAL;
+  }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != ctx->device) cudaSetDevice(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  int dmax = 1;
+  for (int b = 0; b < B; ++b) dmax = std::max(dmax, probs[b].d);
+  const uint64_t key = shape_key(B, probs, K, prec, ctx->device);
+  int bm = -1, chunk = -1;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const TuneEntry& t : g_tune)
+      if (t.key == key) {
+        bm = t.bm;
+        chunk = t.chunk;
+      }
+  }
+  if (bm < 0 && ctx->autotune) {
+    // time each candidate tile shape once on this batch (outside any capture)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusNone) {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float best = 1e30f;
+      for (int cbm : {32, 64}) {
+        if (prec == SAA_FP64 && cbm == 64 && dmax > 256) continue;
+        if (prec == SAA_FP32 && cbm == 64 && dmax > 512) continue;
+        for (int ch : kChunkChoices) {
+          s = run_batch(ctx, B, probs, K, X, prec, f, pbar, var, ws, ws_bytes, st, cbm, ch, true);
+          if (s != SAA_OK) break;
+          cudaEventRecord(e0, st);
+          s = run_batch(ctx, B, probs, K, X, prec, f, pbar, var, ws, ws_bytes, st, cbm, ch, false);
+          cudaEventRecord(e1, st);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (s == SAA_OK && ms < best) {
+            best = ms;
+            bm = cbm;
+            chunk = ch;
+          }
+        }
+        if (s != SAA_OK) break;
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (s != SAA_OK) {
+        if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+        return s;
+      }
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune.push_back({key, bm, chunk});
+    }
+  }
+  if (bm < 0) {
+    bm = pick_bm(prec, dmax);
+    chunk = 32;
+  }
+  s = run_batch(ctx, B, probs, K, X, prec, f, pbar, var, ws, ws_bytes, st, bm, chunk, true);
+  if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+  return s;
+}

@@ -77,6 +77,11 @@ struct saa_ctx {
   int prof_n;                    // recorded event pairs
   cudaEvent_t prof_ev[2 * 256];  // (start, end) pairs, created on enable
   int64_t kernels;               // kernels launched since the last read
+  // ragged batches: pinned staging buffer for the descriptor tables
+  void* stage;
+  size_t stage_bytes;
+  cudaEvent_t stage_ready;       // the last upload from `stage` has completed
+  int autotune;                  // time candidate tile shapes on a new batch shape
 };
 
 namespace saa {

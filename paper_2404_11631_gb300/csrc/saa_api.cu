@@ -178,11 +178,14 @@ saa_status saa_ctx_create(saa_ctx** out, int device) {
   }
   if (s == SAA_OK) s = cuda_status(cudaMalloc((void**)&c->err, sizeof(uint32_t)), "cudaMalloc(error word)");
   if (s == SAA_OK) s = cuda_status(cudaMemset(c->err, 0, sizeof(uint32_t)), "cudaMemset(error word)");
+  if (s == SAA_OK)
+    s = cuda_status(cudaEventCreateWithFlags(&c->stage_ready, cudaEventDisableTiming), "cudaEventCreate(stage)");
   if (s != SAA_OK) {
     if (c->err) cudaFree(c->err);
     delete c;
     return s;
   }
+  c->autotune = 1;
   *out = c;
   return SAA_OK;
 }
@@ -196,6 +199,11 @@ void saa_ctx_destroy(saa_ctx* ctx) {
   }
   if (ctx->prof_on)
     for (int i = 0; i < 2 * 256; ++i) cudaEventDestroy(ctx->prof_ev[i]);
+  if (ctx->stage) {
+    cudaEventSynchronize(ctx->stage_ready);
+    cudaFreeHost(ctx->stage);
+  }
+  if (ctx->stage_ready) cudaEventDestroy(ctx->stage_ready);
   if (ctx->err) cudaFree(ctx->err);
   delete ctx;
 }
@@ -214,6 +222,12 @@ saa_status saa_ctx_sync(saa_ctx* ctx, void* stream) {
     if (w & kErrTimeout) return fail(SAA_ETIMEOUT, "a bounded device wait gave up");
     return fail(SAA_EDEVICE, "a device-side check flagged an error");
   }
+  return SAA_OK;
+}
+
+saa_status saa_ctx_set_autotune(saa_ctx* ctx, int enable) {
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  ctx->autotune = enable ? 1 : 0;
   return SAA_OK;
 }
 

@@ -18,6 +18,7 @@
 
 #include "gen.cuh"
 #include "internal.cuh"
+#include "simt_tile.cuh"
 
 namespace saa {
 
@@ -108,188 +109,43 @@ cudaError_t launch_prologue(const saa_problem* p, int K, const double* X, int pr
 // Every partial element is owned by exactly one thread of one CTA, which
 // writes it on the CTA's first tile and accumulates afterwards.
 // ------------------------------------------------------------------------
-template <typename T> struct Pad;
-template <> struct Pad<float> { static constexpr int v = 4; };
-template <> struct Pad<double> { static constexpr int v = 2; };
-
+// ------------------------------------------------------------------------
+// Main SIMT kernel: persistent over scenario tiles of BM rows; each CTA owns
+// one partial slot (its S1, S2, m~ and, for the gradient, G).
+// ------------------------------------------------------------------------
 template <typename T, int BM>
-__global__ void __launch_bounds__(kThreads) k_simt(LawArgs la, int K, int want_grad, const T* __restrict__ Yt,
+__global__ void __launch_bounds__(kThreads, 2) k_simt(LawArgs la, int K, int want_grad, const T* __restrict__ Yt,
                                                    double* __restrict__ part_s1, double* __restrict__ part_s2,
                                                    double* __restrict__ part_m, T* __restrict__ part_g,
                                                    T* __restrict__ part_gc, int64_t tiles) {
-  constexpr int TM = BM / 16;
-  constexpr int TN = 4;
-  constexpr int BMP = BM + Pad<T>::v;
-  constexpr int PC = gen::Gen<T>::kPerCall;
-  constexpr int QP = kBN + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int d = la.d;
-  T* As = reinterpret_cast<T*>(smem_raw);  // [d][BMP]
-  T* Ys = As + (size_t)d * BMP;            // [kDK][kBN]
-  T* Qs = Ys + kDK * kBN;                  // [BM][QP]
-  T* ss = Qs + BM * QP;                    // [BM]
-
-  const int tid = threadIdx.x;
-  const int ty = tid & 15;  // scenario group
-  const int tx = tid >> 4;  // decision group
+  const SimtSmem<T, BM> sm(smem_raw, d);
   uint32_t epoch = la.epoch;
   if (la.t_dev) epoch += (uint32_t)(*la.t_dev / la.M);
   const gen::Stream st = gen::make_stream(la.seed, epoch, la.instance);
   const uint32_t half = la.N / 2u;
-  const int nb = (d + PC - 1) / PC;
 
   double macc[kMaxDimSimt / kThreads];
 #pragma unroll
   for (int r = 0; r < kMaxDimSimt / kThreads; ++r) macc[r] = 0.0;
+  double* p_s1 = part_s1 + (size_t)blockIdx.x * K;
+  double* p_s2 = part_s2 + (size_t)blockIdx.x * K;
+  T* p_g = want_grad ? part_g + (size_t)blockIdx.x * K * d : nullptr;
+  T* p_gc = want_grad ? part_gc + (size_t)blockIdx.x * K * d : nullptr;
 
   bool first = true;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const uint32_t i0 = (uint32_t)(tile * BM);
     const int nrow = (int)min((int64_t)BM, (int64_t)la.N - (int64_t)i0);
-    __syncthreads();
-    if (tid < BM) ss[tid] = (tid < nrow) ? gen::Gen<T>::scale(st, i0 + tid, la.law, la.nu) : T(0);
-    __syncthreads();
-    for (int idx = tid; idx < nb * BM; idx += kThreads) {
-      const int i = idx % BM;
-      const int b = idx / BM;
-      T z[PC];
-      if (i < nrow) {
-        gen::Gen<T>::block(st, (uint32_t)b, i0 + i, gen::is_lognormal(la.law, i0 + i, half), z);
-        const T s = ss[i];
-#pragma unroll
-        for (int q = 0; q < PC; ++q) z[q] *= s;
-      } else {
-#pragma unroll
-        for (int q = 0; q < PC; ++q) z[q] = T(0);
-      }
-#pragma unroll
-      for (int q = 0; q < PC; ++q) {
-        const int j = b * PC + q;
-        if (j < d) As[(size_t)j * BMP + i] = z[q];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kMaxDimSimt / kThreads; ++r) {
-      const int j = tid + r * kThreads;
-      if (j < d) {
-        T sum = T(0);
-        for (int i = 0; i < nrow; ++i) sum += As[(size_t)j * BMP + i];
-        macc[r] += (double)sum;
-      }
-    }
-
-    for (int k0 = 0; k0 < K; k0 += kBN) {
-      T acc[TM][TN];
-#pragma unroll
-      for (int m = 0; m < TM; ++m)
-#pragma unroll
-        for (int n = 0; n < TN; ++n) acc[m][n] = T(0);
-
-      for (int j0 = 0; j0 < d; j0 += kDK) {
-        __syncthreads();
-        for (int idx = tid; idx < kDK * kBN; idx += kThreads) {
-          const int jj = idx / kBN, kk = idx % kBN;
-          const int j = j0 + jj, k = k0 + kk;
-          Ys[idx] = (j < d && k < K) ? Yt[(size_t)j * K + k] : T(0);
-        }
-        __syncthreads();
-        const int jmax = min(kDK, d - j0);
-        for (int jj = 0; jj < jmax; ++jj) {
-          const T* arow = As + (size_t)(j0 + jj) * BMP + ty * TM;
-          const T* yrow = Ys + jj * kBN + tx * TN;
-          T a[TM], y[TN];
-#pragma unroll
-          for (int m = 0; m < TM; ++m) a[m] = arow[m];
-#pragma unroll
-          for (int n = 0; n < TN; ++n) y[n] = yrow[n];
-#pragma unroll
-          for (int m = 0; m < TM; ++m)
-#pragma unroll
-            for (int n = 0; n < TN; ++n) acc[m][n] = fma(a[m], y[n], acc[m][n]);
-        }
-      }
-
-      // S1 / S2 over the tile's rows: own rows, then the 16 lanes sharing tx.
-#pragma unroll
-      for (int n = 0; n < TN; ++n) {
-        T s1 = T(0), s2 = T(0);
-#pragma unroll
-        for (int m = 0; m < TM; ++m) {
-          s1 += acc[m][n];
-          s2 = fma(acc[m][n], acc[m][n], s2);
-        }
-#pragma unroll
-        for (int off = 8; off > 0; off >>= 1) {
-          s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-          s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-        }
-        const int k = k0 + tx * TN + n;
-        if (ty == 0 && k < K) {
-          double* p1 = part_s1 + (size_t)blockIdx.x * K + k;
-          double* p2 = part_s2 + (size_t)blockIdx.x * K + k;
-          *p1 = first ? (double)s1 : *p1 + (double)s1;
-          *p2 = first ? (double)s2 : *p2 + (double)s2;
-        }
-      }
-
-      if (want_grad) {
-        __syncthreads();
-#pragma unroll
-        for (int m = 0; m < TM; ++m)
-#pragma unroll
-          for (int n = 0; n < TN; ++n) Qs[(ty * TM + m) * QP + tx * TN + n] = acc[m][n];
-        __syncthreads();
-        for (int jd0 = 0; jd0 < d; jd0 += 64) {
-          T g[4][TN];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int n = 0; n < TN; ++n) g[q][n] = T(0);
-          for (int i = 0; i < nrow; ++i) {
-            T a[4], qv[TN];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int j = jd0 + ty + 16 * q;
-              a[q] = (j < d) ? As[(size_t)j * BMP + i] : T(0);
-            }
-#pragma unroll
-            for (int n = 0; n < TN; ++n) qv[n] = Qs[i * QP + tx * TN + n];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-              for (int n = 0; n < TN; ++n) g[q][n] = fma(a[q], qv[n], g[q][n]);
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = jd0 + ty + 16 * q;
-#pragma unroll
-            for (int n = 0; n < TN; ++n) {
-              const int k = k0 + tx * TN + n;
-              if (j < d && k < K) {
-                const size_t e = ((size_t)blockIdx.x * K + k) * d + j;
-                if (first) {
-                  part_g[e] = g[q][n];
-                  part_gc[e] = T(0);
-                } else {  // Kahan: the partial carries its lost low part in part_gc
-                  const T y = g[q][n] - part_gc[e];
-                  const T s = part_g[e];
-                  const T t = s + y;
-                  part_gc[e] = (t - s) - y;
-                  part_g[e] = t;
-                }
-              }
-            }
-          }
-        }
-      }
-    }
+    simt_tile<T, BM>(st, d, la.law, la.nu, half, i0, nrow, K, Yt, sm, macc, first, want_grad, p_s1, p_s2, p_g,
+                     p_gc);
     first = false;
   }
   if (!first) {
 #pragma unroll
     for (int r = 0; r < kMaxDimSimt / kThreads; ++r) {
-      const int j = tid + r * kThreads;
+      const int j = threadIdx.x + r * kThreads;
       if (j < d) part_m[(size_t)blockIdx.x * d + j] = macc[r];
     }
   }

@@ -83,6 +83,13 @@ def lib():
             L.saa_profile_enable.restype = C.c_int
             L.saa_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
             L.saa_profile_read.restype = C.c_int
+            L.saa_workspace_size_batched.argtypes = [vp, C.c_int32, pp, C.POINTER(C.c_int32), C.c_int]
+            L.saa_workspace_size_batched.restype = sz
+            L.saa_eval_batched.argtypes = [vp, C.c_int32, pp, C.POINTER(C.c_int32), vp, C.c_int, vp, vp, vp, vp, sz,
+                                           vp]
+            L.saa_eval_batched.restype = C.c_int
+            L.saa_ctx_set_autotune.argtypes = [vp, C.c_int]
+            L.saa_ctx_set_autotune.restype = C.c_int
             L.saa_max_dim.argtypes = [C.c_int]
             L.saa_max_dim.restype = C.c_int32
             L.saa_status_string.argtypes = [C.c_int]
@@ -257,6 +264,44 @@ def saa_generate(prob: Problem, i0: int, n: int, prec="fp32", want_xi: bool = Fa
     return out
 
 
+class Batch:
+    """Host-side marshalling of a ragged batch for saa_eval_batched (reusable
+    across calls: the descriptor arrays are built once)."""
+
+    def __init__(self, problems: list, Xs: list, prec="fp32", want_pbar=True, want_var=True):
+        self.problems, self.Xs, self.prec = problems, [_decisions(X, p) for X, p in zip(Xs, problems)], prec
+        B = len(problems)
+        dev = problems[0].device
+        self.B, self.device = B, dev
+        self.cprobs = (_CProblem * B)(*[p.c_struct() for p in problems])
+        self.K = (C.c_int32 * B)(*[int(X.shape[0]) for X in self.Xs])
+        self.f = [torch.empty(int(X.shape[0]), dtype=torch.float64, device=dev) for X in self.Xs]
+        self.pbar = [torch.empty_like(t) for t in self.f] if want_pbar else None
+        self.var = [torch.empty_like(t) for t in self.f] if want_var else None
+        ptrs = lambda ts: (C.c_void_p * B)(*[t.data_ptr() for t in ts]) if ts is not None else None  # noqa: E731
+        self.pX, self.pf, self.pp, self.pv = ptrs(self.Xs), ptrs(self.f), ptrs(self.pbar), ptrs(self.var)
+        need = lib().saa_workspace_size_batched(context(dev.index), B, self.cprobs, self.K, _prec(prec))
+        if need == 0:
+            raise SAAError(SAA_EINVAL, lib().saa_last_error().decode())
+        self.ws = torch.empty(need, dtype=torch.uint8, device=dev)
+
+    def run(self) -> dict:
+        _check(lib().saa_eval_batched(context(self.device.index), self.B, self.cprobs, self.K, self.pX,
+                                      _prec(self.prec), self.pf, self.pp, self.pv, _ptr(self.ws), self.ws.numel(),
+                                      _stream(self.device)))
+        out = {"f": self.f}
+        if self.pbar is not None:
+            out["pbar"] = self.pbar
+        if self.var is not None:
+            out["var"] = self.var
+        return out
+
+
+def saa_eval_batched(problems: list, Xs: list, prec="fp32") -> dict:
+    """Eq. 4 for a ragged batch: lists of per-problem f (and pbar, var) tensors."""
+    return Batch(problems, Xs, prec).run()
+
+
 def saa_ctx_sync(device: int | None = None):
     """Waits for the current stream and raises if a device-side check fired."""
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -281,4 +326,5 @@ def max_dim(prec) -> int:
 
 EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_size", "saa_eval", "saa_grad",
             "saa_solve", "saa_generate", "saa_max_dim", "saa_status_string", "saa_last_error",
-            "saa_profile_enable", "saa_profile_read"]
+            "saa_profile_enable", "saa_profile_read", "saa_eval_batched", "saa_workspace_size_batched",
+            "saa_ctx_set_autotune"]

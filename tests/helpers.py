@@ -12,6 +12,11 @@ Error of an estimate a against the oracle's b for decision k is
   |a - b| / max(|b|, lambda V_k + |mu'w_k|),
 because f_hat and w'R_bar can be near zero while their terms are not.
 Gradients use the L2 relative error ||a - b|| / ||b|| per decision.
+The sample variance alone is scored as the variance term of f_hat,
+  lambda |V_a - V_b| / max(|f_b|, lambda V_b + |mu'w_k|),
+because an FP32 contraction's error scales with |a_i||y_k|, not with |Q_ik|:
+a decision with a small variance but large y_k sees a larger relative error
+in V than in f_hat.
 """
 import numpy as np
 
@@ -39,6 +44,11 @@ def make(d, N, law=oracle.LAW_GAUSS, nu=4, lam=0.5, seed=0, instance=0, epoch=0,
 def est_err(a, b, var, X, mu, lam):
     scale = np.maximum(np.abs(b), lam * var + np.abs(X @ mu))
     return np.max(np.abs(a - b) / scale)
+
+
+def var_err(va, vb, fb, X, mu, lam):
+    scale = np.maximum(np.abs(fb), lam * vb + np.abs(X @ mu))
+    return np.max(lam * np.abs(va - vb) / scale)
 
 
 def grad_err(a, b):

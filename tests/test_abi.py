@@ -57,3 +57,32 @@ def test_context_creation_fails_cleanly_without_a_device(libsaa):
     rc = libsaa.saa_ctx_create(C.byref(ctx), 0)
     assert rc == 1 and not ctx.value
     assert b"device" in libsaa.saa_last_error()
+
+
+def _header_params():
+    src = open(os.path.join(ROOT, "include", "saa.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(saa_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        params = [p.strip() for p in m.group(2).split(",") if p.strip() and p.strip() != "void"]
+        out[m.group(1)] = ["ptr" if "*" in p else "int" for p in params]
+    return out
+
+
+def test_binding_argtypes_match_the_header():
+    # argument count and pointer / integer kind of every bound entry point
+    import ctypes
+    from paper_2404_11631_gb300 import saa
+    L = saa.lib()
+    params = _header_params()
+    checked = 0
+    for name, kinds in params.items():
+        fn = getattr(L, name)
+        if fn.argtypes is None:
+            continue
+        assert len(fn.argtypes) == len(kinds), name
+        for t, kind in zip(fn.argtypes, kinds):
+            is_ptr = t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "contents") or t.__name__.startswith("LP_")
+            assert is_ptr == (kind == "ptr"), (name, t, kind)
+        checked += 1
+    assert checked >= 12
