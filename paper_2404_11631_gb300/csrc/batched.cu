@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_batched_prologue(const BInst* __restric
 }
 
 // ---------------------------------------------------------------- main ---
-template <typename T, int BM>
+template <typename T, int BM, int TN>
 __global__ void __launch_bounds__(kThreads, 2) k_batched_main(const BInst* __restrict__ insts,
                                                               const BItem* __restrict__ items, int nitems,
                                                               const T* __restrict__ Yf, double* __restrict__ parts,
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched_main(const BInst* __res
     const BItem item = items[it];
     const BInst& in = insts[item.inst];
     const int d = in.d, K = in.K;
-    const SimtSmem<T, BM> sm(smem_raw, d);
+    const SimtSmem<T, BM, TN> sm(smem_raw, d);
     const gen::Stream st = gen::make_stream(in.seed, in.epoch, in.instance);
     double macc[kMaxDimSimt / kThreads];
 #pragma unroll
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched_main(const BInst* __res
     bool first = true;
     for (uint32_t off = 0; off < item.n; off += BM) {
       const int nrow = (int)min((uint32_t)BM, item.n - off);
-      simt_tile<T, BM>(st, d, in.law, in.nu, in.N / 2u, item.i0 + off, nrow, K, Yt, sm, macc, first, 0, slot,
+      simt_tile<T, BM, TN>(st, d, in.law, in.nu, in.N / 2u, item.i0 + off, nrow, K, Yt, sm, macc, first, 0, slot,
                        slot + K, nullptr, nullptr);
       first = false;
     }
@@ -193,7 +193,7 @@ __global__ void k_batched_finalize(const BInst* __restrict__ insts, const double
 // ------------------------------------------------------------------ host ---
 struct BatchLayout {
   size_t insts, items, yf, y64, c, parts, counter, total;
-  int nitems, pblocks, dmax;
+  int nitems, pblocks, dmax, kmax;
 };
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -206,7 +206,7 @@ static BatchLayout plan_batch(int B, const saa_problem* probs, const int32_t* K,
   BatchLayout L;
   std::memset(&L, 0, sizeof(L));
   int64_t yf = 0, y64 = 0, c = 0, parts = 0;
-  int nitems = 0, pblocks = 0, dmax = 1;
+  int nitems = 0, pblocks = 0, dmax = 1, kmax = 1;
   const uint32_t chunk = (uint32_t)(bm * chunk_tiles);
   if (hi) hi->resize(B);
   if (hitems) hitems->clear();
@@ -241,6 +241,7 @@ static BatchLayout plan_batch(int B, const saa_problem* probs, const int32_t* K,
     nitems += nit;
     pblocks += ((k + kBK - 1) / kBK) * ((d + 31) / 32);
     dmax = std::max(dmax, d);
+    kmax = std::max(kmax, k);
   }
   size_t off = 0;
   L.insts = off; off = al(off + sizeof(BInst) * (size_t)B);
@@ -254,14 +255,15 @@ static BatchLayout plan_batch(int B, const saa_problem* probs, const int32_t* K,
   L.nitems = nitems;
   L.pblocks = pblocks;
   L.dmax = dmax;
+  L.kmax = kmax;
   return L;
 }
 
-template <typename T, int BM>
+template <typename T, int BM, int TN>
 static cudaError_t launch_main(const saa_ctx* ctx, const BatchLayout& L, char* ws, cudaStream_t st) {
   const int prec = sizeof(T) == 8 ? SAA_FP64 : SAA_FP32;
-  const int smem = (int)simt_smem(prec, L.dmax, BM);
-  auto kern = k_batched_main<T, BM>;
+  const int smem = (int)simt_smem(prec, L.dmax, BM, TN);
+  auto kern = k_batched_main<T, BM, TN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -376,10 +378,13 @@ static saa_status run_batch(saa_ctx* ctx, int B, const saa_problem* probs, const
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "batched prologue launch");
+  const bool narrow = simt_tn(L.kmax) == 1;
   if (prec == SAA_FP64)
-    e = (bm == 64) ? launch_main<double, 64>(ctx, L, w, st) : launch_main<double, 32>(ctx, L, w, st);
+    e = (bm == 64) ? (narrow ? launch_main<double, 64, 1>(ctx, L, w, st) : launch_main<double, 64, 4>(ctx, L, w, st))
+                   : (narrow ? launch_main<double, 32, 1>(ctx, L, w, st) : launch_main<double, 32, 4>(ctx, L, w, st));
   else
-    e = (bm == 64) ? launch_main<float, 64>(ctx, L, w, st) : launch_main<float, 32>(ctx, L, w, st);
+    e = (bm == 64) ? (narrow ? launch_main<float, 64, 1>(ctx, L, w, st) : launch_main<float, 64, 4>(ctx, L, w, st))
+                   : (narrow ? launch_main<float, 32, 1>(ctx, L, w, st) : launch_main<float, 32, 4>(ctx, L, w, st));
   if (e != cudaSuccess) return cuda_status(e, "batched sample kernel launch");
   k_batched_finalize<<<B, 64, 0, st>>>((const BInst*)(w + L.insts), (const double*)(w + L.parts),
                                        (const double*)(w + L.c));

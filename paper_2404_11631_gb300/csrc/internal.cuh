@@ -12,7 +12,6 @@
 namespace saa {
 
 constexpr int kThreads = 256;   // threads per CTA of the SIMT kernels
-constexpr int kBN = 64;         // decisions per K-chunk in the SIMT kernels
 constexpr int kDK = 32;         // dimensions per staged Y chunk
 constexpr int kMaxDimSimt = 1024;
 
@@ -57,6 +56,7 @@ struct Workspace {
 struct Plan {
   int prec;       // saa_prec
   int bm;         // scenarios per tile
+  int tn;         // SIMT: decisions per thread column group (K-chunk = 16 tn)
   int grid;       // CTAs of the main kernel
   int smem;       // dynamic shared memory of the main kernel
   int64_t tiles;  // scenario tiles
@@ -106,9 +106,11 @@ cudaError_t launch_generate(const LawArgs& la, int64_t i0, int64_t n, int prec, 
 cudaError_t launch_fw_step(int d, const double* g, const double* f, double* w, const int64_t* t_dev,
                            int64_t t_base, double* f_trace, double* gap_trace, int64_t* t_next, cudaStream_t st);
 
-// SIMT tile shape for (prec, d).
+// SIMT tile shape for (prec, d, K).
 int simt_bm(int prec, int d);
-size_t simt_smem(int prec, int d, int bm);
+int simt_tn(int K);
+size_t simt_smem(int prec, int d, int bm, int tn);
+int simt_occupancy(int prec, int bm, int tn, int smem);
 
 // Tensor-core (tcgen05, BF16 or FP16 hi/lo) value path.
 inline bool is_tc(int prec) { return prec == SAA_BF16X3 || prec == SAA_F16X3; }

@@ -26,8 +26,6 @@
 
 namespace saa {
 
-int simt_occupancy(int prec, int bm, int smem);
-
 namespace {
 
 static __device__ __align__(256) unsigned char g_static_scratch[SAA_STATIC_SCRATCH_BYTES];

@@ -23,7 +23,6 @@ saa_status cuda_status(cudaError_t e, const char* what) {
 }
 
 cudaError_t launch_set_i64(int64_t* p, int64_t v, cudaStream_t st);
-int simt_occupancy(int prec, int bm, int smem);
 
 static saa_status fail(saa_status s, const std::string& msg) {
   set_error(msg);
@@ -56,10 +55,11 @@ saa_status make_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec p
   if (prec != SAA_FP32 && prec != SAA_FP64) return fail(SAA_EUNSUPPORTED, "precision not built");
   if (p->d > kMaxDimSimt) return fail(SAA_EUNSUPPORTED, "d exceeds saa_max_dim for this precision");
   plan->bm = simt_bm(prec, p->d);
-  plan->smem = (int)simt_smem(prec, p->d, plan->bm);
+  plan->tn = simt_tn(K);
+  plan->smem = (int)simt_smem(prec, p->d, plan->bm, plan->tn);
   if (plan->smem > ctx->smem_optin) return fail(SAA_EUNSUPPORTED, "tile does not fit in shared memory");
   plan->tiles = (p->N + plan->bm - 1) / plan->bm;
-  const int occ = simt_occupancy(prec, plan->bm, plan->smem);
+  const int occ = simt_occupancy(prec, plan->bm, plan->tn, plan->smem);
   const int64_t cap = (int64_t)ctx->sm_count * occ;
   plan->grid = (int)(plan->tiles < cap ? plan->tiles : cap);
   return SAA_OK;

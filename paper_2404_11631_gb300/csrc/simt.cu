@@ -113,14 +113,14 @@ cudaError_t launch_prologue(const saa_problem* p, int K, const double* X, int pr
 // Main SIMT kernel: persistent over scenario tiles of BM rows; each CTA owns
 // one partial slot (its S1, S2, m~ and, for the gradient, G).
 // ------------------------------------------------------------------------
-template <typename T, int BM>
+template <typename T, int BM, int TN>
 __global__ void __launch_bounds__(kThreads, 2) k_simt(LawArgs la, int K, int want_grad, const T* __restrict__ Yt,
                                                    double* __restrict__ part_s1, double* __restrict__ part_s2,
                                                    double* __restrict__ part_m, T* __restrict__ part_g,
                                                    T* __restrict__ part_gc, int64_t tiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int d = la.d;
-  const SimtSmem<T, BM> sm(smem_raw, d);
+  const SimtSmem<T, BM, TN> sm(smem_raw, d);
   uint32_t epoch = la.epoch;
   if (la.t_dev) epoch += (uint32_t)(*la.t_dev / la.M);
   const gen::Stream st = gen::make_stream(la.seed, epoch, la.instance);
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_simt(LawArgs la, int K, int wan
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const uint32_t i0 = (uint32_t)(tile * BM);
     const int nrow = (int)min((int64_t)BM, (int64_t)la.N - (int64_t)i0);
-    simt_tile<T, BM>(st, d, la.law, la.nu, half, i0, nrow, K, Yt, sm, macc, first, want_grad, p_s1, p_s2, p_g,
+    simt_tile<T, BM, TN>(st, d, la.law, la.nu, half, i0, nrow, K, Yt, sm, macc, first, want_grad, p_s1, p_s2, p_g,
                      p_gc);
     first = false;
   }
@@ -156,16 +156,19 @@ int simt_bm(int prec, int d) {
   return d <= 512 ? 64 : 32;
 }
 
-size_t simt_smem(int prec, int d, int bm) {
+int simt_tn(int K) { return K <= 16 ? 1 : 4; }
+
+size_t simt_smem(int prec, int d, int bm, int tn) {
   const size_t es = (prec == SAA_FP64) ? 8 : 4;
   const int pad = (prec == SAA_FP64) ? 2 : 4;
-  return es * ((size_t)d * (bm + pad) + (size_t)kDK * kBN + (size_t)bm * (kBN + 1) + bm);
+  const size_t bn = 16 * (size_t)tn;
+  return es * ((size_t)d * (bm + pad) + (size_t)kDK * bn + (size_t)bm * (bn + 1) + bm);
 }
 
-template <typename T, int BM>
+template <typename T, int BM, int TN>
 static cudaError_t launch_simt_t(const LawArgs& la, int K, int want_grad, const Plan& plan, const Workspace& ws,
                                  cudaStream_t st) {
-  auto kern = k_simt<T, BM>;
+  auto kern = k_simt<T, BM, TN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
   if (e != cudaSuccess) return e;
   kern<<<plan.grid, kThreads, plan.smem, st>>>(la, K, want_grad, (const T*)ws.Y, ws.part_s1, ws.part_s2,
@@ -173,29 +176,39 @@ static cudaError_t launch_simt_t(const LawArgs& la, int K, int want_grad, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_simt(const LawArgs& la, int K, int prec, int want_grad, const Plan& plan, const Workspace& ws,
-                        cudaStream_t st) {
+template <int TN>
+static cudaError_t launch_simt_tn(const LawArgs& la, int K, int prec, int want_grad, const Plan& plan,
+                                  const Workspace& ws, cudaStream_t st) {
   if (prec == SAA_FP64) {
     switch (plan.bm) {
-      case 64: return launch_simt_t<double, 64>(la, K, want_grad, plan, ws, st);
-      case 32: return launch_simt_t<double, 32>(la, K, want_grad, plan, ws, st);
-      default: return launch_simt_t<double, 16>(la, K, want_grad, plan, ws, st);
+      case 64: return launch_simt_t<double, 64, TN>(la, K, want_grad, plan, ws, st);
+      case 32: return launch_simt_t<double, 32, TN>(la, K, want_grad, plan, ws, st);
+      default: return launch_simt_t<double, 16, TN>(la, K, want_grad, plan, ws, st);
     }
   }
   switch (plan.bm) {
-    case 64: return launch_simt_t<float, 64>(la, K, want_grad, plan, ws, st);
-    default: return launch_simt_t<float, 32>(la, K, want_grad, plan, ws, st);
+    case 64: return launch_simt_t<float, 64, TN>(la, K, want_grad, plan, ws, st);
+    default: return launch_simt_t<float, 32, TN>(la, K, want_grad, plan, ws, st);
   }
 }
 
-int simt_occupancy(int prec, int bm, int smem) {
-  int n = 0;
-  const void* f = nullptr;
+cudaError_t launch_simt(const LawArgs& la, int K, int prec, int want_grad, const Plan& plan, const Workspace& ws,
+                        cudaStream_t st) {
+  return plan.tn == 1 ? launch_simt_tn<1>(la, K, prec, want_grad, plan, ws, st)
+                      : launch_simt_tn<4>(la, K, prec, want_grad, plan, ws, st);
+}
+
+template <int TN>
+static const void* simt_fn(int prec, int bm) {
   if (prec == SAA_FP64)
-    f = bm == 64 ? (const void*)k_simt<double, 64> : bm == 32 ? (const void*)k_simt<double, 32>
-                                                              : (const void*)k_simt<double, 16>;
-  else
-    f = bm == 64 ? (const void*)k_simt<float, 64> : (const void*)k_simt<float, 32>;
+    return bm == 64 ? (const void*)k_simt<double, 64, TN> : bm == 32 ? (const void*)k_simt<double, 32, TN>
+                                                                      : (const void*)k_simt<double, 16, TN>;
+  return bm == 64 ? (const void*)k_simt<float, 64, TN> : (const void*)k_simt<float, 32, TN>;
+}
+
+int simt_occupancy(int prec, int bm, int tn, int smem) {
+  int n = 0;
+  const void* f = tn == 1 ? simt_fn<1>(prec, bm) : simt_fn<4>(prec, bm);
   if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kThreads, smem) != cudaSuccess || n < 1) return 1;
   return n;

@@ -5,8 +5,8 @@
 //   1. scales s_i (t law) and the tile A' = [s_i zhat_i]' into shared memory,
 //      layout [d][BMP];
 //   2. m~ partial sums per dimension into FP64 registers (macc);
-//   3. per K-chunk of 64 decisions: Q = A Y by register tiling (TM x 4 per
-//      thread), the S1/S2 column sums by a 16-lane shuffle tree into the
+//   3. per K-chunk of BN = 16 TN decisions: Q = A Y by register tiling
+//      (TM x TN per thread), the S1/S2 column sums by a 16-lane shuffle tree into the
 //      slot's FP64 partials, and for the gradient the adjoint tile A'Q
 //      accumulated (Kahan) into the slot's partial G.
 // Every partial element of a slot is owned by one thread, which writes it on
@@ -21,31 +21,34 @@ template <typename T> struct Pad;
 template <> struct Pad<float> { static constexpr int v = 4; };
 template <> struct Pad<double> { static constexpr int v = 2; };
 
-template <typename T, int BM>
+// TN decisions per thread column group: BN = 16 TN decisions per K-chunk
+// (TN = 1 for K <= 16 so that narrow decision sets waste no FMAs).
+template <typename T, int BM, int TN>
 struct SimtSmem {
+  static constexpr int BN = 16 * TN;
   static constexpr int BMP = BM + Pad<T>::v;
-  static constexpr int QP = kBN + 1;
+  static constexpr int QP = BN + 1;
   T* As;  // [d][BMP]
-  T* Ys;  // [kDK][kBN]
+  T* Ys;  // [kDK][BN]
   T* Qs;  // [BM][QP]
   T* ss;  // [BM]
   __device__ SimtSmem(unsigned char* raw, int d) {
     As = reinterpret_cast<T*>(raw);
     Ys = As + (size_t)d * BMP;
-    Qs = Ys + kDK * kBN;
+    Qs = Ys + kDK * BN;
     ss = Qs + BM * QP;
   }
 };
 
-template <typename T, int BM>
+template <typename T, int BM, int TN>
 __device__ __forceinline__ void simt_tile(const gen::Stream& st, int d, int law, int nu, uint32_t half, uint32_t i0,
-                                          int nrow, int K, const T* __restrict__ Yt, const SimtSmem<T, BM>& sm,
+                                          int nrow, int K, const T* __restrict__ Yt, const SimtSmem<T, BM, TN>& sm,
                                           double* macc, bool first, int want_grad, double* __restrict__ p_s1,
                                           double* __restrict__ p_s2, T* __restrict__ p_g, T* __restrict__ p_gc) {
   constexpr int TM = BM / 16;
-  constexpr int TN = 4;
-  constexpr int BMP = SimtSmem<T, BM>::BMP;
-  constexpr int QP = SimtSmem<T, BM>::QP;
+  constexpr int BN = SimtSmem<T, BM, TN>::BN;
+  constexpr int BMP = SimtSmem<T, BM, TN>::BMP;
+  constexpr int QP = SimtSmem<T, BM, TN>::QP;
   constexpr int PC = gen::Gen<T>::kPerCall;
   T* As = sm.As;
   T* Ys = sm.Ys;
@@ -89,7 +92,7 @@ __device__ __forceinline__ void simt_tile(const gen::Stream& st, int d, int law,
     }
   }
 
-  for (int k0 = 0; k0 < K; k0 += kBN) {
+  for (int k0 = 0; k0 < K; k0 += BN) {
     T acc[TM][TN];
 #pragma unroll
     for (int m = 0; m < TM; ++m)
@@ -98,8 +101,8 @@ __device__ __forceinline__ void simt_tile(const gen::Stream& st, int d, int law,
 
     for (int j0 = 0; j0 < d; j0 += kDK) {
       __syncthreads();
-      for (int idx = tid; idx < kDK * kBN; idx += kThreads) {
-        const int jj = idx / kBN, kk = idx % kBN;
+      for (int idx = tid; idx < kDK * BN; idx += kThreads) {
+        const int jj = idx / BN, kk = idx % BN;
         const int j = j0 + jj, k = k0 + kk;
         Ys[idx] = (j < d && k < K) ? Yt[(size_t)j * K + k] : T(0);
       }
@@ -107,7 +110,7 @@ __device__ __forceinline__ void simt_tile(const gen::Stream& st, int d, int law,
       const int jmax = min(kDK, d - j0);
       for (int jj = 0; jj < jmax; ++jj) {
         const T* arow = As + (size_t)(j0 + jj) * BMP + ty * TM;
-        const T* yrow = Ys + jj * kBN + tx * TN;
+        const T* yrow = Ys + jj * BN + tx * TN;
         T a[TM], y[TN];
 #pragma unroll
         for (int m = 0; m < TM; ++m) a[m] = arow[m];
