@@ -57,6 +57,7 @@ struct Plan {
   int prec;       // saa_prec
   int bm;         // scenarios per tile
   int tn;         // SIMT: decisions per thread column group (K-chunk = 16 tn)
+  int narrow;     // SIMT: K <= 4 kernel (dot products fused into the draw)
   int grid;       // CTAs of the main kernel
   int smem;       // dynamic shared memory of the main kernel
   int64_t tiles;  // scenario tiles
@@ -111,6 +112,8 @@ int simt_bm(int prec, int d);
 int simt_tn(int K);
 size_t simt_smem(int prec, int d, int bm, int tn);
 int simt_occupancy(int prec, int bm, int tn, int smem);
+size_t narrow_smem(int prec, int d, int bm);
+int narrow_occupancy(int prec, int bm, int smem);
 
 // Tensor-core (tcgen05, BF16 or FP16 hi/lo) value path.
 inline bool is_tc(int prec) { return prec == SAA_BF16X3 || prec == SAA_F16X3; }

@@ -56,10 +56,12 @@ saa_status make_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec p
   if (p->d > kMaxDimSimt) return fail(SAA_EUNSUPPORTED, "d exceeds saa_max_dim for this precision");
   plan->bm = simt_bm(prec, p->d);
   plan->tn = simt_tn(K);
-  plan->smem = (int)simt_smem(prec, p->d, plan->bm, plan->tn);
+  plan->narrow = (K <= 4) ? 1 : 0;
+  plan->smem = plan->narrow ? (int)narrow_smem(prec, p->d, plan->bm) : (int)simt_smem(prec, p->d, plan->bm, plan->tn);
   if (plan->smem > ctx->smem_optin) return fail(SAA_EUNSUPPORTED, "tile does not fit in shared memory");
   plan->tiles = (p->N + plan->bm - 1) / plan->bm;
-  const int occ = simt_occupancy(prec, plan->bm, plan->tn, plan->smem);
+  const int occ = plan->narrow ? narrow_occupancy(prec, plan->bm, plan->smem)
+                               : simt_occupancy(prec, plan->bm, plan->tn, plan->smem);
   const int64_t cap = (int64_t)ctx->sm_count * occ;
   plan->grid = (int)(plan->tiles < cap ? plan->tiles : cap);
   return SAA_OK;

@@ -156,6 +156,210 @@ int simt_bm(int prec, int d) {
   return d <= 512 ? 64 : 32;
 }
 
+// ------------------------------------------------------------------------
+// Narrow kernel for K <= kNarrowK decisions (Algorithm 1 evaluates K = 1):
+// each generating thread accumulates its partial dot products a_ij y_kj
+// while drawing, the G = 256 / BM threads sharing a scenario are summed in
+// shared memory, and the adjoint sum_i a_i Q_ik is kept per dimension in
+// Kahan-compensated registers for the whole CTA.  Partial slots have the
+// same layout as k_simt, so the finalize is shared.
+// ------------------------------------------------------------------------
+constexpr int kNarrowK = 4;
+
+template <typename T, int BM>
+__global__ void __launch_bounds__(kThreads, 2) k_narrow(LawArgs la, int K, int want_grad,
+                                                        const T* __restrict__ Yt, double* __restrict__ part_s1,
+                                                        double* __restrict__ part_s2, double* __restrict__ part_m,
+                                                        T* __restrict__ part_g, T* __restrict__ part_gc,
+                                                        int64_t tiles) {
+  constexpr int BMP = BM + Pad<T>::v;
+  constexpr int G = kThreads / BM;                 // threads per scenario
+  constexpr int PC = gen::Gen<T>::kPerCall;
+  constexpr int JR = kMaxDimSimt / kThreads;       // dimensions per thread (adjoint, m~)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int d = la.d;
+  T* As = reinterpret_cast<T*>(smem_raw);          // [d][BMP]
+  T* Ys = As + (size_t)d * BMP;                    // [kNarrowK][d]
+  T* qp = Ys + (size_t)kNarrowK * d;               // [G][BM][kNarrowK]
+  T* Qs = qp + (size_t)G * BM * kNarrowK;          // [BM][kNarrowK]
+  T* ss = Qs + (size_t)BM * kNarrowK;              // [BM]
+  const int tid = threadIdx.x;
+  const int i_own = tid % BM, g_own = tid / BM;
+  uint32_t epoch = la.epoch;
+  if (la.t_dev) epoch += (uint32_t)(*la.t_dev / la.M);
+  const gen::Stream st = gen::make_stream(la.seed, epoch, la.instance);
+  const uint32_t half = la.N / 2u;
+  const int nb = (d + PC - 1) / PC;
+
+  for (int idx = tid; idx < kNarrowK * d; idx += kThreads) {
+    const int k = idx / d, j = idx % d;
+    Ys[idx] = (k < K) ? Yt[(size_t)j * K + k] : T(0);
+  }
+  double macc[JR];
+  T gs[JR][kNarrowK], gc[JR][kNarrowK];
+#pragma unroll
+  for (int r = 0; r < JR; ++r) {
+    macc[r] = 0.0;
+#pragma unroll
+    for (int k = 0; k < kNarrowK; ++k) gs[r][k] = gc[r][k] = T(0);
+  }
+  double* p_s1 = part_s1 + (size_t)blockIdx.x * K;
+  double* p_s2 = part_s2 + (size_t)blockIdx.x * K;
+
+  bool first = true;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const uint32_t i0 = (uint32_t)(tile * BM);
+    const int nrow = (int)min((int64_t)BM, (int64_t)la.N - (int64_t)i0);
+    __syncthreads();
+    if (tid < BM) ss[tid] = (tid < nrow) ? gen::Gen<T>::scale(st, i0 + tid, la.law, la.nu) : T(0);
+    __syncthreads();
+    // draw the samples of scenario i_own, blocks g_own, g_own + G, ...
+    T q[kNarrowK];
+#pragma unroll
+    for (int k = 0; k < kNarrowK; ++k) q[k] = T(0);
+    const bool live = i_own < nrow;
+    const uint32_t i = i0 + (uint32_t)i_own;
+    const bool logn = gen::is_lognormal(la.law, i, half);
+    const T s = ss[i_own];
+    for (int b = g_own; b < nb; b += G) {
+      T z[PC];
+      if (live) {
+        gen::Gen<T>::block(st, (uint32_t)b, i, logn, z);
+#pragma unroll
+        for (int e = 0; e < PC; ++e) z[e] *= s;
+      } else {
+#pragma unroll
+        for (int e = 0; e < PC; ++e) z[e] = T(0);
+      }
+#pragma unroll
+      for (int e = 0; e < PC; ++e) {
+        const int j = b * PC + e;
+        if (j < d) {
+          As[(size_t)j * BMP + i_own] = z[e];
+#pragma unroll
+          for (int k = 0; k < kNarrowK; ++k) q[k] = fma(z[e], Ys[k * d + j], q[k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kNarrowK; ++k) qp[((size_t)g_own * BM + i_own) * kNarrowK + k] = q[k];
+    __syncthreads();
+    if (tid < BM * kNarrowK) {
+      const int ii = tid / kNarrowK, k = tid % kNarrowK;
+      T v = T(0);
+#pragma unroll
+      for (int g = 0; g < G; ++g) v += qp[((size_t)g * BM + ii) * kNarrowK + k];
+      Qs[ii * kNarrowK + k] = v;
+    }
+    __syncthreads();
+    if (tid < K) {
+      T s1 = T(0), s2 = T(0);
+      for (int ii = 0; ii < nrow; ++ii) {
+        const T v = Qs[ii * kNarrowK + tid];
+        s1 += v;
+        s2 = fma(v, v, s2);
+      }
+      p_s1[tid] = first ? (double)s1 : p_s1[tid] + (double)s1;
+      p_s2[tid] = first ? (double)s2 : p_s2[tid] + (double)s2;
+    }
+#pragma unroll
+    for (int r = 0; r < JR; ++r) {
+      const int j = tid + r * kThreads;
+      if (j < d) {
+        T sum = T(0);
+        T gt[kNarrowK];
+#pragma unroll
+        for (int k = 0; k < kNarrowK; ++k) gt[k] = T(0);
+        for (int ii = 0; ii < nrow; ++ii) {
+          const T a = As[(size_t)j * BMP + ii];
+          sum += a;
+          if (want_grad) {
+#pragma unroll
+            for (int k = 0; k < kNarrowK; ++k) gt[k] = fma(a, Qs[ii * kNarrowK + k], gt[k]);
+          }
+        }
+        macc[r] += (double)sum;
+        if (want_grad) {
+#pragma unroll
+          for (int k = 0; k < kNarrowK; ++k) {   // Kahan: gc carries the lost low part
+            const T y = gt[k] - gc[r][k];
+            const T t = gs[r][k] + y;
+            gc[r][k] = (t - gs[r][k]) - y;
+            gs[r][k] = t;
+          }
+        }
+      }
+    }
+    first = false;
+  }
+  if (!first) {
+#pragma unroll
+    for (int r = 0; r < JR; ++r) {
+      const int j = tid + r * kThreads;
+      if (j < d) {
+        part_m[(size_t)blockIdx.x * d + j] = macc[r];
+        if (want_grad) {
+#pragma unroll
+          for (int k = 0; k < kNarrowK; ++k)
+            if (k < K) {
+              const size_t e = ((size_t)blockIdx.x * K + k) * d + j;
+              part_g[e] = gs[r][k];
+              part_gc[e] = gc[r][k];
+            }
+        }
+      }
+    }
+  }
+}
+
+size_t narrow_smem(int prec, int d, int bm) {
+  const size_t es = (prec == SAA_FP64) ? 8 : 4;
+  const int pad = (prec == SAA_FP64) ? 2 : 4;
+  const size_t G = kThreads / bm;
+  return es * ((size_t)d * (bm + pad) + (size_t)kNarrowK * d + G * bm * kNarrowK + (size_t)bm * kNarrowK + bm);
+}
+
+template <typename T, int BM>
+static const void* narrow_fn() { return (const void*)k_narrow<T, BM>; }
+
+static const void* narrow_kernel(int prec, int bm) {
+  if (prec == SAA_FP64) return bm == 64 ? narrow_fn<double, 64>() : bm == 32 ? narrow_fn<double, 32>()
+                                                                               : narrow_fn<double, 16>();
+  return bm == 64 ? narrow_fn<float, 64>() : narrow_fn<float, 32>();
+}
+
+int narrow_occupancy(int prec, int bm, int smem) {
+  int n = 0;
+  const void* f = narrow_kernel(prec, bm);
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kThreads, smem) != cudaSuccess || n < 1) return 1;
+  return n;
+}
+
+template <typename T, int BM>
+static cudaError_t launch_narrow_t(const LawArgs& la, int K, int want_grad, const Plan& plan, const Workspace& ws,
+                                   cudaStream_t st) {
+  auto kern = k_narrow<T, BM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
+  if (e != cudaSuccess) return e;
+  kern<<<plan.grid, kThreads, plan.smem, st>>>(la, K, want_grad, (const T*)ws.Y, ws.part_s1, ws.part_s2,
+                                               ws.part_m, (T*)ws.part_g, (T*)ws.part_gc, plan.tiles);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_narrow(const LawArgs& la, int K, int prec, int want_grad, const Plan& plan,
+                                 const Workspace& ws, cudaStream_t st) {
+  if (prec == SAA_FP64) {
+    switch (plan.bm) {
+      case 64: return launch_narrow_t<double, 64>(la, K, want_grad, plan, ws, st);
+      case 32: return launch_narrow_t<double, 32>(la, K, want_grad, plan, ws, st);
+      default: return launch_narrow_t<double, 16>(la, K, want_grad, plan, ws, st);
+    }
+  }
+  return plan.bm == 64 ? launch_narrow_t<float, 64>(la, K, want_grad, plan, ws, st)
+                       : launch_narrow_t<float, 32>(la, K, want_grad, plan, ws, st);
+}
+
 int simt_tn(int K) { return K <= 16 ? 1 : 4; }
 
 size_t simt_smem(int prec, int d, int bm, int tn) {
@@ -194,6 +398,7 @@ static cudaError_t launch_simt_tn(const LawArgs& la, int K, int prec, int want_g
 
 cudaError_t launch_simt(const LawArgs& la, int K, int prec, int want_grad, const Plan& plan, const Workspace& ws,
                         cudaStream_t st) {
+  if (plan.narrow) return launch_narrow(la, K, prec, want_grad, plan, ws, st);
   return plan.tn == 1 ? launch_simt_tn<1>(la, K, prec, want_grad, plan, ws, st)
                       : launch_simt_tn<4>(la, K, prec, want_grad, plan, ws, st);
 }
