@@ -9,7 +9,7 @@ Workload (default): d = 128 assets, N = 2^20 scenarios (first half Gaussian,
 second half standardised lognormal sigma = 1), K = 256 candidate decisions
 x ~ U[0,1]^d, mu ~ U[-1,1]^d, Sigma = LL' + 0.1 I, Philox seed 0.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec P]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec P]   (P defaults to f16x3)
        python bench.py --impl reference ...   (the CPU oracle, bounded sample)
 Under torchrun each rank evaluates its own independent instance (instance id
 = rank): the work is partitioned with no data-path collective (weak scaling).
@@ -126,6 +126,52 @@ def oracle_sample(d, K, law, n_target_s=12.0, N_full=1 << 20, rank=0):
         dt = time.perf_counter() - t0
         n = n2
     return n * K / dt, dt, n, oracle.max_threads()
+
+
+# Algorithmic ALU lane-operations of the scenario generator, per normal, as
+# counted from its specification (each IEEE add/sub/mul/fma/div/sqrt, each
+# integer op, and each fused 3-input xor or 32x32->64 multiply is one
+# operation): Philox4x32-10 10, uniforms 3, log 10.5, radius 1, sin/cos 12.5,
+# products 1 -> 38 for a Gaussian normal; the standardised lognormal adds 18.
+GEN_OPS_GAUSS = 38.0
+GEN_OPS_LOGN = 18.0
+SPLIT_OPS = 4.0       # hi/lo operand split and the m~ sum (tensor paths)
+EPI_OPS_TC = 3.0      # per scenario-decision pair: D1 + D2, square, reduce
+EPI_OPS_SIMT = 2.0    # per pair: S1 and S2 updates (the contraction adds d FMAs)
+
+
+def roofline(prec, d, N, K, law, kern_s, peaks, peak_src):
+    """Roofline of the dominant (sample) kernel.  Every path here is bound by
+    ALU issue (the in-kernel generator), except FP64 which is bound by the
+    FP64 pipe; the tensor-core paths also report their tensor-pipe use."""
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    normals = float(N) * d
+    gen = GEN_OPS_GAUSS + (0.5 * GEN_OPS_LOGN if law == 3 else GEN_OPS_LOGN if law == 1 else 0.0)
+    if prec == "fp64":
+        flops = 2.0 * N * d * K
+        peak = 152 * 2 * 2 * mhz * 1e6 / 1e12
+        return {"bound": "alu", "achieved": flops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / kern_s / 1e12 / peak, "traffic": None, "kernel_ms": kern_s * 1e3,
+                "peak_source": f"derived: 152 SMs x 2 FP64 FMA/clk x 2 x {mhz} MHz (1.25 TFLOP/s class)",
+                "note": "FP64 contraction flops 2NdK; the FP64 generator work is extra"}
+    if prec in ("bf16x3", "f16x3"):
+        ops = normals * (gen + SPLIT_OPS) + float(N) * K * EPI_OPS_TC
+    else:
+        ops = normals * (gen + 1.0) + float(N) * K * (d + EPI_OPS_SIMT)
+    peak = 152 * 128 * mhz * 1e6 / 1e12
+    r = {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+         "frac": ops / kern_s / 1e12 / peak, "traffic": None, "kernel_ms": kern_s * 1e3,
+         "peak_source": f"derived: 152 SMs x 128 lanes x {mhz} MHz (lane-ops/s)",
+         "note": "algorithmic lane-operations: generator spec count per normal + contraction/epilogue per pair"}
+    if prec in ("bf16x3", "f16x3"):
+        # ncu dram__bytes_read.sum + dram__bytes_write.sum of the tensor kernel
+        # (F16, d = 128, K = 256): the per-launch operand image, independent of N
+        if prec == "f16x3" and d == 128 and K == 256:
+            r["traffic"] = 207872
+        tflops = 3 * 2.0 * N * d * K / kern_s / 1e12
+        r["tensor"] = {"achieved": tflops, "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
+                       "frac": tflops / float(peaks["bf16_tflops"]), "peak_source": f"{peak_src} bf16 dense (burst)"}
+    return r
 
 
 def run_reference(args):
@@ -264,22 +310,24 @@ def run_ours(args):
 
     peaks, peak_src = _peaks()
     kern_s = main_ms / 1e3 / max(1, main_n)
-    if prec in ("bf16x3", "f16x3"):
-        flops = 3 * 2.0 * N * d * K
-        peak = float(peaks["bf16_tflops"])
-        roof = {"bound": "tensor", "achieved": flops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": flops / kern_s / 1e12 / peak, "traffic": None,
-                "peak_source": f"{peak_src} bf16 dense (burst); f16 has the same nominal rate",
-                "note": "three tensor products (hi*hi, hi*lo, lo*hi) per scenario-decision-dimension"}
-    else:
-        lanes = 128 if prec == "fp32" else 2   # FP32 FMA lanes / FP64 FMA units per SM per clock
-        flops = 2.0 * N * d * K
-        peak = 152 * lanes * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": flops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": flops / kern_s / 1e12 / peak, "traffic": None,
-                "peak_source": f"derived: 152 SMs x {lanes} FMA/clk x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz",
-                "note": "achieved counts the contraction's 2Nd K flops only (the RNG ALU work is extra)"}
-    roof["kernel_ms"] = kern_s * 1e3
+    roof = roofline(prec, d, N, K, law, kern_s, peaks, peak_src)
+
+    # the plain FP64 GPU path on the same workload (the comparator of the metric)
+    fp64 = None
+    if prec != "fp64" and not args.no_fp64:
+        ws64 = torch.empty(saa.workspace_size(prob, K, "fp64", 0), dtype=torch.uint8, device=dev)
+        saa.saa_eval(prob, X, "fp64", ws=ws64)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            saa.saa_eval(prob, X, "fp64", ws=ws64)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1) / 3
+        v64 = N * K / (ms64 / 1e3)
+        fp64 = {"value": v64, "unit": "evals/s", "ms_per_step": ms64, "speedup": value / world / v64}
+        del ws64
 
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -293,6 +341,8 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roof,
     }
+    if fp64:
+        line["fp64_gpu_path"] = fp64
     if rank == 0:
         line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -313,9 +363,10 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default=os.environ.get("SAA_BENCH_PREC", "fp32"),
+    ap.add_argument("--prec", default=os.environ.get("SAA_BENCH_PREC", "f16x3"),
                     choices=["fp64", "fp32", "bf16x3", "f16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip timing the FP64 GPU comparator")
     ap.add_argument("--N", type=int, default=None, help="override the scenario count (profiling small cases)")
     ap.add_argument("--K", type=int, default=None, help="override the decision count (profiling small cases)")
     args = ap.parse_args()
