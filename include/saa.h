@@ -203,6 +203,14 @@ saa_status saa_generate(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64
 saa_status saa_eval_static(const saa_problem* prob, int32_t K, const double* X, saa_prec prec, double* f,
                            double* pbar, double* var, void* stream);
 
+/* Failure-path self-test: launches one warp that waits, with the same
+ * bounded mbarrier wait the tensor-core kernel uses and a budget of
+ * `budget_us` microseconds (1 .. 100000), on a barrier that nothing
+ * completes.  The wait gives up, sets the timeout bit of the context's
+ * error word and returns: the next saa_ctx_sync reports SAA_ETIMEOUT and
+ * clears it, and the context stays usable.  No fault, trap or hang. */
+saa_status saa_selftest_timeout(saa_ctx* ctx, uint32_t budget_us, void* stream);
+
 /* Kernel timing (tracing).  While enabled, every saa_eval / saa_grad call
  * records a CUDA event pair on its stream around its main sample kernel (the
  * generation + contraction + epilogue kernel) and counts the kernels it

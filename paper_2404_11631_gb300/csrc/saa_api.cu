@@ -23,6 +23,7 @@ saa_status cuda_status(cudaError_t e, const char* what) {
 }
 
 cudaError_t launch_set_i64(int64_t* p, int64_t v, cudaStream_t st);
+cudaError_t launch_selftest_timeout(uint32_t* err, uint32_t budget_us, cudaStream_t st);
 
 static saa_status fail(saa_status s, const std::string& msg) {
   set_error(msg);
@@ -225,6 +226,13 @@ saa_status saa_ctx_sync(saa_ctx* ctx, void* stream) {
     return fail(SAA_EDEVICE, "a device-side check flagged an error");
   }
   return SAA_OK;
+}
+
+saa_status saa_selftest_timeout(saa_ctx* ctx, uint32_t budget_us, void* stream) {
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  if (budget_us < 1 || budget_us > 100000) return fail(SAA_EINVAL, "budget must be in [1 us, 100 ms]");
+  DeviceGuard g(ctx->device);
+  return cuda_status(launch_selftest_timeout(ctx->err, budget_us, (cudaStream_t)stream), "self-test launch");
 }
 
 saa_status saa_ctx_set_autotune(saa_ctx* ctx, int enable) {

@@ -95,18 +95,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0u;
 }
 // Bounded wait: false if the clock budget ran out or another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
-                                          uint32_t* err) {
+__device__ __forceinline__ bool mbar_wait_budget(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
+                                                 uint32_t* err, long long budget) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > budget) {
       *abort_flag = 1u;
       atomicOr(err, kErrTimeout);
       return false;
     }
   }
   return true;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
+                                          uint32_t* err) {
+  return mbar_wait_budget(bar, parity, abort_flag, err, kWaitCycles);
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -540,7 +544,27 @@ __global__ void __launch_bounds__(64) k_tc_image(int d, int K, int Kp, int nkb, 
   }
 }
 
+// Self-test of the failure path: one warp waits, with the tensor kernel's
+// bounded wait and a short budget, on an mbarrier that nothing completes.
+// It gives up, raises the timeout bit of the error word and returns.
+__global__ void k_selftest_timeout(uint32_t* err, long long budget) {
+  __shared__ uint64_t bar;
+  __shared__ uint32_t abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  mbar_wait_budget(smem_u32(&bar), 0u, &abort_flag, err, budget);
+}
+
 }  // namespace tc
+
+cudaError_t launch_selftest_timeout(uint32_t* err, uint32_t budget_us, cudaStream_t st) {
+  tc::k_selftest_timeout<<<1, 32, 0, st>>>(err, (long long)budget_us * 2100ll);
+  return cudaGetLastError();
+}
 
 bool tc_supported(const saa_problem* p, int K, int want_grad) {
   if (want_grad) return false;

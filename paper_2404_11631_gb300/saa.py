@@ -88,6 +88,8 @@ def lib():
             L.saa_eval_batched.argtypes = [vp, C.c_int32, pp, C.POINTER(C.c_int32), vp, C.c_int, vp, vp, vp, vp, sz,
                                            vp]
             L.saa_eval_batched.restype = C.c_int
+            L.saa_selftest_timeout.argtypes = [vp, C.c_uint32, vp]
+            L.saa_selftest_timeout.restype = C.c_int
             L.saa_ctx_set_autotune.argtypes = [vp, C.c_int]
             L.saa_ctx_set_autotune.restype = C.c_int
             L.saa_max_dim.argtypes = [C.c_int]
@@ -302,6 +304,12 @@ def saa_eval_batched(problems: list, Xs: list, prec="fp32") -> dict:
     return Batch(problems, Xs, prec).run()
 
 
+def saa_selftest_timeout(budget_us: int = 1000, device: int | None = None):
+    """Runs the bounded-wait self-test (see saa.h); saa_ctx_sync then raises SAA_ETIMEOUT."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    _check(lib().saa_selftest_timeout(context(dev.index), budget_us, _stream(dev)))
+
+
 def saa_ctx_sync(device: int | None = None):
     """Waits for the current stream and raises if a device-side check fired."""
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -327,4 +335,4 @@ def max_dim(prec) -> int:
 EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_size", "saa_eval", "saa_grad",
             "saa_solve", "saa_generate", "saa_max_dim", "saa_status_string", "saa_last_error",
             "saa_profile_enable", "saa_profile_read", "saa_eval_batched", "saa_workspace_size_batched",
-            "saa_ctx_set_autotune"]
+            "saa_ctx_set_autotune", "saa_selftest_timeout"]

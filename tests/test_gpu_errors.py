@@ -50,3 +50,18 @@ def test_too_large_dimension_is_unsupported():
 def test_ctx_sync_reports_clean_state():
     from paper_2404_11631_gb300 import saa
     saa.saa_ctx_sync()
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    # a wait on an mbarrier that nothing completes gives up after ~1 ms and
+    # reports through the error word; no fault, and the context keeps working
+    from paper_2404_11631_gb300 import saa
+    saa.saa_selftest_timeout(1000)
+    with pytest.raises(saa.SAAError) as e:
+        saa.saa_ctx_sync()
+    assert e.value.status == saa.SAA_ETIMEOUT
+    saa.saa_ctx_sync()    # cleared
+    gp, _, _ = make(8, 1000)
+    out = saa.saa_eval(gp, torch.zeros(2, 8, dtype=torch.float64, device="cuda"), "f16x3")
+    saa.saa_ctx_sync()
+    assert torch.isfinite(out["f"]).all()
