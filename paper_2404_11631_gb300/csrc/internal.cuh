@@ -121,5 +121,13 @@ bool tc_supported(const saa_problem* p, int K, int want_grad);
 saa_status tc_plan(const saa_ctx* ctx, const saa_problem* p, int K, Plan* plan);
 cudaError_t launch_tc(const LawArgs& la, int K, int prec, const Plan& plan, const Workspace& ws, uint32_t* err,
                       cudaStream_t st);
+cudaError_t launch_tc_image(int d, int K, int Kp, int nkb, bool f16, const double* Y64, double* scale2,
+                            double* gaux, uint8_t* img, cudaStream_t st);
+
+// Tensor-core path with the gradient (two passes over each tile).
+bool tc_grad_supported(const saa_problem* p, int K);
+saa_status tc_grad_plan(const saa_ctx* ctx, const saa_problem* p, int K, Plan* plan);
+cudaError_t launch_tc_grad(const LawArgs& la, int K, int prec, const Plan& plan, const Workspace& ws, uint32_t* err,
+                           cudaStream_t st);
 
 }  // namespace saa

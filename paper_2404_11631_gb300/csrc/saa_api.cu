@@ -48,6 +48,11 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 saa_status make_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec prec, int want_grad, Plan* plan) {
   std::memset(plan, 0, sizeof(*plan));
   plan->prec = prec;
+  if (is_tc(prec) && want_grad) {
+    if (!tc_grad_supported(p, K))
+      return fail(SAA_EUNSUPPORTED, "tensor-core gradient path: needs d <= 1024 and K <= 64");
+    return tc_grad_plan(ctx, p, K, plan);
+  }
   if (is_tc(prec)) {
     if (!tc_supported(p, K, want_grad))
       return fail(SAA_EUNSUPPORTED, "tensor-core path: this d/K/gradient combination is not built");
@@ -141,7 +146,9 @@ static saa_status run_estimator(saa_ctx* ctx, const saa_problem* p, int K, const
   if (s != SAA_OK) return s;
   const bool prof = ctx->prof_on && !la.t_dev && ctx->prof_n < 256;
   if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], st);
-  if (is_tc(prec))
+  if (is_tc(prec) && want_grad)
+    s = cuda_status(launch_tc_grad(la, K, prec, plan, ws, ctx->err, st), "tensor-core gradient kernel launch");
+  else if (is_tc(prec))
     s = cuda_status(launch_tc(la, K, prec, plan, ws, ctx->err, st), "tensor-core kernel launch");
   else
     s = cuda_status(launch_simt(la, K, prec, want_grad, plan, ws, st), "sample kernel launch");

@@ -36,6 +36,7 @@
 
 #include "gen.cuh"
 #include "internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace saa {
 namespace tc {
@@ -52,7 +53,6 @@ constexpr int kMmaWarp = 4;         // warps 0..3 epilogue, 4 MMA, 5.. RNG
 constexpr int kRngWarps = SAA_TC_RNG_WARPS;
 constexpr int kThreadsTc = 32 * (5 + kRngWarps);
 constexpr int kRngThreads = 32 * kRngWarps;
-constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 constexpr int kMaxKp = 256;         // MMA N limit (cta_group::1, M = 128)
 constexpr int kMaxDim = 256;
 constexpr int kMaxBBytes = 128 * 1024;
@@ -68,158 +68,6 @@ struct Args {
   uint32_t* err;
 };
 
-// ---------------------------------------------------------------- PTX ----
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-// try_wait with a suspend-time hint: the waiting warp sleeps in hardware
-// (up to ~20 us) until the phase completes instead of spinning on issue slots.
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(20000u)
-      : "memory");
-  return ok != 0u;
-}
-// Bounded wait: false if the clock budget ran out or another role aborted.
-__device__ __forceinline__ bool mbar_wait_budget(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
-                                                 uint32_t* err, long long budget) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > budget) {
-      *abort_flag = 1u;
-      atomicOr(err, kErrTimeout);
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
-                                          uint32_t* err) {
-  return mbar_wait_budget(bar, parity, abort_flag, err, kWaitCycles);
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (bf16 inputs, f32 accumulate).
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-// Arrives on `bar` once every previously issued MMA of this thread is complete.
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 B apart (SBO), descriptor version 1, no base offset.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)(16u >> 4) << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
-  d |= (uint64_t)1u << 46;
-  d |= (uint64_t)2u << 61;
-  return d;
-}
-
-// Instruction descriptor, kind::f16: D f32, A and B both bf16 (fmt 1) or
-// both f16 (fmt 0), both K-major.
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool f16) {
-  return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-#define SAA_R32(r) \
-  "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), \
-      "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),   \
-      "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),  \
-      "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-#define SAA_W32(r) \
-  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), \
-      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), \
-      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]),           \
-      "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
-
-// 32 lanes x 32 consecutive 32-bit columns (lane quadrant of the warp).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : SAA_R32(r)
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
-      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
-      SAA_W32(r)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-// Byte offset of 16-byte unit u of row r in a swizzled K block.
-__device__ __forceinline__ uint32_t sw_off(int r, int u) { return (uint32_t)(r * 128 + ((u ^ (r & 7)) << 4)); }
-
-// Two floats rounded to the operand type (round to nearest even), packed.
-template <bool F16>
-__device__ __forceinline__ uint32_t pack2(float a, float b) {
-  if (F16) {
-    __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-  } else {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-  }
-}
-// The two packed values back as floats (exact).
-template <bool F16>
-__device__ __forceinline__ float2 unpack2(uint32_t w) {
-  if (F16) {
-    __half2 h = *reinterpret_cast<__half2*>(&w);
-    return __half22float2(h);
-  } else {
-    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-  }
-}
-
 // ------------------------------------------------------------- kernel ----
 constexpr int kSBufs = 4;   // t-law scale buffers (producers run at most kStages stages ahead)
 
@@ -232,13 +80,6 @@ struct Smem {
   uint32_t abort_flag;
   float s_buf[kSBufs][kM];
 };
-
-// Warp-uniform bounded wait (tcgen05.ld/st are warp-collective).
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
-                                          uint32_t* err) {
-  const bool ok = mbar_wait(bar, parity, abort_flag, err);
-  return __all_sync(0xffffffffu, ok);
-}
 
 // Layout: [A stages][B image][Smem]; the base must be 1024-byte aligned.
 size_t smem_bytes(int Kp, int nkb) {
@@ -503,12 +344,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
 // Decision operand image, one block per padded decision row n: the scale
 // e_n with max_j |y_nj| 2^-e_n in [1, 2) (e_n = 0 for a zero row; scale2[n] =
 // 4^e_n undoes it on Q^2), then y_n 2^-e_n split into hi + lo of the operand
-// type, laid out as [K block][hi, lo][Kp rows][128 B] in the 128-byte-swizzled
-// K-major order; rows n >= K and dimensions j >= d are zero.
+// type, laid out as [K block][hi, lo][Kp rows][128 B] in the
+// 128-byte-swizzled K-major order; rows n >= K and dimensions j >= d are
+// zero.  When gaux is given (gradient path) it also receives, with f_n the
+// least integer such that 2^f_n > ||y_n 2^-e_n||_2 (0 for a zero row),
+// gaux[n] = 2^(e_n + f_n) and gaux[K + n] = 2^-f_n: the adjoint's operand
+// Q 2^-f_n is bounded by |a_i| and G is recovered exactly.
 template <bool F16>
 __global__ void __launch_bounds__(64) k_tc_image(int d, int K, int Kp, int nkb, const double* __restrict__ Y64,
-                                                 double* __restrict__ scale2, uint8_t* __restrict__ img) {
-  __shared__ double wmax[2];
+                                                 double* __restrict__ scale2, double* __restrict__ gaux,
+                                                 uint8_t* __restrict__ img) {
+  __shared__ double wmax[2], wss[2];
   const int n = blockIdx.x;
   const int lane = threadIdx.x & 31;
   double m = 0.0;
@@ -521,6 +367,29 @@ __global__ void __launch_bounds__(64) k_tc_image(int d, int K, int Kp, int nkb, 
   m = fmax(wmax[0], wmax[1]);
   const int e = (m > 0.0) ? ilogb(m) : 0;
   const double inv = ldexp(1.0, -e);   // exact
+  if (gaux) {
+    double ss = 0.0;
+    if (n < K)
+      for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const double y = Y64[(size_t)n * d + j] * inv;
+        ss = fma(y, y, ss);
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) wss[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    ss = wss[0] + wss[1];
+    // ||.||_2 < 2^f  <=>  ss < 4^f
+    int f = 0;
+    if (ss > 0.0) {
+      f = ilogb(ss) / 2 + 1;
+      while (ldexp(1.0, 2 * (f - 1)) > ss) --f;
+    }
+    if (threadIdx.x == 0 && n < K) {
+      gaux[n] = ldexp(1.0, e + f);
+      gaux[K + n] = ldexp(1.0, -f);
+    }
+  }
   if (threadIdx.x == 0 && n < K) scale2[n] = ldexp(1.0, 2 * e);
   for (int unit = threadIdx.x; unit < nkb * 8; unit += blockDim.x) {
     const int kb = unit >> 3, u = unit & 7;
@@ -560,6 +429,15 @@ __global__ void k_selftest_timeout(uint32_t* err, long long budget) {
 }
 
 }  // namespace tc
+
+cudaError_t launch_tc_image(int d, int K, int Kp, int nkb, bool f16, const double* Y64, double* scale2,
+                            double* gaux, uint8_t* img, cudaStream_t st) {
+  if (f16)
+    tc::k_tc_image<true><<<Kp, 64, 0, st>>>(d, K, Kp, nkb, Y64, scale2, gaux, img);
+  else
+    tc::k_tc_image<false><<<Kp, 64, 0, st>>>(d, K, Kp, nkb, Y64, scale2, gaux, img);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_selftest_timeout(uint32_t* err, uint32_t budget_us, cudaStream_t st) {
   tc::k_selftest_timeout<<<1, 32, 0, st>>>(err, (long long)budget_us * 2100ll);
@@ -611,15 +489,13 @@ cudaError_t launch_tc(const LawArgs& la, int K, int prec, const Plan& plan, cons
   a.part_s2 = ws.part_s2;
   a.part_m = ws.part_m;
   a.err = err;
-  if (f16)
-    tc::k_tc_image<true><<<a.Kp, 64, 0, st>>>(la.d, K, a.Kp, a.nkb, ws.Y64, scale2, img);
-  else
-    tc::k_tc_image<false><<<a.Kp, 64, 0, st>>>(la.d, K, a.Kp, a.nkb, ws.Y64, scale2, img);
+  cudaError_t e = launch_tc_image(la.d, K, a.Kp, a.nkb, f16, ws.Y64, scale2, nullptr, img, st);
+  if (e != cudaSuccess) return e;
   auto kern = f16 ? (a.nkb == 1 ? tc::k_tc_value<true, 1> : a.nkb == 2 ? tc::k_tc_value<true, 2>
                                                                           : tc::k_tc_value<true, 4>)
                   : (a.nkb == 1 ? tc::k_tc_value<false, 1> : a.nkb == 2 ? tc::k_tc_value<false, 2>
                                                                            : tc::k_tc_value<false, 4>);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
   if (e != cudaSuccess) return e;
   kern<<<plan.grid, tc::kThreadsTc, plan.smem, st>>>(a);
   return cudaGetLastError();

@@ -81,4 +81,4 @@ def test_tc_unsupported_shapes_are_rejected():
         saa.saa_eval(gp, torch.zeros(2, 1024, dtype=torch.float64, device="cuda"), "f16x3")
     gp, op, inst = make(16, 1000)
     with pytest.raises(saa.SAAError):
-        saa.saa_grad(gp, torch.zeros(2, 16, dtype=torch.float64, device="cuda"), "f16x3")
+        saa.saa_eval(gp, torch.zeros(257, 16, dtype=torch.float64, device="cuda"), "f16x3")
