@@ -278,18 +278,17 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
       if (tt > 0 && !warp_wait(smem_u32(&sm->w_empty), (uint32_t)((tt - 1) & 1), abort_flag, a.err)) break;
       tc_fence_after();
 #pragma unroll 1
-      for (int g = 0; g < kGMaxKp / 32; ++g) {
-        if (32 * g >= Kp) break;
-        const uint32_t c0 = (uint32_t)(32 * g);
-        uint32_t r1[32], r2[32];
-        tmem_ld32(tq + lane_base + c0, r1);
-        tmem_ld32(td2 + lane_base + c0, r2);
+      for (int pc = 0; pc < Kp / 16; ++pc) {
+        const uint32_t c0 = (uint32_t)(16 * pc);
+        uint32_t r1[16], r2[16];
+        tmem_ld16(tq + lane_base + c0, r1);
+        tmem_ld16(td2 + lane_base + c0, r2);
         tmem_wait_ld();
-        float v[32];
+        float v[16];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < 16; ++i) {
           const float q = __uint_as_float(r1[i]) + __uint_as_float(r2[i]);
-          const int k = 32 * g + i;
+          const int k = (int)c0 + i;
           // element (k, row) of W: row k of the operand, 16-byte unit wil/8 swizzled by k
           const float wq = q * sm->wsc_f[k];   // power of two: exact
           const uint32_t hp = pack2<F16>(wq, 0.0f);
@@ -299,9 +298,9 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
           *reinterpret_cast<uint16_t*>(w_lo + off) = (uint16_t)(lp & 0xffffu);
           v[i] = q * q;
         }
-        // reduce-scatter over the warp's 32 rows: lane l ends with column c0 + l
+        // reduce-scatter over the warp's 32 rows: lanes l and l + 16 end with column c0 + (l & 15)
 #pragma unroll
-        for (int w = 16; w >= 1; w >>= 1) {
+        for (int w = 8; w >= 1; w >>= 1) {
           const bool upper = (lane & w) != 0;
 #pragma unroll
           for (int i = 0; i < w; ++i) {
@@ -310,9 +309,11 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
           }
         }
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
+        // lane l keeps column 32 g + l of s2acc[g]
 #pragma unroll
         for (int h = 0; h < kGMaxKp / 32; ++h)
-          if (h == g) s2acc[h] += (double)v[0];
+          if (h == (pc >> 1) && (lane >> 4) == (pc & 1)) s2acc[h] += (double)v[0];
       }
       fence_proxy_async();   // W: generic-proxy stores -> the MMA's async-proxy reads
       tc_fence_before();
@@ -352,21 +353,24 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
                   a.part_gc[e0 + (size_t)i * d] = 0.0f;
                 }
             } else {
-              float ps[16], pc[16];
 #pragma unroll
-              for (int i = 0; i < 16; ++i)
-                if (i < kn) {
-                  ps[i] = a.part_g[e0 + (size_t)i * d];
-                  pc[i] = a.part_gc[e0 + (size_t)i * d];
-                }
+              for (int hb = 0; hb < 16; hb += 8) {   // two halves: 16 loads in flight, fewer live registers
+                float ps[8], pc[8];
 #pragma unroll
-              for (int i = 0; i < 16; ++i)
-                if (i < kn) {
-                  const float y = gv[i] - pc[i];
-                  const float t = ps[i] + y;
-                  a.part_gc[e0 + (size_t)i * d] = (t - ps[i]) - y;
-                  a.part_g[e0 + (size_t)i * d] = t;
-                }
+                for (int i = 0; i < 8; ++i)
+                  if (hb + i < kn) {
+                    ps[i] = a.part_g[e0 + (size_t)(hb + i) * d];
+                    pc[i] = a.part_gc[e0 + (size_t)(hb + i) * d];
+                  }
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                  if (hb + i < kn) {
+                    const float y = gv[hb + i] - pc[i];
+                    const float t = ps[i] + y;
+                    a.part_gc[e0 + (size_t)(hb + i) * d] = (t - ps[i]) - y;
+                    a.part_g[e0 + (size_t)(hb + i) * d] = t;
+                  }
+              }
             }
           }
         }
@@ -386,10 +390,12 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
     const bool tlaw = la.law == SAA_LAW_STUDENT_T;
     // forward stage: 16-byte unit cu (8 dimensions) of rows rt/8 and rt/8 + 64
     const int cu = rt & 7;
-    // adjoint stage: dimensions 4 b4 .. 4 b4 + 3 of the block, scenarios 8 g8 .. 8 g8 + 7
+    // adjoint stage: dimensions 4 b4 .. 4 b4 + 3 of the block, scenarios 8 g8 .. 8 g8 + 7,
+    // written one scenario pair (4 bytes) at a time; the pair order is staggered by
+    // lane group so that each store instruction covers all 32 banks once
     const int b4 = rt >> 4, g8 = rt & 15;
     const int asb = g8 >> 3, au = g8 & 7;
-    const int hfirst = lane >> 4;   // which 4-scenario half goes first (spreads shared-memory banks)
+    const int pfirst = lane >> 3;
     int st = 0;
     uint32_t ph = 0;
     uint32_t bissued = 0, bpar = 0;   // copy issuer: stages with copies, parity of the next copy per stage
@@ -422,7 +428,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
           bpar ^= 1u << st;
         }
         const int j0 = kb * kGKB + cu * 8;
-#pragma unroll 2
+#pragma unroll 1
         for (int r = rt >> 3; r < kGM; r += kGRngThreads / 8) {
           float v[8];
 #pragma unroll
@@ -461,37 +467,37 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         const int mb = pt - a.nkb;
         const int jb = mb * kGMB + 4 * b4;   // first of this thread's 4 dimensions
         float msum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 1
+        for (int p = 0; p < 4; ++p) {
+          const int pq = (p + pfirst) & 3;   // scenarios 8 g8 + 2 pq, + 1
+          const int r0 = 8 * g8 + 2 * pq;
+          float z0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, z1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          if (jb < d) {
+            if (r0 < nrow) {
+              const uint32_t i = i0 + (uint32_t)r0;
+              gen::Gen<float>::block(gs, (uint32_t)(jb >> 2), i, gen::is_lognormal(la.law, i, half), z0);
+              const float s0 = tlaw ? sm->s_buf[sb4][r0] : 1.0f;
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const int h2 = hh ^ hfirst;
-          float v[4][4];   // [dimension][scenario]
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int r = 8 * g8 + 4 * h2 + q;
-            float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            if (r < nrow && jb < d) {
-              const uint32_t i = i0 + (uint32_t)r;
-              gen::Gen<float>::block(gs, (uint32_t)(jb >> 2), i, gen::is_lognormal(la.law, i, half), z);
-              const float s = tlaw ? sm->s_buf[sb4][r] : 1.0f;
-#pragma unroll
-              for (int e = 0; e < 4; ++e) z[e] = (jb + e < d) ? z[e] * s : 0.0f;
+              for (int e = 0; e < 4; ++e) z0[e] = (jb + e < d) ? z0[e] * s0 : 0.0f;
             }
+            if (r0 + 1 < nrow) {
+              const uint32_t i = i0 + (uint32_t)r0 + 1u;
+              gen::Gen<float>::block(gs, (uint32_t)(jb >> 2), i, gen::is_lognormal(la.law, i, half), z1);
+              const float s1 = tlaw ? sm->s_buf[sb4][r0 + 1] : 1.0f;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              v[e][q] = z[e];
-              msum[e] += z[e];
+              for (int e = 0; e < 4; ++e) z1[e] = (jb + e < d) ? z1[e] * s1 : 0.0f;
             }
           }
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
+            msum[e] += z0[e] + z1[e];
             const int jr = 4 * b4 + e;   // row of the stage
-            const uint32_t h01 = pack2<F16>(v[e][0], v[e][1]), h23 = pack2<F16>(v[e][2], v[e][3]);
-            const float2 f01 = unpack2<F16>(h01), f23 = unpack2<F16>(h23);
-            const uint32_t l01 = pack2<F16>(v[e][0] - f01.x, v[e][1] - f01.y);
-            const uint32_t l23 = pack2<F16>(v[e][2] - f23.x, v[e][3] - f23.y);
-            const uint32_t off = (uint32_t)(jr * 128 + ((au ^ (jr & 7)) << 4) + h2 * 8);
-            *reinterpret_cast<uint2*>(stage + (asb * 2 + 0) * kGSubBytes + off) = make_uint2(h01, h23);
-            *reinterpret_cast<uint2*>(stage + (asb * 2 + 1) * kGSubBytes + off) = make_uint2(l01, l23);
+            const uint32_t h = pack2<F16>(z0[e], z1[e]);
+            const float2 f = unpack2<F16>(h);
+            const uint32_t l = pack2<F16>(z0[e] - f.x, z1[e] - f.y);
+            const uint32_t off = (uint32_t)(jr * 128 + ((au ^ (jr & 7)) << 4) + pq * 4);
+            *reinterpret_cast<uint32_t*>(stage + (asb * 2 + 0) * kGSubBytes + off) = h;
+            *reinterpret_cast<uint32_t*>(stage + (asb * 2 + 1) * kGSubBytes + off) = l;
           }
         }
         // m~: fold the 16 lanes that share these dimensions; lane g8 == 0 owns
