@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
       if (tlaw && !warp_wait(s_bar, (uint32_t)((tt >> 2) & 1), abort_flag, a.err)) break;
       uint8_t* stage = As + st * kStageBytes;
       const int j0 = kb * kKB + cu * 8;   // first dimension of this unit
-#pragma unroll 2
+#pragma unroll 1
       for (int r = rt >> 3; r < kM; r += kRngThreads / 8) {
         float v[8];
 #pragma unroll
