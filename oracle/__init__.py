@@ -17,6 +17,8 @@ Functions and the passages they follow:
 * :func:`saa` / :func:`saa_explicit` -- Eq. 4 with Eq. 5 and its gradient in w.
 * :func:`fw` / :func:`fw_step` -- Algorithm 1.
 * :func:`rse` -- the relative squared error of Table 2's notes.
+* :func:`cholesky` -- the lower Cholesky factor C of Sigma used by the
+  normal law of Sec. 3.1 (R = mu + C z).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force and independent library routines; the
@@ -102,6 +104,8 @@ def lib():
             L.oracle_fw_step.restype = C.c_int
             L.oracle_fw.argtypes = [pp, C.c_int, dp, C.c_int, C.c_int, C.c_int64, dp, dp, dp, dp]
             L.oracle_fw.restype = C.c_int
+            L.oracle_cholesky.argtypes = [C.c_int, dp, dp]
+            L.oracle_cholesky.restype = C.c_int
             L.oracle_rse.argtypes = [C.c_double, C.c_double]
             L.oracle_rse.restype = C.c_double
             L.oracle_max_threads.restype = C.c_int
@@ -264,3 +268,13 @@ def fw(prob, prec, w0, T, M, t0=0, want_w_trace=False):
 def rse(y_t, y_star):
     """Relative squared error in percent (Table 2 notes)."""
     return float(lib().oracle_rse(float(y_t), float(y_star)))
+
+
+def cholesky(S):
+    """Lower Cholesky factor of the symmetric positive definite S (lower
+    triangle read); raises ValueError when a pivot is not positive."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    d = S.shape[0]
+    out = np.empty_like(S)
+    _check(lib().oracle_cholesky(d, _p(S), _p(out)), "cholesky")
+    return out

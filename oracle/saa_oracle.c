@@ -21,6 +21,8 @@
  *   4. Frank-Wolfe, Algorithm 1 (resample every M iterations, LMO over
  *      W = {w >= 0, 1'w <= 1}, step 2/(kM+m+2)).
  *   5. The relative squared error of Table 2's notes.
+ *   6. The lower Cholesky factor C of Sigma (C C' = Sigma), which turns the
+ *      covariance of Sec. 3.1's normal law into the sample map R = mu + C z.
  *
  * Floating-point discipline: compiled with -ffp-contract=off; every fused
  * multiply-add in the generator is an explicit fmaf()/fma() call, so each
@@ -894,6 +896,33 @@ int oracle_fw(const oracle_problem* p, int prec, const double* w0, int T, int M,
 /* ------------------------------------------------------------------------- */
 /* 5. RSE (Table 2 notes): ((y_t - y*) / y_t)^2 * 100 %                      */
 /* ------------------------------------------------------------------------- */
+/* ---------------------------------------------------------------------- */
+/* 6. Cholesky factor: the textbook row-by-row (Cholesky-Banachiewicz)    */
+/*    recurrence, C_jj = sqrt(S_jj - sum_{l<j} C_jl^2) and, for i > j,    */
+/*    C_ij = (S_ij - sum_{l<j} C_il C_jl) / C_jj, each sum in index order.  */
+/*    S is row-major [d][d]; only its lower triangle is read.  C is       */
+/*    row-major lower-triangular with zeros above the diagonal.  Returns  */
+/*    OR_EINVAL when a pivot is not positive (S not positive definite).   */
+/* ---------------------------------------------------------------------- */
+int oracle_cholesky(int d, const double* S, double* C)
+{
+    if (d < 1 || !S || !C) return OR_EINVAL;
+    memset(C, 0, sizeof(double) * (size_t)d * (size_t)d);
+    for (int i = 0; i < d; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double acc = S[(size_t)i * d + j];
+            for (int l = 0; l < j; ++l) acc -= C[(size_t)i * d + l] * C[(size_t)j * d + l];
+            if (i == j) {
+                if (!(acc > 0.0)) return OR_EINVAL;
+                C[(size_t)i * d + i] = sqrt(acc);
+            } else {
+                C[(size_t)i * d + j] = acc / C[(size_t)j * d + j];
+            }
+        }
+    }
+    return OR_OK;
+}
+
 double oracle_rse(double y_t, double y_star)
 {
     double r = (y_t - y_star) / y_t;
