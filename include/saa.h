@@ -96,7 +96,9 @@ typedef struct {
     uint32_t epoch;     /* resample index (counter word 2) */
     const double* mu;   /* device [d]: mean of R */
     const double* chol; /* device [d*d] row-major lower-triangular C, C C' = Sigma;
-                           entries above the diagonal are ignored */
+                           entries above the diagonal are ignored.  A diagonal
+                           entry that is not positive and finite is flagged on
+                           the device (SAA_EDEVICE at the next saa_ctx_sync) */
 } saa_problem;
 
 /* Context: device properties, tuned launch shapes, a device error word and
@@ -180,6 +182,21 @@ saa_status saa_ctx_set_autotune(saa_ctx* ctx, int enable);
  *            chain over l = 0..j of C_jl zhat_il (C, mu rounded first). */
 saa_status saa_generate(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, saa_prec prec, void* z_out,
                         void* s_out, void* xi_out, void* stream);
+
+/* Lower Cholesky factor C of Sigma (C C' = Sigma), the map from standard
+ * normals to the samples of the normal law of Sec. 3.1 (R = mu + C z): the
+ * `chol` input of saa_problem.  FP64, blocked right-looking factorization
+ * with a fixed summation order (deterministic), on `stream`.
+ *   d       1 <= d <= 46340
+ *   Sigma   device [d*d] row-major symmetric positive definite; only the
+ *           lower triangle (j <= i) is read
+ *   chol    device [d*d] row-major: receives C, zeros above the diagonal.
+ *           May equal Sigma (in place); must not partially overlap it.
+ * Returns SAA_EINVAL for bad arguments, SAA_ECUDA on a launch failure.  A
+ * pivot that is not positive (Sigma not positive definite, NaN) is found on
+ * the device: the next saa_ctx_sync reports SAA_EDEVICE and `chol` is
+ * undefined. */
+saa_status saa_cholesky(saa_ctx* ctx, int32_t d, const double* Sigma, double* chol, void* stream);
 
 /* saa_eval without a context or a workspace: for callers that cannot
  * allocate device memory (a CUDA host callback or stream capture, where

@@ -96,7 +96,7 @@ size_t carve(const saa_problem* p, int K, const Plan& plan, int want_grad, void*
 
 // Launchers (host, one per translation unit).
 cudaError_t launch_prologue(const saa_problem* p, int K, const double* X, int prec, const Workspace& ws,
-                            cudaStream_t st);
+                            uint32_t* err, cudaStream_t st);
 cudaError_t launch_simt(const LawArgs& la, int K, int prec, int want_grad, const Plan& plan, const Workspace& ws,
                         cudaStream_t st);
 cudaError_t launch_finalize(const saa_problem* p, int K, int prec, int want_grad, const Plan& plan,

@@ -109,7 +109,7 @@ extern "C" saa_status saa_eval_static(const saa_problem* prob, int32_t K, const 
   la.t_dev = nullptr;
   la.M = 1;
   cudaStream_t st = (cudaStream_t)stream;
-  s = cuda_status(launch_prologue(prob, K, X, prec, ws, st), "saa_eval_static: prologue launch");
+  s = cuda_status(launch_prologue(prob, K, X, prec, ws, nullptr, st), "saa_eval_static: prologue launch");
   if (s != SAA_OK) return s;
   s = cuda_status(launch_simt(la, K, prec, 0, plan, ws, st), "saa_eval_static: sample kernel launch");
   if (s != SAA_OK) return s;

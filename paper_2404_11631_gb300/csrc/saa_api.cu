@@ -142,7 +142,7 @@ static LawArgs law_args(const saa_problem* p) {
 static saa_status run_estimator(saa_ctx* ctx, const saa_problem* p, int K, const double* X, saa_prec prec,
                                 int want_grad, const Plan& plan, const Workspace& ws, const LawArgs& la, double* f,
                                 double* pbar, double* var, double* grad, cudaStream_t st) {
-  saa_status s = cuda_status(launch_prologue(p, K, X, prec, ws, st), "prologue launch");
+  saa_status s = cuda_status(launch_prologue(p, K, X, prec, ws, ctx->err, st), "prologue launch");
   if (s != SAA_OK) return s;
   const bool prof = ctx->prof_on && !la.t_dev && ctx->prof_n < 256;
   if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], st);

@@ -34,7 +34,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_prologue(int d, int K, const double* __restrict__ X,
                                                   const double* __restrict__ mu, const double* __restrict__ C,
                                                   T* __restrict__ Yt, double* __restrict__ Y64,
-                                                  double* __restrict__ c) {
+                                                  double* __restrict__ c, uint32_t* __restrict__ err) {
   extern __shared__ double wsm[];            // [kPrepK][d] decisions
   __shared__ double red[8][kPrepK][32];
   const int k0 = blockIdx.x * kPrepK;
@@ -71,6 +71,11 @@ __global__ void __launch_bounds__(256) k_prologue(int d, int K, const double* __
       if (Yt) Yt[(size_t)jo * K + k] = (T)y;
     }
   }
+  // C must have a positive, finite diagonal (the factor of a positive definite Sigma)
+  if (err && blockIdx.x == 0 && warp == 0 && j < d) {
+    const double cjj = C[(size_t)j * d + j];
+    if (!(cjj > 0.0) || !isfinite(cjj)) atomicOr(err, kErrInput);
+  }
   if (blockIdx.y == 0 && warp < kPrepK && k0 + warp < K) {
     double sdot = 0.0;
     for (int l = lane; l < d; l += 32) sdot = fma(mu[l], wsm[warp * d + l], sdot);
@@ -81,7 +86,7 @@ __global__ void __launch_bounds__(256) k_prologue(int d, int K, const double* __
 }
 
 cudaError_t launch_prologue(const saa_problem* p, int K, const double* X, int prec, const Workspace& ws,
-                            cudaStream_t st) {
+                            uint32_t* err, cudaStream_t st) {
   const dim3 grid((K + kPrepK - 1) / kPrepK, (p->d + 31) / 32);
   const size_t smem = sizeof(double) * kPrepK * p->d;
   if (smem > 48 * 1024) {
@@ -91,10 +96,10 @@ cudaError_t launch_prologue(const saa_problem* p, int K, const double* X, int pr
     if (e != cudaSuccess) return e;
   }
   if (prec == SAA_FP64)
-    k_prologue<double><<<grid, 256, smem, st>>>(p->d, K, X, p->mu, p->chol, (double*)ws.Y, ws.Y64, ws.c);
+    k_prologue<double><<<grid, 256, smem, st>>>(p->d, K, X, p->mu, p->chol, (double*)ws.Y, ws.Y64, ws.c, err);
   else
     k_prologue<float><<<grid, 256, smem, st>>>(p->d, K, X, p->mu, p->chol, is_tc(prec) ? nullptr : (float*)ws.Y,
-                                               ws.Y64, ws.c);
+                                               ws.Y64, ws.c, err);
   return cudaGetLastError();
 }
 

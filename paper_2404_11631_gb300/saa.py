@@ -88,6 +88,8 @@ def lib():
             L.saa_eval_batched.argtypes = [vp, C.c_int32, pp, C.POINTER(C.c_int32), vp, C.c_int, vp, vp, vp, vp, sz,
                                            vp]
             L.saa_eval_batched.restype = C.c_int
+            L.saa_cholesky.argtypes = [vp, C.c_int32, vp, vp, vp]
+            L.saa_cholesky.restype = C.c_int
             L.saa_selftest_timeout.argtypes = [vp, C.c_uint32, vp]
             L.saa_selftest_timeout.restype = C.c_int
             L.saa_ctx_set_autotune.argtypes = [vp, C.c_int]
@@ -266,6 +268,22 @@ def saa_generate(prob: Problem, i0: int, n: int, prec="fp32", want_xi: bool = Fa
     return out
 
 
+def saa_cholesky(sigma: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Lower Cholesky factor C of Sigma (C C' = Sigma) on the device, the
+    ``chol`` of :class:`Problem`; ``out`` may be ``sigma`` itself (in place)."""
+    if not (sigma.is_cuda and sigma.dtype == torch.float64 and sigma.is_contiguous() and sigma.dim() == 2
+            and sigma.shape[0] == sigma.shape[1]):
+        raise ValueError("sigma must be a contiguous square float64 CUDA tensor")
+    d = int(sigma.shape[0])
+    if out is None:
+        out = torch.empty_like(sigma)
+    elif not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.shape == sigma.shape):
+        raise ValueError("out must be a contiguous float64 CUDA tensor shaped like sigma")
+    dev = sigma.device
+    _check(lib().saa_cholesky(context(dev.index), d, _ptr(sigma), _ptr(out), _stream(dev)))
+    return out
+
+
 class Batch:
     """Host-side marshalling of a ragged batch for saa_eval_batched (reusable
     across calls: the descriptor arrays are built once)."""
@@ -335,4 +353,4 @@ def max_dim(prec) -> int:
 EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_size", "saa_eval", "saa_grad",
             "saa_solve", "saa_generate", "saa_max_dim", "saa_status_string", "saa_last_error",
             "saa_profile_enable", "saa_profile_read", "saa_eval_batched", "saa_workspace_size_batched",
-            "saa_ctx_set_autotune", "saa_selftest_timeout"]
+            "saa_ctx_set_autotune", "saa_selftest_timeout", "saa_cholesky"]
