@@ -3,7 +3,9 @@
 One step = one saa_eval of the mean-variance SAA estimate (Eq. 4, Sec. 3.1 of
 arXiv 2404.11631) over the whole workload: prologue (y_k = C'w_k), in-kernel
 Philox scenario generation, the scenario x decision contraction, the fused
-S1/S2 epilogue, the FP64 cross-block reduction and the finalize.
+S1/S2 epilogue, the FP64 cross-block reduction and the finalize.  The line
+also carries "eval_grad": saa_grad (value and gradient in w) on d = 1024,
+N = 2^20 Gaussian scenarios, K = 64, timed the same way.
 
 Workload (default): d = 128 assets, N = 2^20 scenarios (first half Gaussian,
 second half standardised lognormal sigma = 1), K = 256 candidate decisions
@@ -167,11 +169,71 @@ def roofline(prec, d, N, K, law, kern_s, peaks, peak_src):
         # ncu dram__bytes_read.sum + dram__bytes_write.sum of the tensor kernel
         # (F16, d = 128, K = 256): the per-launch operand image, independent of N
         if prec == "f16x3" and d == 128 and K == 256:
-            r["traffic"] = 207872
+            r["traffic"] = 188672
         tflops = 3 * 2.0 * N * d * K / kern_s / 1e12
         r["tensor"] = {"achieved": tflops, "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
                        "frac": tflops / float(peaks["bf16_tflops"]), "peak_source": f"{peak_src} bf16 dense (burst)"}
     return r
+
+
+GRAD_WORKLOAD = dict(name="grad_d1024_N1M_K64_gauss", d=1024, N=1 << 20, K=64, law=0)
+EPI_OPS_TC_GRAD = 8.0   # per pair: chunk fold, D1 + D2, square + reduce, W hi/lo split
+
+
+def grad_roofline(prec, d, N, K, law, kern_s, peaks):
+    """ALU roofline of the value-and-gradient kernel.  Algorithmic work draws
+    each normal once; the tensor-core kernel draws it twice (forward and
+    adjoint passes), so its fraction is at most about one half."""
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    gen = GEN_OPS_GAUSS + (0.5 * GEN_OPS_LOGN if law == 3 else GEN_OPS_LOGN if law == 1 else 0.0)
+    if prec in ("bf16x3", "f16x3"):
+        ops = float(N) * d * (gen + SPLIT_OPS) + float(N) * K * EPI_OPS_TC_GRAD
+    else:
+        ops = float(N) * d * (gen + 1.0) + float(N) * K * (2 * d + EPI_OPS_SIMT)
+    peak = 152 * 128 * mhz * 1e6 / 1e12
+    # ncu DRAM bytes of the F16 kernel at d = 1024, K = 64, N = 2^17 (the
+    # per-tile flush of the gradient partials), scaled by N: it grows with
+    # the number of tiles per CTA
+    traffic = 456862208.0 * N / (1 << 17) if (prec == "f16x3" and d == 1024 and K == 64) else None
+    return {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": ops / kern_s / 1e12 / peak, "traffic": traffic, "kernel_ms": kern_s * 1e3,
+            "note": "algorithmic lane-operations, one draw per normal"}
+
+
+def run_grad(args, dev, world, rank, flush, stream):
+    """Value and gradient (saa_grad) on the adjoint workload: d = 1024,
+    N = 2^20 Gaussian scenarios, K = 64 decisions; L2 flushed between steps."""
+    import torch
+    from paper_2404_11631_gb300 import inputs, saa
+    d, N, K, law = GRAD_WORKLOAD["d"], GRAD_WORKLOAD["N"], GRAD_WORKLOAD["K"], GRAD_WORKLOAD["law"]
+    prec = args.prec
+    inst = inputs.instance(d, 0)
+    prob = saa.Problem(mu=torch.tensor(inst.mu, device=dev), chol=torch.tensor(inst.chol, device=dev), N=N,
+                       law=law, seed=0, instance=rank)
+    X = torch.tensor(inputs.decisions(K, d, 0), device=dev)
+    ws = torch.empty(saa.workspace_size(prob, K, prec, 1), dtype=torch.uint8, device=dev)
+    steps = max(3, min(args.steps, 20))
+    for _ in range(3):
+        saa.saa_grad(prob, X, prec, ws=ws)
+    torch.cuda.synchronize(dev)
+    saa.saa_profile_enable(True, dev.index)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        saa.saa_grad(prob, X, prec, ws=ws)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    main_ms, main_n, launched = saa.saa_profile_read(dev.index)
+    saa.saa_profile_enable(False, dev.index)
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    peaks, _ = _peaks()
+    kern_s = main_ms / 1e3 / max(1, main_n)
+    return {"metric": "scenario-decision evals/s with gradient", "value": world * N * K * steps / total_s,
+            "unit": "evals/s", "ms_per_step": 1e3 * total_s / steps, "steps": steps,
+            "config": {"workload": GRAD_WORKLOAD["name"], "d": d, "N": N, "K": K, "law": "Gaussian",
+                       "prec": prec, "l2": "flushed between timed steps"},
+            "gpu_launches": int(launched), "roofline": grad_roofline(prec, d, N, K, law, kern_s, peaks)}
 
 
 def run_reference(args):
@@ -343,6 +405,8 @@ def run_ours(args):
     }
     if fp64:
         line["fp64_gpu_path"] = fp64
+    if not args.no_grad:
+        line["eval_grad"] = run_grad(args, dev, world, rank, flush, stream)
     if rank == 0:
         line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -367,6 +431,8 @@ def main():
                     choices=["fp64", "fp32", "bf16x3", "f16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the FP64 GPU comparator")
+    ap.add_argument("--no-grad", action="store_true", help="skip the value-and-gradient workload")
+    ap.add_argument("--grad-N", type=int, default=None, help="override the gradient workload's scenario count")
     ap.add_argument("--N", type=int, default=None, help="override the scenario count (profiling small cases)")
     ap.add_argument("--K", type=int, default=None, help="override the decision count (profiling small cases)")
     args = ap.parse_args()
@@ -378,6 +444,9 @@ def main():
     if args.K:
         WORKLOAD["K"] = args.K
         WORKLOAD["name"] += f"_K{args.K}"
+    if args.grad_N:
+        GRAD_WORKLOAD["N"] = args.grad_N
+        GRAD_WORKLOAD["name"] += f"_N{args.grad_N}"
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

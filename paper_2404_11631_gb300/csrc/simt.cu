@@ -507,24 +507,59 @@ __global__ void k_value_out(int K, double N, double lambda, const double* __rest
   if (var) var[k] = V;
 }
 
-// u_k = lambda 2/(N-1) (G_k - S1_k m) - m, with G_k the CTA-ordered sum of
-// the Kahan-carried partials.
+// u_k = lambda 2/(N-1) (G_k - S1_k m) - m.  G_kj is the sum of the CTAs'
+// Kahan-carried partials (value part_g, compensation part_gc): one block per
+// (32 dimensions, decision k), warp w sums CTAs w, w + 8, ... and the eight
+// warp sums are merged in warp order, so the result is deterministic.  FP32
+// partials are summed as float-float pairs (branch-free TwoSum, the running
+// error and the Kahan compensations in a second float): about 2^-48 relative,
+// without the narrow FP64 pipe.  FP64 partials use Neumaier's sum.
 template <typename T>
-__global__ void k_grad_u(int grid, int K, int d, double N, double lambda, const T* __restrict__ part_g,
-                         const T* __restrict__ part_gc, const double* __restrict__ s1, const double* __restrict__ mt,
-                         double* __restrict__ u) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_grad_u(int grid, int K, int d, double N, double lambda,
+                                                const T* __restrict__ part_g, const T* __restrict__ part_gc,
+                                                const double* __restrict__ s1, const double* __restrict__ mt,
+                                                double* __restrict__ u) {
+  __shared__ double sh_s[8][32], sh_c[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
   const int k = blockIdx.y;
-  if (j >= d) return;
   double s = 0.0, c = 0.0;
-  for (int g = 0; g < grid; ++g) {
-    const size_t e = ((size_t)g * K + k) * d + j;
-    neumaier(s, c, (double)part_g[e]);
-    neumaier(s, c, -(double)part_gc[e]);
+  if (j < d) {
+    if constexpr (sizeof(T) == 4) {
+      float S = 0.0f, E = 0.0f;
+#pragma unroll 4
+      for (int g = warp; g < grid; g += 8) {
+        const size_t e = ((size_t)g * K + k) * d + j;
+        const float x = (float)part_g[e], xc = (float)part_gc[e];
+        const float t = __fadd_rn(S, x);
+        const float bb = __fsub_rn(t, S);
+        const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(t, bb)), __fsub_rn(x, bb));
+        S = t;
+        E = __fadd_rn(E, __fsub_rn(err, xc));
+      }
+      s = (double)S;
+      c = (double)E;
+    } else {
+      for (int g = warp; g < grid; g += 8) {
+        const size_t e = ((size_t)g * K + k) * d + j;
+        neumaier(s, c, (double)part_g[e]);
+        neumaier(s, c, -(double)part_gc[e]);
+      }
+    }
   }
-  const double G = s + c;
-  const double mj = mt[j] / N;
-  u[(size_t)k * d + j] = lambda * (2.0 / (N - 1.0)) * (G - s1[k] * mj) - mj;
+  sh_s[warp][lane] = s;
+  sh_c[warp][lane] = c;
+  __syncthreads();
+  if (warp == 0 && j < d) {
+    double S = 0.0, C = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      neumaier(S, C, sh_s[w][lane]);
+      neumaier(S, C, sh_c[w][lane]);
+    }
+    const double G = S + C;
+    const double mj = mt[j] / N;
+    u[(size_t)k * d + j] = lambda * (2.0 / (N - 1.0)) * (G - s1[k] * mj) - mj;
+  }
 }
 
 // grad_kj = sum_{l <= j} C_jl u_kl - mu_j: one warp per (k, j).
@@ -559,7 +594,7 @@ cudaError_t launch_finalize(const saa_problem* p, int K, int prec, int want_grad
   else if (f || pbar || var)
     k_value_out<<<(K + 255) / 256, 256, 0, st>>>(K, N, p->lambda, ws.c, ws.tot_s1, ws.tot_s2, f, pbar, var);
   if (want_grad && grad) {
-    dim3 gu((d + 255) / 256, K);
+    dim3 gu((d + 31) / 32, K);
     if (prec == SAA_FP64)
       k_grad_u<double><<<gu, 256, 0, st>>>(plan.grid, K, d, N, p->lambda, (const double*)ws.part_g,
                                            (const double*)ws.part_gc, ws.tot_s1, ws.tot_m, ws.grad_tmp);
