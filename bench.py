@@ -130,11 +130,18 @@ def oracle_sample(d, K, law, n_target_s=12.0, N_full=1 << 20, rank=0):
     return n * K / dt, dt, n, oracle.max_threads()
 
 
-# Algorithmic ALU lane-operations of the scenario generator, per normal, as
-# counted from its specification (each IEEE add/sub/mul/fma/div/sqrt, each
-# integer op, and each fused 3-input xor or 32x32->64 multiply is one
-# operation): Philox4x32-10 10, uniforms 3, log 10.5, radius 1, sin/cos 12.5,
-# products 1 -> 38 for a Gaussian normal; the standardised lognormal adds 18.
+# Per-normal work of the scenario generator (the roofline's per-unit figure):
+# thread-instructions per normal of the generator-only kernel
+# (saa_generate_moments, FP32 mode, d = 128), counted by ncu
+# (smsp__thread_inst_executed.sum / normals): 57.15 for a Gaussian normal and
+# 72.65 for a standardised lognormal one.  That kernel adds one add and one
+# fma per normal to the draw.
+GEN_INST_GAUSS = 57.15
+GEN_INST_LOGN = 72.65 - 57.15
+# The stricter count from the generator's specification, each IEEE
+# add/sub/mul/fma/div/sqrt, integer op, fused 3-input xor or 32x32->64
+# multiply being one operation: Philox4x32-10 10, uniforms 3, log 10.5,
+# radius 1, sin/cos 12.5, products 1 -> 38 per Gaussian normal, +18 lognormal.
 GEN_OPS_GAUSS = 38.0
 GEN_OPS_LOGN = 18.0
 SPLIT_OPS = 4.0       # hi/lo operand split and the m~ sum (tensor paths)
@@ -142,13 +149,21 @@ EPI_OPS_TC = 3.0      # per scenario-decision pair: D1 + D2, square, reduce
 EPI_OPS_SIMT = 2.0    # per pair: S1 and S2 updates (the contraction adds d FMAs)
 
 
+def _gen_per_normal(law, measured=True):
+    g, l = (GEN_INST_GAUSS, GEN_INST_LOGN) if measured else (GEN_OPS_GAUSS, GEN_OPS_LOGN)
+    return g + (0.5 * l if law == 3 else l if law == 1 else 0.0)
+
+
 def roofline(prec, d, N, K, law, kern_s, peaks, peak_src):
     """Roofline of the dominant (sample) kernel.  Every path here is bound by
     ALU issue (the in-kernel generator), except FP64 which is bound by the
-    FP64 pipe; the tensor-core paths also report their tensor-pipe use."""
+    FP64 pipe; the tensor-core paths also report their tensor-pipe use.
+    Per-normal work: the generator-only kernel's measured instruction count
+    (frac); the specification count is reported beside it (frac_spec_count)."""
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     normals = float(N) * d
-    gen = GEN_OPS_GAUSS + (0.5 * GEN_OPS_LOGN if law == 3 else GEN_OPS_LOGN if law == 1 else 0.0)
+    gen = _gen_per_normal(law)
+    gen_spec = _gen_per_normal(law, measured=False)
     if prec == "fp64":
         flops = 2.0 * N * d * K
         peak = 152 * 2 * 2 * mhz * 1e6 / 1e12
@@ -156,15 +171,18 @@ def roofline(prec, d, N, K, law, kern_s, peaks, peak_src):
                 "frac": flops / kern_s / 1e12 / peak, "traffic": None, "kernel_ms": kern_s * 1e3,
                 "peak_source": f"derived: 152 SMs x 2 FP64 FMA/clk x 2 x {mhz} MHz (1.25 TFLOP/s class)",
                 "note": "FP64 contraction flops 2NdK; the FP64 generator work is extra"}
-    if prec in ("bf16x3", "f16x3"):
-        ops = normals * (gen + SPLIT_OPS) + float(N) * K * EPI_OPS_TC
-    else:
-        ops = normals * (gen + 1.0) + float(N) * K * (d + EPI_OPS_SIMT)
+    def count(g):
+        if prec in ("bf16x3", "f16x3"):
+            return normals * (g + SPLIT_OPS) + float(N) * K * EPI_OPS_TC
+        return normals * (g + 1.0) + float(N) * K * (d + EPI_OPS_SIMT)
+    ops, ops_spec = count(gen), count(gen_spec)
     peak = 152 * 128 * mhz * 1e6 / 1e12
     r = {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
          "frac": ops / kern_s / 1e12 / peak, "traffic": None, "kernel_ms": kern_s * 1e3,
+         "frac_spec_count": ops_spec / kern_s / 1e12 / peak,
          "peak_source": f"derived: 152 SMs x 128 lanes x {mhz} MHz (lane-ops/s)",
-         "note": "algorithmic lane-operations: generator spec count per normal + contraction/epilogue per pair"}
+         "note": "lane-operations: generator-only kernel's instructions per normal (ncu) + split per normal "
+                 "+ contraction/epilogue per pair"}
     if prec in ("bf16x3", "f16x3"):
         # ncu dram__bytes_read.sum + dram__bytes_write.sum of the tensor kernel
         # (F16, d = 128, K = 256): the per-launch operand image, independent of N
@@ -185,11 +203,12 @@ def grad_roofline(prec, d, N, K, law, kern_s, peaks):
     each normal once; the tensor-core kernel draws it twice (forward and
     adjoint passes), so its fraction is at most about one half."""
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    gen = GEN_OPS_GAUSS + (0.5 * GEN_OPS_LOGN if law == 3 else GEN_OPS_LOGN if law == 1 else 0.0)
-    if prec in ("bf16x3", "f16x3"):
-        ops = float(N) * d * (gen + SPLIT_OPS) + float(N) * K * EPI_OPS_TC_GRAD
-    else:
-        ops = float(N) * d * (gen + 1.0) + float(N) * K * (2 * d + EPI_OPS_SIMT)
+
+    def count(g):
+        if prec in ("bf16x3", "f16x3"):
+            return float(N) * d * (g + SPLIT_OPS) + float(N) * K * EPI_OPS_TC_GRAD
+        return float(N) * d * (g + 1.0) + float(N) * K * (2 * d + EPI_OPS_SIMT)
+    ops, ops_spec = count(_gen_per_normal(law)), count(_gen_per_normal(law, measured=False))
     peak = 152 * 128 * mhz * 1e6 / 1e12
     # ncu DRAM bytes of the F16 kernel at d = 1024, K = 64, N = 2^17 (the
     # per-tile flush of the gradient partials), scaled by N: it grows with
@@ -197,7 +216,8 @@ def grad_roofline(prec, d, N, K, law, kern_s, peaks):
     traffic = 456862208.0 * N / (1 << 17) if (prec == "f16x3" and d == 1024 and K == 64) else None
     return {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
             "frac": ops / kern_s / 1e12 / peak, "traffic": traffic, "kernel_ms": kern_s * 1e3,
-            "note": "algorithmic lane-operations, one draw per normal"}
+            "frac_spec_count": ops_spec / kern_s / 1e12 / peak,
+            "note": "lane-operations, one draw per normal (the kernel draws twice)"}
 
 
 def run_grad(args, dev, world, rank, flush, stream):
@@ -234,6 +254,37 @@ def run_grad(args, dev, world, rank, flush, stream):
             "config": {"workload": GRAD_WORKLOAD["name"], "d": d, "N": N, "K": K, "law": "Gaussian",
                        "prec": prec, "l2": "flushed between timed steps"},
             "gpu_launches": int(launched), "roofline": grad_roofline(prec, d, N, K, law, kern_s, peaks)}
+
+
+def run_gen(args):
+    """The bare generator (saa_generate_moments, FP32 mode) on the value
+    workload's d and N, per law: normals/s.  This is the generator-only
+    kernel whose ncu instruction count per normal is the roofline's
+    per-unit figure."""
+    import torch
+    from paper_2404_11631_gb300 import inputs, saa
+    dev = torch.device("cuda", 0)
+    d, N = WORKLOAD["d"], WORKLOAD["N"]
+    inst = inputs.instance(d, 0)
+    out = {"metric": "generator normals/s", "unit": "normals/s", "config": {"d": d, "N": N, "prec": "fp32"}}
+    for name, law in (("gauss", 0), ("lognormal", 1)):
+        prob = saa.Problem(mu=torch.tensor(inst.mu, device=dev), chol=torch.tensor(inst.chol, device=dev), N=N,
+                           law=law, seed=0)
+        buf = saa.saa_generate_moments(prob, 0, N, "fp32")
+        for _ in range(2):
+            saa.saa_generate_moments(prob, 0, N, "fp32", out=buf)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = max(3, min(args.steps, 20))
+        e0.record()
+        for _ in range(steps):
+            saa.saa_generate_moments(prob, 0, N, "fp32", out=buf)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"value": N * d / (ms / 1e3), "ms_per_call": ms}
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -433,6 +484,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the FP64 GPU comparator")
     ap.add_argument("--no-grad", action="store_true", help="skip the value-and-gradient workload")
     ap.add_argument("--grad-N", type=int, default=None, help="override the gradient workload's scenario count")
+    ap.add_argument("--gen-only", action="store_true", help="time the bare generator (per-normal figure)")
     ap.add_argument("--N", type=int, default=None, help="override the scenario count (profiling small cases)")
     ap.add_argument("--K", type=int, default=None, help="override the decision count (profiling small cases)")
     args = ap.parse_args()
@@ -449,6 +501,8 @@ def main():
         GRAD_WORKLOAD["name"] += f"_N{args.grad_N}"
     if args.impl == "reference":
         return run_reference(args)
+    if args.gen_only:
+        return run_gen(args)
     return run_ours(args)
 
 

@@ -183,6 +183,26 @@ saa_status saa_ctx_set_autotune(saa_ctx* ctx, int enable);
 saa_status saa_generate(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, saa_prec prec, void* z_out,
                         void* s_out, void* xi_out, void* stream);
 
+/* Moments of the generator: per-dimension sums of the innovations zhat_ij
+ * (after the law transform, before the t law's scale s_i) and of their
+ * squares over scenarios i0 .. i0+n-1 of resample index prob->epoch, drawn
+ * by the estimator kernels' own in-kernel generator (the samples of
+ * Sec. 3.1).  The standardised laws give mean 0 and variance 1 per
+ * coordinate, so this checks the law on the device at any scale; it is also
+ * the generator-only kernel that the roofline's per-normal figure is
+ * measured on.
+ *   prec     SAA_FP32 or SAA_FP64 (which generator mode draws)
+ *   sum      device [d] FP64: sum_i zhat_ij
+ *   sumsq    device [d] FP64 or NULL: sum_i zhat_ij^2
+ *   ws       device scratch of saa_generate_moments_workspace_size() bytes,
+ *            8-byte aligned
+ * 1 <= d <= 2048, 1 <= n, i0 + n <= N.  Deterministic for a given device.
+ * The workspace-size query returns 0 for invalid arguments. */
+size_t saa_generate_moments_workspace_size(const saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n,
+                                           saa_prec prec);
+saa_status saa_generate_moments(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, saa_prec prec,
+                                double* sum, double* sumsq, void* ws, size_t ws_bytes, void* stream);
+
 /* Lower Cholesky factor C of Sigma (C C' = Sigma), the map from standard
  * normals to the samples of the normal law of Sec. 3.1 (R = mu + C z): the
  * `chol` input of saa_problem.  FP64, blocked right-looking factorization

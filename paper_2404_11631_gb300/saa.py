@@ -88,6 +88,10 @@ def lib():
             L.saa_eval_batched.argtypes = [vp, C.c_int32, pp, C.POINTER(C.c_int32), vp, C.c_int, vp, vp, vp, vp, sz,
                                            vp]
             L.saa_eval_batched.restype = C.c_int
+            L.saa_generate_moments_workspace_size.argtypes = [vp, pp, C.c_int64, C.c_int64, C.c_int]
+            L.saa_generate_moments_workspace_size.restype = sz
+            L.saa_generate_moments.argtypes = [vp, pp, C.c_int64, C.c_int64, C.c_int, vp, vp, vp, sz, vp]
+            L.saa_generate_moments.restype = C.c_int
             L.saa_cholesky.argtypes = [vp, C.c_int32, vp, vp, vp]
             L.saa_cholesky.restype = C.c_int
             L.saa_selftest_timeout.argtypes = [vp, C.c_uint32, vp]
@@ -268,6 +272,28 @@ def saa_generate(prob: Problem, i0: int, n: int, prec="fp32", want_xi: bool = Fa
     return out
 
 
+def saa_generate_moments(prob: Problem, i0: int, n: int, prec="fp32", out: dict | None = None) -> dict:
+    """Per-dimension sums of the innovations and of their squares over
+    scenarios i0 .. i0+n-1: {'sum': [d], 'sumsq': [d]} float64 tensors.
+    ``out`` (a previous result, with its 'ws') is reused instead of
+    allocating."""
+    dev = prob.device
+    cp = prob.c_struct()
+    ctx = context(dev.index)
+    need = lib().saa_generate_moments_workspace_size(ctx, C.byref(cp), i0, n, _prec(prec))
+    if need == 0:
+        raise SAAError(SAA_EINVAL, lib().saa_last_error().decode())
+    if out is not None and out["ws"].numel() >= need and out["sum"].numel() == prob.d:
+        ws, s1, s2 = out["ws"], out["sum"], out["sumsq"]
+    else:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        s1 = torch.empty(prob.d, dtype=torch.float64, device=dev)
+        s2 = torch.empty(prob.d, dtype=torch.float64, device=dev)
+    _check(lib().saa_generate_moments(ctx, C.byref(cp), i0, n, _prec(prec), _ptr(s1), _ptr(s2), _ptr(ws),
+                                      ws.numel(), _stream(dev)))
+    return {"sum": s1, "sumsq": s2, "ws": ws}
+
+
 def saa_cholesky(sigma: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
     """Lower Cholesky factor C of Sigma (C C' = Sigma) on the device, the
     ``chol`` of :class:`Problem`; ``out`` may be ``sigma`` itself (in place)."""
@@ -353,4 +379,5 @@ def max_dim(prec) -> int:
 EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_size", "saa_eval", "saa_grad",
             "saa_solve", "saa_generate", "saa_max_dim", "saa_status_string", "saa_last_error",
             "saa_profile_enable", "saa_profile_read", "saa_eval_batched", "saa_workspace_size_batched",
-            "saa_ctx_set_autotune", "saa_selftest_timeout", "saa_cholesky"]
+            "saa_ctx_set_autotune", "saa_selftest_timeout", "saa_cholesky", "saa_generate_moments",
+            "saa_generate_moments_workspace_size"]
