@@ -5,7 +5,9 @@ arXiv 2404.11631) over the whole workload: prologue (y_k = C'w_k), in-kernel
 Philox scenario generation, the scenario x decision contraction, the fused
 S1/S2 epilogue, the FP64 cross-block reduction and the finalize.  The line
 also carries "eval_grad": saa_grad (value and gradient in w) on d = 1024,
-N = 2^20 Gaussian scenarios, K = 64, timed the same way.
+N = 2^20 Gaussian scenarios, K = 64, timed the same way, and "fw":
+Algorithm 1 (saa_solve) for 200 iterations on d = 1024, N = 2^22 Student-t
+scenarios regenerated every iteration.
 
 Workload (default): d = 128 assets, N = 2^20 scenarios (first half Gaussian,
 second half standardised lognormal sigma = 1), K = 256 candidate decisions
@@ -256,6 +258,41 @@ def run_grad(args, dev, world, rank, flush, stream):
             "gpu_launches": int(launched), "roofline": grad_roofline(prec, d, N, K, law, kern_s, peaks)}
 
 
+FW_WORKLOAD = dict(name="fw_d1024_N4M_t4_T200", d=1024, N=1 << 22, law=2, nu=4, T=200, M=1)
+
+
+def run_fw(args, dev, world, rank):
+    """Algorithm 1 (saa_solve): d = 1024, N = 2^22 Student-t (nu = 4)
+    scenarios regenerated in-kernel every iteration (M = 1), T = 200
+    iterations from w0 = (0.5/d) 1, each iteration one replay of a captured
+    CUDA graph.  Reported per iteration."""
+    import torch
+    from paper_2404_11631_gb300 import inputs, saa
+    d, N, T = FW_WORKLOAD["d"], FW_WORKLOAD["N"], FW_WORKLOAD["T"]
+    prec = "fp32"
+    inst = inputs.instance(d, 0)
+    prob = saa.Problem(mu=torch.tensor(inst.mu, device=dev), chol=torch.tensor(inst.chol, device=dev), N=N,
+                       law=FW_WORKLOAD["law"], nu=FW_WORKLOAD["nu"], seed=0, instance=rank)
+    w0 = torch.tensor(inputs.fw_start(d), device=dev)
+    ws = torch.empty(saa.workspace_size(prob, 1, prec, 2), dtype=torch.uint8, device=dev)
+    saa.saa_solve(prob, w0, T=2, M=FW_WORKLOAD["M"], prec=prec, ws=ws)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = saa.saa_solve(prob, w0, T=T, M=FW_WORKLOAD["M"], prec=prec, ws=ws)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    saa.saa_ctx_sync(dev.index)
+    ms = e0.elapsed_time(e1) / T
+    gap = out["gap_trace"].cpu().numpy()
+    f = out["f_trace"].cpu().numpy()
+    return {"metric": "Frank-Wolfe iterations/s (Algorithm 1)", "value": world * 1e3 / ms, "unit": "iterations/s",
+            "ms_per_iteration": ms, "normals_per_s": N * d / (ms / 1e3), "iterations": T,
+            "config": {"workload": FW_WORKLOAD["name"], "d": d, "N": N, "law": "Student-t nu=4", "M": 1,
+                       "prec": prec, "graph": "one captured iteration replayed T times"},
+            "f_first_last": [float(f[0]), float(f[-1])], "gap_last": float(gap[-1])}
+
+
 def run_gen(args):
     """The bare generator (saa_generate_moments, FP32 mode) on the value
     workload's d and N, per law: normals/s.  This is the generator-only
@@ -458,6 +495,8 @@ def run_ours(args):
         line["fp64_gpu_path"] = fp64
     if not args.no_grad:
         line["eval_grad"] = run_grad(args, dev, world, rank, flush, stream)
+    if not args.no_fw:
+        line["fw"] = run_fw(args, dev, world, rank)
     if rank == 0:
         line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -485,6 +524,10 @@ def main():
     ap.add_argument("--no-grad", action="store_true", help="skip the value-and-gradient workload")
     ap.add_argument("--grad-N", type=int, default=None, help="override the gradient workload's scenario count")
     ap.add_argument("--gen-only", action="store_true", help="time the bare generator (per-normal figure)")
+    ap.add_argument("--no-fw", action="store_true", help="skip the Algorithm 1 (Frank-Wolfe) workload")
+    ap.add_argument("--fw-only", action="store_true", help="run only the Algorithm 1 workload")
+    ap.add_argument("--fw-N", type=int, default=None, help="override the Algorithm 1 scenario count")
+    ap.add_argument("--fw-T", type=int, default=None, help="override the Algorithm 1 iteration count")
     ap.add_argument("--N", type=int, default=None, help="override the scenario count (profiling small cases)")
     ap.add_argument("--K", type=int, default=None, help="override the decision count (profiling small cases)")
     args = ap.parse_args()
@@ -501,8 +544,18 @@ def main():
         GRAD_WORKLOAD["name"] += f"_N{args.grad_N}"
     if args.impl == "reference":
         return run_reference(args)
+    if args.fw_N:
+        FW_WORKLOAD["N"] = args.fw_N
+        FW_WORKLOAD["name"] += f"_N{args.fw_N}"
+    if args.fw_T:
+        FW_WORKLOAD["T"] = args.fw_T
+        FW_WORKLOAD["name"] += f"_T{args.fw_T}"
     if args.gen_only:
         return run_gen(args)
+    if args.fw_only:
+        import torch
+        print(json.dumps(run_fw(args, torch.device("cuda", 0), 1, 0)), flush=True)
+        return 0
     return run_ours(args)
 
 

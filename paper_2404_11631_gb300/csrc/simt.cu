@@ -164,23 +164,30 @@ int simt_bm(int prec, int d) {
 // ------------------------------------------------------------------------
 // Narrow kernel for K <= kNarrowK decisions (Algorithm 1 evaluates K = 1):
 // each generating thread accumulates its partial dot products a_ij y_kj
-// while drawing, the G = 256 / BM threads sharing a scenario are summed in
+// while drawing, the G = NT / BM threads sharing a scenario are summed in
 // shared memory, and the adjoint sum_i a_i Q_ik is kept per dimension in
 // Kahan-compensated registers for the whole CTA.  Partial slots have the
-// same layout as k_simt, so the finalize is shared.
+// same layout as k_simt, so the finalize is shared.  At large d the tile of
+// samples fills shared memory, so one CTA runs per SM; it then uses NT =
+// 1024 threads (SAA_NARROW_WIDE_THREADS) instead of 256 to keep the SM's
+// warp slots busy.
 // ------------------------------------------------------------------------
 constexpr int kNarrowK = 4;
+#ifndef SAA_NARROW_WIDE_THREADS
+#define SAA_NARROW_WIDE_THREADS 1024
+#endif
+constexpr int kNarrowWide = SAA_NARROW_WIDE_THREADS;
 
-template <typename T, int BM>
-__global__ void __launch_bounds__(kThreads, 2) k_narrow(LawArgs la, int K, int want_grad,
+template <typename T, int BM, int NT>
+__global__ void __launch_bounds__(NT, NT == kThreads ? 2 : 1) k_narrow(LawArgs la, int K, int want_grad,
                                                         const T* __restrict__ Yt, double* __restrict__ part_s1,
                                                         double* __restrict__ part_s2, double* __restrict__ part_m,
                                                         T* __restrict__ part_g, T* __restrict__ part_gc,
                                                         int64_t tiles) {
   constexpr int BMP = BM + Pad<T>::v;
-  constexpr int G = kThreads / BM;                 // threads per scenario
+  constexpr int G = NT / BM;                       // threads per scenario
   constexpr int PC = gen::Gen<T>::kPerCall;
-  constexpr int JR = kMaxDimSimt / kThreads;       // dimensions per thread (adjoint, m~)
+  constexpr int JR = kMaxDimSimt / NT;             // dimensions per thread (adjoint, m~)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int d = la.d;
   T* As = reinterpret_cast<T*>(smem_raw);          // [d][BMP]
@@ -196,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_narrow(LawArgs la, int K, int w
   const uint32_t half = la.N / 2u;
   const int nb = (d + PC - 1) / PC;
 
-  for (int idx = tid; idx < kNarrowK * d; idx += kThreads) {
+  for (int idx = tid; idx < kNarrowK * d; idx += NT) {
     const int k = idx / d, j = idx % d;
     Ys[idx] = (k < K) ? Yt[(size_t)j * K + k] : T(0);
   }
@@ -269,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_narrow(LawArgs la, int K, int w
     }
 #pragma unroll
     for (int r = 0; r < JR; ++r) {
-      const int j = tid + r * kThreads;
+      const int j = tid + r * NT;
       if (j < d) {
         T sum = T(0);
         T gt[kNarrowK];
@@ -300,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_narrow(LawArgs la, int K, int w
   if (!first) {
 #pragma unroll
     for (int r = 0; r < JR; ++r) {
-      const int j = tid + r * kThreads;
+      const int j = tid + r * NT;
       if (j < d) {
         part_m[(size_t)blockIdx.x * d + j] = macc[r];
         if (want_grad) {
@@ -317,38 +324,43 @@ __global__ void __launch_bounds__(kThreads, 2) k_narrow(LawArgs la, int K, int w
   }
 }
 
+// Threads per CTA of the narrow kernel: the wide form for the FP32 tile of
+// 32 scenarios (d > 512), where the tile's shared memory allows one CTA per SM.
+int narrow_threads(int prec, int bm) { return (prec != SAA_FP64 && bm == 32) ? kNarrowWide : kThreads; }
+
 size_t narrow_smem(int prec, int d, int bm) {
   const size_t es = (prec == SAA_FP64) ? 8 : 4;
   const int pad = (prec == SAA_FP64) ? 2 : 4;
-  const size_t G = kThreads / bm;
+  const size_t G = (size_t)narrow_threads(prec, bm) / bm;
   return es * ((size_t)d * (bm + pad) + (size_t)kNarrowK * d + G * bm * kNarrowK + (size_t)bm * kNarrowK + bm);
 }
 
-template <typename T, int BM>
-static const void* narrow_fn() { return (const void*)k_narrow<T, BM>; }
+template <typename T, int BM, int NT>
+static const void* narrow_fn() { return (const void*)k_narrow<T, BM, NT>; }
 
 static const void* narrow_kernel(int prec, int bm) {
-  if (prec == SAA_FP64) return bm == 64 ? narrow_fn<double, 64>() : bm == 32 ? narrow_fn<double, 32>()
-                                                                               : narrow_fn<double, 16>();
-  return bm == 64 ? narrow_fn<float, 64>() : narrow_fn<float, 32>();
+  if (prec == SAA_FP64) return bm == 64 ? narrow_fn<double, 64, kThreads>()
+                             : bm == 32 ? narrow_fn<double, 32, kThreads>() : narrow_fn<double, 16, kThreads>();
+  return bm == 64 ? narrow_fn<float, 64, kThreads>() : narrow_fn<float, 32, kNarrowWide>();
 }
 
 int narrow_occupancy(int prec, int bm, int smem) {
   int n = 0;
   const void* f = narrow_kernel(prec, bm);
   if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kThreads, smem) != cudaSuccess || n < 1) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, narrow_threads(prec, bm), smem) != cudaSuccess || n < 1)
+    return 1;
   return n;
 }
 
-template <typename T, int BM>
+template <typename T, int BM, int NT>
 static cudaError_t launch_narrow_t(const LawArgs& la, int K, int want_grad, const Plan& plan, const Workspace& ws,
                                    cudaStream_t st) {
-  auto kern = k_narrow<T, BM>;
+  auto kern = k_narrow<T, BM, NT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
   if (e != cudaSuccess) return e;
-  kern<<<plan.grid, kThreads, plan.smem, st>>>(la, K, want_grad, (const T*)ws.Y, ws.part_s1, ws.part_s2,
-                                               ws.part_m, (T*)ws.part_g, (T*)ws.part_gc, plan.tiles);
+  kern<<<plan.grid, NT, plan.smem, st>>>(la, K, want_grad, (const T*)ws.Y, ws.part_s1, ws.part_s2, ws.part_m,
+                                         (T*)ws.part_g, (T*)ws.part_gc, plan.tiles);
   return cudaGetLastError();
 }
 
@@ -356,13 +368,13 @@ static cudaError_t launch_narrow(const LawArgs& la, int K, int prec, int want_gr
                                  const Workspace& ws, cudaStream_t st) {
   if (prec == SAA_FP64) {
     switch (plan.bm) {
-      case 64: return launch_narrow_t<double, 64>(la, K, want_grad, plan, ws, st);
-      case 32: return launch_narrow_t<double, 32>(la, K, want_grad, plan, ws, st);
-      default: return launch_narrow_t<double, 16>(la, K, want_grad, plan, ws, st);
+      case 64: return launch_narrow_t<double, 64, kThreads>(la, K, want_grad, plan, ws, st);
+      case 32: return launch_narrow_t<double, 32, kThreads>(la, K, want_grad, plan, ws, st);
+      default: return launch_narrow_t<double, 16, kThreads>(la, K, want_grad, plan, ws, st);
     }
   }
-  return plan.bm == 64 ? launch_narrow_t<float, 64>(la, K, want_grad, plan, ws, st)
-                       : launch_narrow_t<float, 32>(la, K, want_grad, plan, ws, st);
+  return plan.bm == 64 ? launch_narrow_t<float, 64, kThreads>(la, K, want_grad, plan, ws, st)
+                       : launch_narrow_t<float, 32, kNarrowWide>(la, K, want_grad, plan, ws, st);
 }
 
 int simt_tn(int K) { return K <= 16 ? 1 : 4; }
