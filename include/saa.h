@@ -172,6 +172,31 @@ saa_status saa_eval_batched(saa_ctx* ctx, int32_t B, const saa_problem* probs, c
                             double* const* var, void* ws, size_t ws_bytes, void* stream);
 saa_status saa_ctx_set_autotune(saa_ctx* ctx, int enable);
 
+/* A ragged batch planned once and replayed as a CUDA graph.  Same problems,
+ * decisions and value outputs as saa_eval_batched; with `grad` non-NULL
+ * (host [B] array of device [K_b*d_b] outputs) it also writes each problem's
+ * gradient of Eq. 4 in w, as saa_grad does.  SAA_FP32 or SAA_FP64.
+ *   saa_batch_workspace_size  bytes of `ws` (0 for invalid arguments)
+ *   saa_batch_create  validates, picks the tile shape (the context's
+ *       autotuner, on the first batch of this shape), uploads the
+ *       descriptor tables into `ws`, waits for `stream`, and captures the
+ *       launch sequence (prologue, persistent main kernel, finalize, and the
+ *       gradient kernels) into a CUDA graph.  X, outputs and ws are bound
+ *       by address: later launches read the current contents of X, mu and
+ *       chol and overwrite the outputs.  ws must outlive the batch.
+ *   saa_batch_launch  replays the graph on `stream` (asynchronous).
+ *   saa_batch_destroy  waits for the device and frees the graph.
+ * Per-problem limits as saa_eval_batched.  Results are deterministic. */
+typedef struct saa_batch saa_batch;
+size_t saa_batch_workspace_size(const saa_ctx* ctx, int32_t B, const saa_problem* probs, const int32_t* K,
+                                saa_prec prec, int want_grad);
+saa_status saa_batch_create(saa_ctx* ctx, int32_t B, const saa_problem* probs, const int32_t* K,
+                            const double* const* X, saa_prec prec, double* const* f, double* const* pbar,
+                            double* const* var, double* const* grad, void* ws, size_t ws_bytes, void* stream,
+                            saa_batch** out);
+saa_status saa_batch_launch(saa_batch* batch, void* stream);
+void saa_batch_destroy(saa_batch* batch);
+
 /* The scenario generator on its own (debugging, streamed mode, parity):
  * scenarios i0 .. i0+n-1 of resample index prob->epoch.
  *   prec     SAA_FP64 (double outputs) or SAA_FP32 (float outputs)

@@ -10,11 +10,18 @@
 // A batched prologue computes every y_k = C_b'w_k; a finalize block per
 // problem merges that problem's item partials in item order.  The tile work
 // itself is the CUDA-core tile of the single-problem kernel (simt_tile).
+// With gradients, every item also keeps Kahan-carried partials of
+// G_k = sum_i a_i Q_ik, and two more kernels form u_k and grad_k = C u_k - mu.
+//
+// saa_batch_create plans a batch once (tile shape by the autotuner, the
+// descriptor tables uploaded) and captures its launch sequence in a CUDA
+// graph; saa_batch_launch replays that graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -41,6 +48,10 @@ struct BInst {
   int64_t part_off;  // double offset of this problem's item partials
   int item0, nitems;
   int pblock0, pad2;  // first prologue block
+  double* grad;       // [K][d] output, or NULL (gradient batches)
+  int64_t gpart_off;  // element offset of the item gradient partials: [nitems][2][K][d]
+  int64_t u_off;      // double offset of u ([K][d])
+  int ublock0, oblock0;  // first block of the u and C u kernels
 };
 
 struct BItem {
@@ -121,6 +132,7 @@ template <typename T, int BM, int TN>
 __global__ void __launch_bounds__(kThreads, 2) k_batched_main(const BInst* __restrict__ insts,
                                                               const BItem* __restrict__ items, int nitems,
                                                               const T* __restrict__ Yf, double* __restrict__ parts,
+                                                              T* __restrict__ gparts, int want_grad,
                                                               uint32_t* __restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
@@ -139,12 +151,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched_main(const BInst* __res
 #pragma unroll
     for (int r = 0; r < kMaxDimSimt / kThreads; ++r) macc[r] = 0.0;
     double* slot = parts + in.part_off + (size_t)item.slot * (2 * K + d);
+    T* gslot = want_grad ? gparts + in.gpart_off + (size_t)item.slot * 2 * K * d : nullptr;
     const T* Yt = Yf + in.y_off;
     bool first = true;
     for (uint32_t off = 0; off < item.n; off += BM) {
       const int nrow = (int)min((uint32_t)BM, item.n - off);
-      simt_tile<T, BM, TN>(st, d, in.law, in.nu, in.N / 2u, item.i0 + off, nrow, K, Yt, sm, macc, first, 0, slot,
-                       slot + K, nullptr, nullptr);
+      simt_tile<T, BM, TN>(st, d, in.law, in.nu, in.N / 2u, item.i0 + off, nrow, K, Yt, sm, macc, first, want_grad,
+                           slot, slot + K, gslot, want_grad ? gslot + (size_t)K * d : nullptr);
       first = false;
     }
 #pragma unroll
@@ -190,10 +203,103 @@ __global__ void k_batched_finalize(const BInst* __restrict__ insts, const double
   }
 }
 
+// ------------------------------------------------------------- gradient ---
+__device__ __forceinline__ int find_block(const BInst* insts, int B, int blk, bool outer) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((outer ? insts[mid].oblock0 : insts[mid].ublock0) <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// u_kj = lambda 2/(N-1) (G_kj - S1_k m_j) - m_j for 32 dimensions of one
+// decision of one problem: warp w sums items w, w + 8, ... of G (float-float
+// pairs for FP32 partials, Neumaier for FP64), merged in warp order; S1_k
+// and m_j are summed over items in item order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_batched_grad_u(const BInst* __restrict__ insts, int B,
+                                                        const double* __restrict__ parts,
+                                                        const T* __restrict__ gparts, double* __restrict__ ubuf) {
+  __shared__ double sh_s[8][32], sh_c[8][32];
+  const int b = find_block(insts, B, blockIdx.x, false);
+  const BInst in = insts[b];
+  const int d = in.d, K = in.K;
+  const int nj = (d + 31) / 32;
+  const int local = blockIdx.x - in.ublock0;
+  const int k = local / nj, jc = (local % nj) * 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = jc + lane;
+  const size_t kd = (size_t)K * d;
+  const T* gp = gparts + in.gpart_off;
+  double s = 0.0, c = 0.0;
+  if (j < d) {
+    if constexpr (sizeof(T) == 4) {
+      float S = 0.0f, E = 0.0f;
+      for (int t = warp; t < in.nitems; t += 8) {
+        const size_t e = (size_t)t * 2 * kd + (size_t)k * d + j;
+        const float x = (float)gp[e], xc = (float)gp[e + kd];
+        const float tt = __fadd_rn(S, x);
+        const float bb = __fsub_rn(tt, S);
+        const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(tt, bb)), __fsub_rn(x, bb));
+        S = tt;
+        E = __fadd_rn(E, __fsub_rn(err, xc));
+      }
+      s = (double)S;
+      c = (double)E;
+    } else {
+      for (int t = warp; t < in.nitems; t += 8) {
+        const size_t e = (size_t)t * 2 * kd + (size_t)k * d + j;
+        nsum_add(s, c, (double)gp[e]);
+        nsum_add(s, c, -(double)gp[e + kd]);
+      }
+    }
+  }
+  sh_s[warp][lane] = s;
+  sh_c[warp][lane] = c;
+  __syncthreads();
+  if (warp == 0 && j < d) {
+    double G = 0.0, Gc = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      nsum_add(G, Gc, sh_s[w][lane]);
+      nsum_add(G, Gc, sh_c[w][lane]);
+    }
+    const int stride = 2 * K + d;
+    const double* p = parts + in.part_off;
+    double s1 = 0.0, c1 = 0.0, m = 0.0, cm = 0.0;
+    for (int t = 0; t < in.nitems; ++t) {
+      nsum_add(s1, c1, p[(size_t)t * stride + k]);
+      nsum_add(m, cm, p[(size_t)t * stride + 2 * K + j]);
+    }
+    const double N = (double)in.N;
+    const double mj = (m + cm) / N;
+    ubuf[in.u_off + (size_t)k * d + j] = in.lambda * (2.0 / (N - 1.0)) * ((G + Gc) - (s1 + c1) * mj) - mj;
+  }
+}
+
+// grad_kj = sum_{l <= j} C_jl u_kl - mu_j: one warp per (k, j) of one problem.
+__global__ void __launch_bounds__(256) k_batched_grad_out(const BInst* __restrict__ insts, int B,
+                                                          const double* __restrict__ ubuf) {
+  const int b = find_block(insts, B, blockIdx.x, true);
+  const BInst in = insts[b];
+  const int d = in.d;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)(blockIdx.x - in.oblock0) * 8 + (threadIdx.x >> 5);
+  if (row >= (int64_t)in.K * d) return;
+  const int k = (int)(row / d), j = (int)(row % d);
+  const double* cj = in.chol + (size_t)j * d;
+  const double* uk = ubuf + in.u_off + (size_t)k * d;
+  double acc = 0.0;
+  for (int l = lane; l <= j; l += 32) acc = fma(cj[l], uk[l], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) in.grad[(size_t)k * d + j] = acc - in.mu[j];
+}
+
 // ------------------------------------------------------------------ host ---
 struct BatchLayout {
-  size_t insts, items, yf, y64, c, parts, counter, total;
-  int nitems, pblocks, dmax, kmax;
+  size_t insts, items, yf, y64, c, parts, gparts, u, counter, total;
+  int nitems, pblocks, ublocks, oblocks, dmax, kmax;
 };
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -201,12 +307,13 @@ static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 // Fills the descriptor tables (host) and the workspace layout for a chunk of
 // `chunk_tiles` tiles of BM scenarios per item.
 static BatchLayout plan_batch(int B, const saa_problem* probs, const int32_t* K, const double* const* X,
-                              double* const* f, double* const* pbar, double* const* var, int es, int bm,
-                              int chunk_tiles, std::vector<BInst>* hi, std::vector<BItem>* hitems) {
+                              double* const* f, double* const* pbar, double* const* var, double* const* grad,
+                              int want_grad, int es, int bm, int chunk_tiles, std::vector<BInst>* hi,
+                              std::vector<BItem>* hitems) {
   BatchLayout L;
   std::memset(&L, 0, sizeof(L));
-  int64_t yf = 0, y64 = 0, c = 0, parts = 0;
-  int nitems = 0, pblocks = 0, dmax = 1, kmax = 1;
+  int64_t yf = 0, y64 = 0, c = 0, parts = 0, gparts = 0, u = 0;
+  int nitems = 0, pblocks = 0, ublocks = 0, oblocks = 0, dmax = 1, kmax = 1;
   const uint32_t chunk = (uint32_t)(bm * chunk_tiles);
   if (hi) hi->resize(B);
   if (hitems) hitems->clear();
@@ -224,6 +331,8 @@ static BatchLayout plan_batch(int B, const saa_problem* probs, const int32_t* K,
       in.f = f[b]; in.pbar = pbar ? pbar[b] : nullptr; in.var = var ? var[b] : nullptr;
       in.y_off = yf; in.y64_off = y64; in.c_off = c; in.part_off = parts;
       in.item0 = nitems; in.nitems = nit; in.pblock0 = pblocks;
+      in.grad = (want_grad && grad) ? grad[b] : nullptr;
+      in.gpart_off = gparts; in.u_off = u; in.ublock0 = ublocks; in.oblock0 = oblocks;
     }
     if (hitems)
       for (int t = 0; t < nit; ++t) {
@@ -238,6 +347,12 @@ static BatchLayout plan_batch(int B, const saa_problem* probs, const int32_t* K,
     y64 += (int64_t)d * k;
     c += k;
     parts += (int64_t)nit * (2 * k + d);
+    if (want_grad) {
+      gparts += (int64_t)nit * 2 * k * d;
+      u += (int64_t)k * d;
+      ublocks += k * ((d + 31) / 32);
+      oblocks += (int)(((int64_t)k * d + 7) / 8);
+    }
     nitems += nit;
     pblocks += ((k + kBK - 1) / kBK) * ((d + 31) / 32);
     dmax = std::max(dmax, d);
@@ -250,17 +365,21 @@ static BatchLayout plan_batch(int B, const saa_problem* probs, const int32_t* K,
   L.y64 = off; off = al(off + 8 * (size_t)y64);
   L.c = off; off = al(off + 8 * (size_t)c);
   L.parts = off; off = al(off + 8 * (size_t)parts);
+  L.gparts = off; off = al(off + (size_t)es * gparts);
+  L.u = off; off = al(off + 8 * (size_t)u);
   L.counter = off; off = al(off + 8);
   L.total = off;
   L.nitems = nitems;
   L.pblocks = pblocks;
+  L.ublocks = ublocks;
+  L.oblocks = oblocks;
   L.dmax = dmax;
   L.kmax = kmax;
   return L;
 }
 
 template <typename T, int BM, int TN>
-static cudaError_t launch_main(const saa_ctx* ctx, const BatchLayout& L, char* ws, cudaStream_t st) {
+static cudaError_t launch_main(const saa_ctx* ctx, const BatchLayout& L, char* ws, int want_grad, cudaStream_t st) {
   const int prec = sizeof(T) == 8 ? SAA_FP64 : SAA_FP32;
   const int smem = (int)simt_smem(prec, L.dmax, BM, TN);
   auto kern = k_batched_main<T, BM, TN>;
@@ -273,7 +392,8 @@ static cudaError_t launch_main(const saa_ctx* ctx, const BatchLayout& L, char* w
   e = cudaMemsetAsync(ws + L.counter, 0, 8, st);
   if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, smem, st>>>((const BInst*)(ws + L.insts), (const BItem*)(ws + L.items), L.nitems,
-                                     (const T*)(ws + L.yf), (double*)(ws + L.parts), (uint32_t*)(ws + L.counter));
+                                     (const T*)(ws + L.yf), (double*)(ws + L.parts), (T*)(ws + L.gparts), want_grad,
+                                     (uint32_t*)(ws + L.counter));
   return cudaGetLastError();
 }
 
@@ -328,15 +448,68 @@ int pick_bm(int prec, int dmax) { return (prec == SAA_FP64) ? (dmax <= 256 ? 64 
 
 }  // namespace
 
+// The launch sequence of a planned batch (capturable): prologue, the
+// persistent main kernel, the value finalize and, with gradients, the u and
+// C u kernels.  Returns the number of kernels launched in *nk.
+static saa_status launch_sequence(saa_ctx* ctx, int B, const BatchLayout& L, saa_prec prec, int bm, int want_grad,
+                                  char* w, cudaStream_t st, int* nk) {
+  const size_t psmem = sizeof(double) * kBK * L.dmax;
+  if (prec == SAA_FP64) {
+    if (psmem > 48 * 1024)
+      cudaFuncSetAttribute(k_batched_prologue<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    k_batched_prologue<double><<<L.pblocks, 256, psmem, st>>>((const BInst*)(w + L.insts), B, (double*)(w + L.yf),
+                                                              (double*)(w + L.y64), (double*)(w + L.c));
+  } else {
+    if (psmem > 48 * 1024)
+      cudaFuncSetAttribute(k_batched_prologue<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    k_batched_prologue<float><<<L.pblocks, 256, psmem, st>>>((const BInst*)(w + L.insts), B, (float*)(w + L.yf),
+                                                             (double*)(w + L.y64), (double*)(w + L.c));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, "batched prologue launch");
+  const bool narrow = simt_tn(L.kmax) == 1;
+  if (prec == SAA_FP64)
+    e = (bm == 64) ? (narrow ? launch_main<double, 64, 1>(ctx, L, w, want_grad, st)
+                             : launch_main<double, 64, 4>(ctx, L, w, want_grad, st))
+                   : (narrow ? launch_main<double, 32, 1>(ctx, L, w, want_grad, st)
+                             : launch_main<double, 32, 4>(ctx, L, w, want_grad, st));
+  else
+    e = (bm == 64) ? (narrow ? launch_main<float, 64, 1>(ctx, L, w, want_grad, st)
+                             : launch_main<float, 64, 4>(ctx, L, w, want_grad, st))
+                   : (narrow ? launch_main<float, 32, 1>(ctx, L, w, want_grad, st)
+                             : launch_main<float, 32, 4>(ctx, L, w, want_grad, st));
+  if (e != cudaSuccess) return cuda_status(e, "batched sample kernel launch");
+  k_batched_finalize<<<B, 64, 0, st>>>((const BInst*)(w + L.insts), (const double*)(w + L.parts),
+                                       (const double*)(w + L.c));
+  *nk = 3;
+  if (want_grad && L.ublocks > 0) {
+    if (prec == SAA_FP64)
+      k_batched_grad_u<double><<<L.ublocks, 256, 0, st>>>((const BInst*)(w + L.insts), B,
+                                                          (const double*)(w + L.parts),
+                                                          (const double*)(w + L.gparts), (double*)(w + L.u));
+    else
+      k_batched_grad_u<float><<<L.ublocks, 256, 0, st>>>((const BInst*)(w + L.insts), B, (const double*)(w + L.parts),
+                                                         (const float*)(w + L.gparts), (double*)(w + L.u));
+    k_batched_grad_out<<<L.oblocks, 256, 0, st>>>((const BInst*)(w + L.insts), B, (const double*)(w + L.u));
+    *nk += 2;
+  }
+  return cuda_status(cudaGetLastError(), "batched finalize launch");
+}
+
+// Plans the batch with tile shape (bm, chunk), optionally uploads its
+// descriptor tables through the context's pinned staging buffer, and
+// launches it.
 static saa_status run_batch(saa_ctx* ctx, int B, const saa_problem* probs, const int32_t* K, const double* const* X,
-                            saa_prec prec, double* const* f, double* const* pbar, double* const* var, void* ws,
-                            size_t ws_bytes, cudaStream_t st, int bm, int chunk, bool upload) {
+                            saa_prec prec, double* const* f, double* const* pbar, double* const* var,
+                            double* const* grad, int want_grad, void* ws, size_t ws_bytes, cudaStream_t st, int bm,
+                            int chunk, bool upload, bool launch, BatchLayout* out_layout) {
   const int es = prec == SAA_FP64 ? 8 : 4;
   std::vector<BInst> hi;
   std::vector<BItem> hitems;
-  const BatchLayout L = plan_batch(B, probs, K, X, f, pbar, var, es, bm, chunk, &hi, &hitems);
+  const BatchLayout L = plan_batch(B, probs, K, X, f, pbar, var, grad, want_grad, es, bm, chunk, &hi, &hitems);
+  if (out_layout) *out_layout = L;
   if (ws_bytes < L.total) {
-    set_error("saa_eval_batched: workspace smaller than saa_workspace_size_batched()");
+    set_error("batched: workspace smaller than the workspace-size query");
     return SAA_ENOMEM;
   }
   char* w = (char*)ws;
@@ -364,47 +537,113 @@ static saa_status run_batch(saa_ctx* ctx, int B, const saa_problem* probs, const
     s = cuda_status(cudaEventRecord(ctx->stage_ready, st), "stage event");
     if (s != SAA_OK) return s;
   }
-  const size_t psmem = sizeof(double) * kBK * L.dmax;
-  if (prec == SAA_FP64) {
-    if (psmem > 48 * 1024)
-      cudaFuncSetAttribute(k_batched_prologue<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
-    k_batched_prologue<double><<<L.pblocks, 256, psmem, st>>>((const BInst*)(w + L.insts), B, (double*)(w + L.yf),
-                                                              (double*)(w + L.y64), (double*)(w + L.c));
-  } else {
-    if (psmem > 48 * 1024)
-      cudaFuncSetAttribute(k_batched_prologue<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
-    k_batched_prologue<float><<<L.pblocks, 256, psmem, st>>>((const BInst*)(w + L.insts), B, (float*)(w + L.yf),
-                                                             (double*)(w + L.y64), (double*)(w + L.c));
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_status(e, "batched prologue launch");
-  const bool narrow = simt_tn(L.kmax) == 1;
-  if (prec == SAA_FP64)
-    e = (bm == 64) ? (narrow ? launch_main<double, 64, 1>(ctx, L, w, st) : launch_main<double, 64, 4>(ctx, L, w, st))
-                   : (narrow ? launch_main<double, 32, 1>(ctx, L, w, st) : launch_main<double, 32, 4>(ctx, L, w, st));
-  else
-    e = (bm == 64) ? (narrow ? launch_main<float, 64, 1>(ctx, L, w, st) : launch_main<float, 64, 4>(ctx, L, w, st))
-                   : (narrow ? launch_main<float, 32, 1>(ctx, L, w, st) : launch_main<float, 32, 4>(ctx, L, w, st));
-  if (e != cudaSuccess) return cuda_status(e, "batched sample kernel launch");
-  k_batched_finalize<<<B, 64, 0, st>>>((const BInst*)(w + L.insts), (const double*)(w + L.parts),
-                                       (const double*)(w + L.c));
-  ctx->kernels += 3;
-  return cuda_status(cudaGetLastError(), "batched finalize launch");
+  if (!launch) return SAA_OK;
+  int nk = 0;
+  saa_status s = launch_sequence(ctx, B, L, prec, bm, want_grad, w, st, &nk);
+  ctx->kernels += nk;
+  return s;
 }
 
-extern "C" size_t saa_workspace_size_batched(const saa_ctx* ctx, int32_t B, const saa_problem* probs,
-                                             const int32_t* K, saa_prec prec) {
-  if (!ctx || B < 1 || !probs || !K) return 0;
+static size_t batch_ws(int32_t B, const saa_problem* probs, const int32_t* K, saa_prec prec, int want_grad) {
   const int es = prec == SAA_FP64 ? 8 : 4;
-  int dmax = 1;
-  for (int b = 0; b < B; ++b) dmax = std::max(dmax, probs[b].d);
   size_t need = 0;
   // the largest layout over the tile shapes the autotuner may pick
   for (int bm : {32, 64})
     for (int ch : kChunkChoices)
-      need = std::max(need, plan_batch(B, probs, K, nullptr, nullptr, nullptr, nullptr, es, bm, ch, nullptr, nullptr)
+      need = std::max(need, plan_batch(B, probs, K, nullptr, nullptr, nullptr, nullptr, nullptr, want_grad, es, bm, ch,
+                                       nullptr, nullptr)
                                 .total);
   return need;
+}
+
+// Tile shape for this batch shape: the autotuner's cached choice, else (when
+// enabled and not capturing) time every candidate once, else a default.
+static saa_status choose_shape(saa_ctx* ctx, int B, const saa_problem* probs, const int32_t* K, const double* const* X,
+                               saa_prec prec, double* const* f, double* const* pbar, double* const* var,
+                               double* const* grad, int want_grad, void* ws, size_t ws_bytes, cudaStream_t st,
+                               int* bm_out, int* chunk_out) {
+  int dmax = 1;
+  for (int b = 0; b < B; ++b) dmax = std::max(dmax, probs[b].d);
+  const uint64_t key = shape_key(B, probs, K, prec, ctx->device) ^ ((uint64_t)want_grad << 63);
+  int bm = -1, chunk = -1;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const TuneEntry& t : g_tune)
+      if (t.key == key) {
+        bm = t.bm;
+        chunk = t.chunk;
+      }
+  }
+  if (bm < 0 && ctx->autotune) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusNone) {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float best = 1e30f;
+      saa_status s = SAA_OK;
+      for (int cbm : {32, 64}) {
+        if (prec == SAA_FP64 && cbm == 64 && dmax > 256) continue;
+        if (prec == SAA_FP32 && cbm == 64 && dmax > 512) continue;
+        for (int ch : kChunkChoices) {
+          s = run_batch(ctx, B, probs, K, X, prec, f, pbar, var, grad, want_grad, ws, ws_bytes, st, cbm, ch, true,
+                        true, nullptr);
+          if (s != SAA_OK) break;
+          cudaEventRecord(e0, st);
+          s = run_batch(ctx, B, probs, K, X, prec, f, pbar, var, grad, want_grad, ws, ws_bytes, st, cbm, ch, false,
+                        true, nullptr);
+          cudaEventRecord(e1, st);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (s == SAA_OK && ms < best) {
+            best = ms;
+            bm = cbm;
+            chunk = ch;
+          }
+        }
+        if (s != SAA_OK) break;
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (s != SAA_OK) return s;
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune.push_back({key, bm, chunk});
+    }
+  }
+  if (bm < 0) {
+    bm = pick_bm(prec, dmax);
+    chunk = 32;
+  }
+  *bm_out = bm;
+  *chunk_out = chunk;
+  return SAA_OK;
+}
+
+// Makes ctx->device current for the duration of a call.
+struct BatchDeviceGuard {
+  int prev = -1;
+  explicit BatchDeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~BatchDeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+struct saa_batch {
+  saa_ctx* ctx;
+  cudaGraphExec_t exec;
+  int kernels;   // kernels per replay
+};
+
+extern "C" size_t saa_workspace_size_batched(const saa_ctx* ctx, int32_t B, const saa_problem* probs,
+                                             const int32_t* K, saa_prec prec) {
+  if (!ctx || B < 1 || !probs || !K) return 0;
+  return batch_ws(B, probs, K, prec, 0);
 }
 
 extern "C" saa_status saa_eval_batched(saa_ctx* ctx, int32_t B, const saa_problem* probs, const int32_t* K,
@@ -420,66 +659,102 @@ extern "C" saa_status saa_eval_batched(saa_ctx* ctx, int32_t B, const saa_proble
     set_error("workspace must be non-NULL and 256-byte aligned");
     return SAA_EINVAL;
   }
-  int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != ctx->device) cudaSetDevice(ctx->device);
+  BatchDeviceGuard g(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
-  int dmax = 1;
-  for (int b = 0; b < B; ++b) dmax = std::max(dmax, probs[b].d);
-  const uint64_t key = shape_key(B, probs, K, prec, ctx->device);
-  int bm = -1, chunk = -1;
-  {
-    std::lock_guard<std::mutex> lock(g_tune_mu);
-    for (const TuneEntry& t : g_tune)
-      if (t.key == key) {
-        bm = t.bm;
-        chunk = t.chunk;
-      }
+  int bm = 0, chunk = 0;
+  s = choose_shape(ctx, B, probs, K, X, prec, f, pbar, var, nullptr, 0, ws, ws_bytes, st, &bm, &chunk);
+  if (s != SAA_OK) return s;
+  return run_batch(ctx, B, probs, K, X, prec, f, pbar, var, nullptr, 0, ws, ws_bytes, st, bm, chunk, true, true,
+                   nullptr);
+}
+
+extern "C" size_t saa_batch_workspace_size(const saa_ctx* ctx, int32_t B, const saa_problem* probs, const int32_t* K,
+                                           saa_prec prec, int want_grad) {
+  if (!ctx || B < 1 || !probs || !K) return 0;
+  return batch_ws(B, probs, K, prec, want_grad ? 1 : 0);
+}
+
+extern "C" saa_status saa_batch_create(saa_ctx* ctx, int32_t B, const saa_problem* probs, const int32_t* K,
+                                       const double* const* X, saa_prec prec, double* const* f, double* const* pbar,
+                                       double* const* var, double* const* grad, void* ws, size_t ws_bytes,
+                                       void* stream, saa_batch** out) {
+  if (!ctx || !out) {
+    set_error("saa_batch_create: ctx and out must be non-NULL");
+    return SAA_EINVAL;
   }
-  if (bm < 0 && ctx->autotune) {
-    // time each candidate tile shape once on this batch (outside any capture)
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(st, &cs);
-    if (cs == cudaStreamCaptureStatusNone) {
-      cudaEvent_t e0, e1;
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
-      float best = 1e30f;
-      for (int cbm : {32, 64}) {
-        if (prec == SAA_FP64 && cbm == 64 && dmax > 256) continue;
-        if (prec == SAA_FP32 && cbm == 64 && dmax > 512) continue;
-        for (int ch : kChunkChoices) {
-          s = run_batch(ctx, B, probs, K, X, prec, f, pbar, var, ws, ws_bytes, st, cbm, ch, true);
-          if (s != SAA_OK) break;
-          cudaEventRecord(e0, st);
-          s = run_batch(ctx, B, probs, K, X, prec, f, pbar, var, ws, ws_bytes, st, cbm, ch, false);
-          cudaEventRecord(e1, st);
-          cudaEventSynchronize(e1);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (s == SAA_OK && ms < best) {
-            best = ms;
-            bm = cbm;
-            chunk = ch;
-          }
-        }
-        if (s != SAA_OK) break;
+  *out = nullptr;
+  saa_status s = validate(B, probs, K, X, f, prec);
+  if (s != SAA_OK) return s;
+  const int want_grad = grad ? 1 : 0;
+  if (grad)
+    for (int b = 0; b < B; ++b)
+      if (!grad[b]) {
+        set_error("saa_batch_create: grad[" + std::to_string(b) + "] is NULL");
+        return SAA_EINVAL;
       }
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      if (s != SAA_OK) {
-        if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
-        return s;
-      }
-      std::lock_guard<std::mutex> lock(g_tune_mu);
-      g_tune.push_back({key, bm, chunk});
-    }
+  if (!ws || (((uintptr_t)ws) & 255u)) {
+    set_error("workspace must be non-NULL and 256-byte aligned");
+    return SAA_EINVAL;
   }
-  if (bm < 0) {
-    bm = pick_bm(prec, dmax);
-    chunk = 32;
+  if (ws_bytes < batch_ws(B, probs, K, prec, want_grad)) {
+    set_error("saa_batch_create: workspace smaller than saa_batch_workspace_size()");
+    return SAA_ENOMEM;
   }
-  s = run_batch(ctx, B, probs, K, X, prec, f, pbar, var, ws, ws_bytes, st, bm, chunk, true);
-  if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
-  return s;
+  BatchDeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  int bm = 0, chunk = 0;
+  s = choose_shape(ctx, B, probs, K, X, prec, f, pbar, var, grad, want_grad, ws, ws_bytes, st, &bm, &chunk);
+  if (s != SAA_OK) return s;
+  // upload the descriptor tables once, and wait for them
+  BatchLayout L;
+  s = run_batch(ctx, B, probs, K, X, prec, f, pbar, var, grad, want_grad, ws, ws_bytes, st, bm, chunk, true, false,
+                &L);
+  if (s == SAA_OK) s = cuda_status(cudaStreamSynchronize(st), "saa_batch_create: descriptor upload");
+  if (s != SAA_OK) return s;
+  // capture the launch sequence on a private stream
+  cudaStream_t cap;
+  s = cuda_status(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "saa_batch_create: capture stream");
+  if (s != SAA_OK) return s;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int nk = 0;
+  s = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "saa_batch_create: begin capture");
+  if (s == SAA_OK) {
+    const saa_status r = launch_sequence(ctx, B, L, prec, bm, want_grad, (char*)ws, cap, &nk);
+    const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+    s = (r != SAA_OK) ? r : cuda_status(e, "saa_batch_create: end capture");
+  }
+  if (s == SAA_OK) s = cuda_status(cudaGraphInstantiate(&exec, graph, 0), "saa_batch_create: instantiate");
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  if (s != SAA_OK) return s;
+  saa_batch* bt = new (std::nothrow) saa_batch();
+  if (!bt) {
+    cudaGraphExecDestroy(exec);
+    set_error("saa_batch_create: host allocation failed");
+    return SAA_ENOMEM;
+  }
+  bt->ctx = ctx;
+  bt->exec = exec;
+  bt->kernels = nk;
+  *out = bt;
+  return SAA_OK;
+}
+
+extern "C" saa_status saa_batch_launch(saa_batch* batch, void* stream) {
+  if (!batch) {
+    set_error("saa_batch_launch: batch is NULL");
+    return SAA_EINVAL;
+  }
+  BatchDeviceGuard g(batch->ctx->device);
+  batch->ctx->kernels += batch->kernels;
+  return cuda_status(cudaGraphLaunch(batch->exec, (cudaStream_t)stream), "saa_batch_launch: graph launch");
+}
+
+extern "C" void saa_batch_destroy(saa_batch* batch) {
+  if (!batch) return;
+  BatchDeviceGuard g(batch->ctx->device);
+  cudaDeviceSynchronize();
+  cudaGraphExecDestroy(batch->exec);
+  delete batch;
 }

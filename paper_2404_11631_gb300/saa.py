@@ -94,6 +94,15 @@ def lib():
             L.saa_generate_moments.restype = C.c_int
             L.saa_cholesky.argtypes = [vp, C.c_int32, vp, vp, vp]
             L.saa_cholesky.restype = C.c_int
+            L.saa_batch_workspace_size.argtypes = [vp, C.c_int32, pp, C.POINTER(C.c_int32), C.c_int, C.c_int]
+            L.saa_batch_workspace_size.restype = sz
+            L.saa_batch_create.argtypes = [vp, C.c_int32, pp, C.POINTER(C.c_int32), vp, C.c_int, vp, vp, vp, vp, vp,
+                                           sz, vp, C.POINTER(vp)]
+            L.saa_batch_create.restype = C.c_int
+            L.saa_batch_launch.argtypes = [vp, vp]
+            L.saa_batch_launch.restype = C.c_int
+            L.saa_batch_destroy.argtypes = [vp]
+            L.saa_batch_destroy.restype = None
             L.saa_selftest_timeout.argtypes = [vp, C.c_uint32, vp]
             L.saa_selftest_timeout.restype = C.c_int
             L.saa_ctx_set_autotune.argtypes = [vp, C.c_int]
@@ -311,41 +320,87 @@ def saa_cholesky(sigma: torch.Tensor, out: torch.Tensor | None = None) -> torch.
 
 
 class Batch:
-    """Host-side marshalling of a ragged batch for saa_eval_batched (reusable
-    across calls: the descriptor arrays are built once)."""
+    """A ragged batch of problems, marshalled once.  With ``graph=True`` (the
+    default) it is a saa_batch: planned once and replayed as a CUDA graph by
+    :meth:`run`, optionally with gradients.  With ``graph=False`` every run
+    is one saa_eval_batched call (values only).  The decision tensors, mu and
+    chol are bound by address: update them in place between runs."""
 
-    def __init__(self, problems: list, Xs: list, prec="fp32", want_pbar=True, want_var=True):
+    def __init__(self, problems: list, Xs: list, prec="fp32", want_pbar=True, want_var=True, want_grad=False,
+                 graph=True):
         self.problems, self.Xs, self.prec = problems, [_decisions(X, p) for X, p in zip(Xs, problems)], prec
+        if want_grad and not graph:
+            raise ValueError("gradients of a batch need graph=True (saa_batch)")
         B = len(problems)
         dev = problems[0].device
-        self.B, self.device = B, dev
+        self.B, self.device, self.handle = B, dev, None
         self.cprobs = (_CProblem * B)(*[p.c_struct() for p in problems])
         self.K = (C.c_int32 * B)(*[int(X.shape[0]) for X in self.Xs])
         self.f = [torch.empty(int(X.shape[0]), dtype=torch.float64, device=dev) for X in self.Xs]
         self.pbar = [torch.empty_like(t) for t in self.f] if want_pbar else None
         self.var = [torch.empty_like(t) for t in self.f] if want_var else None
+        self.grad = [torch.empty(int(X.shape[0]), p.d, dtype=torch.float64, device=dev)
+                     for X, p in zip(self.Xs, problems)] if want_grad else None
         ptrs = lambda ts: (C.c_void_p * B)(*[t.data_ptr() for t in ts]) if ts is not None else None  # noqa: E731
         self.pX, self.pf, self.pp, self.pv = ptrs(self.Xs), ptrs(self.f), ptrs(self.pbar), ptrs(self.var)
-        need = lib().saa_workspace_size_batched(context(dev.index), B, self.cprobs, self.K, _prec(prec))
+        self.pg = ptrs(self.grad)
+        ctx = context(dev.index)
+        if graph:
+            need = lib().saa_batch_workspace_size(ctx, B, self.cprobs, self.K, _prec(prec), int(want_grad))
+        else:
+            need = lib().saa_workspace_size_batched(ctx, B, self.cprobs, self.K, _prec(prec))
         if need == 0:
             raise SAAError(SAA_EINVAL, lib().saa_last_error().decode())
         self.ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        if graph:
+            h = C.c_void_p()
+            _check(lib().saa_batch_create(ctx, B, self.cprobs, self.K, self.pX, _prec(prec), self.pf, self.pp,
+                                          self.pv, self.pg, _ptr(self.ws), self.ws.numel(), _stream(dev),
+                                          C.byref(h)))
+            self.handle = h
 
     def run(self) -> dict:
-        _check(lib().saa_eval_batched(context(self.device.index), self.B, self.cprobs, self.K, self.pX,
-                                      _prec(self.prec), self.pf, self.pp, self.pv, _ptr(self.ws), self.ws.numel(),
-                                      _stream(self.device)))
+        if self.handle is not None:
+            _check(lib().saa_batch_launch(self.handle, _stream(self.device)))
+        else:
+            _check(lib().saa_eval_batched(context(self.device.index), self.B, self.cprobs, self.K, self.pX,
+                                          _prec(self.prec), self.pf, self.pp, self.pv, _ptr(self.ws),
+                                          self.ws.numel(), _stream(self.device)))
         out = {"f": self.f}
         if self.pbar is not None:
             out["pbar"] = self.pbar
         if self.var is not None:
             out["var"] = self.var
+        if self.grad is not None:
+            out["grad"] = self.grad
         return out
+
+    def close(self):
+        if self.handle is not None and _lib is not None:
+            lib().saa_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def saa_eval_batched(problems: list, Xs: list, prec="fp32") -> dict:
-    """Eq. 4 for a ragged batch: lists of per-problem f (and pbar, var) tensors."""
-    return Batch(problems, Xs, prec).run()
+    """Eq. 4 for a ragged batch (one saa_eval_batched call): lists of
+    per-problem f, pbar and var tensors."""
+    return Batch(problems, Xs, prec, graph=False).run()
+
+
+def saa_grad_batched(problems: list, Xs: list, prec="fp32") -> dict:
+    """Eq. 4 and its gradient for a ragged batch (a saa_batch, launched once):
+    lists of per-problem f, pbar, var and grad [K_b, d_b] tensors."""
+    b = Batch(problems, Xs, prec, want_grad=True)
+    out = b.run()
+    torch.cuda.current_stream(b.device).synchronize()
+    b.close()
+    return out
 
 
 def saa_selftest_timeout(budget_us: int = 1000, device: int | None = None):
@@ -380,4 +435,5 @@ EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_
             "saa_solve", "saa_generate", "saa_max_dim", "saa_status_string", "saa_last_error",
             "saa_profile_enable", "saa_profile_read", "saa_eval_batched", "saa_workspace_size_batched",
             "saa_ctx_set_autotune", "saa_selftest_timeout", "saa_cholesky", "saa_generate_moments",
-            "saa_generate_moments_workspace_size"]
+            "saa_generate_moments_workspace_size", "saa_batch_workspace_size", "saa_batch_create",
+            "saa_batch_launch", "saa_batch_destroy"]

@@ -63,3 +63,64 @@ def test_full_ragged_4096_sampled_instances():
         single = saa.saa_eval(probs[b], Xs[b], "fp32")["f"]
         rel = ((out["f"][b] - single).abs() / (0.5 * out["var"][b] + (Xs[b] @ probs[b].mu).abs())).max().item()
         assert rel <= 1e-6, b
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batched_gradient_matches_oracle(prec):
+    # value and gradient of Eq. 4 per problem from one graph-replayed batch
+    from helpers import TOL_GRAD, grad_err
+    from paper_2404_11631_gb300 import saa
+    rb = inputs.ragged_batch(23, seed=9, d_range=(1, 260), logN_range=(0.4, 4.0), K_range=(1, 9))
+    laws = [oracle.LAW_MIX, oracle.LAW_GAUSS, oracle.LAW_STUDENT_T]
+    probs, Xs, ops = _build(rb, laws, prec)
+    batch = saa.Batch(probs, Xs, prec, want_grad=True)
+    out = batch.run()
+    out = batch.run()
+    saa.saa_ctx_sync()
+    for b in range(len(probs)):
+        ref = oracle.saa(ops[b], 64 if prec == "fp64" else 32, rb.X[b], grad=True)
+        assert est_err(out["f"][b].cpu().numpy(), ref["f"], ref["var"], rb.X[b], rb.instances[b].mu,
+                       0.5) <= TOL[prec], b
+        assert grad_err(out["grad"][b].cpu().numpy(), ref["grad"]) <= TOL_GRAD[prec], b
+    batch.close()
+
+
+def test_graph_replay_reads_current_decisions_and_matches_one_shot():
+    from paper_2404_11631_gb300 import saa
+    rb = inputs.ragged_batch(9, seed=2, d_range=(4, 90), logN_range=(2.0, 3.5), K_range=(1, 6))
+    probs, Xs, ops = _build(rb, [oracle.LAW_GAUSS, oracle.LAW_MIX], "fp32")
+    g = saa.Batch(probs, Xs, "fp32")
+    one = saa.saa_eval_batched(probs, Xs, "fp32")
+    out = g.run()
+    saa.saa_ctx_sync()
+    for b in range(len(probs)):
+        assert torch.equal(out["f"][b], one["f"][b]) and torch.equal(out["var"][b], one["var"][b])
+    # new decisions written in place: the replayed graph evaluates them
+    rng = np.random.default_rng(4)
+    newX = []
+    for b, X in enumerate(Xs):
+        x = rng.uniform(0.0, 1.0, size=tuple(X.shape))
+        X.copy_(torch.tensor(x, device="cuda"))
+        newX.append(x)
+    out = g.run()
+    saa.saa_ctx_sync()
+    for b in range(len(probs)):
+        ref = oracle.saa(ops[b], 32, newX[b])
+        assert est_err(out["f"][b].cpu().numpy(), ref["f"], ref["var"], newX[b], rb.instances[b].mu,
+                       0.5) <= TOL["fp32"], b
+    g.close()
+
+
+def test_full_ragged_4096_gradient_sampled_instances():
+    # the 4096-instance ragged workload with gradients; oracle on problems small enough to check
+    from helpers import TOL_GRAD, grad_err
+    from paper_2404_11631_gb300 import saa
+    rb = inputs.ragged_batch(4096, seed=0)
+    probs, Xs, ops = _build(rb, [oracle.LAW_GAUSS], "fp32")
+    out = saa.saa_grad_batched(probs, Xs, "fp32")
+    saa.saa_ctx_sync()
+    cost = rb.N.astype(np.float64) * rb.d.astype(np.float64) ** 2
+    picks = [int(b) for b in np.argsort(cost)[[0, 1, 500, 1500, 2500]]]
+    for b in picks:
+        ref = oracle.saa(ops[b], 32, rb.X[b], grad=True)
+        assert grad_err(out["grad"][b].cpu().numpy(), ref["grad"]) <= TOL_GRAD["fp32"], b
