@@ -7,7 +7,8 @@ S1/S2 epilogue, the FP64 cross-block reduction and the finalize.  The line
 also carries "eval_grad": saa_grad (value and gradient in w) on d = 1024,
 N = 2^20 Gaussian scenarios, K = 64, timed the same way, and "fw":
 Algorithm 1 (saa_solve) for 200 iterations on d = 1024, N = 2^22 Student-t
-scenarios regenerated every iteration.
+scenarios regenerated every iteration, and "ragged": 4096 independent
+instances in one graph-replayed persistent launch.
 
 Workload (default): d = 128 assets, N = 2^20 scenarios (first half Gaussian,
 second half standardised lognormal sigma = 1), K = 256 candidate decisions
@@ -293,6 +294,45 @@ def run_fw(args, dev, world, rank):
             "f_first_last": [float(f[0]), float(f[-1])], "gap_last": float(gap[-1])}
 
 
+def run_ragged(args, dev, world, rank, flush, stream):
+    """The ragged batch: 4096 independent Gaussian instances, d ~ U{8..512},
+    N = floor(10^U[3,5]), K ~ U{1..16}, each with its own Sigma; FP32; one
+    saa_batch (autotuned tile shape, the whole launch sequence captured in a
+    CUDA graph) replayed per step.  evals = sum_b N_b K_b per replay."""
+    import torch
+    from paper_2404_11631_gb300 import inputs, saa
+    rb = inputs.ragged_batch(args.ragged_B, seed=rank)
+    probs, Xs = [], []
+    for b in range(len(rb.d)):
+        inst = rb.instances[b]
+        probs.append(saa.Problem(mu=torch.tensor(inst.mu, device=dev), chol=torch.tensor(inst.chol, device=dev),
+                                 N=int(rb.N[b]), law=0, seed=int(rb.seeds[b]), instance=b))
+        Xs.append(torch.tensor(rb.X[b], device=dev))
+    batch = saa.Batch(probs, Xs, "fp32", want_pbar=False, want_var=False)
+    for _ in range(3):
+        batch.run()
+    torch.cuda.synchronize(dev)
+    steps = max(3, min(args.steps, 10))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        batch.run()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    saa.saa_ctx_sync(dev.index)
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    evals = float(np.sum(rb.N.astype(np.float64) * rb.K))
+    normals = float(np.sum(rb.N.astype(np.float64) * rb.d))
+    batch.close()
+    return {"metric": "scenario-decision evals/s (ragged batch)", "value": world * evals * steps / total_s,
+            "unit": "evals/s", "ms_per_step": 1e3 * total_s / steps, "steps": steps,
+            "normals_per_s": normals * steps / total_s,
+            "config": {"workload": f"ragged_{len(rb.d)}_gauss", "instances": len(rb.d), "d": "U{8..512}",
+                       "N": "floor(10^U[3,5])", "K": "U{1..16}", "prec": "fp32", "sum_NK": evals, "sum_Nd": normals,
+                       "graph": "autotuned tile shape, launch sequence captured once and replayed"}}
+
+
 def run_gen(args):
     """The bare generator (saa_generate_moments, FP32 mode) on the value
     workload's d and N, per law: normals/s.  This is the generator-only
@@ -497,6 +537,8 @@ def run_ours(args):
         line["eval_grad"] = run_grad(args, dev, world, rank, flush, stream)
     if not args.no_fw:
         line["fw"] = run_fw(args, dev, world, rank)
+    if not args.no_ragged:
+        line["ragged"] = run_ragged(args, dev, world, rank, flush, stream)
     if rank == 0:
         line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -526,6 +568,9 @@ def main():
     ap.add_argument("--gen-only", action="store_true", help="time the bare generator (per-normal figure)")
     ap.add_argument("--no-fw", action="store_true", help="skip the Algorithm 1 (Frank-Wolfe) workload")
     ap.add_argument("--fw-only", action="store_true", help="run only the Algorithm 1 workload")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the 4096-instance ragged batch")
+    ap.add_argument("--ragged-B", type=int, default=4096, help="instances of the ragged batch (profiling small cases)")
+    ap.add_argument("--ragged-only", action="store_true", help="run only the ragged batch")
     ap.add_argument("--fw-N", type=int, default=None, help="override the Algorithm 1 scenario count")
     ap.add_argument("--fw-T", type=int, default=None, help="override the Algorithm 1 iteration count")
     ap.add_argument("--N", type=int, default=None, help="override the scenario count (profiling small cases)")
@@ -552,6 +597,12 @@ def main():
         FW_WORKLOAD["name"] += f"_T{args.fw_T}"
     if args.gen_only:
         return run_gen(args)
+    if args.ragged_only:
+        import torch
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps(run_ragged(args, dev, 1, 0, flush, torch.cuda.current_stream(dev))), flush=True)
+        return 0
     if args.fw_only:
         import torch
         print(json.dumps(run_fw(args, torch.device("cuda", 0), 1, 0)), flush=True)

@@ -168,6 +168,135 @@ __global__ void __launch_bounds__(kThreads, 2) k_batched_main(const BInst* __res
   }
 }
 
+// ----------------------------------------------------- fused value path ---
+// Value-only batches with K_b <= 16 (the ragged workloads): no tile of
+// samples is stored.  Each thread draws one scenario and accumulates its K
+// dot products zhat_i'y_k while drawing, with y read from a padded copy in
+// shared memory four decisions at a time; the 32 lanes of a warp read the
+// same row of y, a broadcast.  The t-law scale s_i is applied once per
+// scenario.  (The group reduction below is kept general: G = 1 here.)  S1 and S2 collect in
+// shared memory per pass of 256/G scenarios: 16 parts per decision sum the
+// pass in FP32 and carry the pass totals in FP64, and the parts are merged
+// in order at the end of the item, so the result is deterministic.
+constexpr int kFusedK = 16;
+
+// four consecutive decisions' y_jk from shared memory (16-byte aligned)
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_batched_fused(
+    const BInst* __restrict__ insts, const BItem* __restrict__ items, int nitems, const T* __restrict__ Yf,
+    double* __restrict__ parts, uint32_t* __restrict__ counter) {
+  constexpr int PC = gen::Gen<T>::kPerCall;
+  extern __shared__ __align__(16) unsigned char fsm_raw[];
+  T* Ys = reinterpret_cast<T*>(fsm_raw);   // [d][kFusedK] (decisions padded with zeros)
+  __shared__ T Qs[256][kFusedK + 1];       // one row per scenario of the pass
+  __shared__ double red[2][16][kFusedK];
+  __shared__ int s_item;
+  const int tid = threadIdx.x;
+  const int kq = tid % kFusedK, part = tid / kFusedK;   // S1/S2 collection role
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    const BItem item = items[it];
+    const BInst& in = insts[item.inst];
+    const int d = in.d, K = in.K;
+    const int nb = (d + PC - 1) / PC;
+    // one thread per scenario: the 32 lanes of a warp draw 32 scenarios
+    // and read the same row of y (a shared-memory broadcast)
+    const int G = 1;
+    const int spp = 256 / G;   // scenarios per pass
+    const int g = tid % G, sl = tid / G;
+    for (int e = tid; e < d * kFusedK; e += 256) {
+      const int j = e / kFusedK, k = e % kFusedK;
+      Ys[e] = (k < K) ? Yf[in.y_off + (size_t)j * K + k] : T(0);
+    }
+    const gen::Stream st = gen::make_stream(in.seed, in.epoch, in.instance);
+    const uint32_t half = in.N / 2u;
+    const int kg = (K + 3) / 4;   // groups of four decisions (uniform over the CTA)
+    double d1 = 0.0, d2 = 0.0;   // pass totals of this thread's (decision kq, part)
+    for (uint32_t base = 0; base < item.n; base += (uint32_t)spp) {
+      __syncthreads();   // Ys staged / the previous pass's Qs consumed
+      const uint32_t r = base + (uint32_t)sl;
+      const bool live = r < item.n;
+      const uint32_t i = item.i0 + r;
+      T q[kFusedK];
+#pragma unroll
+      for (int k = 0; k < kFusedK; ++k) q[k] = T(0);
+      if (live) {
+        const bool logn = gen::is_lognormal(in.law, i, half);
+        for (int b = g; b < nb; b += G) {
+          T z[PC];
+          gen::Gen<T>::block(st, (uint32_t)b, i, logn, z);
+#pragma unroll
+          for (int e = 0; e < PC; ++e) {
+            const int j = b * PC + e;
+            if (j < d) {
+              const T* yj = Ys + (size_t)j * kFusedK;
+#pragma unroll
+              for (int c = 0; c < kFusedK / 4; ++c)
+                if (c < kg) {
+                  T y4[4];
+                  load4(yj + 4 * c, y4);
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) q[4 * c + u] = fma(z[e], y4[u], q[4 * c + u]);
+                }
+            }
+          }
+        }
+      }
+      // the G threads of a scenario are consecutive lanes of one warp
+      for (int o = G >> 1; o >= 1; o >>= 1) {
+#pragma unroll
+        for (int c = 0; c < kFusedK / 4; ++c)
+          if (c < kg) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) q[4 * c + u] += __shfl_xor_sync(0xffffffffu, q[4 * c + u], o);
+          }
+      }
+      if (g == 0) {
+        const T s = (live && in.law == SAA_LAW_STUDENT_T) ? gen::Gen<T>::scale(st, i, in.law, in.nu) : T(1);
+#pragma unroll
+        for (int k = 0; k < kFusedK; ++k) Qs[sl][k] = live ? q[k] * s : T(0);
+      }
+      __syncthreads();
+      if (kq < K) {
+        T f1 = T(0), f2 = T(0);
+        for (int x = part; x < spp; x += 16) {
+          const T v = Qs[x][kq];
+          f1 += v;
+          f2 = fma(v, v, f2);
+        }
+        d1 += (double)f1;
+        d2 += (double)f2;
+      }
+    }
+    red[0][part][kq] = d1;
+    red[1][part][kq] = d2;
+    __syncthreads();
+    if (tid < K) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int pp = 0; pp < 16; ++pp) {
+        s1 += red[0][pp][tid];
+        s2 += red[1][pp][tid];
+      }
+      double* slot = parts + in.part_off + (size_t)item.slot * (2 * K + d);
+      slot[tid] = s1;
+      slot[K + tid] = s2;
+    }
+  }
+}
+
 // ------------------------------------------------------------ finalize ---
 __device__ __forceinline__ void nsum_add(double& s, double& c, double x) {
   const double t = s + x;
@@ -397,6 +526,23 @@ static cudaError_t launch_main(const saa_ctx* ctx, const BatchLayout& L, char* w
   return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t launch_fused(const saa_ctx* ctx, const BatchLayout& L, char* ws, cudaStream_t st) {
+  const int smem = (int)(sizeof(T) * (size_t)L.dmax * kFusedK);
+  auto kern = k_batched_fused<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(L.nitems, ctx->sm_count * std::max(occ, 1)));
+  e = cudaMemsetAsync(ws + L.counter, 0, 8, st);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 256, smem, st>>>((const BInst*)(ws + L.insts), (const BItem*)(ws + L.items), L.nitems,
+                                (const T*)(ws + L.yf), (double*)(ws + L.parts), (uint32_t*)(ws + L.counter));
+  return cudaGetLastError();
+}
+
 }  // namespace saa
 
 using namespace saa;
@@ -468,7 +614,9 @@ static saa_status launch_sequence(saa_ctx* ctx, int B, const BatchLayout& L, saa
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "batched prologue launch");
   const bool narrow = simt_tn(L.kmax) == 1;
-  if (prec == SAA_FP64)
+  if (!want_grad && L.kmax <= kFusedK)
+    e = (prec == SAA_FP64) ? launch_fused<double>(ctx, L, w, st) : launch_fused<float>(ctx, L, w, st);
+  else if (prec == SAA_FP64)
     e = (bm == 64) ? (narrow ? launch_main<double, 64, 1>(ctx, L, w, want_grad, st)
                              : launch_main<double, 64, 4>(ctx, L, w, want_grad, st))
                    : (narrow ? launch_main<double, 32, 1>(ctx, L, w, want_grad, st)
