@@ -19,6 +19,9 @@ Functions and the passages they follow:
 * :func:`rse` -- the relative squared error of Table 2's notes.
 * :func:`cholesky` -- the lower Cholesky factor C of Sigma used by the
   normal law of Sec. 3.1 (R = mu + C z).
+* :func:`newsvendor_grad`, :func:`newsvendor_demands` -- the newsvendor's
+  Monte Carlo gradient (Sec. 3.2, the approximated gradient) and the
+  standardised demand samples it counts.
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force and independent library routines; the
@@ -73,6 +76,23 @@ class Problem(C.Structure):
     ]
 
 
+class Newsvendor(C.Structure):
+    """Mirror of the oracle's newsvendor struct (see saa_oracle.c)."""
+
+    _fields_ = [
+        ("n", C.c_int64),
+        ("S", C.c_int64),
+        ("seed", C.c_uint64),
+        ("instance", C.c_uint32),
+        ("epoch", C.c_uint32),
+        ("mu", C.POINTER(C.c_double)),
+        ("sigma", C.POINTER(C.c_double)),
+        ("k", C.POINTER(C.c_double)),
+        ("h", C.POINTER(C.c_double)),
+        ("v", C.POINTER(C.c_double)),
+    ]
+
+
 def _p(a, ct=C.c_double):
     return a.ctypes.data_as(C.POINTER(ct)) if a is not None else None
 
@@ -104,6 +124,11 @@ def lib():
             L.oracle_fw_step.restype = C.c_int
             L.oracle_fw.argtypes = [pp, C.c_int, dp, C.c_int, C.c_int, C.c_int64, dp, dp, dp, dp]
             L.oracle_fw.restype = C.c_int
+            nvp = C.POINTER(Newsvendor)
+            L.oracle_newsvendor_demands.argtypes = [nvp, C.c_int64, fp]
+            L.oracle_newsvendor_demands.restype = C.c_int
+            L.oracle_newsvendor_grad.argtypes = [nvp, C.c_int, dp, dp, C.POINTER(C.c_int64)]
+            L.oracle_newsvendor_grad.restype = C.c_int
             L.oracle_cholesky.argtypes = [C.c_int, dp, dp]
             L.oracle_cholesky.restype = C.c_int
             L.oracle_rse.argtypes = [C.c_double, C.c_double]
@@ -278,3 +303,30 @@ def cholesky(S):
     out = np.empty_like(S)
     _check(lib().oracle_cholesky(d, _p(S), _p(out)), "cholesky")
     return out
+
+
+def make_newsvendor(mu, sigma, k, h, v, S, seed=0, instance=0, epoch=0):
+    """Returns (Newsvendor, keepalive) for n products with S demand samples each."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (mu, sigma, k, h, v)]
+    n = arrs[0].shape[0]
+    P = Newsvendor(n, S, seed, instance, epoch, *[_p(a) for a in arrs])
+    return P, arrs
+
+
+def newsvendor_demands(prob, j):
+    """Standardised demand samples z_j0 .. z_j(S-1) of product j (float32)."""
+    P, keep = prob
+    z = np.empty(P.S, np.float32)
+    _check(lib().oracle_newsvendor_demands(C.byref(P), j, _p(z, C.c_float)), "newsvendor_demands")
+    return z
+
+
+def newsvendor_grad(prob, X):
+    """Monte Carlo gradient estimates [K, n] at decisions X [K, n], and the counts."""
+    P, keep = prob
+    X = np.ascontiguousarray(np.atleast_2d(X), dtype=np.float64)
+    K = X.shape[0]
+    g = np.empty_like(X)
+    cnt = np.empty(X.shape, np.int64)
+    _check(lib().oracle_newsvendor_grad(C.byref(P), K, _p(X), _p(g), _p(cnt, C.c_int64)), "newsvendor_grad")
+    return g, cnt

@@ -23,6 +23,9 @@
  *   5. The relative squared error of Table 2's notes.
  *   6. The lower Cholesky factor C of Sigma (C C' = Sigma), which turns the
  *      covariance of Sec. 3.1's normal law into the sample map R = mu + C z.
+ *   7. The newsvendor's Monte Carlo gradient (Sec. 3.2, the approximated
+ *      gradient): per product j, k_j - v_j + (h_j + v_j) times the fraction
+ *      of S normal demand samples d_j = mu_j + sigma_j z that are <= x_j.
  *
  * Floating-point discipline: compiled with -ffp-contract=off; every fused
  * multiply-add in the generator is an explicit fmaf()/fma() call, so each
@@ -918,6 +921,93 @@ int oracle_cholesky(int d, const double* S, double* C)
             } else {
                 C[(size_t)i * d + j] = acc / C[(size_t)j * d + j];
             }
+        }
+    }
+    return OR_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* 7. Newsvendor Monte Carlo gradient                                      */
+/* ---------------------------------------------------------------------- */
+/* Demand samples: product j's s-th demand is d_js = mu_j + sigma_j z_js,
+ * with z_js the generator's FP32 normals on counter (s / 4, j, epoch,
+ * (3 << 24) | instance), element s mod 4 of the four normals of that call.
+ * The indicator d_js <= x_j is decided on the standardised demand in FP32:
+ * z_js <= tau, tau = (float)((x_j - mu_j) / sigma_j) with the subtraction
+ * and the division in FP64 (sigma_j > 0).  The estimate is then
+ * (k_j - v_j) + (h_j + v_j) * (count / S) in FP64, in that order. */
+#define TAG_DEMAND 3u
+
+typedef struct {
+    int64_t n;          /* products */
+    int64_t S;          /* demand samples per product */
+    uint64_t seed;
+    uint32_t instance;
+    uint32_t epoch;
+    const double* mu;    /* [n] demand means */
+    const double* sigma; /* [n] demand standard deviations, > 0 */
+    const double* k;     /* [n] unit ordering cost */
+    const double* h;     /* [n] unit holding cost */
+    const double* v;     /* [n] unit shortage cost */
+} oracle_newsvendor;
+
+static void demand_block(const oracle_newsvendor* p, int64_t j, int64_t b, float z[4])
+{
+    uint32_t c[4], x[4];
+    c[0] = (uint32_t)b;
+    c[1] = (uint32_t)j;
+    c[2] = p->epoch;
+    c[3] = (TAG_DEMAND << 24) | (p->instance & 0xffffffu);
+    philox10(c, (uint32_t)(p->seed & 0xffffffffu), (uint32_t)(p->seed >> 32), x);
+    box_muller_f(u24(x[0]), u24_num(x[1]), &z[0], &z[1]);
+    box_muller_f(u24(x[2]), u24_num(x[3]), &z[2], &z[3]);
+}
+
+static int check_newsvendor(const oracle_newsvendor* p)
+{
+    if (!p || p->n < 1 || p->n > 0xffffffffll || p->S < 1 || p->S > 0x3fffffffll || !p->mu || !p->sigma) return OR_EINVAL;
+    for (int64_t j = 0; j < p->n; ++j)
+        if (!(p->sigma[j] > 0.0)) return OR_EINVAL;
+    return OR_OK;
+}
+
+/* The standardised demands z_j0 .. z_j(S-1) of product j. */
+int oracle_newsvendor_demands(const oracle_newsvendor* p, int64_t j, float* z)
+{
+    if (check_newsvendor(p) != OR_OK || j < 0 || j >= p->n || !z) return OR_EINVAL;
+    for (int64_t b = 0; 4 * b < p->S; ++b) {
+        float w[4];
+        demand_block(p, j, b, w);
+        for (int q = 0; q < 4 && 4 * b + q < p->S; ++q) z[4 * b + q] = w[q];
+    }
+    return OR_OK;
+}
+
+/* Gradient estimates grad[K][n] at the K decisions X[K][n]; counts[K][n]
+ * (optional) receives the number of samples with z <= tau. */
+int oracle_newsvendor_grad(const oracle_newsvendor* p, int K, const double* X, double* grad, int64_t* counts)
+{
+    if (check_newsvendor(p) != OR_OK || K < 1 || K > 64 || !X || !grad || !p->k || !p->h || !p->v) return OR_EINVAL;
+    const int64_t n = p->n;
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; ++j) {
+        float tau[64];
+        int64_t cnt[64];
+        for (int kk = 0; kk < K; ++kk) {
+            tau[kk] = (float)((X[(size_t)kk * n + j] - p->mu[j]) / p->sigma[j]);
+            cnt[kk] = 0;
+        }
+        for (int64_t b = 0; 4 * b < p->S; ++b) {
+            float z[4];
+            demand_block(p, j, b, z);
+            for (int q = 0; q < 4 && 4 * b + q < p->S; ++q)
+                for (int kk = 0; kk < K; ++kk)
+                    if (z[q] <= tau[kk]) cnt[kk] += 1;
+        }
+        for (int kk = 0; kk < K; ++kk) {
+            const double frac = (double)cnt[kk] / (double)p->S;
+            grad[(size_t)kk * n + j] = (p->k[j] - p->v[j]) + (p->h[j] + p->v[j]) * frac;
+            if (counts) counts[(size_t)kk * n + j] = cnt[kk];
         }
     }
     return OR_OK;
