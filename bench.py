@@ -7,8 +7,9 @@ S1/S2 epilogue, the FP64 cross-block reduction and the finalize.  The line
 also carries "eval_grad": saa_grad (value and gradient in w) on d = 1024,
 N = 2^20 Gaussian scenarios, K = 64, timed the same way, and "fw":
 Algorithm 1 (saa_solve) for 200 iterations on d = 1024, N = 2^22 Student-t
-scenarios regenerated every iteration, and "ragged": 4096 independent
-instances in one graph-replayed persistent launch.
+scenarios regenerated every iteration, "ragged": 4096 independent
+instances in one graph-replayed persistent launch, and "newsvendor": the
+Monte Carlo gradient of Sec. 3.2 for 10^6 products x 1000 demand samples.
 
 Workload (default): d = 128 assets, N = 2^20 scenarios (first half Gaussian,
 second half standardised lognormal sigma = 1), K = 256 candidate decisions
@@ -333,6 +334,49 @@ def run_ragged(args, dev, world, rank, flush, stream):
                        "graph": "autotuned tile shape, launch sequence captured once and replayed"}}
 
 
+NV_WORKLOAD = dict(name="newsvendor_n1M_S1000_K1", n=1_000_000, S=1000, K=1)
+
+
+def run_newsvendor(args, dev, world, rank, flush, stream):
+    """The newsvendor's Monte Carlo gradient (Sec. 3.2): n = 10^6 products
+    (the largest inventory of Sec. 4.1), S = 1000 normal demand samples per
+    product, mu ~ U(20, 50), sigma ~ U(10, 20), one decision vector.  The
+    unit is one demand sample of one product (one normal + its compare)."""
+    import torch
+    from paper_2404_11631_gb300 import saa
+    n, S, K = NV_WORKLOAD["n"], NV_WORKLOAD["S"], NV_WORKLOAD["K"]
+    rng = np.random.default_rng([n, S, 11])
+    arrs = dict(mu=rng.uniform(20.0, 50.0, n), sigma=rng.uniform(10.0, 20.0, n), k=rng.uniform(0.5, 2.0, n),
+                h=rng.uniform(0.1, 1.0, n), v=rng.uniform(1.0, 4.0, n))
+    prob = saa.Newsvendor(**{a: torch.tensor(x, device=dev) for a, x in arrs.items()}, S=S, seed=0, instance=rank)
+    X = torch.tensor(arrs["mu"] + arrs["sigma"] * np.random.default_rng(1).uniform(-3.0, 3.0, (K, n)), device=dev)
+    for _ in range(3):
+        saa.saa_newsvendor_grad(prob, X)
+    torch.cuda.synchronize(dev)
+    steps = max(3, min(args.steps, 20))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        saa.saa_newsvendor_grad(prob, X)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    saa.saa_ctx_sync(dev.index)
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    samples = float(n) * S
+    peaks, _ = _peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = 152 * 128 * mhz * 1e6 / 1e12
+    ops = samples * (GEN_INST_GAUSS + 2.0 * K)   # generator per normal + compare and count per decision
+    return {"metric": "demand samples/s (newsvendor MC gradient)", "value": world * samples * steps / total_s,
+            "unit": "samples/s", "ms_per_step": 1e3 * total_s / steps, "steps": steps,
+            "config": {"workload": NV_WORKLOAD["name"], "n": n, "S": S, "K": K, "prec": "fp32 normals, exact counts",
+                       "l2": "flushed between timed steps"},
+            "roofline": {"bound": "alu", "achieved": ops * steps / total_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ops * steps / total_s / 1e12 / peak,
+                         "note": "generator-only kernel's instructions per normal + 2 per sample and decision"}}
+
+
 def run_gen(args):
     """The bare generator (saa_generate_moments, FP32 mode) on the value
     workload's d and N, per law: normals/s.  This is the generator-only
@@ -539,6 +583,8 @@ def run_ours(args):
         line["fw"] = run_fw(args, dev, world, rank)
     if not args.no_ragged:
         line["ragged"] = run_ragged(args, dev, world, rank, flush, stream)
+    if not args.no_newsvendor:
+        line["newsvendor"] = run_newsvendor(args, dev, world, rank, flush, stream)
     if rank == 0:
         line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -571,6 +617,9 @@ def main():
     ap.add_argument("--no-ragged", action="store_true", help="skip the 4096-instance ragged batch")
     ap.add_argument("--ragged-B", type=int, default=4096, help="instances of the ragged batch (profiling small cases)")
     ap.add_argument("--ragged-only", action="store_true", help="run only the ragged batch")
+    ap.add_argument("--no-newsvendor", action="store_true", help="skip the newsvendor gradient workload")
+    ap.add_argument("--nv-only", action="store_true", help="run only the newsvendor gradient workload")
+    ap.add_argument("--nv-n", type=int, default=None, help="override the newsvendor product count")
     ap.add_argument("--fw-N", type=int, default=None, help="override the Algorithm 1 scenario count")
     ap.add_argument("--fw-T", type=int, default=None, help="override the Algorithm 1 iteration count")
     ap.add_argument("--N", type=int, default=None, help="override the scenario count (profiling small cases)")
@@ -597,6 +646,15 @@ def main():
         FW_WORKLOAD["name"] += f"_T{args.fw_T}"
     if args.gen_only:
         return run_gen(args)
+    if args.nv_n:
+        NV_WORKLOAD["n"] = args.nv_n
+        NV_WORKLOAD["name"] = f"newsvendor_n{args.nv_n}_S{NV_WORKLOAD['S']}_K1"
+    if args.nv_only:
+        import torch
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps(run_newsvendor(args, dev, 1, 0, flush, torch.cuda.current_stream(dev))), flush=True)
+        return 0
     if args.ragged_only:
         import torch
         dev = torch.device("cuda", 0)

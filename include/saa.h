@@ -228,6 +228,36 @@ size_t saa_generate_moments_workspace_size(const saa_ctx* ctx, const saa_problem
 saa_status saa_generate_moments(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, saa_prec prec,
                                 double* sum, double* sumsq, void* ws, size_t ws_bytes, void* stream);
 
+/* The newsvendor's Monte Carlo gradient (Sec. 3.2, the approximated
+ * gradient), for n products with normal demands:
+ *   grad_kj = (k_j - v_j) + (h_j + v_j) * (count_kj / S),
+ *   count_kj = #{s < S : z_js <= tau_kj},  tau_kj = RN_f32((x_kj - mu_j) / sigma_j)
+ * (subtraction and division in FP64), z_js the generator's FP32 normals on
+ * counter (s / 4, j, epoch, (3 << 24) | instance), element s mod 4 -- the
+ * comparison d_js = mu_j + sigma_j z_js <= x_kj taken on the standardised
+ * demand in one fixed precision, so the counts are exact integers.
+ *   X     device [K*n] FP64, K decision vectors (1 <= K <= 8), row-major
+ *   grad  device [K*n] FP64 output
+ *   ws    device scratch of saa_newsvendor_workspace_size() bytes (the
+ *         counts, uint32 [K][n]), 4-byte aligned
+ * Deterministic.  A sigma_j that is not positive is flagged on the device
+ * (SAA_EDEVICE at the next saa_ctx_sync). */
+typedef struct {
+    int64_t n;            /* products, 1 <= n < 2^32 */
+    int64_t S;            /* demand samples per product, 1 <= S < 2^30 */
+    uint64_t seed;        /* Philox key */
+    uint32_t instance;    /* stream id (counter word 3, low 24 bits) */
+    uint32_t epoch;       /* resample index (counter word 2) */
+    const double* mu;     /* device [n] demand means */
+    const double* sigma;  /* device [n] demand standard deviations, > 0 */
+    const double* k;      /* device [n] unit ordering costs */
+    const double* h;      /* device [n] unit holding costs */
+    const double* v;      /* device [n] unit shortage costs */
+} saa_newsvendor;
+size_t saa_newsvendor_workspace_size(const saa_newsvendor* prob, int32_t K);
+saa_status saa_newsvendor_grad(saa_ctx* ctx, const saa_newsvendor* prob, int32_t K, const double* X, double* grad,
+                               void* ws, size_t ws_bytes, void* stream);
+
 /* Lower Cholesky factor C of Sigma (C C' = Sigma), the map from standard
  * normals to the samples of the normal law of Sec. 3.1 (R = mu + C z): the
  * `chol` input of saa_problem.  FP64, blocked right-looking factorization

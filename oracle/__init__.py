@@ -129,6 +129,9 @@ def lib():
             L.oracle_newsvendor_demands.restype = C.c_int
             L.oracle_newsvendor_grad.argtypes = [nvp, C.c_int, dp, dp, C.POINTER(C.c_int64)]
             L.oracle_newsvendor_grad.restype = C.c_int
+            L.oracle_newsvendor_grad_range.argtypes = [nvp, C.c_int, dp, C.c_int64, C.c_int64, dp,
+                                                       C.POINTER(C.c_int64)]
+            L.oracle_newsvendor_grad_range.restype = C.c_int
             L.oracle_cholesky.argtypes = [C.c_int, dp, dp]
             L.oracle_cholesky.restype = C.c_int
             L.oracle_rse.argtypes = [C.c_double, C.c_double]
@@ -321,12 +324,15 @@ def newsvendor_demands(prob, j):
     return z
 
 
-def newsvendor_grad(prob, X):
-    """Monte Carlo gradient estimates [K, n] at decisions X [K, n], and the counts."""
+def newsvendor_grad(prob, X, products=None):
+    """Monte Carlo gradient estimates [K, m] at decisions X [K, n], and the
+    counts, for all products or for the range products = (j0, j1)."""
     P, keep = prob
     X = np.ascontiguousarray(np.atleast_2d(X), dtype=np.float64)
     K = X.shape[0]
-    g = np.empty_like(X)
-    cnt = np.empty(X.shape, np.int64)
-    _check(lib().oracle_newsvendor_grad(C.byref(P), K, _p(X), _p(g), _p(cnt, C.c_int64)), "newsvendor_grad")
+    j0, j1 = (0, P.n) if products is None else products
+    g = np.empty((K, j1 - j0))
+    cnt = np.empty((K, j1 - j0), np.int64)
+    _check(lib().oracle_newsvendor_grad_range(C.byref(P), K, _p(X), j0, j1, _p(g), _p(cnt, C.c_int64)),
+           "newsvendor_grad")
     return g, cnt

@@ -983,14 +983,17 @@ int oracle_newsvendor_demands(const oracle_newsvendor* p, int64_t j, float* z)
     return OR_OK;
 }
 
-/* Gradient estimates grad[K][n] at the K decisions X[K][n]; counts[K][n]
- * (optional) receives the number of samples with z <= tau. */
-int oracle_newsvendor_grad(const oracle_newsvendor* p, int K, const double* X, double* grad, int64_t* counts)
+/* Gradient estimates at the K decisions X[K][n] for the products j0 <= j < j1:
+ * grad[K][j1 - j0] and counts[K][j1 - j0] (optional, the number of samples
+ * with z <= tau). */
+int oracle_newsvendor_grad_range(const oracle_newsvendor* p, int K, const double* X, int64_t j0, int64_t j1,
+                                 double* grad, int64_t* counts)
 {
     if (check_newsvendor(p) != OR_OK || K < 1 || K > 64 || !X || !grad || !p->k || !p->h || !p->v) return OR_EINVAL;
-    const int64_t n = p->n;
+    if (j0 < 0 || j1 > p->n || j0 >= j1) return OR_EINVAL;
+    const int64_t n = p->n, m = j1 - j0;
 #pragma omp parallel for schedule(static)
-    for (int64_t j = 0; j < n; ++j) {
+    for (int64_t j = j0; j < j1; ++j) {
         float tau[64];
         int64_t cnt[64];
         for (int kk = 0; kk < K; ++kk) {
@@ -1006,11 +1009,18 @@ int oracle_newsvendor_grad(const oracle_newsvendor* p, int K, const double* X, d
         }
         for (int kk = 0; kk < K; ++kk) {
             const double frac = (double)cnt[kk] / (double)p->S;
-            grad[(size_t)kk * n + j] = (p->k[j] - p->v[j]) + (p->h[j] + p->v[j]) * frac;
-            if (counts) counts[(size_t)kk * n + j] = cnt[kk];
+            grad[(size_t)kk * m + (j - j0)] = (p->k[j] - p->v[j]) + (p->h[j] + p->v[j]) * frac;
+            if (counts) counts[(size_t)kk * m + (j - j0)] = cnt[kk];
         }
     }
     return OR_OK;
+}
+
+/* All products: grad[K][n], counts[K][n] (optional). */
+int oracle_newsvendor_grad(const oracle_newsvendor* p, int K, const double* X, double* grad, int64_t* counts)
+{
+    if (!p) return OR_EINVAL;
+    return oracle_newsvendor_grad_range(p, K, X, 0, p->n, grad, counts);
 }
 
 double oracle_rse(double y_t, double y_star)

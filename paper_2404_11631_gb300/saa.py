@@ -48,6 +48,21 @@ class _CProblem(C.Structure):
     ]
 
 
+class _CNewsvendor(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64),
+        ("S", C.c_int64),
+        ("seed", C.c_uint64),
+        ("instance", C.c_uint32),
+        ("epoch", C.c_uint32),
+        ("mu", C.c_void_p),
+        ("sigma", C.c_void_p),
+        ("k", C.c_void_p),
+        ("h", C.c_void_p),
+        ("v", C.c_void_p),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 _ctx: dict[int, C.c_void_p] = {}
@@ -92,6 +107,11 @@ def lib():
             L.saa_generate_moments_workspace_size.restype = sz
             L.saa_generate_moments.argtypes = [vp, pp, C.c_int64, C.c_int64, C.c_int, vp, vp, vp, sz, vp]
             L.saa_generate_moments.restype = C.c_int
+            nvp = C.POINTER(_CNewsvendor)
+            L.saa_newsvendor_workspace_size.argtypes = [nvp, C.c_int32]
+            L.saa_newsvendor_workspace_size.restype = sz
+            L.saa_newsvendor_grad.argtypes = [vp, nvp, C.c_int32, vp, vp, vp, sz, vp]
+            L.saa_newsvendor_grad.restype = C.c_int
             L.saa_cholesky.argtypes = [vp, C.c_int32, vp, vp, vp]
             L.saa_cholesky.restype = C.c_int
             L.saa_batch_workspace_size.argtypes = [vp, C.c_int32, pp, C.POINTER(C.c_int32), C.c_int, C.c_int]
@@ -303,6 +323,54 @@ def saa_generate_moments(prob: Problem, i0: int, n: int, prec="fp32", out: dict 
     return {"sum": s1, "sumsq": s2, "ws": ws}
 
 
+@dataclass
+class Newsvendor:
+    """Newsvendor problem of Sec. 3.2 with normal demands: n products, S
+    demand samples each; mu, sigma, k (ordering), h (holding), v (shortage)
+    are [n] float64 CUDA tensors."""
+
+    mu: torch.Tensor
+    sigma: torch.Tensor
+    k: torch.Tensor
+    h: torch.Tensor
+    v: torch.Tensor
+    S: int
+    seed: int = 0
+    instance: int = 0
+    epoch: int = 0
+
+    @property
+    def n(self) -> int:
+        return int(self.mu.shape[0])
+
+    def c_struct(self) -> _CNewsvendor:
+        ts = (self.mu, self.sigma, self.k, self.h, self.v)
+        for t in ts:
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.shape == (self.n,)):
+                raise ValueError("newsvendor arrays must be contiguous float64 CUDA tensors of shape [n]")
+        return _CNewsvendor(self.n, self.S, self.seed, self.instance, self.epoch, *[t.data_ptr() for t in ts])
+
+
+def saa_newsvendor_grad(prob: Newsvendor, X: torch.Tensor, return_counts: bool = False):
+    """Monte Carlo gradient of the newsvendor cost at K decision vectors X [K, n]."""
+    dev = prob.mu.device
+    X = X if X.dim() == 2 else X.unsqueeze(0)
+    if not (X.is_cuda and X.dtype == torch.float64 and X.is_contiguous() and X.shape[1] == prob.n):
+        raise ValueError("X must be a contiguous float64 CUDA tensor [K, n]")
+    K = int(X.shape[0])
+    cp = prob.c_struct()
+    need = lib().saa_newsvendor_workspace_size(C.byref(cp), K)
+    if need == 0:
+        raise SAAError(SAA_EINVAL, lib().saa_last_error().decode())
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    g = torch.empty(K, prob.n, dtype=torch.float64, device=dev)
+    _check(lib().saa_newsvendor_grad(context(dev.index), C.byref(cp), K, _ptr(X), _ptr(g), _ptr(ws), ws.numel(),
+                                     _stream(dev)))
+    if return_counts:
+        return g, ws.view(torch.int32).view(K, prob.n)
+    return g
+
+
 def saa_cholesky(sigma: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
     """Lower Cholesky factor C of Sigma (C C' = Sigma) on the device, the
     ``chol`` of :class:`Problem`; ``out`` may be ``sigma`` itself (in place)."""
@@ -436,4 +504,4 @@ EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_
             "saa_profile_enable", "saa_profile_read", "saa_eval_batched", "saa_workspace_size_batched",
             "saa_ctx_set_autotune", "saa_selftest_timeout", "saa_cholesky", "saa_generate_moments",
             "saa_generate_moments_workspace_size", "saa_batch_workspace_size", "saa_batch_create",
-            "saa_batch_launch", "saa_batch_destroy"]
+            "saa_batch_launch", "saa_batch_destroy", "saa_newsvendor_workspace_size", "saa_newsvendor_grad"]
