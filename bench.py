@@ -9,7 +9,9 @@ N = 2^20 Gaussian scenarios, K = 64, timed the same way, and "fw":
 Algorithm 1 (saa_solve) for 200 iterations on d = 1024, N = 2^22 Student-t
 scenarios regenerated every iteration, "ragged": 4096 independent
 instances in one graph-replayed persistent launch, and "newsvendor": the
-Monte Carlo gradient of Sec. 3.2 for 10^6 products x 1000 demand samples.
+Monte Carlo gradient of Sec. 3.2 for 10^6 products x 1000 demand samples,
+and "covariance_first": the value workload through saa_moments +
+saa_eval_moments (value, and value with gradient).
 
 Workload (default): d = 128 assets, N = 2^20 scenarios (first half Gaussian,
 second half standardised lognormal sigma = 1), K = 256 candidate decisions
@@ -377,6 +379,56 @@ def run_newsvendor(args, dev, world, rank, flush, stream):
                          "note": "generator-only kernel's instructions per normal + 2 per sample and decision"}}
 
 
+def run_covariance(args, dev, world, rank, flush, stream):
+    """Covariance-first form on the value workload (d = 128, N = 2^20 half
+    Gaussian / half lognormal, K = 256): one step is saa_moments (the sums
+    M = sum_i a_i a_i', mt = sum_i a_i on the tensor cores) plus
+    saa_eval_moments for all K decisions, value only and value + gradient."""
+    import torch
+    from paper_2404_11631_gb300 import inputs, saa
+    d, N, K, law = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["K"], WORKLOAD["law"]
+    prec = args.prec if args.prec in ("f16x3", "bf16x3") else "f16x3"
+    inst = inputs.instance(d, 0)
+    prob = saa.Problem(mu=torch.tensor(inst.mu, device=dev), chol=torch.tensor(inst.chol, device=dev), N=N, law=law,
+                       seed=0, instance=rank)
+    X = torch.tensor(inputs.decisions(K, d, 0), device=dev)
+    mws = torch.empty(1 << 26, dtype=torch.uint8, device=dev)
+    ews = torch.empty(1 << 24, dtype=torch.uint8, device=dev)
+    res = {}
+    for mode, grad in (("value", False), ("value_and_gradient", True)):
+        def step():
+            mom = saa.saa_moments(prob, prec, ws=mws)
+            return saa.saa_eval_moments(prob, X, mom, want_grad=grad, ws=ews)
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize(dev)
+        saa.saa_profile_enable(True, dev.index)
+        steps = max(3, min(args.steps, 50))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        main_ms, main_n, launched = saa.saa_profile_read(dev.index)
+        saa.saa_profile_enable(False, dev.index)
+        total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        kern_s = main_ms / 1e3 / max(1, main_n)
+        peaks, _ = _peaks()
+        mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = 152 * 128 * mhz * 1e6 / 1e12
+        ops = float(N) * d * (_gen_per_normal(law) + SPLIT_OPS)
+        res[mode] = {"value": world * N * K * steps / total_s, "unit": "evals/s", "ms_per_step": 1e3 * total_s / steps,
+                     "gram_kernel_ms": kern_s * 1e3, "gpu_launches_per_step": launched / steps,
+                     "roofline": {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                                  "frac": ops / kern_s / 1e12 / peak,
+                                  "note": "Gram kernel: generator-only kernel's instructions per normal + split"}}
+    return {"metric": "scenario-decision evals/s (covariance-first)", "config": {
+        "workload": WORKLOAD["name"], "d": d, "N": N, "K": K, "prec": prec,
+        "method": "M = sum a a' once on tcgen05, then S2 = y'My, G = My per decision in FP64"}, **res}
+
+
 def run_gen(args):
     """The bare generator (saa_generate_moments, FP32 mode) on the value
     workload's d and N, per law: normals/s.  This is the generator-only
@@ -585,6 +637,8 @@ def run_ours(args):
         line["ragged"] = run_ragged(args, dev, world, rank, flush, stream)
     if not args.no_newsvendor:
         line["newsvendor"] = run_newsvendor(args, dev, world, rank, flush, stream)
+    if not args.no_cov:
+        line["covariance_first"] = run_covariance(args, dev, world, rank, flush, stream)
     if rank == 0:
         line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -618,6 +672,8 @@ def main():
     ap.add_argument("--ragged-B", type=int, default=4096, help="instances of the ragged batch (profiling small cases)")
     ap.add_argument("--ragged-only", action="store_true", help="run only the ragged batch")
     ap.add_argument("--no-newsvendor", action="store_true", help="skip the newsvendor gradient workload")
+    ap.add_argument("--no-cov", action="store_true", help="skip the covariance-first workload")
+    ap.add_argument("--cov-only", action="store_true", help="run only the covariance-first workload")
     ap.add_argument("--nv-only", action="store_true", help="run only the newsvendor gradient workload")
     ap.add_argument("--nv-n", type=int, default=None, help="override the newsvendor product count")
     ap.add_argument("--fw-N", type=int, default=None, help="override the Algorithm 1 scenario count")
@@ -649,6 +705,12 @@ def main():
     if args.nv_n:
         NV_WORKLOAD["n"] = args.nv_n
         NV_WORKLOAD["name"] = f"newsvendor_n{args.nv_n}_S{NV_WORKLOAD['S']}_K1"
+    if args.cov_only:
+        import torch
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps(run_covariance(args, dev, 1, 0, flush, torch.cuda.current_stream(dev))), flush=True)
+        return 0
     if args.nv_only:
         import torch
         dev = torch.device("cuda", 0)

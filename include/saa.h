@@ -228,6 +228,29 @@ size_t saa_generate_moments_workspace_size(const saa_ctx* ctx, const saa_problem
 saa_status saa_generate_moments(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, saa_prec prec,
                                 double* sum, double* sumsq, void* ws, size_t ws_bytes, void* stream);
 
+/* Covariance-first form (Sec. 3.1: the sample mean and covariance formed
+ * once per resample), for d <= 128 on the tensor cores.  With the whitened
+ * samples a_i = s_i zhat_i of resample prob->epoch:
+ *   saa_moments       M = sum_i a_i a_i' (device [d*d] FP64, row-major) and
+ *                     mt = sum_i a_i (device [d] FP64); prec SAA_F16X3 or
+ *                     SAA_BF16X3 (the hi/lo operand type of A'A).  Scratch:
+ *                     saa_moments_workspace_size() bytes, 256-byte aligned.
+ *   saa_eval_moments  for K decisions X [K*d]: y_k = C'w_k, S1 = mt'y_k,
+ *                     S2 = y_k'M y_k, and f, pbar, var (each optional) as
+ *                     saa_eval computes them, plus grad [K*d] (optional) =
+ *                     C[lambda 2/(N-1) (M y_k - S1 m) - m] - mu, m = mt/N,
+ *                     all in FP64.  Scratch: saa_eval_moments_workspace_size().
+ * The moments' work does not depend on K: evaluating many decisions, or
+ * many iterations of Algorithm 1 on one resample, costs K d^2 FP64
+ * multiply-adds each after one saa_moments.  EUNSUPPORTED for d > 128. */
+size_t saa_moments_workspace_size(const saa_ctx* ctx, const saa_problem* prob, saa_prec prec);
+saa_status saa_moments(saa_ctx* ctx, const saa_problem* prob, saa_prec prec, double* M, double* mt, void* ws,
+                       size_t ws_bytes, void* stream);
+size_t saa_eval_moments_workspace_size(const saa_problem* prob, int32_t K);
+saa_status saa_eval_moments(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, const double* M,
+                            const double* mt, double* f, double* pbar, double* var, double* grad, void* ws,
+                            size_t ws_bytes, void* stream);
+
 /* The newsvendor's Monte Carlo gradient (Sec. 3.2, the approximated
  * gradient), for n products with normal demands:
  *   grad_kj = (k_j - v_j) + (h_j + v_j) * (count_kj / S),

@@ -102,6 +102,9 @@ cudaError_t launch_simt(const LawArgs& la, int K, int prec, int want_grad, const
 cudaError_t launch_finalize(const saa_problem* p, int K, int prec, int want_grad, const Plan& plan,
                             const Workspace& ws, double* f, double* pbar, double* var, double* grad,
                             cudaStream_t st);
+// grad_kj = sum_{l <= j} C_jl u_kl - mu_j (FP64, one warp per output).
+cudaError_t launch_grad_out(int K, int d, const double* chol, const double* mu, const double* u, double* grad,
+                            cudaStream_t st);
 cudaError_t launch_generate(const LawArgs& la, int64_t i0, int64_t n, int prec, const double* mu,
                             const double* chol, void* z, void* s, void* xi, cudaStream_t st);
 cudaError_t launch_fw_step(int d, const double* g, const double* f, double* w, const int64_t* t_dev,

@@ -590,6 +590,13 @@ __global__ void k_grad_out(int K, int d, const double* __restrict__ C, const dou
   if (lane == 0) grad[(size_t)k * d + j] = s - mu[j];
 }
 
+cudaError_t launch_grad_out(int K, int d, const double* chol, const double* mu, const double* u, double* grad,
+                            cudaStream_t st) {
+  const int64_t warps = (int64_t)K * d;
+  k_grad_out<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(K, d, chol, mu, u, grad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const saa_problem* p, int K, int prec, int want_grad, const Plan& plan,
                             const Workspace& ws, double* f, double* pbar, double* var, double* grad,
                             cudaStream_t st) {

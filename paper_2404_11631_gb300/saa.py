@@ -112,6 +112,14 @@ def lib():
             L.saa_newsvendor_workspace_size.restype = sz
             L.saa_newsvendor_grad.argtypes = [vp, nvp, C.c_int32, vp, vp, vp, sz, vp]
             L.saa_newsvendor_grad.restype = C.c_int
+            L.saa_moments_workspace_size.argtypes = [vp, pp, C.c_int]
+            L.saa_moments_workspace_size.restype = sz
+            L.saa_moments.argtypes = [vp, pp, C.c_int, vp, vp, vp, sz, vp]
+            L.saa_moments.restype = C.c_int
+            L.saa_eval_moments_workspace_size.argtypes = [pp, C.c_int32]
+            L.saa_eval_moments_workspace_size.restype = sz
+            L.saa_eval_moments.argtypes = [vp, pp, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+            L.saa_eval_moments.restype = C.c_int
             L.saa_cholesky.argtypes = [vp, C.c_int32, vp, vp, vp]
             L.saa_cholesky.restype = C.c_int
             L.saa_batch_workspace_size.argtypes = [vp, C.c_int32, pp, C.POINTER(C.c_int32), C.c_int, C.c_int]
@@ -371,6 +379,49 @@ def saa_newsvendor_grad(prob: Newsvendor, X: torch.Tensor, return_counts: bool =
     return g
 
 
+def saa_moments(prob: Problem, prec="f16x3", ws: torch.Tensor | None = None) -> dict:
+    """Covariance-first sums of the whitened samples of resample prob.epoch:
+    {'M': [d, d] = sum_i a_i a_i', 'mt': [d] = sum_i a_i} (float64)."""
+    dev = prob.device
+    cp = prob.c_struct()
+    ctx = context(dev.index)
+    need = lib().saa_moments_workspace_size(ctx, C.byref(cp), _prec(prec))
+    if need == 0:
+        raise SAAError(SAA_EINVAL, lib().saa_last_error().decode())
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    M = torch.empty(prob.d, prob.d, dtype=torch.float64, device=dev)
+    mt = torch.empty(prob.d, dtype=torch.float64, device=dev)
+    _check(lib().saa_moments(ctx, C.byref(cp), _prec(prec), _ptr(M), _ptr(mt), _ptr(ws), ws.numel(), _stream(dev)))
+    return {"M": M, "mt": mt}
+
+
+def saa_eval_moments(prob: Problem, X: torch.Tensor, moments: dict, want_grad: bool = True,
+                     ws: torch.Tensor | None = None) -> dict:
+    """Eq. 4 (f, pbar, var) and, with want_grad, its gradient for the K
+    decisions X [K, d] from the moments of saa_moments."""
+    X = _decisions(X, prob)
+    K = int(X.shape[0])
+    dev = prob.device
+    cp = prob.c_struct()
+    need = lib().saa_eval_moments_workspace_size(C.byref(cp), K)
+    if need == 0:
+        raise SAAError(SAA_EINVAL, "saa_eval_moments: invalid problem size")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    f = torch.empty(K, dtype=torch.float64, device=dev)
+    pb = torch.empty_like(f)
+    var = torch.empty_like(f)
+    g = torch.empty(K, prob.d, dtype=torch.float64, device=dev) if want_grad else None
+    _check(lib().saa_eval_moments(context(dev.index), C.byref(cp), K, _ptr(X), _ptr(moments["M"]),
+                                  _ptr(moments["mt"]), _ptr(f), _ptr(pb), _ptr(var), _ptr(g), _ptr(ws), ws.numel(),
+                                  _stream(dev)))
+    out = {"f": f, "pbar": pb, "var": var}
+    if want_grad:
+        out["grad"] = g
+    return out
+
+
 def saa_cholesky(sigma: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
     """Lower Cholesky factor C of Sigma (C C' = Sigma) on the device, the
     ``chol`` of :class:`Problem`; ``out`` may be ``sigma`` itself (in place)."""
@@ -504,4 +555,5 @@ EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_
             "saa_profile_enable", "saa_profile_read", "saa_eval_batched", "saa_workspace_size_batched",
             "saa_ctx_set_autotune", "saa_selftest_timeout", "saa_cholesky", "saa_generate_moments",
             "saa_generate_moments_workspace_size", "saa_batch_workspace_size", "saa_batch_create",
-            "saa_batch_launch", "saa_batch_destroy", "saa_newsvendor_workspace_size", "saa_newsvendor_grad"]
+            "saa_batch_launch", "saa_batch_destroy", "saa_newsvendor_workspace_size", "saa_newsvendor_grad",
+            "saa_moments_workspace_size", "saa_moments", "saa_eval_moments_workspace_size", "saa_eval_moments"]
