@@ -429,6 +429,63 @@ def run_covariance(args, dev, world, rank, flush, stream):
         "method": "M = sum a a' once on tcgen05, then S2 = y'My, G = My per decision in FP64"}, **res}
 
 
+def run_streamed(args, dev, world, rank, flush, stream):
+    """Streamed mode on the value workload's shape (d = 128, N = 2^20,
+    K = 256): the N samples R_i are materialised once in HBM as FP32 rows
+    (by saa_generate, outside the timed region) and every step reads them
+    back through TMA into the tensor-core contraction (saa_eval_samples,
+    center mu, sigma = sqrt(diag Sigma)).  The 512 MB sample matrix is
+    larger than L2, so each step streams it from HBM."""
+    import torch
+    from paper_2404_11631_gb300 import inputs, saa
+    d, N, K, law = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["K"], WORKLOAD["law"]
+    prec = args.prec if args.prec in ("f16x3", "bf16x3") else "f16x3"
+    inst = inputs.instance(d, 0)
+    prob = saa.Problem(mu=torch.tensor(inst.mu, device=dev), chol=torch.tensor(inst.chol, device=dev), N=N, law=law,
+                       seed=0, instance=rank)
+    R = saa.saa_generate(prob, 0, N, "fp32", want_xi=True)["xi"]
+    X = torch.tensor(inputs.decisions(K, d, 0), device=dev)
+    sd = torch.tensor(np.sqrt(np.diag(inst.sigma)), device=dev)
+    ws = saa.saa_eval_samples(R, X, prob.lam, prec, center=prob.mu, sigma=sd)["ws"]
+    for _ in range(3):
+        saa.saa_eval_samples(R, X, prob.lam, prec, center=prob.mu, sigma=sd, ws=ws)
+    torch.cuda.synchronize(dev)
+    saa.saa_profile_enable(True, dev.index)
+    steps = max(3, min(args.steps, 50))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        ev[i][0].record(stream)
+        saa.saa_eval_samples(R, X, prob.lam, prec, center=prob.mu, sigma=sd, ws=ws)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    main_ms, main_n, launched = saa.saa_profile_read(dev.index)
+    saa.saa_profile_enable(False, dev.index)
+    saa.saa_ctx_sync(dev.index)
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    kern_s = main_ms / 1e3 / max(1, main_n)
+    peaks, src = _peaks()
+    hbm_bytes = float(N) * d * 4                 # d FP32 values per scenario, one pass
+    tc_flops = 3.0 * 2.0 * N * d * K             # three split products of 2 N d K
+    t_hbm = hbm_bytes / (peaks["hbm_gbs"] * 1e9)
+    t_tc = tc_flops / (peaks["bf16_tflops"] * 1e12)
+    if t_tc >= t_hbm:
+        roof = {"bound": "tensor", "achieved": tc_flops / kern_s / 1e12, "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": tc_flops / kern_s / 1e12 / peaks["bf16_tflops"]}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_bytes / kern_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm_bytes / kern_s / 1e9 / peaks["hbm_gbs"]}
+    roof["peak_source"] = src
+    roof["hbm"] = {"achieved_gbs": hbm_bytes / kern_s / 1e9, "frac": hbm_bytes / kern_s / 1e9 / peaks["hbm_gbs"]}
+    roof["tensor"] = {"achieved_tflops": tc_flops / kern_s / 1e12,
+                      "frac": tc_flops / kern_s / 1e12 / peaks["bf16_tflops"]}
+    del R
+    return {"metric": "scenario-decision evals/s (streamed samples)", "value": world * N * K * steps / total_s,
+            "unit": "evals/s", "ms_per_step": 1e3 * total_s / steps, "stream_kernel_ms": kern_s * 1e3,
+            "gpu_launches_per_step": launched / steps, "roofline": roof,
+            "config": {"workload": "streamed_" + WORKLOAD["name"], "d": d, "N": N, "K": K, "prec": prec,
+                       "samples": "FP32 [N, d] in HBM (512 MB > L2), center mu, sigma sqrt(diag Sigma)"}}
+
+
 def run_gen(args):
     """The bare generator (saa_generate_moments, FP32 mode) on the value
     workload's d and N, per law: normals/s.  This is the generator-only
@@ -639,6 +696,8 @@ def run_ours(args):
         line["newsvendor"] = run_newsvendor(args, dev, world, rank, flush, stream)
     if not args.no_cov:
         line["covariance_first"] = run_covariance(args, dev, world, rank, flush, stream)
+    if not args.no_streamed:
+        line["streamed"] = run_streamed(args, dev, world, rank, flush, stream)
     if rank == 0:
         line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -675,6 +734,8 @@ def main():
     ap.add_argument("--no-cov", action="store_true", help="skip the covariance-first workload")
     ap.add_argument("--cov-only", action="store_true", help="run only the covariance-first workload")
     ap.add_argument("--nv-only", action="store_true", help="run only the newsvendor gradient workload")
+    ap.add_argument("--no-streamed", action="store_true", help="skip the streamed-samples workload")
+    ap.add_argument("--streamed-only", action="store_true", help="run only the streamed-samples workload")
     ap.add_argument("--nv-n", type=int, default=None, help="override the newsvendor product count")
     ap.add_argument("--fw-N", type=int, default=None, help="override the Algorithm 1 scenario count")
     ap.add_argument("--fw-T", type=int, default=None, help="override the Algorithm 1 iteration count")
@@ -710,6 +771,11 @@ def main():
         dev = torch.device("cuda", 0)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
         print(json.dumps(run_covariance(args, dev, 1, 0, flush, torch.cuda.current_stream(dev))), flush=True)
+        return 0
+    if args.streamed_only:
+        import torch
+        dev = torch.device("cuda", 0)
+        print(json.dumps(run_streamed(args, dev, 1, 0, None, torch.cuda.current_stream(dev))), flush=True)
         return 0
     if args.nv_only:
         import torch

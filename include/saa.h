@@ -208,6 +208,41 @@ void saa_batch_destroy(saa_batch* batch);
 saa_status saa_generate(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, saa_prec prec, void* z_out,
                         void* s_out, void* xi_out, void* stream);
 
+/* Streamed mode: Eq. 4 / Eq. 5 on samples held in device memory instead of
+ * regenerated (the sample set {R_i} of Sec. 3.1 materialised, e.g. by
+ * saa_generate's xi_out or supplied by the caller), for d <= 256 and
+ * K <= 256 on the tensor cores, the sample tiles brought in by TMA.
+ *   R        device [N*d] FP32, row-major (scenario i = row i); 16-byte
+ *            aligned, d a multiple of 4 (rows of 16-byte multiples)
+ *   center   device [d] FP64 or NULL (0): subtracted from every row before
+ *            the split-precision contraction, in FP32; p_ik = c'x_k +
+ *            (R_i - c)'x_k with c = center rounded to FP32, so the result
+ *            does not depend on it beyond rounding; pass the samples' mean
+ *            (or mu): without it the FP32 accumulation error of the
+ *            contraction, relative to |R_i'x_k|, reaches V multiplied by
+ *            (pbar^2 + V) / V
+ *   sigma    device [d] FP64 or NULL (1): per-column spreads; column j is
+ *            multiplied by 2^-a_j and x_kj by 2^a_j, 2^(a_j-1) < sigma_j <=
+ *            2^a_j (exact), so the split products stay in range.  At
+ *            SAA_F16X3 every |R_ij - c_j| 2^-a_j must be below 2^15
+ *            (violations and sigma_j outside [2^-100, 2^100] or not finite
+ *            are reported by the next saa_ctx_sync as SAA_EDEVICE)
+ *   X        device [K*d] FP64 decisions w_k (the scenario vector already
+ *            holds the returns: no mu or C is applied)
+ *   lambda   risk weight of Eq. 2
+ *   prec     SAA_F16X3 or SAA_BF16X3 (operand type of the hi/lo products)
+ *   f, pbar, var  device [K] FP64, each optional: lambda V - pbar, the
+ *            sample mean of R_i'x_k, and its unbiased sample variance
+ *   ws       device scratch of saa_eval_samples_workspace_size() bytes,
+ *            256-byte aligned
+ * 2 <= N < 2^31.  The workspace query returns 0 for invalid or unsupported
+ * arguments; the call returns SAA_EINVAL / SAA_EUNSUPPORTED for them.
+ * Deterministic for a given device and N. */
+size_t saa_eval_samples_workspace_size(const saa_ctx* ctx, int64_t N, int32_t d, int32_t K, saa_prec prec);
+saa_status saa_eval_samples(saa_ctx* ctx, int64_t N, int32_t d, const float* R, const double* center,
+                            const double* sigma, int32_t K, const double* X, double lambda, saa_prec prec,
+                            double* f, double* pbar, double* var, void* ws, size_t ws_bytes, void* stream);
+
 /* Moments of the generator: per-dimension sums of the innovations zhat_ij
  * (after the law transform, before the t law's scale s_i) and of their
  * squares over scenarios i0 .. i0+n-1 of resample index prob->epoch, drawn

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
   const int my_tiles = (int)((a.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
   const int iters = my_tiles * a.nkb;
   float macc[NKB][8];             // RNG warps: per-dimension sums of a_i (NKB >= a.nkb)
-  double s2acc[kMaxKp / 32];      // epilogue warps: S2 of column c0 + lane, c0 = 32 g
+  float s2h[kMaxKp / 32], s2l[kMaxKp / 32];   // epilogue warps: S2 of column 32 g + lane (float-float)
 
   if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA ---
@@ -184,39 +184,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
     // ------------------------------------------------------- epilogue ---
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
 #pragma unroll
-    for (int g = 0; g < kMaxKp / 32; ++g) s2acc[g] = 0.0;
+    for (int g = 0; g < kMaxKp / 32; ++g) s2h[g] = s2l[g] = 0.0f;
     for (int tt = 0; tt < my_tiles; ++tt) {
       if (!warp_wait(smem_u32(&sm->q_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
       tc_fence_after();
-#pragma unroll 1
-      for (int g = 0; g < kMaxKp / 32; ++g) {
-        if (32 * g >= a.Kp) break;
-        const uint32_t c0 = (uint32_t)(32 * g);
-        uint32_t r1[32], r2[32];
-        tmem_ld32(td1 + lane_base + c0, r1);
-        tmem_ld32(td2 + lane_base + c0, r2);
-        tmem_wait_ld();
-        float v[32];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float q = __uint_as_float(r1[i]) + __uint_as_float(r2[i]);
-          v[i] = q * q;
+      for (int g = 0; g < kMaxKp / 32; ++g)
+        if (32 * g < a.Kp) {
+          const uint32_t c0 = (uint32_t)(32 * g);
+          ff_add(s2h[g], s2l[g], epi_sq_colsum32(td1 + lane_base + c0, td2 + lane_base + c0, lane));
         }
-        // reduce-scatter over the warp's 32 rows: lane l ends with column c0 + l
-#pragma unroll
-        for (int w = 16; w >= 1; w >>= 1) {
-          const bool upper = (lane & w) != 0;
-#pragma unroll
-          for (int i = 0; i < w; ++i) {
-            const float send = upper ? v[i] : v[i + w];
-            const float keep = upper ? v[i + w] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-          }
-        }
-#pragma unroll
-        for (int h = 0; h < kMaxKp / 32; ++h)
-          if (h == g) s2acc[h] += (double)v[0];
-      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty));
@@ -322,7 +299,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
   if (warp < kEpiWarps) {
 #pragma unroll
     for (int g = 0; g < kMaxKp / 32; ++g)
-      if (32 * g < a.Kp) red_s2[warp * a.Kp + 32 * g + lane] = s2acc[g];
+      if (32 * g < a.Kp) red_s2[warp * a.Kp + 32 * g + lane] = (double)s2h[g] + (double)s2l[g];
   }
   __syncthreads();
   for (int j = threadIdx.x; j < d; j += blockDim.x) {

@@ -183,6 +183,52 @@ __device__ __forceinline__ float2 unpack2(uint32_t w) {
   }
 }
 
+// Error-free float addition (Knuth's TwoSum): the pair hi + lo carries a
+// running sum to about 2^-44 relative without the narrow FP64 pipe.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+
+// Column sums of q^2, q = D1 + D2, over a warp's 32 TMEM lanes (rows) for
+// the 32 columns at t1 / t2 (lane quadrant already in the address): lane l
+// returns column l's sum.  Each 16-column half is reduce-scattered over
+// lanes (xor 8, 4, 2, 1: lane l ends with column l & 15 of its 16 rows),
+// then one exchange across xor 16 joins the halves' two row groups.
+__device__ __forceinline__ float epi_sq_colsum32(uint32_t t1, uint32_t t2, int lane) {
+  float u[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t r1[16], r2[16];
+    tmem_ld16(t1 + 16u * h, r1);
+    tmem_ld16(t2 + 16u * h, r2);
+    tmem_wait_ld();
+    float v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float q = __uint_as_float(r1[i]) + __uint_as_float(r2[i]);
+      v[i] = q * q;
+    }
+#pragma unroll
+    for (int w = 8; w >= 1; w >>= 1) {
+      const bool upper = (lane & w) != 0;
+#pragma unroll
+      for (int i = 0; i < w; ++i) {
+        const float send = upper ? v[i] : v[i + w];
+        const float keep = upper ? v[i + w] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+      }
+    }
+    u[h] = v[0];
+  }
+  const bool upper = (lane & 16) != 0;
+  const float send = upper ? u[0] : u[1];
+  const float keep = upper ? u[1] : u[0];
+  return keep + __shfl_xor_sync(0xffffffffu, send, 16);
+}
+
 // Warp-uniform bounded wait (tcgen05.ld/st are warp-collective).
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
                                           uint32_t* err) {

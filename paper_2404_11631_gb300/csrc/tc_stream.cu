@@ -1,0 +1,614 @@
+// tc_stream.cu -- saa_eval_samples: Eq. 4 on samples held in device memory
+// (the streamed form of the estimate: scenarios read from HBM instead of
+// regenerated), on tcgen05 tensor cores fed by TMA tensor loads.
+//
+// For samples R_i (FP32, [N][d] row-major), a center c (the caller's mean
+// estimate, or 0), per-column spreads sigma (or 1) and decisions x_k:
+//   p_ik = c'x_k + sum_j v_ij x'_kj,  v_ij = (R_ij - c_j) 2^-a_j,
+//   x'_kj = x_kj 2^a_j,  2^(a_j - 1) < sigma_j <= 2^a_j.
+// The power-of-two scaling is exact; it keeps the operands of the split
+// products in the normal range of the 16-bit types.  The contraction
+// Q_ik = v_i'x'_k runs in split precision like the value kernel;
+// S1_k = m~'x'_k with m~ = sum_i v_i and S2_k = sum_i Q_ik^2 give p_bar, V
+// and f_hat as in saa_eval.  Centring keeps the variance well-conditioned
+// when the samples' mean is far from 0.
+//
+// Per CTA (one per SM, persistent over 128-row tiles), per 64-column K block:
+//   producer   one thread loads the block's two FP32 boxes (columns 0-31 and
+//              32-63, 128 rows, 128-byte swizzle) by TMA tensor loads into
+//              the two 16 KB halves of a stage;
+//   converters 16 warps; the four threads of each row read their 16 values,
+//              subtract c, split them into hi + lo of the operand type and,
+//              after a warp sync, write hi over the first half's row and lo
+//              over the second half's row -- exactly the K-major 128-byte
+//              swizzled layout tcgen05.mma reads (no other thread touches the
+//              row, so the conversion is in place);
+//   MMA and epilogue as in the value kernel (hi*hi into D1, corrections
+//              into D2, S2 reduce-scatter in FP64 registers).
+// m~ comes from the converters: each warp reduce-scatters its 8 rows by
+// shuffles, every lane keeps float-float running sums of its two columns per
+// K block, and the CTA folds its 16 warps in warp order at the end
+// (deterministic).  Every wait is bounded.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace saa {
+namespace tc {
+
+constexpr int kSM = 128;                  // rows (scenarios) per tile = MMA M
+constexpr int kSKB = 64;                  // columns per K block
+constexpr int kSStages = 3;
+constexpr int kSStageBytes = 2 * kSM * 128;   // two 16 KB halves (FP32 boxes in, hi/lo out)
+constexpr int kSEpi = 4;
+constexpr int kSMma = 4;
+constexpr int kSProd = 5;
+constexpr int kSConv = 16;                // converter warps (8 rows each)
+constexpr int kSThreads = 32 * (6 + kSConv);
+constexpr int kSMaxKp = 256;
+
+struct SArgs {
+  int d, K, Kp, nkb;
+  uint32_t N;
+  int64_t tiles;
+  const float* cf;        // [dpad] center in FP32 (0 past d)
+  const float* isf;       // [dpad] 2^-a_j (0 past d)
+  const uint8_t* bimage;  // [nkb][hi, lo][Kp][128 B]
+  const double* scale2;   // [K]
+  double* part_s2;        // [grid][K]
+  double* part_m;         // [grid][dpad]
+  uint32_t* err;
+};
+
+struct SSmem {
+  uint64_t ld_full[kSStages];
+  uint64_t a_full[kSStages];
+  uint64_t a_empty[kSStages];
+  uint64_t q_full, q_empty, b_full, drain;
+  uint32_t tmem_base;
+  uint32_t abort_flag;
+};
+
+size_t stream_smem_bytes(int Kp, int nkb) {
+  return (size_t)kSStages * kSStageBytes + (size_t)nkb * 2 * Kp * 128 + sizeof(SSmem) +
+         2 * sizeof(float) * (size_t)nkb * kSKB;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+template <bool F16, int NKB>
+__global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const uint32_t base = smem_u32(smem_raw);
+  if (base & 1023u) {
+    if (threadIdx.x == 0) atomicOr(a.err, kErrBounds);
+    return;
+  }
+  const int bbytes = a.nkb * 2 * a.Kp * 128;
+  uint8_t* As = smem_raw;
+  SSmem* sm = reinterpret_cast<SSmem*>(smem_raw + kSStages * kSStageBytes + bbytes);
+  const int dpad = a.nkb * kSKB;
+  float* s_cf = reinterpret_cast<float*>(sm + 1);   // [dpad]
+  float* s_is = s_cf + dpad;                        // [dpad]
+  const uint32_t sA = base, sB = base + (uint32_t)(kSStages * kSStageBytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile uint32_t* abort_flag = &sm->abort_flag;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSStages; ++s) {
+      mbar_init(smem_u32(&sm->ld_full[s]), 1);
+      mbar_init(smem_u32(&sm->a_full[s]), kSConv);
+      mbar_init(smem_u32(&sm->a_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&sm->q_full), 1);
+    mbar_init(smem_u32(&sm->q_empty), kSEpi);
+    mbar_init(smem_u32(&sm->b_full), 1);
+    mbar_init(smem_u32(&sm->drain), 1);
+    sm->abort_flag = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int j = threadIdx.x; j < dpad; j += blockDim.x) {
+    s_cf[j] = a.cf[j];
+    s_is[j] = a.isf[j];
+  }
+  const uint32_t ncols = (2 * a.Kp <= 64) ? 64u : (2 * a.Kp <= 128) ? 128u : (2 * a.Kp <= 256) ? 256u : 512u;
+  if (warp == kSMma) tmem_alloc(smem_u32(&sm->tmem_base), ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm->tmem_base;
+  const uint32_t td1 = tmem, td2 = tmem + (uint32_t)a.Kp;
+  const int my_tiles = (int)((a.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+  const int iters = my_tiles * a.nkb;
+  float s2h[kSMaxKp / 32], s2l[kSMaxKp / 32];   // epilogue: S2 of column 32 g + lane (float-float)
+  float mh[NKB][2], ml[NKB][2];                   // converters: m~ of the lane's two columns per K block
+
+  if (warp == kSMma) {
+    // ------------------------------------------------------------ MMA ---
+    if (lane == 0) {
+      const uint32_t bb = smem_u32(&sm->b_full);
+      mbar_expect_tx(bb, (uint32_t)bbytes);
+      for (int off = 0; off < bbytes; off += 32768) {
+        const int n = min(32768, bbytes - off);
+        bulk_g2s(sB + (uint32_t)off, a.bimage + off, (uint32_t)n, bb);
+      }
+      bool ok = mbar_wait(bb, 0, abort_flag, a.err);
+      const bool b_landed = ok;
+      const uint32_t idesc = idesc_f16(kSM, a.Kp, F16);
+      const uint32_t hl_b = (uint32_t)(a.Kp * 128);
+      int tt = 0, kb = 0, st = 0;
+      uint32_t ph = 0;
+      for (int it = 0; ok && it < iters; ++it) {
+        if (kb == 0 && tt > 0) {
+          ok = mbar_wait(smem_u32(&sm->q_empty), (uint32_t)((tt - 1) & 1), abort_flag, a.err);
+          if (!ok) break;
+        }
+        ok = mbar_wait(smem_u32(&sm->a_full[st]), ph, abort_flag, a.err);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t a_hi = sA + (uint32_t)(st * kSStageBytes);
+        const uint32_t a_lo = a_hi + kSM * 128;
+        const uint32_t b_hi = sB + (uint32_t)(kb * 2) * hl_b;
+        const uint32_t b_lo = b_hi + hl_b;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t o = (uint32_t)(kk * 32);
+          const uint32_t acc0 = (kb == 0 && kk == 0) ? 0u : 1u;
+          mma_bf16(td1, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idesc, acc0);
+          mma_bf16(td2, desc_sw128(a_hi + o), desc_sw128(b_lo + o), idesc, acc0);
+          mma_bf16(td2, desc_sw128(a_lo + o), desc_sw128(b_hi + o), idesc, 1u);
+        }
+        mma_commit(smem_u32(&sm->a_empty[st]));
+        if (kb == a.nkb - 1) mma_commit(smem_u32(&sm->q_full));
+        if (++kb == a.nkb) { kb = 0; ++tt; }
+        if (++st == kSStages) { st = 0; ph ^= 1u; }
+      }
+      mma_commit(smem_u32(&sm->drain));
+      uint32_t never = 0u;
+      mbar_wait(smem_u32(&sm->drain), 0, &never, a.err);
+      if (!b_landed) mbar_wait(bb, 0, &never, a.err);
+    }
+    __syncwarp();
+  } else if (warp == kSProd) {
+    // ------------------------------------------------------- producer ---
+    if (lane == 0) {
+      int tt = 0, kb = 0, st = 0;
+      uint32_t ph = 0, issued = 0, lpar = 0;   // stages with loads, parity of the next load per stage
+      for (int it = 0; it < iters; ++it) {
+        if (!mbar_wait(smem_u32(&sm->a_empty[st]), ph ^ 1u, abort_flag, a.err)) break;
+        const uint32_t tile = blockIdx.x + (uint32_t)tt * gridDim.x;
+        const uint32_t fb = smem_u32(&sm->ld_full[st]);
+        mbar_expect_tx(fb, (uint32_t)kSStageBytes);
+        const uint32_t dst = sA + (uint32_t)(st * kSStageBytes);
+        tma_load_2d(dst, &tmap, kb * kSKB, (int)(tile * kSM), fb);
+        tma_load_2d(dst + (uint32_t)(kSM * 128), &tmap, kb * kSKB + 32, (int)(tile * kSM), fb);
+        issued |= 1u << st;
+        lpar ^= 1u << st;
+        if (++kb == a.nkb) { kb = 0; ++tt; }
+        if (++st == kSStages) { st = 0; ph ^= 1u; }
+      }
+      // the last load into each stage has landed before the CTA moves on
+      uint32_t never = 0u;
+      for (int s = 0; s < kSStages; ++s)
+        if ((issued >> s) & 1u) mbar_wait(smem_u32(&sm->ld_full[s]), ((lpar >> s) & 1u) ^ 1u, &never, a.err);
+    }
+    __syncwarp();
+  } else if (warp < kSEpi) {
+    // ------------------------------------------------------- epilogue ---
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+    for (int g = 0; g < kSMaxKp / 32; ++g) s2h[g] = s2l[g] = 0.0f;
+    for (int tt = 0; tt < my_tiles; ++tt) {
+      if (!warp_wait(smem_u32(&sm->q_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
+      tc_fence_after();
+#pragma unroll
+      for (int g = 0; g < kSMaxKp / 32; ++g)
+        if (32 * g < a.Kp) {
+          const uint32_t c0 = (uint32_t)(32 * g);
+          ff_add(s2h[g], s2l[g], epi_sq_colsum32(td1 + lane_base + c0, td2 + lane_base + c0, lane));
+        }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty));
+    }
+  } else {
+    // ----------------------------------------------------- converters ---
+    const int cw = warp - (kSProd + 1);            // 0 .. 15: rows 8 cw .. 8 cw + 7
+    const int r = 8 * cw + (lane >> 2);            // row of the tile
+    const int q = lane & 3;                        // columns 16 q .. 16 q + 15 of the K block
+    const int box = q >> 1, u0 = (q & 1) * 4;      // FP32 box and its first 16-byte unit
+    // Box-1 threads (q = 2, 3) visit their 16-byte units in the order
+    // uu ^ 2, so that no two threads of a quarter-warp hit the same banks in
+    // the two boxes; their v[] then holds the two 8-column halves swapped.
+    const int hsw = q >> 1;
+    const int rr2 = ((lane >> 1) & 14) ^ (8 * hsw);   // m~ columns owned (within the 16)
+#pragma unroll
+    for (int b = 0; b < NKB; ++b) mh[b][0] = mh[b][1] = ml[b][0] = ml[b][1] = 0.0f;
+    bool in_range = true;
+    int tt = 0, kb = 0, st = 0;
+    uint32_t ph = 0;
+    for (int it = 0; it < iters; ++it) {
+      if (!warp_wait(smem_u32(&sm->ld_full[st]), ph, abort_flag, a.err)) break;
+      const uint32_t tile = blockIdx.x + (uint32_t)tt * gridDim.x;
+      const bool row_ok = (uint32_t)r < a.N - tile * (uint32_t)kSM;
+      uint8_t* stage = As + st * kSStageBytes;
+      const uint8_t* rowp = stage + box * (kSM * 128) + r * 128;
+      const int j0 = kb * kSKB + 16 * q;
+      float v[16];
+#pragma unroll
+      for (int uu = 0; uu < 4; ++uu) {
+        const int uc = uu ^ (2 * hsw);
+        const float4 t = *reinterpret_cast<const float4*>(rowp + (((u0 + uc) ^ (r & 7)) << 4));
+        const float4 c = *reinterpret_cast<const float4*>(s_cf + j0 + 4 * uc);
+        const float4 w = *reinterpret_cast<const float4*>(s_is + j0 + 4 * uc);
+        v[4 * uu + 0] = (t.x - c.x) * w.x;
+        v[4 * uu + 1] = (t.y - c.y) * w.y;
+        v[4 * uu + 2] = (t.z - c.z) * w.z;
+        v[4 * uu + 3] = (t.w - c.w) * w.w;
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        v[e] = row_ok ? v[e] : 0.0f;
+        if constexpr (F16) in_range = in_range && fabsf(v[e]) < 32768.0f;
+      }
+      uint32_t hi[8], lo[8];
+#pragma unroll
+      for (int e = 0; e < 16; e += 2) {
+        hi[e / 2] = pack2<F16>(v[e], v[e + 1]);
+        const float2 h = unpack2<F16>(hi[e / 2]);
+        lo[e / 2] = pack2<F16>(v[e] - h.x, v[e + 1] - h.y);
+      }
+      __syncwarp();   // every thread of these rows has read its FP32 values
+      uint8_t* hrow = stage;                    // hi over the first half
+      uint8_t* lrow = stage + kSM * 128;        // lo over the second half
+      const int ua = 2 * q + hsw, ub = 2 * q + 1 - hsw;   // units of v[0..7] and v[8..15]
+      *reinterpret_cast<uint4*>(hrow + sw_off(r, ua)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(hrow + sw_off(r, ub)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+      *reinterpret_cast<uint4*>(lrow + sw_off(r, ua)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      *reinterpret_cast<uint4*>(lrow + sw_off(r, ub)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&sm->a_full[st]));
+      // m~: reduce-scatter of the warp's 8 rows (lanes 4 apart share the
+      // columns); lane (row rr, quarter q) ends with v[2 rr], v[2 rr + 1]
+#pragma unroll
+      for (int w = 16; w >= 4; w >>= 1) {
+        const bool upper = (lane & w) != 0;
+        const int hw = w >> 1;   // values kept: 8, 4, 2
+#pragma unroll
+        for (int e = 0; e < hw; ++e) {
+          const float send = upper ? v[e] : v[e + hw];
+          const float keep = upper ? v[e + hw] : v[e];
+          v[e] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < NKB; ++b)
+        if (b == kb) {
+          ff_add(mh[b][0], ml[b][0], v[0]);
+          ff_add(mh[b][1], ml[b][1], v[1]);
+        }
+      if (++kb == a.nkb) { kb = 0; ++tt; }
+      if (++st == kSStages) { st = 0; ph ^= 1u; }
+    }
+    if (!in_range) atomicOr(a.err, kErrInput);
+  }
+
+  // ----------------------------------------------------- CTA reductions ---
+  __syncthreads();   // MMAs drained, loads landed: the A stages are free
+  double* red_s2 = reinterpret_cast<double*>(As);   // [kSEpi][Kp]
+  double* red_m = red_s2 + kSEpi * a.Kp;            // [kSConv][dpad]
+  if (warp < kSEpi) {
+#pragma unroll
+    for (int g = 0; g < kSMaxKp / 32; ++g)
+      if (32 * g < a.Kp) red_s2[warp * a.Kp + 32 * g + lane] = (double)s2h[g] + (double)s2l[g];
+  } else if (warp > kSProd) {
+    const int cw = warp - (kSProd + 1);
+    const int col = 16 * (lane & 3) + (((lane >> 1) & 14) ^ (8 * ((lane & 3) >> 1)));
+#pragma unroll
+    for (int b = 0; b < NKB; ++b)
+      if (b < a.nkb) {
+        red_m[cw * dpad + b * kSKB + col] = (double)mh[b][0] + (double)ml[b][0];
+        red_m[cw * dpad + b * kSKB + col + 1] = (double)mh[b][1] + (double)ml[b][1];
+      }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < dpad; j += blockDim.x) {
+    double t = 0.0;
+#pragma unroll 4
+    for (int w = 0; w < kSConv; ++w) t += red_m[w * dpad + j];
+    a.part_m[(size_t)blockIdx.x * dpad + j] = t;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < kSEpi; ++w) s += red_s2[w * a.Kp + k];
+    a.part_s2[(size_t)blockIdx.x * a.K + k] = s * a.scale2[k];
+  }
+  if (warp == kSMma) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
+}  // namespace tc
+
+namespace {
+
+// Power-of-two exponent a with 2^(a-1) < sigma <= 2^a; -1000 for a spread
+// that is not a positive finite number in [2^-100, 2^100].
+__device__ __forceinline__ int spread_exp(double sigma) {
+  if (!(sigma > 0.0) || !isfinite(sigma)) return -1000;
+  int e;
+  const double m = frexp(sigma, &e);   // sigma = m 2^e, m in [0.5, 1)
+  if (m == 0.5) --e;                   // an exact power of two keeps its own exponent
+  return (e < -100 || e > 100) ? -1000 : e;
+}
+
+// Operands of the streamed kernel: cf = center in FP32, isf = 2^-a_j (both 0
+// past d), Xs = x_kj 2^a_j.
+__global__ void k_stream_prep(int K, int d, int dpad, const double* __restrict__ center,
+                              const double* __restrict__ sigma, const double* __restrict__ X, float* __restrict__ cf,
+                              float* __restrict__ isf, double* __restrict__ Xs, uint32_t* err) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < dpad) {
+    const int j = (int)t;
+    int e = 0;
+    if (j < d && sigma) {
+      e = spread_exp(sigma[j]);
+      if (e == -1000) {
+        atomicOr(err, kErrInput);
+        e = 0;
+      }
+    }
+    cf[j] = (j < d && center) ? (float)center[j] : 0.0f;
+    isf[j] = (j < d) ? ldexpf(1.0f, -e) : 0.0f;
+  } else if (t < dpad + (int64_t)K * d) {
+    const int64_t u = t - dpad;
+    const int j = (int)(u % d);
+    int e = sigma ? spread_exp(sigma[j]) : 0;
+    if (e == -1000) e = 0;
+    Xs[u] = ldexp(X[u], e);
+  }
+}
+
+// m~_j = sum over CTAs of their slot-0 totals: one block per 32 columns,
+// warp w adds CTAs w, w + 8, ... and the eight warp sums are merged in warp
+// order (deterministic).  Plain FP64 adds: the partials are FP64 sums of
+// FP32 values, so the rounding of a few hundred adds is far below FP32's.
+__global__ void __launch_bounds__(256) k_stream_mfinal(int grid, int dpad, const double* __restrict__ part_m,
+                                                       double* __restrict__ tot_m) {
+  __shared__ double sh[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  for (int g = warp; g < grid; g += 8) s += part_m[(size_t)g * dpad + j];
+  sh[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += sh[w][lane];
+    tot_m[j] = t;
+  }
+}
+
+// One warp per decision: S2_k over the CTAs' partials, c_k = fl32(center)'x_k
+// (the center the kernel subtracted), S1_k = m~'x'_k, then the outputs of
+// Eq. 4.  Lane-strided FP64 sums merged by a fixed shuffle tree.
+__global__ void __launch_bounds__(256) k_stream_out(int grid, int K, int d, double N, double lambda,
+                                                    const double* __restrict__ part_s2,
+                                                    const double* __restrict__ tot_m, const float* __restrict__ cf,
+                                                    const double* __restrict__ X, const double* __restrict__ Xs,
+                                                    double* __restrict__ f, double* __restrict__ pbar,
+                                                    double* __restrict__ var) {
+  const int k = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= K) return;
+  double s2 = 0.0, c = 0.0, s1 = 0.0;
+  for (int g = lane; g < grid; g += 32) s2 += part_s2[(size_t)g * K + k];
+  for (int j = lane; j < d; j += 32) {
+    c = fma((double)cf[j], X[(size_t)k * d + j], c);
+    s1 = fma(tot_m[j], Xs[(size_t)k * d + j], s1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if (lane == 0) {
+    const double qbar = s1 / N;
+    const double pb = c + qbar;
+    const double V = (s2 - s1 * qbar) / (N - 1.0);
+    if (f) f[k] = lambda * V - pb;
+    if (pbar) pbar[k] = pb;
+    if (var) var[k] = V;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+std::mutex g_enc_mu;
+EncodeTiledFn g_encode = nullptr;
+
+saa_status encode_fn(EncodeTiledFn* out) {
+  std::lock_guard<std::mutex> lock(g_enc_mu);
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+      set_error("saa_eval_samples: cuTensorMapEncodeTiled is not available");
+      return SAA_ECUDA;
+    }
+    g_encode = (EncodeTiledFn)fn;
+  }
+  *out = g_encode;
+  return SAA_OK;
+}
+
+struct SPlan {
+  int Kp, nkb, grid, smem, dpad;
+  int64_t tiles;
+  size_t img, s2, pm, cf, xs, tots, total;
+};
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+SPlan stream_plan(const saa_ctx* ctx, int64_t N, int d, int K) {
+  SPlan p;
+  p.Kp = (K + 31) / 32 * 32;
+  p.nkb = (d + tc::kSKB - 1) / tc::kSKB;
+  p.dpad = p.nkb * tc::kSKB;
+  p.tiles = (N + tc::kSM - 1) / tc::kSM;
+  p.grid = (int)(p.tiles < ctx->sm_count ? p.tiles : ctx->sm_count);
+  p.smem = (int)tc::stream_smem_bytes(p.Kp, p.nkb);
+  size_t off = 0;
+  p.img = off; off = a256(off + (size_t)p.nkb * 2 * p.Kp * 128 + 8 * (size_t)K);
+  p.s2 = off; off = a256(off + 8 * (size_t)p.grid * K);
+  p.pm = off; off = a256(off + 8 * (size_t)p.grid * p.dpad);
+  p.cf = off; off = a256(off + 4 * 2 * (size_t)p.dpad);
+  p.xs = off; off = a256(off + 8 * (size_t)K * d);
+  p.tots = off; off = a256(off + 8 * (size_t)p.dpad);
+  p.total = off;
+  return p;
+}
+
+saa_status stream_check(const saa_ctx* ctx, int64_t N, int d, int K, saa_prec prec) {
+  if (!ctx) {
+    set_error("saa_eval_samples: ctx is NULL");
+    return SAA_EINVAL;
+  }
+  if (N < 2 || N >= (int64_t)1 << 31 || d < 4 || (d & 3) || K < 1) {
+    set_error("saa_eval_samples: need 2 <= N < 2^31, d >= 4 a multiple of 4 (16-byte rows for TMA), K >= 1");
+    return SAA_EINVAL;
+  }
+  if (!is_tc(prec)) {
+    set_error("saa_eval_samples: streamed samples run at SAA_F16X3 or SAA_BF16X3");
+    return SAA_EUNSUPPORTED;
+  }
+  const SPlan p = stream_plan(ctx, N, d, K);
+  if (d > 256 || p.Kp > tc::kSMaxKp || (size_t)p.nkb * 2 * p.Kp * 128 > 128 * 1024 || p.smem > ctx->smem_optin) {
+    set_error("saa_eval_samples: needs d <= 256, K <= 256 and a decision image of at most 128 KB");
+    return SAA_EUNSUPPORTED;
+  }
+  return SAA_OK;
+}
+
+}  // namespace
+}  // namespace saa
+
+using namespace saa;
+
+extern "C" size_t saa_eval_samples_workspace_size(const saa_ctx* ctx, int64_t N, int32_t d, int32_t K,
+                                                  saa_prec prec) {
+  if (stream_check(ctx, N, d, K, prec) != SAA_OK) return 0;
+  return stream_plan(ctx, N, d, K).total;
+}
+
+extern "C" saa_status saa_eval_samples(saa_ctx* ctx, int64_t N, int32_t d, const float* R, const double* center,
+                                       const double* sigma, int32_t K, const double* X, double lambda,
+                                       saa_prec prec, double* f, double* pbar, double* var, void* ws,
+                                       size_t ws_bytes, void* stream) {
+  saa_status s = stream_check(ctx, N, d, K, prec);
+  if (s != SAA_OK) return s;
+  if (!R || (((uintptr_t)R) & 15u) || !X || !ws || (((uintptr_t)ws) & 255u)) {
+    set_error("saa_eval_samples: R (16-byte aligned), X and a 256-byte aligned ws are required");
+    return SAA_EINVAL;
+  }
+  const SPlan p = stream_plan(ctx, N, d, K);
+  if (ws_bytes < p.total) {
+    set_error("saa_eval_samples: workspace smaller than saa_eval_samples_workspace_size()");
+    return SAA_ENOMEM;
+  }
+  EncodeTiledFn encode = nullptr;
+  s = encode_fn(&encode);
+  if (s != SAA_OK) return s;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) {
+    set_error("saa_eval_samples: cudaSetDevice failed");
+    return SAA_ECUDA;
+  }
+  // 2-D map of R: inner dimension d (FP32, rows of 4 d bytes), outer N;
+  // boxes of 32 columns x 128 rows with the 128-byte swizzle; zero fill
+  CUtensorMap tmap;
+  std::memset(&tmap, 0, sizeof(tmap));
+  const cuuint64_t gdim[2] = {(cuuint64_t)d, (cuuint64_t)N};
+  const cuuint64_t gstride[1] = {(cuuint64_t)d * 4};
+  const cuuint32_t box[2] = {32, (cuuint32_t)tc::kSM};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult cr = encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)R, gdim, gstride, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    set_error("saa_eval_samples: cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
+    return SAA_ECUDA;
+  }
+  char* w = (char*)ws;
+  uint8_t* img = (uint8_t*)(w + p.img);
+  double* scale2 = (double*)(img + (size_t)p.nkb * 2 * p.Kp * 128);
+  double* part_s2 = (double*)(w + p.s2);
+  double* part_m = (double*)(w + p.pm);
+  float* cf = (float*)(w + p.cf);
+  float* isf = cf + p.dpad;
+  double* Xs = (double*)(w + p.xs);
+  double* tot_m = (double*)(w + p.tots);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f16 = prec == SAA_F16X3;
+  const int64_t nprep = p.dpad + (int64_t)K * d;
+  k_stream_prep<<<(unsigned)((nprep + 255) / 256), 256, 0, st>>>(K, d, p.dpad, center, sigma, X, cf, isf, Xs,
+                                                                ctx->err);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_tc_image(d, K, p.Kp, p.nkb, f16, Xs, scale2, nullptr, img, st);
+  tc::SArgs a;
+  a.d = d;
+  a.K = K;
+  a.Kp = p.Kp;
+  a.nkb = p.nkb;
+  a.N = (uint32_t)N;
+  a.tiles = p.tiles;
+  a.cf = cf;
+  a.isf = isf;
+  a.bimage = img;
+  a.scale2 = scale2;
+  a.part_s2 = part_s2;
+  a.part_m = part_m;
+  a.err = ctx->err;
+  auto kern = f16 ? (p.nkb == 1 ? tc::k_tc_stream<true, 1> : p.nkb == 2 ? tc::k_tc_stream<true, 2>
+                                                                        : tc::k_tc_stream<true, 4>)
+                  : (p.nkb == 1 ? tc::k_tc_stream<false, 1> : p.nkb == 2 ? tc::k_tc_stream<false, 2>
+                                                                         : tc::k_tc_stream<false, 4>);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+  const bool prof = ctx->prof_on && ctx->prof_n < 256;
+  if (e == cudaSuccess) {
+    if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], st);
+    kern<<<p.grid, tc::kSThreads, p.smem, st>>>(a, tmap);
+    e = cudaGetLastError();
+    if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n++ + 1], st);
+  }
+  if (e == cudaSuccess) {
+    k_stream_mfinal<<<p.dpad / 32, 256, 0, st>>>(p.grid, p.dpad, part_m, tot_m);
+    k_stream_out<<<(K * 32 + 255) / 256, 256, 0, st>>>(p.grid, K, d, (double)N, lambda, part_s2, tot_m, cf, X, Xs, f,
+                                                       pbar, var);
+    e = cudaGetLastError();
+  }
+  ctx->kernels += 5;
+  if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+  return cuda_status(e, "saa_eval_samples: launch");
+}

@@ -11,6 +11,11 @@ Law parameters follow the mean-variance task of Sec. 3.1 (R ~ N(mu, Sigma)):
 * ``paper_instance``: the setup of Sec. 4.1 for the asset task,
   mu_i ~ U(-1,1), sigma_i ~ U(0, 0.025), diagonal Sigma.
 * ``decisions``: K candidate decisions x ~ U[0,1]^d.
+* ``sample_matrix``: a materialised sample set {R_i} (FP32 rows) for the
+  streamed mode, R_i = mu + C z_i with z_i drawn by numpy (standard normal,
+  or Student-t with 4 degrees of freedom for the second half when
+  ``heavy``).  These are plain numpy draws standing in for scenario data the
+  caller already holds; they are not the estimator's in-kernel law.
 """
 from __future__ import annotations
 
@@ -53,6 +58,22 @@ def decisions(K: int, d: int, seed: int = 0) -> np.ndarray:
     """K candidate decisions x ~ U[0,1]^d, row-major [K, d]."""
     rng = np.random.default_rng([seed, d, K, 3])
     return rng.uniform(0.0, 1.0, size=(K, d))
+
+
+def sample_matrix(N: int, d: int, seed: int = 0, inst_seed: int = 0, heavy: bool = False,
+                  chunk: int = 1 << 16) -> tuple[np.ndarray, Instance]:
+    """(R [N, d] float32 row-major, the Instance whose mu and C shaped it)."""
+    inst = instance(d, inst_seed)
+    rng = np.random.default_rng([seed, N, d, 4])
+    R = np.empty((N, d), dtype=np.float32)
+    for i0 in range(0, N, chunk):
+        n = min(chunk, N - i0)
+        z = rng.standard_normal((n, d))
+        if heavy:
+            tail = np.arange(i0, i0 + n) >= N // 2
+            z[tail] = rng.standard_t(4.0, size=(int(tail.sum()), d))
+        R[i0:i0 + n] = inst.mu + z @ inst.chol.T
+    return R, inst
 
 
 def fw_start(d: int) -> np.ndarray:

@@ -120,6 +120,11 @@ def lib():
             L.saa_eval_moments_workspace_size.restype = sz
             L.saa_eval_moments.argtypes = [vp, pp, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
             L.saa_eval_moments.restype = C.c_int
+            L.saa_eval_samples_workspace_size.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32, C.c_int]
+            L.saa_eval_samples_workspace_size.restype = sz
+            L.saa_eval_samples.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, vp, C.c_int32, vp, C.c_double, C.c_int,
+                                           vp, vp, vp, vp, sz, vp]
+            L.saa_eval_samples.restype = C.c_int
             L.saa_cholesky.argtypes = [vp, C.c_int32, vp, vp, vp]
             L.saa_cholesky.restype = C.c_int
             L.saa_batch_workspace_size.argtypes = [vp, C.c_int32, pp, C.POINTER(C.c_int32), C.c_int, C.c_int]
@@ -422,6 +427,41 @@ def saa_eval_moments(prob: Problem, X: torch.Tensor, moments: dict, want_grad: b
     return out
 
 
+def saa_eval_samples(R: torch.Tensor, X: torch.Tensor, lam: float, prec="f16x3",
+                     center: torch.Tensor | None = None, sigma: torch.Tensor | None = None,
+                     ws: torch.Tensor | None = None) -> dict:
+    """Streamed mode: Eq. 4 (f, pbar, var) over samples held in device
+    memory, R [N, d] float32 (scenario i = row i), for the decisions X [K, d]
+    float64.  ``center`` [d] float64 (e.g. the samples' mean) is subtracted
+    before the split-precision contraction and ``sigma`` [d] float64 (e.g.
+    per-column standard deviations) sets the exact power-of-two column
+    scaling; neither changes the result beyond rounding."""
+    if not (R.is_cuda and R.dtype == torch.float32 and R.is_contiguous() and R.dim() == 2):
+        raise ValueError("R must be a contiguous float32 CUDA tensor [N, d]")
+    N, d = int(R.shape[0]), int(R.shape[1])
+    if X.dim() == 1:
+        X = X.unsqueeze(0)
+    if not (X.is_cuda and X.dtype == torch.float64 and X.is_contiguous() and X.shape[1] == d):
+        raise ValueError("X must be a contiguous float64 CUDA tensor [K, d]")
+    for name, v in (("center", center), ("sigma", sigma)):
+        if v is not None and not (v.is_cuda and v.dtype == torch.float64 and v.is_contiguous() and v.numel() == d):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor [d]")
+    K = int(X.shape[0])
+    dev = R.device
+    ctx = context(dev.index)
+    need = lib().saa_eval_samples_workspace_size(ctx, N, d, K, _prec(prec))
+    if need == 0:
+        raise SAAError(SAA_EINVAL, lib().saa_last_error().decode())
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    f = torch.empty(K, dtype=torch.float64, device=dev)
+    pb = torch.empty_like(f)
+    var = torch.empty_like(f)
+    _check(lib().saa_eval_samples(ctx, N, d, _ptr(R), _ptr(center), _ptr(sigma), K, _ptr(X), float(lam), _prec(prec),
+                                  _ptr(f), _ptr(pb), _ptr(var), _ptr(ws), ws.numel(), _stream(dev)))
+    return {"f": f, "pbar": pb, "var": var, "ws": ws}
+
+
 def saa_cholesky(sigma: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
     """Lower Cholesky factor C of Sigma (C C' = Sigma) on the device, the
     ``chol`` of :class:`Problem`; ``out`` may be ``sigma`` itself (in place)."""
@@ -556,4 +596,5 @@ EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_
             "saa_ctx_set_autotune", "saa_selftest_timeout", "saa_cholesky", "saa_generate_moments",
             "saa_generate_moments_workspace_size", "saa_batch_workspace_size", "saa_batch_create",
             "saa_batch_launch", "saa_batch_destroy", "saa_newsvendor_workspace_size", "saa_newsvendor_grad",
-            "saa_moments_workspace_size", "saa_moments", "saa_eval_moments_workspace_size", "saa_eval_moments"]
+            "saa_moments_workspace_size", "saa_moments", "saa_eval_moments_workspace_size", "saa_eval_moments",
+            "saa_eval_samples_workspace_size", "saa_eval_samples"]
