@@ -188,12 +188,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
     for (int tt = 0; tt < my_tiles; ++tt) {
       if (!warp_wait(smem_u32(&sm->q_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
       tc_fence_after();
-#pragma unroll
-      for (int g = 0; g < kMaxKp / 32; ++g)
+      // the group loop stays rolled (register pressure); the running sums
+      // rotate so that group g's pair is s2h[0] / s2l[0] when it is added
+#pragma unroll 1
+      for (int g = 0; g < kMaxKp / 32; ++g) {
         if (32 * g < a.Kp) {
           const uint32_t c0 = (uint32_t)(32 * g);
-          ff_add(s2h[g], s2l[g], epi_sq_colsum32(td1 + lane_base + c0, td2 + lane_base + c0, lane));
+          ff_add(s2h[0], s2l[0], epi_sq_colsum32(td1 + lane_base + c0, td2 + lane_base + c0, lane));
         }
+        rot_left(s2h);
+        rot_left(s2l);
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty));

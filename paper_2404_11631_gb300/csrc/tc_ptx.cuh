@@ -194,39 +194,46 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
 
 // Column sums of q^2, q = D1 + D2, over a warp's 32 TMEM lanes (rows) for
 // the 32 columns at t1 / t2 (lane quadrant already in the address): lane l
-// returns column l's sum.  Each 16-column half is reduce-scattered over
-// lanes (xor 8, 4, 2, 1: lane l ends with column l & 15 of its 16 rows),
-// then one exchange across xor 16 joins the halves' two row groups.
+// returns column l's sum.  Reduce-scatter over the lanes: at each of the 5
+// levels a lane keeps half of its values and adds its partner's other half,
+// so lane l ends with column l.
 __device__ __forceinline__ float epi_sq_colsum32(uint32_t t1, uint32_t t2, int lane) {
-  float u[2];
+  float v[32];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < 2; ++h) {   // two 16-column loads keep fewer registers live
     uint32_t r1[16], r2[16];
     tmem_ld16(t1 + 16u * h, r1);
     tmem_ld16(t2 + 16u * h, r2);
     tmem_wait_ld();
-    float v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const float q = __uint_as_float(r1[i]) + __uint_as_float(r2[i]);
-      v[i] = q * q;
+      v[16 * h + i] = q * q;
     }
-#pragma unroll
-    for (int w = 8; w >= 1; w >>= 1) {
-      const bool upper = (lane & w) != 0;
-#pragma unroll
-      for (int i = 0; i < w; ++i) {
-        const float send = upper ? v[i] : v[i + w];
-        const float keep = upper ? v[i + w] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-      }
-    }
-    u[h] = v[0];
   }
-  const bool upper = (lane & 16) != 0;
-  const float send = upper ? u[0] : u[1];
-  const float keep = upper ? u[1] : u[0];
-  return keep + __shfl_xor_sync(0xffffffffu, send, 16);
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool upper = (lane & w) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float send = upper ? v[i] : v[i + w];
+      const float keep = upper ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
+}
+
+// Rotates a register array left by one (a[i] = a[i + 1], the first value
+// to the end).  Running sums for a group loop that is not unrolled stay in
+// registers this way: the current group's sum is always a[0], and n
+// rotations per pass over n entries restore the order.
+template <int N>
+__device__ __forceinline__ void rot_left(float (&a)[N]) {
+  const float t = a[0];
+#pragma unroll
+  for (int i = 0; i + 1 < N; ++i) a[i] = a[i + 1];
+  a[N - 1] = t;
 }
 
 // Warp-uniform bounded wait (tcgen05.ld/st are warp-collective).

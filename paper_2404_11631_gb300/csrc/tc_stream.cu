@@ -43,20 +43,25 @@ namespace tc {
 
 constexpr int kSM = 128;                  // rows (scenarios) per tile = MMA M
 constexpr int kSKB = 64;                  // columns per K block
-constexpr int kSStages = 3;
+constexpr int kSMaxStages = 6;            // stages in flight: as many as shared memory holds
 constexpr int kSStageBytes = 2 * kSM * 128;   // two 16 KB halves (FP32 boxes in, hi/lo out)
-constexpr int kSEpi = 4;
-constexpr int kSMma = 4;
-constexpr int kSProd = 5;
+#ifndef SAA_STREAM_EPI_WARPS
+#define SAA_STREAM_EPI_WARPS 8
+#endif
+constexpr int kSEpi = SAA_STREAM_EPI_WARPS;   // epilogue warps: 4 or 8 (two per TMEM lane quadrant)
+constexpr int kSEpiStride = kSEpi / 4;        // column groups are dealt round-robin over a quadrant's warps
+constexpr int kSMma = kSEpi;
+constexpr int kSProd = kSEpi + 1;
 constexpr int kSConv = 16;                // converter warps (8 rows each)
-constexpr int kSThreads = 32 * (6 + kSConv);
+constexpr int kSThreads = 32 * (kSEpi + 2 + kSConv);
+static_assert(kSEpi == 4 || kSEpi == 8, "4 or 8 epilogue warps");
 constexpr int kSMaxKp = 256;
 
 struct SArgs {
-  int d, K, Kp, nkb;
+  int d, K, Kp, nkb, nst;
   uint32_t N;
   int64_t tiles;
-  const float* cf;        // [dpad] center in FP32 (0 past d)
+  const float* ncs;       // [dpad] -fl32(c_j) 2^-a_j (0 past d)
   const float* isf;       // [dpad] 2^-a_j (0 past d)
   const uint8_t* bimage;  // [nkb][hi, lo][Kp][128 B]
   const double* scale2;   // [K]
@@ -65,17 +70,22 @@ struct SArgs {
   uint32_t* err;
 };
 
-struct SSmem {
-  uint64_t ld_full[kSStages];
-  uint64_t a_full[kSStages];
-  uint64_t a_empty[kSStages];
-  uint64_t q_full, q_empty, b_full, drain;
+// 16-byte aligned size: the FP32 center / scale arrays that follow it are
+// read as float4.
+struct alignas(16) SSmem {
+  uint64_t ld_full[kSMaxStages];
+  uint64_t a_full[kSMaxStages];
+  uint64_t a_empty[kSMaxStages];
+  uint64_t q_full[2], q_empty[2];   // accumulator slots: MMA -> epilogue, epilogue -> MMA
+  uint64_t b_full, drain;
   uint32_t tmem_base;
   uint32_t abort_flag;
 };
 
-size_t stream_smem_bytes(int Kp, int nkb) {
-  return (size_t)kSStages * kSStageBytes + (size_t)nkb * 2 * Kp * 128 + sizeof(SSmem) +
+static_assert(sizeof(SSmem) % 16 == 0, "the arrays after SSmem are read as float4");
+
+size_t stream_smem_bytes(int Kp, int nkb, int nst) {
+  return (size_t)nst * kSStageBytes + (size_t)nkb * 2 * Kp * 128 + sizeof(SSmem) +
          2 * sizeof(float) * (size_t)nkb * kSKB;
 }
 
@@ -97,41 +107,49 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
   }
   const int bbytes = a.nkb * 2 * a.Kp * 128;
   uint8_t* As = smem_raw;
-  SSmem* sm = reinterpret_cast<SSmem*>(smem_raw + kSStages * kSStageBytes + bbytes);
+  const int nst = a.nst;
+  SSmem* sm = reinterpret_cast<SSmem*>(smem_raw + nst * kSStageBytes + bbytes);
   const int dpad = a.nkb * kSKB;
-  float* s_cf = reinterpret_cast<float*>(sm + 1);   // [dpad]
+  float* s_cf = reinterpret_cast<float*>(sm + 1);   // [dpad] -c_j 2^-a_j
   float* s_is = s_cf + dpad;                        // [dpad]
-  const uint32_t sA = base, sB = base + (uint32_t)(kSStages * kSStageBytes);
+  const uint32_t sA = base, sB = base + (uint32_t)(nst * kSStageBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile uint32_t* abort_flag = &sm->abort_flag;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kSStages; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(smem_u32(&sm->ld_full[s]), 1);
       mbar_init(smem_u32(&sm->a_full[s]), kSConv);
       mbar_init(smem_u32(&sm->a_empty[s]), 1);
     }
-    mbar_init(smem_u32(&sm->q_full), 1);
-    mbar_init(smem_u32(&sm->q_empty), kSEpi);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(smem_u32(&sm->q_full[q]), 1);
+      mbar_init(smem_u32(&sm->q_empty[q]), kSEpi);
+    }
     mbar_init(smem_u32(&sm->b_full), 1);
     mbar_init(smem_u32(&sm->drain), 1);
     sm->abort_flag = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int j = threadIdx.x; j < dpad; j += blockDim.x) {
-    s_cf[j] = a.cf[j];
+    s_cf[j] = a.ncs[j];
     s_is[j] = a.isf[j];
   }
-  const uint32_t ncols = (2 * a.Kp <= 64) ? 64u : (2 * a.Kp <= 128) ? 128u : (2 * a.Kp <= 256) ? 256u : 512u;
+  // TMEM: two accumulator slots of 256 columns, each D1 (hi*hi) at +0 and
+  // D2 (hi*lo + lo*hi) at +128.  Kp <= 128: tiles alternate between the
+  // slots.  Kp > 128: a tile's decision columns split into halves [0, 128)
+  // (slot 0) and [128, Kp) (slot 1).  Either way the MMAs of the next slot
+  // run while the epilogue drains the other one.
+  const uint32_t ncols = 512u;
   if (warp == kSMma) tmem_alloc(smem_u32(&sm->tmem_base), ncols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sm->tmem_base;
-  const uint32_t td1 = tmem, td2 = tmem + (uint32_t)a.Kp;
+  const int nh = a.Kp > 128 ? 2 : 1;   // column halves per tile
   const int my_tiles = (int)((a.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
   const int iters = my_tiles * a.nkb;
-  float s2h[kSMaxKp / 32], s2l[kSMaxKp / 32];   // epilogue: S2 of column 32 g + lane (float-float)
+  float s2h[kSMaxKp / 32 / kSEpiStride], s2l[kSMaxKp / 32 / kSEpiStride];   // epilogue: S2 (float-float)
   float mh[NKB][2], ml[NKB][2];                   // converters: m~ of the lane's two columns per K block
 
   if (warp == kSMma) {
@@ -145,13 +163,18 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
       }
       bool ok = mbar_wait(bb, 0, abort_flag, a.err);
       const bool b_landed = ok;
-      const uint32_t idesc = idesc_f16(kSM, a.Kp, F16);
+      const uint32_t idesc0 = idesc_f16(kSM, nh == 2 ? 128 : a.Kp, F16);
+      const uint32_t idesc1 = idesc_f16(kSM, nh == 2 ? a.Kp - 128 : a.Kp, F16);
       const uint32_t hl_b = (uint32_t)(a.Kp * 128);
       int tt = 0, kb = 0, st = 0;
       uint32_t ph = 0;
       for (int it = 0; ok && it < iters; ++it) {
-        if (kb == 0 && tt > 0) {
-          ok = mbar_wait(smem_u32(&sm->q_empty), (uint32_t)((tt - 1) & 1), abort_flag, a.err);
+        // slot of the first (or only) half; its n-th use waits for the
+        // epilogue's (n-1)-th release
+        const int s0 = nh == 2 ? 0 : (tt & 1);
+        const int n0 = nh == 2 ? tt : (tt >> 1);
+        if (kb == 0 && n0 > 0) {
+          ok = mbar_wait(smem_u32(&sm->q_empty[s0]), (uint32_t)((n0 - 1) & 1), abort_flag, a.err);
           if (!ok) break;
         }
         ok = mbar_wait(smem_u32(&sm->a_full[st]), ph, abort_flag, a.err);
@@ -161,18 +184,30 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
         const uint32_t a_lo = a_hi + kSM * 128;
         const uint32_t b_hi = sB + (uint32_t)(kb * 2) * hl_b;
         const uint32_t b_lo = b_hi + hl_b;
+        for (int h = 0; h < nh; ++h) {
+          const int sl = nh == 2 ? h : s0;
+          if (h == 1 && kb == 0 && tt > 0) {
+            ok = mbar_wait(smem_u32(&sm->q_empty[1]), (uint32_t)((tt - 1) & 1), abort_flag, a.err);
+            if (!ok) break;
+            tc_fence_after();
+          }
+          const uint32_t d1 = tmem + 256u * (uint32_t)sl, d2 = d1 + 128u;
+          const uint32_t bo = (uint32_t)h * (128u * 128u);   // decision rows 128 h ..
+          const uint32_t idesc = h == 0 ? idesc0 : idesc1;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint32_t o = (uint32_t)(kk * 32);
-          const uint32_t acc0 = (kb == 0 && kk == 0) ? 0u : 1u;
-          mma_bf16(td1, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idesc, acc0);
-          mma_bf16(td2, desc_sw128(a_hi + o), desc_sw128(b_lo + o), idesc, acc0);
-          mma_bf16(td2, desc_sw128(a_lo + o), desc_sw128(b_hi + o), idesc, 1u);
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t o = (uint32_t)(kk * 32);
+            const uint32_t acc0 = (kb == 0 && kk == 0) ? 0u : 1u;
+            mma_bf16(d1, desc_sw128(a_hi + o), desc_sw128(b_hi + bo + o), idesc, acc0);
+            mma_bf16(d2, desc_sw128(a_hi + o), desc_sw128(b_lo + bo + o), idesc, acc0);
+            mma_bf16(d2, desc_sw128(a_lo + o), desc_sw128(b_hi + bo + o), idesc, 1u);
+          }
+          if (kb == a.nkb - 1) mma_commit(smem_u32(&sm->q_full[sl]));
         }
+        if (!ok) break;
         mma_commit(smem_u32(&sm->a_empty[st]));
-        if (kb == a.nkb - 1) mma_commit(smem_u32(&sm->q_full));
         if (++kb == a.nkb) { kb = 0; ++tt; }
-        if (++st == kSStages) { st = 0; ph ^= 1u; }
+        if (++st == nst) { st = 0; ph ^= 1u; }
       }
       mma_commit(smem_u32(&sm->drain));
       uint32_t never = 0u;
@@ -196,31 +231,51 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
         issued |= 1u << st;
         lpar ^= 1u << st;
         if (++kb == a.nkb) { kb = 0; ++tt; }
-        if (++st == kSStages) { st = 0; ph ^= 1u; }
+        if (++st == nst) { st = 0; ph ^= 1u; }
       }
       // the last load into each stage has landed before the CTA moves on
       uint32_t never = 0u;
-      for (int s = 0; s < kSStages; ++s)
+      for (int s = 0; s < nst; ++s)
         if ((issued >> s) & 1u) mbar_wait(smem_u32(&sm->ld_full[s]), ((lpar >> s) & 1u) ^ 1u, &never, a.err);
     }
     __syncwarp();
   } else if (warp < kSEpi) {
     // ------------------------------------------------------- epilogue ---
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 and the column groups
+    // g = w / 4, w / 4 + kSEpiStride, ...
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const int g0 = warp >> 2;
 #pragma unroll
-    for (int g = 0; g < kSMaxKp / 32; ++g) s2h[g] = s2l[g] = 0.0f;
-    for (int tt = 0; tt < my_tiles; ++tt) {
-      if (!warp_wait(smem_u32(&sm->q_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
-      tc_fence_after();
-#pragma unroll
-      for (int g = 0; g < kSMaxKp / 32; ++g)
-        if (32 * g < a.Kp) {
-          const uint32_t c0 = (uint32_t)(32 * g);
-          ff_add(s2h[g], s2l[g], epi_sq_colsum32(td1 + lane_base + c0, td2 + lane_base + c0, lane));
+    for (int g = 0; g < kSMaxKp / 32 / kSEpiStride; ++g) s2h[g] = s2l[g] = 0.0f;
+    bool ok = true;
+    for (int tt = 0; ok && tt < my_tiles; ++tt) {
+      for (int h = 0; h < nh; ++h) {
+        const int sl = nh == 2 ? h : (tt & 1);
+        const int n = nh == 2 ? tt : (tt >> 1);
+        if (!warp_wait(smem_u32(&sm->q_full[sl]), (uint32_t)(n & 1), abort_flag, a.err)) {
+          ok = false;
+          break;
         }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty));
+        tc_fence_after();
+        const uint32_t d1 = tmem + lane_base + 256u * (uint32_t)sl, d2 = d1 + 128u;
+        // groups of this half: [0, 8) with one half, [4 h, 4 h + 4) with two.
+        // The group loop stays rolled (register pressure); the running sums
+        // rotate so that the current group's pair is s2h[0] / s2l[0], and
+        // every warp visits 8 / kSEpiStride groups per tile.
+        const int gb = nh == 2 ? 4 * h : 0, ge = nh == 2 ? 4 * h + 4 : 8;
+#pragma unroll 1
+        for (int g = gb + g0; g < ge; g += kSEpiStride) {
+          if (32 * g < a.Kp) {
+            const uint32_t c = (uint32_t)(32 * g - 128 * h);
+            ff_add(s2h[0], s2l[0], epi_sq_colsum32(d1 + c, d2 + c, lane));
+          }
+          rot_left(s2h);
+          rot_left(s2l);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty[sl]));
+      }
     }
   } else {
     // ----------------------------------------------------- converters ---
@@ -232,7 +287,6 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
     // uu ^ 2, so that no two threads of a quarter-warp hit the same banks in
     // the two boxes; their v[] then holds the two 8-column halves swapped.
     const int hsw = q >> 1;
-    const int rr2 = ((lane >> 1) & 14) ^ (8 * hsw);   // m~ columns owned (within the 16)
 #pragma unroll
     for (int b = 0; b < NKB; ++b) mh[b][0] = mh[b][1] = ml[b][0] = ml[b][1] = 0.0f;
     bool in_range = true;
@@ -252,10 +306,12 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
         const float4 t = *reinterpret_cast<const float4*>(rowp + (((u0 + uc) ^ (r & 7)) << 4));
         const float4 c = *reinterpret_cast<const float4*>(s_cf + j0 + 4 * uc);
         const float4 w = *reinterpret_cast<const float4*>(s_is + j0 + 4 * uc);
-        v[4 * uu + 0] = (t.x - c.x) * w.x;
-        v[4 * uu + 1] = (t.y - c.y) * w.y;
-        v[4 * uu + 2] = (t.z - c.z) * w.z;
-        v[4 * uu + 3] = (t.w - c.w) * w.w;
+        // (R - c) 2^-a as one fma: both products are exact (power-of-two
+        // scale), so the single rounding equals that of R - c, scaled
+        v[4 * uu + 0] = fmaf(t.x, w.x, c.x);
+        v[4 * uu + 1] = fmaf(t.y, w.y, c.y);
+        v[4 * uu + 2] = fmaf(t.z, w.z, c.z);
+        v[4 * uu + 3] = fmaf(t.w, w.w, c.w);
       }
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
@@ -300,19 +356,21 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
           ff_add(mh[b][1], ml[b][1], v[1]);
         }
       if (++kb == a.nkb) { kb = 0; ++tt; }
-      if (++st == kSStages) { st = 0; ph ^= 1u; }
+      if (++st == nst) { st = 0; ph ^= 1u; }
     }
     if (!in_range) atomicOr(a.err, kErrInput);
   }
 
   // ----------------------------------------------------- CTA reductions ---
   __syncthreads();   // MMAs drained, loads landed: the A stages are free
-  double* red_s2 = reinterpret_cast<double*>(As);   // [kSEpi][Kp]
-  double* red_m = red_s2 + kSEpi * a.Kp;            // [kSConv][dpad]
+  double* red_s2 = reinterpret_cast<double*>(As);   // [4 lane quadrants][Kp]
+  double* red_m = red_s2 + 4 * a.Kp;                // [kSConv][dpad]
   if (warp < kSEpi) {
 #pragma unroll
-    for (int g = 0; g < kSMaxKp / 32; ++g)
-      if (32 * g < a.Kp) red_s2[warp * a.Kp + 32 * g + lane] = (double)s2h[g] + (double)s2l[g];
+    for (int i = 0; i < kSMaxKp / 32 / kSEpiStride; ++i) {
+      const int g = (warp >> 2) + i * kSEpiStride;
+      if (32 * g < a.Kp) red_s2[(warp & 3) * a.Kp + 32 * g + lane] = (double)s2h[i] + (double)s2l[i];
+    }
   } else if (warp > kSProd) {
     const int cw = warp - (kSProd + 1);
     const int col = 16 * (lane & 3) + (((lane >> 1) & 14) ^ (8 * ((lane & 3) >> 1)));
@@ -333,7 +391,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
   __syncthreads();
   for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
     double s = 0.0;
-    for (int w = 0; w < kSEpi; ++w) s += red_s2[w * a.Kp + k];
+    for (int w = 0; w < 4; ++w) s += red_s2[w * a.Kp + k];
     a.part_s2[(size_t)blockIdx.x * a.K + k] = s * a.scale2[k];
   }
   if (warp == kSMma) {
@@ -356,11 +414,12 @@ __device__ __forceinline__ int spread_exp(double sigma) {
   return (e < -100 || e > 100) ? -1000 : e;
 }
 
-// Operands of the streamed kernel: cf = center in FP32, isf = 2^-a_j (both 0
-// past d), Xs = x_kj 2^a_j.
+// Operands of the streamed kernel: cf = center in FP32, isf = 2^-a_j,
+// ncs = -cf isf (all 0 past d), Xs = x_kj 2^a_j.
 __global__ void k_stream_prep(int K, int d, int dpad, const double* __restrict__ center,
                               const double* __restrict__ sigma, const double* __restrict__ X, float* __restrict__ cf,
-                              float* __restrict__ isf, double* __restrict__ Xs, uint32_t* err) {
+                              float* __restrict__ isf, float* __restrict__ ncs, double* __restrict__ Xs,
+                              uint32_t* err) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < dpad) {
     const int j = (int)t;
@@ -374,6 +433,7 @@ __global__ void k_stream_prep(int K, int d, int dpad, const double* __restrict__
     }
     cf[j] = (j < d && center) ? (float)center[j] : 0.0f;
     isf[j] = (j < d) ? ldexpf(1.0f, -e) : 0.0f;
+    ncs[j] = -cf[j] * isf[j];
   } else if (t < dpad + (int64_t)K * d) {
     const int64_t u = t - dpad;
     const int j = (int)(u % d);
@@ -462,7 +522,7 @@ saa_status encode_fn(EncodeTiledFn* out) {
 }
 
 struct SPlan {
-  int Kp, nkb, grid, smem, dpad;
+  int Kp, nkb, nst, grid, smem, dpad;
   int64_t tiles;
   size_t img, s2, pm, cf, xs, tots, total;
 };
@@ -476,12 +536,15 @@ SPlan stream_plan(const saa_ctx* ctx, int64_t N, int d, int K) {
   p.dpad = p.nkb * tc::kSKB;
   p.tiles = (N + tc::kSM - 1) / tc::kSM;
   p.grid = (int)(p.tiles < ctx->sm_count ? p.tiles : ctx->sm_count);
-  p.smem = (int)tc::stream_smem_bytes(p.Kp, p.nkb);
+  // as many 32 KB stages as the shared memory left by the decision image holds
+  p.nst = tc::kSMaxStages;
+  while (p.nst > 2 && (int)tc::stream_smem_bytes(p.Kp, p.nkb, p.nst) > ctx->smem_optin) --p.nst;
+  p.smem = (int)tc::stream_smem_bytes(p.Kp, p.nkb, p.nst);
   size_t off = 0;
   p.img = off; off = a256(off + (size_t)p.nkb * 2 * p.Kp * 128 + 8 * (size_t)K);
   p.s2 = off; off = a256(off + 8 * (size_t)p.grid * K);
   p.pm = off; off = a256(off + 8 * (size_t)p.grid * p.dpad);
-  p.cf = off; off = a256(off + 4 * 2 * (size_t)p.dpad);
+  p.cf = off; off = a256(off + 4 * 3 * (size_t)p.dpad);
   p.xs = off; off = a256(off + 8 * (size_t)K * d);
   p.tots = off; off = a256(off + 8 * (size_t)p.dpad);
   p.total = off;
@@ -567,13 +630,14 @@ extern "C" saa_status saa_eval_samples(saa_ctx* ctx, int64_t N, int32_t d, const
   double* part_m = (double*)(w + p.pm);
   float* cf = (float*)(w + p.cf);
   float* isf = cf + p.dpad;
+  float* ncs = isf + p.dpad;
   double* Xs = (double*)(w + p.xs);
   double* tot_m = (double*)(w + p.tots);
   cudaStream_t st = (cudaStream_t)stream;
   const bool f16 = prec == SAA_F16X3;
   const int64_t nprep = p.dpad + (int64_t)K * d;
-  k_stream_prep<<<(unsigned)((nprep + 255) / 256), 256, 0, st>>>(K, d, p.dpad, center, sigma, X, cf, isf, Xs,
-                                                                ctx->err);
+  k_stream_prep<<<(unsigned)((nprep + 255) / 256), 256, 0, st>>>(K, d, p.dpad, center, sigma, X, cf, isf, ncs,
+                                                                Xs, ctx->err);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_tc_image(d, K, p.Kp, p.nkb, f16, Xs, scale2, nullptr, img, st);
   tc::SArgs a;
@@ -581,9 +645,10 @@ extern "C" saa_status saa_eval_samples(saa_ctx* ctx, int64_t N, int32_t d, const
   a.K = K;
   a.Kp = p.Kp;
   a.nkb = p.nkb;
+  a.nst = p.nst;
   a.N = (uint32_t)N;
   a.tiles = p.tiles;
-  a.cf = cf;
+  a.ncs = ncs;
   a.isf = isf;
   a.bimage = img;
   a.scale2 = scale2;
