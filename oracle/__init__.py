@@ -293,6 +293,27 @@ def fw(prob, prec, w0, T, M, t0=0, want_w_trace=False):
     return out
 
 
+def fw_adaptive(probs, prec, w0, M, k0=0, want_w_trace=False):
+    """Algorithm 1 with a sample size per epoch (the resampling step's
+    N_k "adapted to k"): epoch k0 + k draws its N samples from probs[k]
+    (one problem per epoch, equal but for N) and runs M iterations from the
+    global iteration (k0 + k) M, so the step size and the resample index
+    follow the global count.  Returns dict w, f_trace, gap_trace (w_trace)."""
+    w = np.ascontiguousarray(w0, dtype=np.float64)
+    ft, gt, wt = [], [], []
+    for k, prob in enumerate(probs):
+        out = fw(prob, prec, w, T=M, M=M, t0=(k0 + k) * M, want_w_trace=want_w_trace)
+        w = out["w"]
+        ft.append(out["f_trace"])
+        gt.append(out["gap_trace"])
+        if want_w_trace:
+            wt.append(out["w_trace"])
+    res = {"w": w, "f_trace": np.concatenate(ft), "gap_trace": np.concatenate(gt)}
+    if want_w_trace:
+        res["w_trace"] = np.concatenate(wt)
+    return res
+
+
 def rse(y_t, y_star):
     """Relative squared error in percent (Table 2 notes)."""
     return float(lib().oracle_rse(float(y_t), float(y_star)))
