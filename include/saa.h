@@ -151,6 +151,26 @@ saa_status saa_solve(saa_ctx* ctx, const saa_problem* prob, const double* w0, in
                      saa_prec prec, double* w_out, double* f_trace, double* gap_trace, void* ws, size_t ws_bytes,
                      void* stream);
 
+/* Algorithm 1 with a sample size per epoch (the resampling step allows the
+ * sample size N_k to depend on the epoch k).  Epoch k0 + k, for k = 0 ..
+ * n_epochs-1, draws N_sched[k] samples of resample index prob->epoch + k0 + k
+ * and runs M iterations at the global iteration t = (k0 + k) M + m, so
+ * gamma_t = 2/(t+2) and the resampling follow the global count; prob->N is
+ * ignored.  Each run of epochs with equal N_k is one captured graph
+ * replayed over those epochs.  Resuming with (k0, w) continues a run bit
+ * for bit; a constant schedule gives saa_solve's iterates.
+ *   N_sched    HOST [n_epochs]: 2 <= N_k < 2^32
+ *   w0, w_out  device [d] (w0 in W)
+ *   f_trace, gap_trace  device [n_epochs*M] or NULL, as saa_solve's
+ *   ws         device scratch of saa_solve_adaptive_workspace_size() bytes
+ *              (the largest epoch's saa_solve workspace), 256-byte aligned
+ * Errors as saa_solve; the workspace query returns 0 for invalid arguments. */
+size_t saa_solve_adaptive_workspace_size(const saa_ctx* ctx, const saa_problem* prob, const int64_t* N_sched,
+                                         int32_t n_epochs, saa_prec prec);
+saa_status saa_solve_adaptive(saa_ctx* ctx, const saa_problem* prob, const double* w0, const int64_t* N_sched,
+                              int32_t n_epochs, int32_t M, int32_t k0, saa_prec prec, double* w_out,
+                              double* f_trace, double* gap_trace, void* ws, size_t ws_bytes, void* stream);
+
 /* A ragged batch of B independent problems (Eq. 4 for each), in one
  * persistent launch: problem b has its own d, N, law, stream, K[b]
  * decisions X[b] and outputs f[b] (pbar[b], var[b] optional; pass NULL for

@@ -73,6 +73,8 @@ struct saa_ctx {
   uint32_t* err;                 // device error word
   // graph of the last saa_solve (kept until the next solve or destroy)
   cudaGraphExec_t fw_exec;
+  cudaGraphExec_t* fw_more;      // graphs of the last saa_solve_adaptive (one per run of equal N)
+  int fw_more_n;
   // kernel timing (saa_profile_*)
   int prof_on;
   int prof_n;                    // recorded event pairs

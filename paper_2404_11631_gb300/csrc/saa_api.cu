@@ -161,6 +161,66 @@ static saa_status run_estimator(saa_ctx* ctx, const saa_problem* p, int K, const
   return s;
 }
 
+// Frees the graphs of the previous solve (their replays may still be queued
+// on another stream, hence the device-wide wait).
+void release_fw_graphs(saa_ctx* ctx) {
+  if (!ctx->fw_exec && ctx->fw_more_n == 0) return;
+  cudaDeviceSynchronize();
+  if (ctx->fw_exec) cudaGraphExecDestroy(ctx->fw_exec);
+  ctx->fw_exec = nullptr;
+  for (int i = 0; i < ctx->fw_more_n; ++i) cudaGraphExecDestroy(ctx->fw_more[i]);
+  delete[] ctx->fw_more;
+  ctx->fw_more = nullptr;
+  ctx->fw_more_n = 0;
+}
+
+// T iterations of Algorithm 1 from global iteration t0 on the samples of
+// prob (its N), starting from w_in (copied to w_out unless they are the
+// same array): one iteration captured as a graph and replayed T times.  The
+// instantiated graph is returned in *exec for the caller to keep alive.
+saa_status solve_run(saa_ctx* ctx, const saa_problem* prob, const double* w_in, int32_t T, int32_t M,
+                            int64_t t0, saa_prec prec, double* w_out, double* f_trace, double* gap_trace, void* ws,
+                            size_t ws_bytes, cudaStream_t st, cudaGraphExec_t* exec) {
+  *exec = nullptr;
+  Plan plan;
+  saa_status s = make_plan(ctx, prob, 1, prec, 1, &plan);
+  if (s != SAA_OK) return s;
+  Workspace w;
+  const size_t need = carve(prob, 1, plan, 2, ws, &w);
+  if (ws_bytes < need) return fail(SAA_ENOMEM, "workspace smaller than saa_workspace_size(..., want_grad=2)");
+  const int d = prob->d;
+  if (w_in != w_out) {
+    s = cuda_status(cudaMemcpyAsync(w_out, w_in, sizeof(double) * d, cudaMemcpyDeviceToDevice, st), "copy w0");
+    if (s != SAA_OK) return s;
+  }
+  s = cuda_status(launch_set_i64(w.t_dev, t0, st), "set iteration counter");
+  if (s != SAA_OK || T == 0) return s;
+
+  LawArgs la = law_args(prob);
+  la.t_dev = w.t_dev;
+  la.M = M;
+  // Capture one iteration on a private stream, replay it T times on `st`.
+  cudaStream_t cap;
+  s = cuda_status(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "create capture stream");
+  if (s != SAA_OK) return s;
+  cudaGraph_t graph = nullptr;
+  s = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (s == SAA_OK) {
+    saa_status r = run_estimator(ctx, prob, 1, w_out, prec, 1, plan, w, la, w.f_tmp, nullptr, nullptr, w.grad_out,
+                                 cap);
+    if (r == SAA_OK)
+      r = cuda_status(launch_fw_step(d, w.grad_out, w.f_tmp, w_out, w.t_dev, t0, f_trace, gap_trace, w.t_dev, cap),
+                      "Frank-Wolfe step launch");
+    cudaError_t e = cudaStreamEndCapture(cap, &graph);
+    s = (r != SAA_OK) ? r : cuda_status(e, "end capture");
+  }
+  if (s == SAA_OK) s = cuda_status(cudaGraphInstantiate(exec, graph, 0), "instantiate graph");
+  for (int32_t it = 0; s == SAA_OK && it < T; ++it) s = cuda_status(cudaGraphLaunch(*exec, st), "graph launch");
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  return s;
+}
+
 }  // namespace saa
 
 using namespace saa;
@@ -203,10 +263,7 @@ saa_status saa_ctx_create(saa_ctx** out, int device) {
 void saa_ctx_destroy(saa_ctx* ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
-  if (ctx->fw_exec) {
-    cudaDeviceSynchronize();
-    cudaGraphExecDestroy(ctx->fw_exec);
-  }
+  release_fw_graphs(ctx);
   if (ctx->prof_on)
     for (int i = 0; i < 2 * 256; ++i) cudaEventDestroy(ctx->prof_ev[i]);
   if (ctx->stage) {
@@ -353,49 +410,64 @@ saa_status saa_solve(saa_ctx* ctx, const saa_problem* prob, const double* w0, in
   if ((int64_t)prob->epoch + (t0 + T) / M > 0xffffffffll) return fail(SAA_EINVAL, "resample index overflows");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(SAA_ECUDA, "cudaSetDevice failed");
-  Plan plan;
-  s = make_plan(ctx, prob, 1, prec, 1, &plan);
-  if (s != SAA_OK) return s;
-  Workspace w;
-  const size_t need = carve(prob, 1, plan, 2, ws, &w);
-  if (ws_bytes < need) return fail(SAA_ENOMEM, "workspace smaller than saa_workspace_size(..., want_grad=2)");
-  cudaStream_t st = (cudaStream_t)stream;
-  const int d = prob->d;
-  s = cuda_status(cudaMemcpyAsync(w_out, w0, sizeof(double) * d, cudaMemcpyDeviceToDevice, st), "copy w0");
-  if (s != SAA_OK) return s;
-  s = cuda_status(launch_set_i64(w.t_dev, t0, st), "set iteration counter");
-  if (s != SAA_OK || T == 0) return s;
-
-  LawArgs la = law_args(prob);
-  la.t_dev = w.t_dev;
-  la.M = M;
-  // Capture one iteration on a private stream, replay it T times on `st`.
-  cudaStream_t cap;
-  s = cuda_status(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "create capture stream");
-  if (s != SAA_OK) return s;
-  cudaGraph_t graph = nullptr;
+  release_fw_graphs(ctx);
   cudaGraphExec_t exec = nullptr;
-  s = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-  if (s == SAA_OK) {
-    saa_status r = run_estimator(ctx, prob, 1, w_out, prec, 1, plan, w, la, w.f_tmp, nullptr, nullptr, w.grad_out,
-                                 cap);
-    if (r == SAA_OK)
-      r = cuda_status(launch_fw_step(d, w.grad_out, w.f_tmp, w_out, w.t_dev, t0, f_trace, gap_trace, w.t_dev, cap),
-                      "Frank-Wolfe step launch");
-    cudaError_t e = cudaStreamEndCapture(cap, &graph);
-    s = (r != SAA_OK) ? r : cuda_status(e, "end capture");
-  }
-  if (s == SAA_OK) s = cuda_status(cudaGraphInstantiate(&exec, graph, 0), "instantiate graph");
-  for (int32_t it = 0; s == SAA_OK && it < T; ++it) s = cuda_status(cudaGraphLaunch(exec, st), "graph launch");
-  if (ctx->fw_exec) {
-    // the previous call's graph may still be queued on another stream
-    cudaDeviceSynchronize();
-    cudaGraphExecDestroy(ctx->fw_exec);
-    ctx->fw_exec = nullptr;
-  }
+  s = solve_run(ctx, prob, w0, T, M, t0, prec, w_out, f_trace, gap_trace, ws, ws_bytes, (cudaStream_t)stream, &exec);
   ctx->fw_exec = exec;  // destroyed by the next solve or by saa_ctx_destroy
-  if (graph) cudaGraphDestroy(graph);
-  cudaStreamDestroy(cap);
+  return s;
+}
+
+size_t saa_solve_adaptive_workspace_size(const saa_ctx* ctx, const saa_problem* prob, const int64_t* N_sched,
+                                         int32_t n_epochs, saa_prec prec) {
+  if (!ctx || !prob || !N_sched || n_epochs < 1) return 0;
+  size_t most = 0;
+  for (int32_t k = 0; k < n_epochs; ++k) {
+    saa_problem p = *prob;
+    p.N = N_sched[k];
+    const size_t need = saa_workspace_size(ctx, &p, 1, prec, 2);
+    if (need == 0) return 0;
+    most = need > most ? need : most;
+  }
+  return most;
+}
+
+saa_status saa_solve_adaptive(saa_ctx* ctx, const saa_problem* prob, const double* w0, const int64_t* N_sched,
+                              int32_t n_epochs, int32_t M, int32_t k0, saa_prec prec, double* w_out,
+                              double* f_trace, double* gap_trace, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  if (!N_sched || n_epochs < 1 || M < 1 || k0 < 0) return fail(SAA_EINVAL, "need N_sched, n_epochs >= 1, M >= 1, k0 >= 0");
+  if (!w0 || !w_out) return fail(SAA_EINVAL, "w0 and w_out must be device pointers");
+  if (!ws || (((uintptr_t)ws) & 255u)) return fail(SAA_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if ((int64_t)prob->epoch + (int64_t)k0 + n_epochs > 0xffffffffll) return fail(SAA_EINVAL, "resample index overflows");
+  for (int32_t k = 0; k < n_epochs; ++k) {
+    saa_problem p = *prob;
+    p.N = N_sched[k];
+    saa_status s = check_problem(&p);
+    if (s != SAA_OK) return s;
+  }
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(SAA_ECUDA, "cudaSetDevice failed");
+  release_fw_graphs(ctx);
+  // one graph per run of epochs with the same N, replayed over those epochs
+  int runs = 0;
+  for (int32_t k = 0; k < n_epochs; ++k)
+    if (k == 0 || N_sched[k] != N_sched[k - 1]) ++runs;
+  ctx->fw_more = new (std::nothrow) cudaGraphExec_t[runs];
+  if (!ctx->fw_more) return fail(SAA_ENOMEM, "host allocation failed");
+  saa_status s = SAA_OK;
+  for (int32_t k = 0; s == SAA_OK && k < n_epochs;) {
+    int32_t e = k + 1;
+    while (e < n_epochs && N_sched[e] == N_sched[k]) ++e;
+    saa_problem p = *prob;
+    p.N = N_sched[k];
+    const int64_t off = (int64_t)k * M;
+    cudaGraphExec_t exec = nullptr;
+    s = solve_run(ctx, &p, k == 0 ? w0 : w_out, (int32_t)((e - k) * M), M, (int64_t)(k0 + k) * M, prec, w_out,
+                  f_trace ? f_trace + off : nullptr, gap_trace ? gap_trace + off : nullptr, ws, ws_bytes,
+                  (cudaStream_t)stream, &exec);
+    if (exec) ctx->fw_more[ctx->fw_more_n++] = exec;
+    k = e;
+  }
   return s;
 }
 

@@ -120,6 +120,11 @@ def lib():
             L.saa_eval_moments_workspace_size.restype = sz
             L.saa_eval_moments.argtypes = [vp, pp, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
             L.saa_eval_moments.restype = C.c_int
+            L.saa_solve_adaptive_workspace_size.argtypes = [vp, pp, C.POINTER(C.c_int64), C.c_int32, C.c_int]
+            L.saa_solve_adaptive_workspace_size.restype = sz
+            L.saa_solve_adaptive.argtypes = [vp, pp, vp, C.POINTER(C.c_int64), C.c_int32, C.c_int32, C.c_int32,
+                                             C.c_int, vp, vp, vp, vp, sz, vp]
+            L.saa_solve_adaptive.restype = C.c_int
             L.saa_eval_samples_workspace_size.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32, C.c_int]
             L.saa_eval_samples_workspace_size.restype = sz
             L.saa_eval_samples.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, vp, C.c_int32, vp, C.c_double, C.c_int,
@@ -296,6 +301,30 @@ def saa_solve(prob: Problem, w0: torch.Tensor, T: int, M: int = 1, t0: int = 0, 
     _check(lib().saa_solve(context(dev.index), C.byref(cp), _ptr(w0), T, M, t0, _prec(prec), _ptr(w), _ptr(ft),
                            _ptr(gt), _ptr(ws), ws.numel(), _stream(dev)))
     return {"w": w, "f_trace": ft[:T], "gap_trace": gt[:T]}
+
+
+def saa_solve_adaptive(prob: Problem, w0: torch.Tensor, N_sched, M: int = 1, k0: int = 0, prec="fp32",
+                       ws: torch.Tensor | None = None) -> dict:
+    """Algorithm 1 with N_sched[k] samples in epoch k0 + k (M iterations
+    each): {'w', 'f_trace', 'gap_trace'}; prob.N is not used."""
+    dev = prob.device
+    if not (w0.is_cuda and w0.dtype == torch.float64 and w0.is_contiguous() and w0.shape == (prob.d,)):
+        raise ValueError("w0 must be a contiguous float64 CUDA tensor [d]")
+    sched = (C.c_int64 * len(N_sched))(*[int(n) for n in N_sched])
+    n = len(N_sched)
+    cp = prob.c_struct()
+    ctx = context(dev.index)
+    need = lib().saa_solve_adaptive_workspace_size(ctx, C.byref(cp), sched, n, _prec(prec))
+    if need == 0:
+        raise SAAError(SAA_EINVAL, "saa_solve_adaptive: invalid schedule or problem")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    w = torch.empty(prob.d, dtype=torch.float64, device=dev)
+    ft = torch.empty(n * M, dtype=torch.float64, device=dev)
+    gt = torch.empty(n * M, dtype=torch.float64, device=dev)
+    _check(lib().saa_solve_adaptive(ctx, C.byref(cp), _ptr(w0), sched, n, M, k0, _prec(prec), _ptr(w), _ptr(ft),
+                                    _ptr(gt), _ptr(ws), ws.numel(), _stream(dev)))
+    return {"w": w, "f_trace": ft, "gap_trace": gt}
 
 
 def saa_generate(prob: Problem, i0: int, n: int, prec="fp32", want_xi: bool = False) -> dict:
@@ -597,4 +626,5 @@ EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_
             "saa_generate_moments_workspace_size", "saa_batch_workspace_size", "saa_batch_create",
             "saa_batch_launch", "saa_batch_destroy", "saa_newsvendor_workspace_size", "saa_newsvendor_grad",
             "saa_moments_workspace_size", "saa_moments", "saa_eval_moments_workspace_size", "saa_eval_moments",
-            "saa_eval_samples_workspace_size", "saa_eval_samples"]
+            "saa_eval_samples_workspace_size", "saa_eval_samples", "saa_solve_adaptive_workspace_size",
+            "saa_solve_adaptive"]
