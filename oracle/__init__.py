@@ -93,6 +93,19 @@ class Newsvendor(C.Structure):
     ]
 
 
+class Logistic(C.Structure):
+    """Mirror of the oracle's binary-classification data set (saa_oracle.c)."""
+
+    _fields_ = [
+        ("n", C.c_int32),
+        ("N", C.c_int64),
+        ("seed", C.c_uint64),
+        ("instance", C.c_uint32),
+        ("flip", C.c_uint32),
+        ("wstar", C.POINTER(C.c_int32)),
+    ]
+
+
 def _p(a, ct=C.c_double):
     return a.ctypes.data_as(C.POINTER(ct)) if a is not None else None
 
@@ -132,6 +145,12 @@ def lib():
             L.oracle_newsvendor_grad_range.argtypes = [nvp, C.c_int, dp, C.c_int64, C.c_int64, dp,
                                                        C.POINTER(C.c_int64)]
             L.oracle_newsvendor_grad_range.restype = C.c_int
+            lgp = C.POINTER(Logistic)
+            u8p = C.POINTER(C.c_uint8)
+            L.oracle_logistic_data.argtypes = [lgp, C.c_int64, C.c_int64, u8p, u8p]
+            L.oracle_logistic_data.restype = C.c_int
+            L.oracle_logistic_eval.argtypes = [lgp, C.POINTER(C.c_int64), C.c_int64, C.c_int, dp, dp, dp, dp, dp]
+            L.oracle_logistic_eval.restype = C.c_int
             L.oracle_cholesky.argtypes = [C.c_int, dp, dp]
             L.oracle_cholesky.restype = C.c_int
             L.oracle_rse.argtypes = [C.c_double, C.c_double]
@@ -312,6 +331,54 @@ def fw_adaptive(probs, prec, w0, M, k0=0, want_w_trace=False):
     if want_w_trace:
         res["w_trace"] = np.concatenate(wt)
     return res
+
+
+# --- binary classification (Sec. 3.3) --------------------------------------
+
+LABEL_NOISE_10PCT = 429496730   # round(0.1 * 2^32): a label flips when its noise word is below this
+
+
+def make_logistic(n, N, wstar, seed=0, instance=0, flip=LABEL_NOISE_10PCT):
+    """Returns (Logistic, keepalive) for N points with n binary features and
+    the integer labelling weights ``wstar`` [n]."""
+    w = np.ascontiguousarray(wstar, dtype=np.int32)
+    assert w.shape == (n,)
+    P = Logistic(n, N, seed, instance, flip, _p(w, C.c_int32))
+    return P, w
+
+
+def logistic_data(prob, i0=0, rows=None):
+    """(features uint8 [rows, n], labels uint8 [rows]) of points i0 .. i0+rows-1."""
+    P, keep = prob
+    rows = P.N - i0 if rows is None else rows
+    x = np.empty((rows, P.n), np.uint8)
+    z = np.empty(rows, np.uint8)
+    _check(lib().oracle_logistic_data(C.byref(P), i0, rows, _p(x, C.c_uint8), _p(z, C.c_uint8)), "logistic_data")
+    return x, z
+
+
+def logistic_eval(prob, W, V=None, idx=None, want=("F", "grad", "hvp")):
+    """F [K], grad [K, n] and (with V) hvp [K, n] over the sample idx (all
+    points when None), for the parameter vectors W [K, n]."""
+    P, keep = prob
+    W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
+    K = W.shape[0]
+    V = None if V is None else np.ascontiguousarray(np.atleast_2d(V), dtype=np.float64)
+    ix = None if idx is None else np.ascontiguousarray(idx, dtype=np.int64)
+    b = P.N if ix is None else ix.size
+    F = np.empty(K) if "F" in want else None
+    g = np.empty((K, P.n)) if "grad" in want else None
+    h = np.empty((K, P.n)) if ("hvp" in want and V is not None) else None
+    _check(lib().oracle_logistic_eval(C.byref(P), _p(ix, C.c_int64), b, K, _p(W), _p(V), _p(F), _p(g), _p(h)),
+           "logistic_eval")
+    out = {}
+    if F is not None:
+        out["F"] = F
+    if g is not None:
+        out["grad"] = g
+    if h is not None:
+        out["hvp"] = h
+    return out
 
 
 def rse(y_t, y_star):

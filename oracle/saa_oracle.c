@@ -26,6 +26,11 @@
  *   7. The newsvendor's Monte Carlo gradient (Sec. 3.2, the approximated
  *      gradient): per product j, k_j - v_j + (h_j + v_j) times the fraction
  *      of S normal demand samples d_j = mu_j + sigma_j z that are <= x_j.
+ *   8. The binary-classification task of Sec. 3.3: the synthetic data set of
+ *      Sec. 4.1's setup (binary features, labels from a random linear rule
+ *      with 10 % label noise), the objective F(omega) (negative mean
+ *      log-likelihood of the logistic model), its sample-average gradient
+ *      and the sub-sampled Hessian applied to a vector.
  *
  * Floating-point discipline: compiled with -ffp-contract=off; every fused
  * multiply-add in the generator is an explicit fmaf()/fma() call, so each
@@ -1021,6 +1026,166 @@ int oracle_newsvendor_grad(const oracle_newsvendor* p, int K, const double* X, d
 {
     if (!p) return OR_EINVAL;
     return oracle_newsvendor_grad_range(p, K, X, 0, p->n, grad, counts);
+}
+
+/* ------------------------------------------------------------------------- */
+/* 8. Binary classification (Sec. 3.3)                                        */
+/* ------------------------------------------------------------------------- */
+/* Data set {(x_i, z_i)}, i < N, x_i in {0,1}^n.  Feature j = 128 b + 32 q + t
+ * of point i is bit t of word q of Philox4x32-10(counter (b, i, 0,
+ * (4 << 24) | instance), key seed): Bernoulli(1/2) features.  The label is
+ * a random linear rule with label noise: z_i = [2 x_i'w* > 1'w*] (strict,
+ * integer arithmetic) flipped when word 0 of Philox(counter (0, i, 0,
+ * (5 << 24) | instance)) is below `flip` (flip = 0.1 * 2^32 gives the 10 %
+ * of Sec. 4.1). */
+typedef struct {
+    int32_t n;            /* features */
+    int64_t N;            /* data points */
+    uint64_t seed;
+    uint32_t instance;
+    uint32_t flip;
+    const int32_t* wstar; /* [n] integer weights of the labelling rule */
+} oracle_logistic;
+
+static int check_logistic(const oracle_logistic* p)
+{
+    if (!p || p->n < 1 || p->N < 1 || p->N > 0xffffffffll || !p->wstar) return OR_EINVAL;
+    return OR_OK;
+}
+
+static void logi_features(const oracle_logistic* p, int64_t i, uint8_t* x)
+{
+    const uint32_t k0 = (uint32_t)(p->seed & 0xffffffffu), k1 = (uint32_t)(p->seed >> 32);
+    for (int32_t b = 0; 128 * b < p->n; ++b) {
+        const uint32_t c[4] = {(uint32_t)b, (uint32_t)i, 0u, (4u << 24) | (p->instance & 0xffffffu)};
+        uint32_t w[4];
+        philox10(c, k0, k1, w);
+        for (int q = 0; q < 4; ++q)
+            for (int t = 0; t < 32; ++t) {
+                const int32_t j = 128 * b + 32 * q + t;
+                if (j < p->n) x[j] = (uint8_t)((w[q] >> t) & 1u);
+            }
+    }
+}
+
+static uint8_t logi_label(const oracle_logistic* p, int64_t i, const uint8_t* x)
+{
+    int64_t dot = 0, tot = 0;
+    for (int32_t j = 0; j < p->n; ++j) {
+        tot += p->wstar[j];
+        if (x[j]) dot += p->wstar[j];
+    }
+    uint8_t z = (uint8_t)(2 * dot > tot);
+    const uint32_t c[4] = {0u, (uint32_t)i, 0u, (5u << 24) | (p->instance & 0xffffffu)};
+    uint32_t w[4];
+    philox10(c, (uint32_t)(p->seed & 0xffffffffu), (uint32_t)(p->seed >> 32), w);
+    if (w[0] < p->flip) z ^= 1u;
+    return z;
+}
+
+/* Features x[rows][n] and labels z[rows] of points i0 .. i0 + rows - 1 (either
+ * output may be NULL). */
+int oracle_logistic_data(const oracle_logistic* p, int64_t i0, int64_t rows, uint8_t* x, uint8_t* z)
+{
+    if (check_logistic(p) != OR_OK || i0 < 0 || rows < 0 || i0 + rows > p->N) return OR_EINVAL;
+    uint8_t* row = (uint8_t*)malloc((size_t)p->n);
+    if (!row) return OR_ENOMEM;
+    for (int64_t r = 0; r < rows; ++r) {
+        logi_features(p, i0 + r, row);
+        if (x) memcpy(x + (size_t)r * p->n, row, (size_t)p->n);
+        if (z) z[r] = logi_label(p, i0 + r, row);
+    }
+    free(row);
+    return OR_OK;
+}
+
+/* The objective and its derivatives over the sample S (indices idx[0..b-1],
+ * repeats allowed; idx == NULL means every point 0 .. N-1, b = N), for K
+ * parameter vectors W[K][n] (omega_k) and optional directions V[K][n]:
+ *   F[k]    = -(1/b) sum_S [ z log c + (1 - z) log(1 - c) ],  c = 1/(1 + e^(-x'omega))
+ *           =  (1/b) sum_S [ log(1 + e^t) - z t ],  t = x'omega          (Sec. 3.3)
+ *   grad[k] =  (1/b) sum_S (c - z) x                 (derivative of F, the
+ *                                                     mini-batch gradient's mean)
+ *   hvp[k]  =  (1/b) sum_S c (1 - c) (x'v_k) x       (sub-sampled Hessian times v_k)
+ * Each output may be NULL (hvp needs V).  Sums run over a fixed partition of
+ * S into chunks merged in chunk order with Neumaier compensation. */
+int oracle_logistic_eval(const oracle_logistic* p, const int64_t* idx, int64_t b, int K, const double* W,
+                         const double* V, double* F, double* grad, double* hvp)
+{
+    if (check_logistic(p) != OR_OK || K < 1 || !W || (hvp && !V)) return OR_EINVAL;
+    if (!idx) b = p->N;
+    if (b < 1) return OR_EINVAL;
+    if (idx)
+        for (int64_t s = 0; s < b; ++s)
+            if (idx[s] < 0 || idx[s] >= p->N) return OR_EINVAL;
+    const int n = p->n;
+    enum { NCH = 64 };
+    const size_t per = (size_t)K * (size_t)n;
+    nsum* pf = (nsum*)calloc((size_t)NCH * K, sizeof(nsum));
+    nsum* pg = (nsum*)calloc((size_t)NCH * per, sizeof(nsum));
+    nsum* ph = hvp ? (nsum*)calloc((size_t)NCH * per, sizeof(nsum)) : NULL;
+    if (!pf || !pg || (hvp && !ph)) {
+        free(pf); free(pg); free(ph);
+        return OR_ENOMEM;
+    }
+    int bad = 0;
+#pragma omp parallel for schedule(static)
+    for (int ch = 0; ch < NCH; ++ch) {
+        const int64_t s0 = b * ch / NCH, s1 = b * (ch + 1) / NCH;
+        uint8_t* x = (uint8_t*)malloc((size_t)n);
+        if (!x) {
+            bad = 1;
+            continue;
+        }
+        for (int64_t s = s0; s < s1; ++s) {
+            const int64_t i = idx ? idx[s] : s;
+            logi_features(p, i, x);
+            const double z = (double)logi_label(p, i, x);
+            for (int k = 0; k < K; ++k) {
+                const double* w = W + (size_t)k * n;
+                double t = 0.0;
+                for (int j = 0; j < n; ++j)
+                    if (x[j]) t += w[j];
+                const double c = 1.0 / (1.0 + exp(-t));
+                /* log(1 + e^t) without overflow */
+                const double sp = t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t));
+                nadd(&pf[(size_t)ch * K + k], sp - z * t);
+                const double r = c - z;
+                double hr = 0.0;
+                if (hvp) {
+                    const double* v = V + (size_t)k * n;
+                    double u = 0.0;
+                    for (int j = 0; j < n; ++j)
+                        if (x[j]) u += v[j];
+                    hr = c * (1.0 - c) * u;
+                }
+                for (int j = 0; j < n; ++j)
+                    if (x[j]) {
+                        nadd(&pg[(size_t)ch * per + (size_t)k * n + j], r);
+                        if (hvp) nadd(&ph[(size_t)ch * per + (size_t)k * n + j], hr);
+                    }
+            }
+        }
+        free(x);
+    }
+    if (!bad) {
+        for (int k = 0; k < K; ++k) {
+            nsum a = {0.0, 0.0};
+            for (int ch = 0; ch < NCH; ++ch) nadd(&a, nval(&pf[(size_t)ch * K + k]));
+            if (F) F[k] = nval(&a) / (double)b;
+        }
+        for (size_t e = 0; e < per; ++e) {
+            nsum a = {0.0, 0.0}, h = {0.0, 0.0};
+            for (int ch = 0; ch < NCH; ++ch) {
+                nadd(&a, nval(&pg[(size_t)ch * per + e]));
+                if (hvp) nadd(&h, nval(&ph[(size_t)ch * per + e]));
+            }
+            if (grad) grad[e] = nval(&a) / (double)b;
+            if (hvp) hvp[e] = nval(&h) / (double)b;
+        }
+    }
+    free(pf); free(pg); free(ph);
+    return bad ? OR_ENOMEM : OR_OK;
 }
 
 double oracle_rse(double y_t, double y_star)

@@ -11,6 +11,10 @@ Law parameters follow the mean-variance task of Sec. 3.1 (R ~ N(mu, Sigma)):
 * ``paper_instance``: the setup of Sec. 4.1 for the asset task,
   mu_i ~ U(-1,1), sigma_i ~ U(0, 0.025), diagonal Sigma.
 * ``decisions``: K candidate decisions x ~ U[0,1]^d.
+* ``logistic_weights``: the random linear combination that labels the
+  binary-classification data set (Sec. 4.1's Task 3 setup): integer weights
+  in [-3, 3], so the rule is exact in any arithmetic.  ``logistic_sizes``
+  lists Sec. 4.1's feature counts with N = 30 n.
 * ``sample_matrix``: a materialised sample set {R_i} (FP32 rows) for the
   streamed mode, R_i = mu + C z_i with z_i drawn by numpy (standard normal,
   or Student-t with 4 degrees of freedom for the second half when
@@ -74,6 +78,17 @@ def sample_matrix(N: int, d: int, seed: int = 0, inst_seed: int = 0, heavy: bool
             z[tail] = rng.standard_t(4.0, size=(int(tail.sum()), d))
         R[i0:i0 + n] = inst.mu + z @ inst.chol.T
     return R, inst
+
+
+def logistic_weights(n: int, seed: int = 0) -> np.ndarray:
+    """Integer weights w* in [-3, 3]^n of the labelling rule z = [2 x'w* > 1'w*]."""
+    rng = np.random.default_rng([seed, n, 5])
+    return rng.integers(-3, 4, size=n).astype(np.int32)
+
+
+def logistic_sizes() -> list[tuple[int, int]]:
+    """(n, N) of Sec. 4.1's binary-classification runs: n features, N = 30 n points."""
+    return [(n, 30 * n) for n in (50, 500, 1000, 5000)]
 
 
 def fw_start(d: int) -> np.ndarray:
