@@ -356,6 +356,84 @@ def run_ragged(args, dev, world, rank, flush, stream):
 NV_WORKLOAD = dict(name="newsvendor_n1M_S1000_K1", n=1_000_000, S=1000, K=1)
 
 
+LG_WORKLOAD = dict(name="logistic_n5000_N150000", n=5000, N=150_000, b=50, bH=600)
+
+
+def run_logistic(args, dev, world, rank, flush, stream):
+    """The binary-classification task (Sec. 3.3) at Sec. 4.1's largest size:
+    n = 5000 binary features, N = 30 n = 150000 points (10 % label noise).
+    One step is the full-data objective, gradient and Hessian product at one
+    parameter vector; the unit is one (point, feature) pair.  The SQN-sized
+    calls (gradient on b = 50 points, Hessian product on b_H = 600) are timed
+    too: they are launch-bound."""
+    import torch
+    from paper_2404_11631_gb300 import inputs, saa
+    n, N = LG_WORKLOAD["n"], LG_WORKLOAD["N"]
+    wstar = torch.tensor(inputs.logistic_weights(n, 0), device=dev)
+    data = saa.saa_logistic_generate(n, N, wstar, seed=0, instance=rank)
+    rng = np.random.default_rng(0)
+    W = torch.tensor(0.02 * rng.normal(size=(1, n)), device=dev)
+    V = torch.tensor(rng.normal(size=(1, n)), device=dev)
+    out = saa.saa_logistic_eval(data["X"], data["z"], n, W, V)
+    ws = out["ws"]
+    for _ in range(3):
+        saa.saa_logistic_eval(data["X"], data["z"], n, W, V, ws=ws)
+    torch.cuda.synchronize(dev)
+    saa.saa_profile_enable(True, dev.index)
+    steps = max(3, min(args.steps, 20))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        saa.saa_logistic_eval(data["X"], data["z"], n, W, V, ws=ws)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    main_ms, main_n, launched = saa.saa_profile_read(dev.index)
+    saa.saa_profile_enable(False, dev.index)
+    saa.saa_ctx_sync(dev.index)
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    kern_s = main_ms / 1e3 / max(1, main_n)
+    pairs = float(N) * n
+    # masked adds per (point, feature): omega and v in the forward pass,
+    # gradient and Hessian product in the adjoint
+    ops = 4.0 * pairs
+    peaks, _ = _peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = 152 * 128 * mhz * 1e6 / 1e12
+    # SQN-sized calls: mini-batch gradient (b = 50) and Hessian product (b_H = 600)
+    mini = {}
+    for name, b, want_v in (("grad_b50", LG_WORKLOAD["b"], False), ("hvp_b600", LG_WORKLOAD["bH"], True)):
+        idx = torch.tensor(rng.integers(0, N, size=b), dtype=torch.int64, device=dev)
+        for _ in range(3):
+            saa.saa_logistic_eval(data["X"], data["z"], n, W, V if want_v else None, idx=idx)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            saa.saa_logistic_eval(data["X"], data["z"], n, W, V if want_v else None, idx=idx)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        mini[name] = {"us_per_call": 1e3 * e0.elapsed_time(e1) / 20}
+    res = {"metric": "logistic point-feature pairs/s (F, gradient, Hessian product)",
+           "value": world * pairs * steps / total_s, "unit": "pairs/s", "ms_per_step": 1e3 * total_s / steps,
+           "kernels_ms": kern_s * 1e3, "gpu_launches_per_step": launched / steps,
+           "roofline": {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": ops / kern_s / 1e12 / peak,
+                        "note": "lane-ops: 4 masked adds per (point, feature) pair; forward + adjoint kernels"},
+           "mini_batch": mini,
+           "config": {"workload": LG_WORKLOAD["name"], "n": n, "N": N, "K": 1, "features": "bits, Bernoulli(1/2)",
+                      "labels": "integer linear rule, 10% flips", "data_bytes": int(data["X"].numel()) * 4}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        op = oracle.make_logistic(n, N, inputs.logistic_weights(n, 0), seed=0, instance=rank)
+        t0 = time.perf_counter()
+        oracle.logistic_eval(op, W.cpu().numpy(), V=V.cpu().numpy())
+        dt = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": float(N) * n / dt, "unit": "pairs/s", "cores": oracle.max_threads(),
+                               "kind": "oracle", "sample": f"all {N} points x {n} features, {dt:.1f} s"}
+    return res
+
+
 def run_newsvendor(args, dev, world, rank, flush, stream):
     """The newsvendor's Monte Carlo gradient (Sec. 3.2): n = 10^6 products
     (the largest inventory of Sec. 4.1), S = 1000 normal demand samples per
@@ -715,6 +793,8 @@ def run_ours(args):
         line["covariance_first"] = run_covariance(args, dev, world, rank, flush, stream)
     if not args.no_streamed:
         line["streamed"] = run_streamed(args, dev, world, rank, flush, stream)
+    if not args.no_logistic:
+        line["logistic"] = run_logistic(args, dev, world, rank, flush, stream)
     if rank == 0:
         line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -752,6 +832,8 @@ def main():
     ap.add_argument("--cov-only", action="store_true", help="run only the covariance-first workload")
     ap.add_argument("--nv-only", action="store_true", help="run only the newsvendor gradient workload")
     ap.add_argument("--no-streamed", action="store_true", help="skip the streamed-samples workload")
+    ap.add_argument("--no-logistic", action="store_true", help="skip the binary-classification workload")
+    ap.add_argument("--logistic-only", action="store_true", help="run only the binary-classification workload")
     ap.add_argument("--streamed-only", action="store_true", help="run only the streamed-samples workload")
     ap.add_argument("--nv-n", type=int, default=None, help="override the newsvendor product count")
     ap.add_argument("--fw-N", type=int, default=None, help="override the Algorithm 1 scenario count")
@@ -788,6 +870,12 @@ def main():
         dev = torch.device("cuda", 0)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
         print(json.dumps(run_covariance(args, dev, 1, 0, flush, torch.cuda.current_stream(dev))), flush=True)
+        return 0
+    if args.logistic_only:
+        import torch
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps(run_logistic(args, dev, 1, 0, flush, torch.cuda.current_stream(dev))), flush=True)
         return 0
     if args.streamed_only:
         import torch

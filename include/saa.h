@@ -263,6 +263,48 @@ saa_status saa_eval_samples(saa_ctx* ctx, int64_t N, int32_t d, const float* R, 
                             const double* sigma, int32_t K, const double* X, double lambda, saa_prec prec,
                             double* f, double* pbar, double* var, void* ws, size_t ws_bytes, void* stream);
 
+/* The binary-classification task of Sec. 3.3 (logistic model):
+ *   t = x_i'omega_k, c = 1 / (1 + e^-t)
+ *   F_k    = -(1/b) sum_S [ z log c + (1 - z) log(1 - c) ]
+ *   grad_k = (1/b) sum_S (c - z) x_i            (the mini-batch gradient)
+ *   hvp_k  = (1/b) sum_S c (1 - c) (x_i'v_k) x_i (sub-sampled Hessian times v_k)
+ * over a sample S of a binary data set, for K parameter vectors at once.
+ *
+ * Data layout: row i of X holds saa_logistic_pitch(n) 32-bit words; feature
+ * j of point i is bit j % 32 of word j / 32 (bits past n are 0); z [N]
+ * holds the labels (0 or 1).
+ *
+ * saa_logistic_generate writes rows i0 .. i0+rows-1 of the synthetic data
+ * set of Sec. 4.1's setup (X starts at row i0; z optional): feature j =
+ * 128 b + 32 q + t of point i is bit t of word q of Philox4x32-10(counter
+ * (b, i, 0, (4 << 24) | instance), key seed), and the label is [2 x_i'w* >
+ * 1'w*] (integer arithmetic) flipped when word 0 of Philox(counter (0, i,
+ * 0, (5 << 24) | instance)) is below `flip` (429496730 for the paper's 10 %
+ * label noise).  X must be 16-byte aligned.
+ *
+ * saa_logistic_eval: idx device [b] int64 row indices of S (repeats
+ * allowed), or NULL for every row (b = N); W device [K*n] FP64; V device
+ * [K*n] FP64 (needed for hvp); F [K], grad [K*n], hvp [K*n] device FP64,
+ * each optional.  Scratch: saa_logistic_workspace_size(n, b, K, has_v)
+ * bytes, 256-byte aligned (has_v = V and hvp both given).  EUNSUPPORTED for
+ * n > 43648.  Deterministic for a given device. */
+typedef struct {
+    int32_t n;            /* features */
+    int32_t reserved;     /* must be 0 */
+    int64_t N;            /* data points, 1 <= N < 2^32 */
+    uint64_t seed;        /* Philox key */
+    uint32_t instance;    /* low 24 bits used (counter word 3) */
+    uint32_t flip;        /* label-noise threshold on a 32-bit word */
+    const int32_t* wstar; /* device [n]: integer weights of the labelling rule */
+} saa_logistic;
+int32_t saa_logistic_pitch(int32_t n);
+saa_status saa_logistic_generate(saa_ctx* ctx, const saa_logistic* prob, int64_t i0, int64_t rows, uint32_t* X,
+                                 uint8_t* z, void* stream);
+size_t saa_logistic_workspace_size(const saa_ctx* ctx, int32_t n, int64_t b, int32_t K, int has_v);
+saa_status saa_logistic_eval(saa_ctx* ctx, int32_t n, int64_t N, const uint32_t* X, const uint8_t* z,
+                             const int64_t* idx, int64_t b, int32_t K, const double* W, const double* V, double* F,
+                             double* grad, double* hvp, void* ws, size_t ws_bytes, void* stream);
+
 /* Moments of the generator: per-dimension sums of the innovations zhat_ij
  * (after the law transform, before the t law's scale s_i) and of their
  * squares over scenarios i0 .. i0+n-1 of resample index prob->epoch, drawn

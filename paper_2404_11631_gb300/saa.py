@@ -120,6 +120,16 @@ def lib():
             L.saa_eval_moments_workspace_size.restype = sz
             L.saa_eval_moments.argtypes = [vp, pp, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
             L.saa_eval_moments.restype = C.c_int
+            lgp = C.POINTER(_CLogistic)
+            L.saa_logistic_pitch.argtypes = [C.c_int32]
+            L.saa_logistic_pitch.restype = C.c_int32
+            L.saa_logistic_generate.argtypes = [vp, lgp, C.c_int64, C.c_int64, vp, vp, vp]
+            L.saa_logistic_generate.restype = C.c_int
+            L.saa_logistic_workspace_size.argtypes = [vp, C.c_int32, C.c_int64, C.c_int32, C.c_int]
+            L.saa_logistic_workspace_size.restype = sz
+            L.saa_logistic_eval.argtypes = [vp, C.c_int32, C.c_int64, vp, vp, vp, C.c_int64, C.c_int32, vp, vp, vp,
+                                            vp, vp, vp, sz, vp]
+            L.saa_logistic_eval.restype = C.c_int
             L.saa_solve_adaptive_workspace_size.argtypes = [vp, pp, C.POINTER(C.c_int64), C.c_int32, C.c_int]
             L.saa_solve_adaptive_workspace_size.restype = sz
             L.saa_solve_adaptive.argtypes = [vp, pp, vp, C.POINTER(C.c_int64), C.c_int32, C.c_int32, C.c_int32,
@@ -363,6 +373,74 @@ def saa_generate_moments(prob: Problem, i0: int, n: int, prec="fp32", out: dict 
     _check(lib().saa_generate_moments(ctx, C.byref(cp), i0, n, _prec(prec), _ptr(s1), _ptr(s2), _ptr(ws),
                                       ws.numel(), _stream(dev)))
     return {"sum": s1, "sumsq": s2, "ws": ws}
+
+
+class _CLogistic(C.Structure):
+    _fields_ = [("n", C.c_int32), ("reserved", C.c_int32), ("N", C.c_int64), ("seed", C.c_uint64),
+                ("instance", C.c_uint32), ("flip", C.c_uint32), ("wstar", C.c_void_p)]
+
+
+LABEL_NOISE_10PCT = 429496730   # round(0.1 * 2^32): the paper's 10 % label noise
+
+
+def saa_logistic_generate(n: int, N: int, wstar: torch.Tensor, seed: int = 0, instance: int = 0,
+                          flip: int = LABEL_NOISE_10PCT, i0: int = 0, rows: int | None = None) -> dict:
+    """Synthetic binary-classification data (Sec. 4.1's setup) on the device:
+    {'X': int32 [rows, pitch] feature bits, 'z': uint8 [rows] labels}."""
+    if not (wstar.is_cuda and wstar.dtype == torch.int32 and wstar.is_contiguous() and wstar.numel() == n):
+        raise ValueError("wstar must be a contiguous int32 CUDA tensor [n]")
+    dev = wstar.device
+    rows = N - i0 if rows is None else rows
+    pitch = int(lib().saa_logistic_pitch(n))
+    X = torch.empty(rows, pitch, dtype=torch.int32, device=dev)
+    z = torch.empty(rows, dtype=torch.uint8, device=dev)
+    cp = _CLogistic(n, 0, N, seed, instance, flip, wstar.data_ptr())
+    _check(lib().saa_logistic_generate(context(dev.index), C.byref(cp), i0, rows, _ptr(X), _ptr(z), _stream(dev)))
+    return {"X": X, "z": z}
+
+
+def saa_logistic_eval(X: torch.Tensor, z: torch.Tensor, n: int, W: torch.Tensor, V: torch.Tensor | None = None,
+                      idx: torch.Tensor | None = None, want_grad: bool = True, want_hvp: bool | None = None,
+                      ws: torch.Tensor | None = None) -> dict:
+    """F [K], grad [K, n] and (with V) hvp [K, n] of the logistic objective
+    over the rows idx (int64, repeats allowed; all rows when None) of the
+    bit matrix X [N, pitch] with labels z [N], for omega = W [K, n]."""
+    if W.dim() == 1:
+        W = W.unsqueeze(0)
+    if V is not None and V.dim() == 1:
+        V = V.unsqueeze(0)
+    N = int(X.shape[0])
+    if not (X.is_cuda and X.dtype == torch.int32 and X.is_contiguous() and X.shape[1] == lib().saa_logistic_pitch(n)):
+        raise ValueError("X must be the contiguous int32 CUDA bit matrix [N, saa_logistic_pitch(n)]")
+    if not (z.is_cuda and z.dtype == torch.uint8 and z.numel() == N):
+        raise ValueError("z must be a uint8 CUDA tensor [N]")
+    for name, t in (("W", W), ("V", V)):
+        if t is not None and not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.shape[1] == n):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor [K, n]")
+    if idx is not None and not (idx.is_cuda and idx.dtype == torch.int64 and idx.is_contiguous()):
+        raise ValueError("idx must be a contiguous int64 CUDA tensor")
+    want_hvp = (V is not None) if want_hvp is None else want_hvp
+    K = int(W.shape[0])
+    b = N if idx is None else int(idx.numel())
+    dev = X.device
+    ctx = context(dev.index)
+    has_v = 1 if (V is not None and want_hvp) else 0
+    need = lib().saa_logistic_workspace_size(ctx, n, b, K, has_v)
+    if need == 0:
+        raise SAAError(SAA_EINVAL, lib().saa_last_error().decode())
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    F = torch.empty(K, dtype=torch.float64, device=dev)
+    g = torch.empty(K, n, dtype=torch.float64, device=dev) if want_grad else None
+    h = torch.empty(K, n, dtype=torch.float64, device=dev) if has_v else None
+    _check(lib().saa_logistic_eval(ctx, n, N, _ptr(X), _ptr(z), _ptr(idx), b, K, _ptr(W), _ptr(V), _ptr(F), _ptr(g),
+                                   _ptr(h), _ptr(ws), ws.numel(), _stream(dev)))
+    out = {"F": F, "ws": ws}
+    if g is not None:
+        out["grad"] = g
+    if h is not None:
+        out["hvp"] = h
+    return out
 
 
 @dataclass
@@ -627,4 +705,5 @@ EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_
             "saa_batch_launch", "saa_batch_destroy", "saa_newsvendor_workspace_size", "saa_newsvendor_grad",
             "saa_moments_workspace_size", "saa_moments", "saa_eval_moments_workspace_size", "saa_eval_moments",
             "saa_eval_samples_workspace_size", "saa_eval_samples", "saa_solve_adaptive_workspace_size",
-            "saa_solve_adaptive"]
+            "saa_solve_adaptive", "saa_logistic_pitch", "saa_logistic_generate", "saa_logistic_workspace_size",
+            "saa_logistic_eval"]
