@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
   if (warp < kEpiWarps) {
 #pragma unroll
     for (int g = 0; g < kMaxKp / 32; ++g)
-      if (32 * g < a.Kp) red_s2[warp * a.Kp + 32 * g + lane] = (double)s2h[g] + (double)s2l[g];
+      if (32 * g < a.Kp) red_s2[warp * a.Kp + 32 * g + epi_col(lane)] = (double)s2h[g] + (double)s2l[g];
   }
   __syncthreads();
   for (int j = threadIdx.x; j < d; j += blockDim.x) {

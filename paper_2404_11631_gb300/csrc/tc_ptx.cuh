@@ -192,32 +192,53 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
   hi = s;
 }
 
+// 16 lanes x 32 consecutive 32-bit columns (the 16x256b shape, 4 repeats):
+// thread t receives r[4j + 2h + b] = lane (t/4 + 8h), column 8j + 2(t%4) + b.
+__device__ __forceinline__ void tmem_ld16x256_x4(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+// Column of the 32 that epi_sq_colsum32 leaves in lane t.
+__device__ __forceinline__ int epi_col(int lane) {
+  return 8 * ((lane >> 3) & 3) + 2 * (lane & 3) + ((lane >> 2) & 1);
+}
+
 // Column sums of q^2, q = D1 + D2, over a warp's 32 TMEM lanes (rows) for
-// the 32 columns at t1 / t2 (lane quadrant already in the address): lane l
-// returns column l's sum.  Reduce-scatter over the lanes: at each of the 5
-// levels a lane keeps half of its values and adds its partner's other half,
-// so lane l ends with column l.
+// the 32 columns at t1 / t2 (lane quadrant already in the address): lane t
+// returns column epi_col(t)'s sum.  With the 16x256b shape each thread holds
+// four rows of two columns per 8-column block (rows t/4, t/4 + 8, t/4 + 16,
+// t/4 + 24), so the rows fold in registers first; a reduce-scatter over the
+// eight row groups (lanes 4 apart) leaves one column per lane.
 __device__ __forceinline__ float epi_sq_colsum32(uint32_t t1, uint32_t t2, int lane) {
-  float v[32];
+  float v[8];   // v[2j + b]: column 8j + 2(t%4) + b over the thread's rows
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {   // two 16-column loads keep fewer registers live
+  for (int half = 0; half < 2; ++half) {
     uint32_t r1[16], r2[16];
-    tmem_ld16(t1 + 16u * h, r1);
-    tmem_ld16(t2 + 16u * h, r2);
+    tmem_ld16x256_x4(t1 + ((16u * half) << 16), r1);
+    tmem_ld16x256_x4(t2 + ((16u * half) << 16), r2);
     tmem_wait_ld();
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const float q = __uint_as_float(r1[i]) + __uint_as_float(r2[i]);
-      v[16 * h + i] = q * q;
-    }
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const float qa = __uint_as_float(r1[4 * j + b]) + __uint_as_float(r2[4 * j + b]);
+        const float qb = __uint_as_float(r1[4 * j + 2 + b]) + __uint_as_float(r2[4 * j + 2 + b]);
+        const float sq = fmaf(qa, qa, qb * qb);
+        v[2 * j + b] = half ? v[2 * j + b] + sq : sq;
+      }
   }
 #pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
+  for (int w = 16; w >= 4; w >>= 1) {
     const bool upper = (lane & w) != 0;
+    const int hw = w >> 2;   // values kept: 4, 2, 1
 #pragma unroll
-    for (int i = 0; i < w; ++i) {
-      const float send = upper ? v[i] : v[i + w];
-      const float keep = upper ? v[i + w] : v[i];
+    for (int i = 0; i < hw; ++i) {
+      const float send = upper ? v[i] : v[i + hw];
+      const float keep = upper ? v[i + hw] : v[i];
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
     }
   }

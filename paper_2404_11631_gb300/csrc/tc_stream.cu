@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
 #pragma unroll
     for (int i = 0; i < kSMaxKp / 32 / kSEpiStride; ++i) {
       const int g = (warp >> 2) + i * kSEpiStride;
-      if (32 * g < a.Kp) red_s2[(warp & 3) * a.Kp + 32 * g + lane] = (double)s2h[i] + (double)s2l[i];
+      if (32 * g < a.Kp) red_s2[(warp & 3) * a.Kp + 32 * g + epi_col(lane)] = (double)s2h[i] + (double)s2l[i];
     }
   } else if (warp > kSProd) {
     const int cw = warp - (kSProd + 1);
