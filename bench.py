@@ -307,8 +307,18 @@ def run_fw(args, dev, world, rank):
                 "N_first_last": [sched[0], sched[-1]], "graphs": len(set(sched)),
                 "note": "time includes capturing one graph per distinct N_k",
                 "f_last": float(ad["f_trace"].cpu().numpy()[-1])}
+    # ALU roofline per iteration: the generator-only kernel's count per
+    # (Gaussian) normal, the t law's chi-square draws and one multiply-add
+    # each for the forward dot product and the adjoint per normal
+    peaks, _ = _peaks()
+    peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    ops = float(N) * d * (GEN_INST_GAUSS + 2.0)
+    achieved = ops / (ms / 1e3) / 1e12
     return {"metric": "Frank-Wolfe iterations/s (Algorithm 1)", "value": world * 1e3 / ms, "unit": "iterations/s",
             "ms_per_iteration": ms, "normals_per_s": N * d / (ms / 1e3), "iterations": T,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak,
+                         "note": "lane-ops per iteration: generator per normal + 2 fma per normal; whole iteration"},
             "config": {"workload": FW_WORKLOAD["name"], "d": d, "N": N, "law": "Student-t nu=4", "M": 1,
                        "prec": prec, "graph": "one captured iteration replayed T times"},
             "f_first_last": [float(f[0]), float(f[-1])], "gap_last": float(gap[-1]), "adaptive_N": adaptive}
@@ -345,9 +355,19 @@ def run_ragged(args, dev, world, rank, flush, stream):
     evals = float(np.sum(rb.N.astype(np.float64) * rb.K))
     normals = float(np.sum(rb.N.astype(np.float64) * rb.d))
     batch.close()
+    # ALU roofline: the generator-only kernel's count per (Gaussian) normal
+    # plus the fused kernel's K_b multiply-adds per normal (dot products
+    # formed while drawing), over the whole replay
+    peaks, _ = _peaks()
+    peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    ops = normals * GEN_INST_GAUSS + float(np.sum(rb.N.astype(np.float64) * rb.d * rb.K))
+    achieved = ops * steps / total_s / 1e12
     return {"metric": "scenario-decision evals/s (ragged batch)", "value": world * evals * steps / total_s,
             "unit": "evals/s", "ms_per_step": 1e3 * total_s / steps, "steps": steps,
             "normals_per_s": normals * steps / total_s,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak,
+                         "note": "lane-ops: generator per normal + K_b fma per normal; whole replay time"},
             "config": {"workload": f"ragged_{len(rb.d)}_gauss", "instances": len(rb.d), "d": "U{8..512}",
                        "N": "floor(10^U[3,5])", "K": "U{1..16}", "prec": "fp32", "sum_NK": evals, "sum_Nd": normals,
                        "graph": "autotuned tile shape, launch sequence captured once and replayed"}}
