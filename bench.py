@@ -193,7 +193,7 @@ def roofline(prec, d, N, K, law, kern_s, peaks, peak_src):
         # ncu dram__bytes_read.sum + dram__bytes_write.sum of the tensor kernel
         # (F16, d = 128, K = 256): the per-launch operand image, independent of N
         if prec == "f16x3" and d == 128 and K == 256:
-            r["traffic"] = 188672
+            r["traffic"] = 188928
         tflops = 3 * 2.0 * N * d * K / kern_s / 1e12
         r["tensor"] = {"achieved": tflops, "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
                        "frac": tflops / float(peaks["bf16_tflops"]), "peak_source": f"{peak_src} bf16 dense (burst)"}
