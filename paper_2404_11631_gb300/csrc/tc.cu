@@ -86,7 +86,9 @@ size_t smem_bytes(int Kp, int nkb) {
   return (size_t)kStages * kStageBytes + (size_t)nkb * 2 * Kp * 128 + sizeof(Smem);
 }
 
-template <bool F16, int NKB>
+// D8: d is a multiple of 8, so every 8-dimension unit below d is whole and
+// the per-element guards drop out.
+template <bool F16, int NKB, bool D8>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // The 128-byte swizzle is address based: operands need a 1024-byte aligned base.
@@ -231,6 +233,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
       if (tlaw && !warp_wait(s_bar, (uint32_t)((tt >> 2) & 1), abort_flag, a.err)) break;
       uint8_t* stage = As + st * kStageBytes;
       const int j0 = kb * kKB + cu * 8;   // first dimension of this unit
+      float vs[8];                         // this stage's rows, summed (m~)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) vs[e] = 0.0f;
 #pragma unroll 1
       for (int r = rt >> 3; r < kM; r += kRngThreads / 8) {
         float v[8];
@@ -242,11 +247,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
           float z[4];
           gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2), i, logn, z);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) v[e] = (j0 + e < d) ? z[e] : 0.0f;
-          if (j0 + 4 < d) {
+          for (int e = 0; e < 4; ++e) v[e] = (D8 || j0 + e < d) ? z[e] : 0.0f;
+          if (D8 || j0 + 4 < d) {
             gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2) + 1u, i, logn, z);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) v[4 + e] = (j0 + 4 + e < d) ? z[e] : 0.0f;
+            for (int e = 0; e < 4; ++e) v[4 + e] = (D8 || j0 + 4 + e < d) ? z[e] : 0.0f;
           }
           if (tlaw) {
             const float s = sm->s_buf[sb][r];
@@ -265,11 +270,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
         *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         *reinterpret_cast<uint4*>(stage + kM * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
 #pragma unroll
-        for (int b = 0; b < NKB; ++b)
-          if (b == kb)
-#pragma unroll
-            for (int e = 0; e < 8; ++e) macc[b][e] += v[e];
+        for (int e = 0; e < 8; ++e) vs[e] += v[e];
       }
+#pragma unroll
+      for (int b = 0; b < NKB; ++b)
+        if (b == kb)
+#pragma unroll
+          for (int e = 0; e < 8; ++e) macc[b][e] += vs[e];
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sm->a_full[st]));
@@ -473,10 +480,15 @@ cudaError_t launch_tc(const LawArgs& la, int K, int prec, const Plan& plan, cons
   a.err = err;
   cudaError_t e = launch_tc_image(la.d, K, a.Kp, a.nkb, f16, ws.Y64, scale2, nullptr, img, st);
   if (e != cudaSuccess) return e;
-  auto kern = f16 ? (a.nkb == 1 ? tc::k_tc_value<true, 1> : a.nkb == 2 ? tc::k_tc_value<true, 2>
-                                                                          : tc::k_tc_value<true, 4>)
-                  : (a.nkb == 1 ? tc::k_tc_value<false, 1> : a.nkb == 2 ? tc::k_tc_value<false, 2>
-                                                                           : tc::k_tc_value<false, 4>);
+  const bool d8 = (la.d & 7) == 0;
+  auto kern = f16 ? (d8 ? (a.nkb == 1 ? tc::k_tc_value<true, 1, true> : a.nkb == 2 ? tc::k_tc_value<true, 2, true>
+                                                                                  : tc::k_tc_value<true, 4, true>)
+                        : (a.nkb == 1 ? tc::k_tc_value<true, 1, false> : a.nkb == 2 ? tc::k_tc_value<true, 2, false>
+                                                                                   : tc::k_tc_value<true, 4, false>))
+                  : (d8 ? (a.nkb == 1 ? tc::k_tc_value<false, 1, true> : a.nkb == 2 ? tc::k_tc_value<false, 2, true>
+                                                                                   : tc::k_tc_value<false, 4, true>)
+                        : (a.nkb == 1 ? tc::k_tc_value<false, 1, false>
+                                      : a.nkb == 2 ? tc::k_tc_value<false, 2, false> : tc::k_tc_value<false, 4, false>));
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
   if (e != cudaSuccess) return e;
   kern<<<plan.grid, tc::kThreadsTc, plan.smem, st>>>(a);
