@@ -97,7 +97,9 @@ struct GSmem {
 // Layout: [stages][W: 2 scenario blocks x hi/lo x Kp rows x 128 B][GSmem]; 1024-byte aligned base.
 size_t grad_smem_bytes(int Kp) { return (size_t)kGStages * kGStageBytes + (size_t)4 * Kp * 128 + sizeof(GSmem); }
 
-template <bool F16>
+// D8: d is a multiple of 8, so every unit below d is whole and the
+// per-element guards drop out.
+template <bool F16, bool D8>
 __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t base = smem_u32(smem_raw);
@@ -439,11 +441,11 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
             float z[4];
             gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2), i, logn, z);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) v[e] = (j0 + e < d) ? z[e] : 0.0f;
-            if (j0 + 4 < d) {
+            for (int e = 0; e < 4; ++e) v[e] = (D8 || j0 + e < d) ? z[e] : 0.0f;
+            if (D8 || j0 + 4 < d) {
               gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2) + 1u, i, logn, z);
 #pragma unroll
-              for (int e = 0; e < 4; ++e) v[4 + e] = (j0 + 4 + e < d) ? z[e] : 0.0f;
+              for (int e = 0; e < 4; ++e) v[4 + e] = (D8 || j0 + 4 + e < d) ? z[e] : 0.0f;
             }
             if (tlaw) {
               const float s = sm->s_buf[sb4][r];
@@ -476,16 +478,24 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
             if (r0 < nrow) {
               const uint32_t i = i0 + (uint32_t)r0;
               gen::Gen<float>::block(gs, (uint32_t)(jb >> 2), i, gen::is_lognormal(la.law, i, half), z0);
-              const float s0 = tlaw ? sm->s_buf[sb4][r0] : 1.0f;
+              if (tlaw) {
+                const float s0 = sm->s_buf[sb4][r0];
 #pragma unroll
-              for (int e = 0; e < 4; ++e) z0[e] = (jb + e < d) ? z0[e] * s0 : 0.0f;
+                for (int e = 0; e < 4; ++e) z0[e] *= s0;
+              }
+#pragma unroll
+              for (int e = 0; e < 4; ++e) z0[e] = (D8 || jb + e < d) ? z0[e] : 0.0f;
             }
             if (r0 + 1 < nrow) {
               const uint32_t i = i0 + (uint32_t)r0 + 1u;
               gen::Gen<float>::block(gs, (uint32_t)(jb >> 2), i, gen::is_lognormal(la.law, i, half), z1);
-              const float s1 = tlaw ? sm->s_buf[sb4][r0 + 1] : 1.0f;
+              if (tlaw) {
+                const float s1 = sm->s_buf[sb4][r0 + 1];
 #pragma unroll
-              for (int e = 0; e < 4; ++e) z1[e] = (jb + e < d) ? z1[e] * s1 : 0.0f;
+                for (int e = 0; e < 4; ++e) z1[e] *= s1;
+              }
+#pragma unroll
+              for (int e = 0; e < 4; ++e) z1[e] = (D8 || jb + e < d) ? z1[e] : 0.0f;
             }
           }
 #pragma unroll
@@ -600,7 +610,9 @@ cudaError_t launch_tc_grad(const LawArgs& la, int K, int prec, const Plan& plan,
   a.err = err;
   cudaError_t e = launch_tc_image(la.d, K, a.Kp, a.nkb, f16, ws.Y64, scale2, gaux, img, st);
   if (e != cudaSuccess) return e;
-  auto kern = f16 ? tc::k_tc_grad<true> : tc::k_tc_grad<false>;
+  const bool d8 = (la.d & 7) == 0;
+  auto kern = f16 ? (d8 ? tc::k_tc_grad<true, true> : tc::k_tc_grad<true, false>)
+                  : (d8 ? tc::k_tc_grad<false, true> : tc::k_tc_grad<false, false>);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
   if (e != cudaSuccess) return e;
   kern<<<plan.grid, tc::kGThreads, plan.smem, st>>>(a);

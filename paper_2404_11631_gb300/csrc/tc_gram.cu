@@ -66,7 +66,9 @@ struct QSmem {
 
 size_t gram_smem_bytes() { return (size_t)kQStages * kQStageBytes + sizeof(QSmem); }
 
-template <bool F16>
+// D4: d is a multiple of 4, so every 4-dimension block below d is whole and
+// the per-element guards drop out.
+template <bool F16, bool D4>
 __global__ void __launch_bounds__(kQThreads, 1) k_tc_gram(QArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t base = smem_u32(smem_raw);
@@ -222,16 +224,24 @@ __global__ void __launch_bounds__(kQThreads, 1) k_tc_gram(QArgs a) {
           if (r0 < nrow) {
             const uint32_t i = i0 + (uint32_t)r0;
             gen::Gen<float>::block(gs, (uint32_t)(jb >> 2), i, gen::is_lognormal(la.law, i, half), z0);
-            const float s0 = tlaw ? sm->s_buf[sb4][r0] : 1.0f;
+            if (tlaw) {
+              const float s0 = sm->s_buf[sb4][r0];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) z0[e] = (jb + e < d) ? z0[e] * s0 : 0.0f;
+              for (int e = 0; e < 4; ++e) z0[e] *= s0;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) z0[e] = (D4 || jb + e < d) ? z0[e] : 0.0f;
           }
           if (r0 + 1 < nrow) {
             const uint32_t i = i0 + (uint32_t)r0 + 1u;
             gen::Gen<float>::block(gs, (uint32_t)(jb >> 2), i, gen::is_lognormal(la.law, i, half), z1);
-            const float s1 = tlaw ? sm->s_buf[sb4][r0 + 1] : 1.0f;
+            if (tlaw) {
+              const float s1 = sm->s_buf[sb4][r0 + 1];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) z1[e] = (jb + e < d) ? z1[e] * s1 : 0.0f;
+              for (int e = 0; e < 4; ++e) z1[e] *= s1;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) z1[e] = (D4 || jb + e < d) ? z1[e] : 0.0f;
           }
         }
 #pragma unroll
@@ -456,7 +466,9 @@ extern "C" saa_status saa_moments(saa_ctx* ctx, const saa_problem* prob, saa_pre
   a.err = ctx->err;
   const int smem = (int)tc::gram_smem_bytes();
   cudaStream_t st = (cudaStream_t)stream;
-  auto kern = (prec == SAA_F16X3) ? tc::k_tc_gram<true> : tc::k_tc_gram<false>;
+  const bool d4 = (prob->d & 3) == 0;
+  auto kern = (prec == SAA_F16X3) ? (d4 ? tc::k_tc_gram<true, true> : tc::k_tc_gram<true, false>)
+                                  : (d4 ? tc::k_tc_gram<false, true> : tc::k_tc_gram<false, false>);
   s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                   "saa_moments: shared-memory attribute");
   if (s != SAA_OK) return s;
