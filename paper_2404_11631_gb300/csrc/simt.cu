@@ -178,7 +178,9 @@ constexpr int kNarrowK = 4;
 #endif
 constexpr int kNarrowWide = SAA_NARROW_WIDE_THREADS;
 
-template <typename T, int BM, int NT>
+// KN: decisions handled (K <= KN <= kNarrowK); the buffers keep the kNarrowK
+// stride.
+template <typename T, int BM, int NT, int KN>
 __global__ void __launch_bounds__(NT, NT == kThreads ? 2 : 1) k_narrow(LawArgs la, int K, int want_grad,
                                                         const T* __restrict__ Yt, double* __restrict__ part_s1,
                                                         double* __restrict__ part_s2, double* __restrict__ part_m,
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? 2 : 1) k_narrow(LawArgs l
   const gen::Stream st = gen::make_stream(la.seed, epoch, la.instance);
   const uint32_t half = la.N / 2u;
   const int nb = (d + PC - 1) / PC;
+  const bool tlaw = la.law == SAA_LAW_STUDENT_T;   // other laws have s = 1
 
   for (int idx = tid; idx < kNarrowK * d; idx += NT) {
     const int k = idx / d, j = idx % d;
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? 2 : 1) k_narrow(LawArgs l
   for (int r = 0; r < JR; ++r) {
     macc[r] = 0.0;
 #pragma unroll
-    for (int k = 0; k < kNarrowK; ++k) gs[r][k] = gc[r][k] = T(0);
+    for (int k = 0; k < KN; ++k) gs[r][k] = gc[r][k] = T(0);
   }
   double* p_s1 = part_s1 + (size_t)blockIdx.x * K;
   double* p_s2 = part_s2 + (size_t)blockIdx.x * K;
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? 2 : 1) k_narrow(LawArgs l
     // draw the samples of scenario i_own, blocks g_own, g_own + G, ...
     T q[kNarrowK];
 #pragma unroll
-    for (int k = 0; k < kNarrowK; ++k) q[k] = T(0);
+    for (int k = 0; k < KN; ++k) q[k] = T(0);
     const bool live = i_own < nrow;
     const uint32_t i = i0 + (uint32_t)i_own;
     const bool logn = gen::is_lognormal(la.law, i, half);
@@ -237,8 +240,9 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? 2 : 1) k_narrow(LawArgs l
       T z[PC];
       if (live) {
         gen::Gen<T>::block(st, (uint32_t)b, i, logn, z);
+        if (tlaw)
 #pragma unroll
-        for (int e = 0; e < PC; ++e) z[e] *= s;
+          for (int e = 0; e < PC; ++e) z[e] *= s;
       } else {
 #pragma unroll
         for (int e = 0; e < PC; ++e) z[e] = T(0);
@@ -249,18 +253,19 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? 2 : 1) k_narrow(LawArgs l
         if (j < d) {
           As[(size_t)j * BMP + i_own] = z[e];
 #pragma unroll
-          for (int k = 0; k < kNarrowK; ++k) q[k] = fma(z[e], Ys[k * d + j], q[k]);
+          for (int k = 0; k < KN; ++k) q[k] = fma(z[e], Ys[k * d + j], q[k]);
         }
       }
     }
 #pragma unroll
-    for (int k = 0; k < kNarrowK; ++k) qp[((size_t)g_own * BM + i_own) * kNarrowK + k] = q[k];
+    for (int k = 0; k < KN; ++k) qp[((size_t)g_own * BM + i_own) * kNarrowK + k] = q[k];
     __syncthreads();
     if (tid < BM * kNarrowK) {
       const int ii = tid / kNarrowK, k = tid % kNarrowK;
       T v = T(0);
+      if (k < KN)
 #pragma unroll
-      for (int g = 0; g < G; ++g) v += qp[((size_t)g * BM + ii) * kNarrowK + k];
+        for (int g = 0; g < G; ++g) v += qp[((size_t)g * BM + ii) * kNarrowK + k];
       Qs[ii * kNarrowK + k] = v;
     }
     __syncthreads();
@@ -281,19 +286,19 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? 2 : 1) k_narrow(LawArgs l
         T sum = T(0);
         T gt[kNarrowK];
 #pragma unroll
-        for (int k = 0; k < kNarrowK; ++k) gt[k] = T(0);
+        for (int k = 0; k < KN; ++k) gt[k] = T(0);
         for (int ii = 0; ii < nrow; ++ii) {
           const T a = As[(size_t)j * BMP + ii];
           sum += a;
           if (want_grad) {
 #pragma unroll
-            for (int k = 0; k < kNarrowK; ++k) gt[k] = fma(a, Qs[ii * kNarrowK + k], gt[k]);
+            for (int k = 0; k < KN; ++k) gt[k] = fma(a, Qs[ii * kNarrowK + k], gt[k]);
           }
         }
         macc[r] += (double)sum;
         if (want_grad) {
 #pragma unroll
-          for (int k = 0; k < kNarrowK; ++k) {   // Kahan: gc carries the lost low part
+          for (int k = 0; k < KN; ++k) {   // Kahan: gc carries the lost low part
             const T y = gt[k] - gc[r][k];
             const T t = gs[r][k] + y;
             gc[r][k] = (t - gs[r][k]) - y;
@@ -312,7 +317,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? 2 : 1) k_narrow(LawArgs l
         part_m[(size_t)blockIdx.x * d + j] = macc[r];
         if (want_grad) {
 #pragma unroll
-          for (int k = 0; k < kNarrowK; ++k)
+          for (int k = 0; k < KN; ++k)
             if (k < K) {
               const size_t e = ((size_t)blockIdx.x * K + k) * d + j;
               part_g[e] = gs[r][k];
@@ -336,7 +341,7 @@ size_t narrow_smem(int prec, int d, int bm) {
 }
 
 template <typename T, int BM, int NT>
-static const void* narrow_fn() { return (const void*)k_narrow<T, BM, NT>; }
+static const void* narrow_fn() { return (const void*)k_narrow<T, BM, NT, kNarrowK>; }
 
 static const void* narrow_kernel(int prec, int bm) {
   if (prec == SAA_FP64) return bm == 64 ? narrow_fn<double, 64, kThreads>()
@@ -356,7 +361,7 @@ int narrow_occupancy(int prec, int bm, int smem) {
 template <typename T, int BM, int NT>
 static cudaError_t launch_narrow_t(const LawArgs& la, int K, int want_grad, const Plan& plan, const Workspace& ws,
                                    cudaStream_t st) {
-  auto kern = k_narrow<T, BM, NT>;
+  auto kern = K == 1 ? k_narrow<T, BM, NT, 1> : K == 2 ? k_narrow<T, BM, NT, 2> : k_narrow<T, BM, NT, kNarrowK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
   if (e != cudaSuccess) return e;
   kern<<<plan.grid, NT, plan.smem, st>>>(la, K, want_grad, (const T*)ws.Y, ws.part_s1, ws.part_s2, ws.part_m,
