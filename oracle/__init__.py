@@ -73,6 +73,7 @@ class Problem(C.Structure):
         ("epoch", C.c_uint32),
         ("mu", C.POINTER(C.c_double)),
         ("chol", C.POINTER(C.c_double)),
+        ("sd", C.POINTER(C.c_double)),
     ]
 
 
@@ -236,13 +237,20 @@ def constants(which: int) -> np.ndarray:
 
 # --- problem marshalling ---------------------------------------------------
 
-def make_problem(d, N, mu, chol, law=LAW_GAUSS, nu=4, lam=0.5, seed=0, instance=0, epoch=0):
-    """Returns (Problem, keepalive) for the given law parameters."""
+def make_problem(d, N, mu, chol, law=LAW_GAUSS, nu=4, lam=0.5, seed=0, instance=0, epoch=0, sd=None):
+    """Returns (Problem, keepalive) for the given law parameters; chol None
+    with ``sd`` [d] gives Sigma = diag(sd^2)."""
     mu = np.ascontiguousarray(mu, dtype=np.float64)
-    chol = np.ascontiguousarray(chol, dtype=np.float64)
-    assert mu.shape == (d,) and chol.shape == (d, d)
-    P = Problem(d, N, law, nu, lam, seed, instance, epoch, _p(mu), _p(chol))
-    return P, (mu, chol)
+    assert mu.shape == (d,)
+    if chol is not None:
+        chol = np.ascontiguousarray(chol, dtype=np.float64)
+        assert chol.shape == (d, d)
+    if sd is not None:
+        sd = np.ascontiguousarray(sd, dtype=np.float64)
+        assert sd.shape == (d,)
+    assert chol is not None or sd is not None
+    P = Problem(d, N, law, nu, lam, seed, instance, epoch, _p(mu), _p(chol), _p(sd))
+    return P, (mu, chol, sd)
 
 
 def generate(prob, prec, i0, n, epoch=None, want_xi=False):

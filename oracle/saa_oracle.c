@@ -68,7 +68,8 @@ typedef struct {
     uint32_t instance;/* instance id (low 24 bits of counter word 3) */
     uint32_t epoch;   /* resample index (counter word 2) */
     const double* mu;   /* [d] mean of R */
-    const double* chol; /* [d*d] row-major lower-triangular C with C C' = Sigma */
+    const double* chol; /* [d*d] row-major lower-triangular C with C C' = Sigma, or NULL */
+    const double* sd;   /* [d] with chol NULL: Sigma = diag(sd^2), the independent assets of Sec. 4.1 */
 } oracle_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -538,7 +539,7 @@ static int check_problem(const oracle_problem* p)
     if (!p || p->d < 1 || p->N < 2 || p->N > 0xffffffffll) return OR_EINVAL;
     if (p->law < 0 || p->law > OR_LAW_MIX) return OR_EINVAL;
     if (p->law == OR_LAW_STUDENT_T && (p->nu < 2 || (p->nu & 1))) return OR_EINVAL;
-    if (!p->mu || !p->chol) return OR_EINVAL;
+    if (!p->mu || (!p->chol && !p->sd)) return OR_EINVAL;
     return OR_OK;
 }
 
@@ -552,6 +553,7 @@ int oracle_generate(const oracle_problem* p, int prec, uint32_t epoch, int64_t i
 {
     if (check_problem(p) != OR_OK || (prec != 32 && prec != 64) || i0 < 0 || n < 0 || i0 + n > p->N)
         return OR_EINVAL;
+    if (xi && !p->chol) return OR_EINVAL;   /* the sample map of this output needs the dense C */
     const int d = p->d;
     int err = OR_OK;
 #pragma omp parallel
@@ -662,6 +664,12 @@ static void get_sample(const sample_src* S, sample_buf* B, int64_t i, double* ou
         s = (double)sf;
     } else {
         gen_f64(S->p, i, S->epoch, B->zd, &s);
+    }
+    if (!S->Ct) {
+        /* C = diag(sd): out_j = mu_j + s_i * (sd_j zhat_j), the same roundings as
+         * the sum below for a diagonal C (whose other terms add exact zeros). */
+        for (int j = 0; j < d; ++j) out[j] = S->p->mu[j] + s * (S->p->sd[j] * B->zd[j]);
+        return;
     }
     /* R_i = mu + s_i C zhat_i: out_j = mu_j + s_i * sum_{l<=j} C_jl zhat_l,
      * each sum taken in increasing l (loops interchanged over j only). */
@@ -821,8 +829,11 @@ int oracle_saa(const oracle_problem* p, int prec, uint32_t epoch, int K, const d
                double* var, double* grad)
 {
     if (check_problem(p) != OR_OK || (prec != 32 && prec != 64) || K < 1 || !W) return OR_EINVAL;
-    double* Ct = transpose_chol(p);
-    if (!Ct) return OR_ENOMEM;
+    double* Ct = NULL;   /* diagonal C (chol NULL): the samples use sd directly */
+    if (p->chol) {
+        Ct = transpose_chol(p);
+        if (!Ct) return OR_ENOMEM;
+    }
     sample_src S;
     memset(&S, 0, sizeof(S));
     S.p = p;
