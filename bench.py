@@ -10,8 +10,9 @@ Algorithm 1 (saa_solve) for 200 iterations on d = 1024, N = 2^22 Student-t
 scenarios regenerated every iteration, "ragged": 4096 independent
 instances in one graph-replayed persistent launch, and "newsvendor": the
 Monte Carlo gradient of Sec. 3.2 for 10^6 products x 1000 demand samples,
-and "covariance_first": the value workload through saa_moments +
-saa_eval_moments (value, and value with gradient).
+"covariance_first": the value workload through saa_moments +
+saa_eval_moments (value, and value with gradient), and "portfolio_large_d":
+value and gradient, and Algorithm 1, for Sec. 4.1's 10^5 independent assets.
 
 Workload (default): d = 128 assets, N = 2^20 scenarios (first half Gaussian,
 second half standardised lognormal sigma = 1), K = 256 candidate decisions
@@ -374,6 +375,101 @@ def run_ragged(args, dev, world, rank, flush, stream):
 
 
 NV_WORKLOAD = dict(name="newsvendor_n1M_S1000_K1", n=1_000_000, S=1000, K=1)
+
+
+LD_WORKLOAD = dict(name="portfolio_diag_d100000_N65536", d=100_000, N=1 << 16, M=50, T=20, d_small=5000, M_small=25,
+                   T_small=1500)
+
+
+def run_large_d(args, dev, world, rank, flush, stream):
+    """Sec. 4.1's portfolio at its largest size: d = 10^5 independent assets
+    (mu ~ U(-1,1), sigma ~ U(0, 0.025), Sigma = diag(sigma^2), no dense
+    factor), N = 2^16 Gaussian samples, FP32.  One step is saa_grad at one
+    decision (value and gradient); the unit is one (sample, asset) normal.
+    Algorithm 1 is timed on the same problem (M = 50, as Sec. 4.1 uses at
+    this size; T = 20 iterations, per-iteration time) and at d = 5000 for the
+    paper's full 1500 iterations (M = 25)."""
+    import torch
+    from paper_2404_11631_gb300 import inputs, saa
+    d, N = LD_WORKLOAD["d"], LD_WORKLOAD["N"]
+
+    def problem(dd):
+        mu, sd = inputs.paper_assets(dd, 0)
+        return saa.Problem(mu=torch.tensor(mu, device=dev), chol=None, sd=torch.tensor(sd, device=dev), N=N,
+                           seed=0, instance=rank)
+    prob = problem(d)
+    X = torch.tensor(inputs.fw_start(d)[None], device=dev)
+    ws = torch.empty(saa.workspace_size(prob, 1, "fp32", 1), dtype=torch.uint8, device=dev)
+    steps = max(3, min(args.steps, 10))
+    res_k = {}
+    for name, fn in (("value", lambda: saa.saa_eval(prob, X, "fp32", ws=ws)),
+                     ("grad", lambda: saa.saa_grad(prob, X, "fp32", ws=ws))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        saa.saa_profile_enable(True, dev.index)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        main_ms, main_n, launched = saa.saa_profile_read(dev.index)
+        saa.saa_profile_enable(False, dev.index)
+        saa.saa_ctx_sync(dev.index)
+        res_k[name] = (sum(a.elapsed_time(b) for a, b in ev) / 1e3 / steps, main_ms / 1e3 / max(1, main_n),
+                       launched / steps)
+    step_s, kern_s, launches = res_k["grad"]
+    fwd_s = res_k["value"][1]
+    normals = float(N) * d
+    peaks, _ = _peaks()
+    peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    # lane-ops: the forward and the adjoint each draw every normal and spend
+    # one multiply-add on it (the adjoint also its m~ sum)
+    ops_fwd = normals * (GEN_INST_GAUSS + 1.0)
+    ops = normals * (2.0 * GEN_INST_GAUSS + 3.0)
+    fw = {}
+    for tag, dd, M, T in (("d100000", d, LD_WORKLOAD["M"], LD_WORKLOAD["T"]),
+                          ("d5000", LD_WORKLOAD["d_small"], LD_WORKLOAD["M_small"], LD_WORKLOAD["T_small"])):
+        pr = problem(dd)
+        w0 = torch.tensor(inputs.fw_start(dd), device=dev)
+        wsf = torch.empty(saa.workspace_size(pr, 1, "fp32", 2), dtype=torch.uint8, device=dev)
+        saa.saa_solve(pr, w0, T=2, M=M, ws=wsf)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = saa.saa_solve(pr, w0, T=T, M=M, ws=wsf)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        saa.saa_ctx_sync(dev.index)
+        ms = e0.elapsed_time(e1)
+        fw[tag] = {"d": dd, "N": N, "M": M, "T": T, "ms_total": ms, "ms_per_iteration": ms / T,
+                   "s_for_1500_iterations": 1.5 * ms / T, "f_first_last": [float(out["f_trace"][0]),
+                                                                          float(out["f_trace"][-1])],
+                   "gap_last": float(out["gap_trace"][-1])}
+    res = {"metric": "normals/s (portfolio value and gradient, diagonal Sigma)", "value": world * normals / step_s,
+           "unit": "normals/s", "ms_per_step": 1e3 * step_s, "steps": steps, "kernels_ms": 1e3 * kern_s,
+           "forward_kernel_ms": 1e3 * fwd_s, "value_only_ms_per_step": 1e3 * res_k["value"][0],
+           "gpu_launches_per_step": launches,
+           "roofline": {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": ops / kern_s / 1e12 / peak, "forward_frac": ops_fwd / fwd_s / 1e12 / peak,
+                        "note": "lane-ops: two draws per normal (forward, adjoint) + 3 per normal; forward + adjoint"},
+           "fw": fw,
+           "config": {"workload": LD_WORKLOAD["name"], "d": d, "N": N, "K": 1, "law": "Gaussian",
+                      "sigma": "diag, U(0, 0.025)", "prec": "fp32", "l2": "flushed between timed steps"}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        mu, sd = inputs.paper_assets(d, 0)
+        n = 16384
+        op = oracle.make_problem(d, n, mu, None, seed=0, instance=rank, sd=sd)
+        t0 = time.perf_counter()
+        oracle.saa(op, 32, inputs.fw_start(d), grad=True)
+        dt = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": float(n) * d / dt, "unit": "normals/s", "cores": oracle.max_threads(),
+                               "kind": "oracle", "sample": f"{n} of {N} samples x all {d} assets, value and gradient,"
+                                                           f" {dt:.1f} s"}
+    return res
 
 
 LG_WORKLOAD = dict(name="logistic_n5000_N150000", n=5000, N=150_000, b=50, bH=600)
@@ -815,6 +911,8 @@ def run_ours(args):
         line["streamed"] = run_streamed(args, dev, world, rank, flush, stream)
     if not args.no_logistic:
         line["logistic"] = run_logistic(args, dev, world, rank, flush, stream)
+    if not args.no_large_d:
+        line["portfolio_large_d"] = run_large_d(args, dev, world, rank, flush, stream)
     if rank == 0:
         line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -855,6 +953,8 @@ def main():
     ap.add_argument("--no-logistic", action="store_true", help="skip the binary-classification workload")
     ap.add_argument("--logistic-only", action="store_true", help="run only the binary-classification workload")
     ap.add_argument("--streamed-only", action="store_true", help="run only the streamed-samples workload")
+    ap.add_argument("--no-large-d", action="store_true", help="skip the 10^5-asset diagonal portfolio workload")
+    ap.add_argument("--large-d-only", action="store_true", help="run only the 10^5-asset diagonal portfolio workload")
     ap.add_argument("--nv-n", type=int, default=None, help="override the newsvendor product count")
     ap.add_argument("--fw-N", type=int, default=None, help="override the Algorithm 1 scenario count")
     ap.add_argument("--fw-T", type=int, default=None, help="override the Algorithm 1 iteration count")
@@ -890,6 +990,12 @@ def main():
         dev = torch.device("cuda", 0)
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
         print(json.dumps(run_covariance(args, dev, 1, 0, flush, torch.cuda.current_stream(dev))), flush=True)
+        return 0
+    if args.large_d_only:
+        import torch
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps(run_large_d(args, dev, 1, 0, flush, torch.cuda.current_stream(dev))), flush=True)
         return 0
     if args.logistic_only:
         import torch

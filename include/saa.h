@@ -98,7 +98,15 @@ typedef struct {
     const double* chol; /* device [d*d] row-major lower-triangular C, C C' = Sigma;
                            entries above the diagonal are ignored.  A diagonal
                            entry that is not positive and finite is flagged on
-                           the device (SAA_EDEVICE at the next saa_ctx_sync) */
+                           the device (SAA_EDEVICE at the next saa_ctx_sync).
+                           NULL selects the diagonal form below. */
+    const double* sd;   /* device [d] or NULL: with chol NULL, Sigma = diag(sd^2)
+                           (C = diag(sd)), the independent assets of Sec. 4.1.
+                           This form has no dimension limit (Sec. 4.1 runs up
+                           to 10^5 assets): saa_eval, saa_grad and saa_solve
+                           take it at SAA_FP32 with K <= 4; the other entry
+                           points need chol.  A spread that is not positive
+                           and finite is flagged like a bad chol diagonal. */
 } saa_problem;
 
 /* Context: device properties, tuned launch shapes, a device error word and

@@ -50,6 +50,10 @@ struct Workspace {
   double* f_tmp;      // [K]    (solve)
   int64_t* t_dev;     // [1]    (solve: iteration counter)
   void* tc;           // tensor-path operand area
+  float* q_dev;       // diagonal path: [N][K] Q_ik of the forward pass
+  float* s_dev;       // diagonal path: [N] scales s_i
+  double* part_gd;    // diagonal path: [slices][K][d] adjoint partials of G
+  double* part_md;    // diagonal path: [slices][d] adjoint partials of m~
   size_t bytes;       // total
 };
 
@@ -62,6 +66,9 @@ struct Plan {
   int smem;       // dynamic shared memory of the main kernel
   int64_t tiles;  // scenario tiles
   size_t tc_bytes;
+  int diag;       // diagonal covariance path (chol NULL, sd given)
+  int nsplit;     // diagonal path: scenario slices of the adjoint
+  int ablk;       // diagonal path: adjoint blocks over the dimensions
 };
 
 }  // namespace saa
@@ -119,6 +126,13 @@ size_t simt_smem(int prec, int d, int bm, int tn);
 int simt_occupancy(int prec, int bm, int tn, int smem);
 size_t narrow_smem(int prec, int d, int bm);
 int narrow_occupancy(int prec, int bm, int smem);
+
+// Diagonal-covariance path of any dimension (large_d.cu).
+saa_status diag_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec prec, int want_grad, Plan* plan);
+size_t diag_carve(const saa_problem* p, int K, const Plan& plan, int want_grad, void* base, Workspace* ws);
+cudaError_t launch_diag(const saa_problem* p, int K, const double* X, const LawArgs& la, int want_grad,
+                        const Plan& plan, const Workspace& w, double* f, double* pbar, double* var, double* grad,
+                        uint32_t* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
 
 // Tensor-core (tcgen05, BF16 or FP16 hi/lo) value path.
 inline bool is_tc(int prec) { return prec == SAA_BF16X3 || prec == SAA_F16X3; }

@@ -1,0 +1,391 @@
+// large_d.cu -- the estimator of Eq. 4 / Eq. 5 and its gradient for a
+// diagonal covariance, Sigma = diag(sd^2) (the asset setup of Sec. 4.1), at
+// any dimension: Sec. 4.1 runs 500 to 100000 assets, where a dense factor C
+// no longer fits (80 GB at d = 10^5) and the sample tile of the CUDA-core
+// kernels no longer fits shared memory.
+//
+// With C = diag(sd): w'R_i = c + s_i zhat_i'y, c = mu'w, y = sd o w.  Per
+// call (FP32 normals, the generator of every other path, bit-exact):
+//   forward  tiles of 32 scenarios, one warp per 4 of them; the decisions y
+//            are staged through shared memory 8192 / K dimensions at a time, so
+//            a tile reads y once; lanes draw 4-dimension blocks and add
+//            each block's FP32 dot product into a float-float sum; Q_ik = s_i (sum) and s_i go to HBM, S1 and S2 to the CTA's
+//            FP64 partials.
+//   adjoint  (gradient only) one thread per 4-dimension block over a slice
+//            of the scenarios: it draws its block again and keeps
+//            Kahan-compensated FP32 sums of a_ij Q_ik (G) and a_ij (m~),
+//            written per slice in FP64.  Drawing twice keeps nothing of size
+//            N x d in memory.
+//   finalize S1, S2 and the slices added in fixed order (FP64), then p_bar,
+//            V, f_hat and grad = sd o [lambda 2/(N-1) (G - S1 m) - m] - mu.
+// Every sum has a fixed order: results are bitwise deterministic.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "gen.cuh"
+#include "internal.cuh"
+
+namespace saa {
+namespace {
+
+constexpr int kLdThreads = 256;
+constexpr int kLdWarps = kLdThreads / 32;
+constexpr int kLdSPW = 4;                       // scenarios per warp in a forward tile
+constexpr int kLdTile = kLdWarps * kLdSPW;     // 32 scenarios per forward tile
+constexpr int kLdChunkFloats = 8192;            // y staged per pass: 8192 / K dimensions (32 KB)
+constexpr int kLdMaxK = 4;
+
+__device__ __forceinline__ void ld_ff_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+
+// y_kj = sd_j x_kj (FP32 copy for the contraction); c_k = mu'x_k (FP64, one
+// block per decision, fixed-order tree).
+__global__ void __launch_bounds__(kLdThreads) k_ld_prologue(int d, int K, const double* __restrict__ X,
+                                                            const double* __restrict__ mu,
+                                                            const double* __restrict__ sd, float* __restrict__ y,
+                                                            double* __restrict__ c, uint32_t* __restrict__ err) {
+  __shared__ double red[kLdWarps];
+  const int k = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x) {
+    const double s = sd[j];
+    if (k == 0 && (!(s > 0.0) || !isfinite(s))) atomicOr(err, kErrInput);
+    y[(size_t)k * d + j] = (float)(s * X[(size_t)k * d + j]);
+  }
+  if (blockIdx.x != 0) return;
+  double t = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) t = fma(mu[j], X[(size_t)k * d + j], t);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) red[warp] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int w = 0; w < kLdWarps; ++w) u += red[w];
+    c[k] = u;
+  }
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kLdThreads) k_ld_fwd(LawArgs la, int K, const float* __restrict__ y,
+                                                       float* __restrict__ Q, float* __restrict__ S,
+                                                       double* __restrict__ part_s1, double* __restrict__ part_s2,
+                                                       int64_t tiles) {
+  constexpr int kLdChunk = kLdChunkFloats / KT;
+  __shared__ __align__(16) float ys[KT][kLdChunk];
+  __shared__ double red[kLdWarps][2][KT];
+  const int d = la.d;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t epoch = la.epoch;
+  if (la.t_dev) epoch += (uint32_t)(*la.t_dev / la.M);
+  const gen::Stream st = gen::make_stream(la.seed, epoch, la.instance);
+  const uint32_t half = la.N / 2u;
+  double s1[KT], s2[KT];   // this warp's sums over its scenarios (FP64)
+#pragma unroll
+  for (int k = 0; k < KT; ++k) s1[k] = s2[k] = 0.0;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    float hi[kLdSPW][KT], lo[kLdSPW][KT];
+#pragma unroll
+    for (int q = 0; q < kLdSPW; ++q)
+#pragma unroll
+      for (int k = 0; k < KT; ++k) hi[q][k] = lo[q][k] = 0.0f;
+    const int64_t i_base = tile * kLdTile + warp * kLdSPW;
+    for (int j0 = 0; j0 < d; j0 += kLdChunk) {
+      const int dc = min(kLdChunk, d - j0);
+      __syncthreads();   // the previous chunk is consumed
+      for (int e = threadIdx.x; e < KT * kLdChunk; e += blockDim.x) {
+        const int k = e / kLdChunk, j = e % kLdChunk;
+        ys[k][j] = (k < K && j < dc) ? y[(size_t)k * d + j0 + j] : 0.0f;
+      }
+      __syncthreads();
+      const int nbc = (dc + 3) / 4;   // 4-dimension blocks of the chunk
+#pragma unroll
+      for (int q = 0; q < kLdSPW; ++q) {
+        const int64_t i = i_base + q;
+        if (i >= (int64_t)la.N) break;   // warp-uniform
+        const bool logn = gen::is_lognormal(la.law, (uint32_t)i, half);
+        for (int bc = lane; bc < nbc; bc += 32) {
+          float z[4];
+          gen::Gen<float>::block(st, (uint32_t)((j0 >> 2) + bc), (uint32_t)i, logn, z);
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (4 * bc + e >= dc) z[e] = 0.0f;   // the chunk's ragged tail (ys is zero there too)
+          // the block's 4-term FP32 dot product, then one float-float add: the
+          // error stays at the FP32 rounding of each block's partial
+#pragma unroll
+          for (int k = 0; k < KT; ++k) {
+            float p = z[0] * ys[k][4 * bc];
+#pragma unroll
+            for (int e = 1; e < 4; ++e) p = fmaf(z[e], ys[k][4 * bc + e], p);
+            ld_ff_add(hi[q][k], lo[q][k], p);
+          }
+        }
+      }
+    }
+    // per scenario: warp sum (float-float tree), the t-law scale, Q and S1/S2
+#pragma unroll
+    for (int q = 0; q < kLdSPW; ++q) {
+      const int64_t i = i_base + q;
+#pragma unroll
+      for (int k = 0; k < KT; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, hi[q][k], o);
+          const float ol = __shfl_xor_sync(0xffffffffu, lo[q][k], o);
+          ld_ff_add(hi[q][k], lo[q][k], oh);
+          lo[q][k] += ol;
+        }
+      }
+      if (i < (int64_t)la.N) {
+        const float s = gen::Gen<float>::scale(st, (uint32_t)i, la.law, la.nu);
+        if (lane == 0 && S) S[i] = s;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+          if (k < K) {
+            const double qv = (double)s * ((double)hi[q][k] + (double)lo[q][k]);
+            if (lane == 0) Q[(size_t)i * K + k] = (float)qv;
+            s1[k] += qv;
+            s2[k] = fma(qv, qv, s2[k]);
+          }
+        }
+      }
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      red[warp][0][k] = s1[k];
+      red[warp][1][k] = s2[k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kLdWarps; ++w) {
+      a += red[w][0][threadIdx.x];
+      b += red[w][1][threadIdx.x];
+    }
+    part_s1[(size_t)blockIdx.x * K + threadIdx.x] = a;
+    part_s2[(size_t)blockIdx.x * K + threadIdx.x] = b;
+  }
+}
+
+// Adjoint: thread t of block (x, slice) owns the 4-dimension block
+// b = 256 x + t and adds, over the slice's scenarios, a_ij Q_ik (G) and
+// a_ij (m~) with Kahan compensation; the slice's sums go to part_g / part_m.
+template <int KT>
+__global__ void __launch_bounds__(kLdThreads) k_ld_adj(LawArgs la, int K, int64_t per_slice,
+                                                       const float* __restrict__ Q, const float* __restrict__ S,
+                                                       double* __restrict__ part_g, double* __restrict__ part_m) {
+  const int d = la.d;
+  const int nb = (d + 3) / 4;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sl = blockIdx.y;
+  uint32_t epoch = la.epoch;
+  if (la.t_dev) epoch += (uint32_t)(*la.t_dev / la.M);
+  const gen::Stream st = gen::make_stream(la.seed, epoch, la.instance);
+  const uint32_t half = la.N / 2u;
+  const bool tlaw = la.law == SAA_LAW_STUDENT_T;
+  const int64_t i0 = (int64_t)sl * per_slice;
+  const int64_t i1 = min((int64_t)la.N, i0 + per_slice);
+  float gs[KT][4], gc[KT][4], ms[4], mc[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    ms[e] = mc[e] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) gs[k][e] = gc[k][e] = 0.0f;
+  }
+  if (b < nb) {
+    for (int64_t i = i0; i < i1; ++i) {
+      float z[4];
+      gen::Gen<float>::block(st, (uint32_t)b, (uint32_t)i, gen::is_lognormal(la.law, (uint32_t)i, half), z);
+      const float s = tlaw ? S[i] : 1.0f;
+      float qk[KT];
+#pragma unroll
+      for (int k = 0; k < KT; ++k) qk[k] = k < K ? Q[(size_t)i * K + k] : 0.0f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float a = z[e] * s;
+        {   // Kahan: the compensation carries the lost low part
+          const float yv = a - mc[e];
+          const float t = ms[e] + yv;
+          mc[e] = (t - ms[e]) - yv;
+          ms[e] = t;
+        }
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+          const float yv = a * qk[k] - gc[k][e];
+          const float t = gs[k][e] + yv;
+          gc[k][e] = (t - gs[k][e]) - yv;
+          gs[k][e] = t;
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = 4 * b + e;
+      if (j < d) {
+        part_m[(size_t)sl * d + j] = (double)ms[e] - (double)mc[e];
+#pragma unroll
+        for (int k = 0; k < KT; ++k)
+          if (k < K) part_g[((size_t)sl * K + k) * d + j] = (double)gs[k][e] - (double)gc[k][e];
+      }
+    }
+  }
+}
+
+// One warp per decision: S1, S2 over the forward CTAs (lane-strided, fixed
+// tree), then p_bar, V and f_hat; S1 is kept for the gradient.
+__global__ void k_ld_value_out(int grid, int K, double N, double lambda, const double* __restrict__ part_s1,
+                               const double* __restrict__ part_s2, const double* __restrict__ c,
+                               double* __restrict__ tot_s1, double* __restrict__ f, double* __restrict__ pbar,
+                               double* __restrict__ var) {
+  const int k = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= K) return;
+  double a = 0.0, b = 0.0;
+  for (int g = lane; g < grid; g += 32) {
+    a += part_s1[(size_t)g * K + k];
+    b += part_s2[(size_t)g * K + k];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) {
+    tot_s1[k] = a;
+    const double qbar = a / N;
+    const double pb = c[k] + qbar;
+    const double V = (b - a * qbar) / (N - 1.0);
+    if (f) f[k] = lambda * V - pb;
+    if (pbar) pbar[k] = pb;
+    if (var) var[k] = V;
+  }
+}
+
+// grad_kj = sd_j [lambda 2/(N-1) (G_kj - S1_k m_j) - m_j] - mu_j, m = m~/N,
+// the slices added in order.
+__global__ void k_ld_grad_out(int nsl, int K, int d, double N, double lambda, const double* __restrict__ part_g,
+                              const double* __restrict__ part_m, const double* __restrict__ tot_s1,
+                              const double* __restrict__ sd, const double* __restrict__ mu,
+                              double* __restrict__ grad) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)K * d) return;
+  const int k = (int)(e / d), j = (int)(e % d);
+  double G = 0.0, m = 0.0;
+  for (int sl = 0; sl < nsl; ++sl) {
+    G += part_g[((size_t)sl * K + k) * d + j];
+    m += part_m[(size_t)sl * d + j];
+  }
+  m /= N;
+  const double u = lambda * 2.0 / (N - 1.0) * (G - tot_s1[k] * m) - m;
+  grad[e] = sd[j] * u - mu[j];
+}
+
+template <int KT>
+cudaError_t launch_ld_kt(const LawArgs& la, int K, int want_grad, const Plan& plan, const Workspace& w,
+                         cudaStream_t st) {
+  k_ld_fwd<KT><<<plan.grid, kLdThreads, 0, st>>>(la, K, (const float*)w.Y, w.q_dev, w.s_dev, w.part_s1, w.part_s2,
+                                                 plan.tiles);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !want_grad) return e;
+  const int64_t per = (la.N + plan.nsplit - 1) / plan.nsplit;
+  k_ld_adj<KT><<<dim3((unsigned)plan.ablk, (unsigned)plan.nsplit), kLdThreads, 0, st>>>(la, K, per, w.q_dev,
+                                                                                        w.s_dev, w.part_gd,
+                                                                                        w.part_md);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+saa_status diag_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec prec, int want_grad, Plan* plan) {
+  if (prec != SAA_FP32) {
+    set_error("diagonal covariance (chol NULL, sd given): SAA_FP32 only");
+    return SAA_EUNSUPPORTED;
+  }
+  if (K > kLdMaxK) {
+    set_error("diagonal covariance path: K <= 4 decisions per call");
+    return SAA_EUNSUPPORTED;
+  }
+  plan->prec = prec;
+  plan->diag = 1;
+  plan->tiles = (p->N + kLdTile - 1) / kLdTile;
+  const int64_t cap = 2 * (int64_t)ctx->sm_count;
+  plan->grid = (int)(plan->tiles < cap ? plan->tiles : cap);
+  const int nb = (p->d + 3) / 4;
+  plan->ablk = (nb + kLdThreads - 1) / kLdThreads;
+  if (want_grad) {
+    // enough slices for about four CTAs per SM, each at least 256 scenarios
+    int64_t ns = (4 * (int64_t)ctx->sm_count + plan->ablk - 1) / plan->ablk;
+    const int64_t most = (p->N + 255) / 256;
+    if (ns > most) ns = most;
+    plan->nsplit = (int)(ns < 1 ? 1 : ns);
+  }
+  return SAA_OK;
+}
+
+size_t diag_carve(const saa_problem* p, int K, const Plan& plan, int want_grad, void* base, Workspace* ws) {
+  const size_t d = (size_t)p->d, k = (size_t)K, g = (size_t)plan.grid, n = (size_t)p->N;
+  char* b = (char*)base;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> void* {
+    void* r = b ? (void*)(b + off) : nullptr;
+    off = (off + bytes + 255) & ~(size_t)255;
+    return r;
+  };
+  Workspace w;
+  std::memset(&w, 0, sizeof(w));
+  w.Y = take(k * d * 4);
+  w.c = (double*)take(k * 8);
+  w.part_s1 = (double*)take(g * k * 8);
+  w.part_s2 = (double*)take(g * k * 8);
+  w.tot_s1 = (double*)take(k * 8);
+  w.q_dev = (float*)take(n * k * 4);
+  w.s_dev = (float*)take(n * 4);
+  if (want_grad) {
+    w.part_gd = (double*)take((size_t)plan.nsplit * k * d * 8);
+    w.part_md = (double*)take((size_t)plan.nsplit * d * 8);
+  }
+  if (want_grad == 2) {
+    w.f_tmp = (double*)take(k * 8);
+    w.t_dev = (int64_t*)take(8);
+    w.grad_out = (double*)take(k * d * 8);
+  }
+  w.bytes = off;
+  if (ws) *ws = w;
+  return off;
+}
+
+cudaError_t launch_diag(const saa_problem* p, int K, const double* X, const LawArgs& la, int want_grad,
+                        const Plan& plan, const Workspace& w, double* f, double* pbar, double* var, double* grad,
+                        uint32_t* err, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+  const int d = p->d;
+  const dim3 pg((unsigned)min((d + kLdThreads - 1) / kLdThreads, 1024), (unsigned)K);
+  k_ld_prologue<<<pg, kLdThreads, 0, st>>>(d, K, X, p->mu, p->sd, (float*)w.Y, w.c, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (ev0) cudaEventRecord(ev0, st);
+  switch (K) {
+    case 1: e = launch_ld_kt<1>(la, K, want_grad, plan, w, st); break;
+    case 2: e = launch_ld_kt<2>(la, K, want_grad, plan, w, st); break;
+    default: e = launch_ld_kt<4>(la, K, want_grad, plan, w, st); break;
+  }
+  if (ev1) cudaEventRecord(ev1, st);
+  if (e != cudaSuccess) return e;
+  k_ld_value_out<<<(K * 32 + 255) / 256, 256, 0, st>>>(plan.grid, K, (double)p->N, p->lambda, w.part_s1, w.part_s2,
+                                                       w.c, w.tot_s1, f, pbar, var);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !want_grad || !grad) return e;
+  const int64_t tot = (int64_t)K * d;
+  k_ld_grad_out<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(plan.nsplit, K, d, (double)p->N, p->lambda, w.part_gd,
+                                                               w.part_md, w.tot_s1, p->sd, p->mu, grad);
+  return cudaGetLastError();
+}
+
+}  // namespace saa

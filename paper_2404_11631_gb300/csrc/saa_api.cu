@@ -39,7 +39,7 @@ static saa_status check_problem(const saa_problem* p) {
   if (p->law == SAA_LAW_STUDENT_T && (p->nu < 2 || (p->nu & 1) || p->nu > 64))
     return fail(SAA_EINVAL, "t law needs an even nu in [2, 64]");
   if (p->reserved != 0) return fail(SAA_EINVAL, "reserved field must be 0");
-  if (!p->mu || !p->chol) return fail(SAA_EINVAL, "mu and chol must be device pointers");
+  if (!p->mu || (!p->chol && !p->sd)) return fail(SAA_EINVAL, "mu and chol (or sd) must be device pointers");
   return SAA_OK;
 }
 
@@ -48,6 +48,7 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 saa_status make_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec prec, int want_grad, Plan* plan) {
   std::memset(plan, 0, sizeof(*plan));
   plan->prec = prec;
+  if (!p->chol) return diag_plan(ctx, p, K, prec, want_grad, plan);
   if (is_tc(prec) && want_grad) {
     if (!tc_grad_supported(p, K))
       return fail(SAA_EUNSUPPORTED, "tensor-core gradient path: needs d <= 1024 and K <= 64");
@@ -74,6 +75,7 @@ saa_status make_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec p
 }
 
 size_t carve(const saa_problem* p, int K, const Plan& plan, int want_grad, void* base, Workspace* ws) {
+  if (plan.diag) return diag_carve(p, K, plan, want_grad, base, ws);
   const size_t d = (size_t)p->d, k = (size_t)K, g = (size_t)plan.grid;
   const size_t es = (plan.prec == SAA_FP64) ? 8 : 4;
   char* b = (char*)base;
@@ -142,6 +144,17 @@ static LawArgs law_args(const saa_problem* p) {
 static saa_status run_estimator(saa_ctx* ctx, const saa_problem* p, int K, const double* X, saa_prec prec,
                                 int want_grad, const Plan& plan, const Workspace& ws, const LawArgs& la, double* f,
                                 double* pbar, double* var, double* grad, cudaStream_t st) {
+  if (plan.diag) {
+    const bool prof = ctx->prof_on && !la.t_dev && ctx->prof_n < 256;
+    cudaEvent_t e0 = prof ? ctx->prof_ev[2 * ctx->prof_n] : nullptr;
+    cudaEvent_t e1 = prof ? ctx->prof_ev[2 * ctx->prof_n + 1] : nullptr;
+    if (prof) ++ctx->prof_n;
+    const saa_status s = cuda_status(launch_diag(p, K, X, la, want_grad, plan, ws, f, pbar, var, grad, ctx->err, st,
+                                                 e0, e1),
+                                     "diagonal-covariance path launch");
+    ctx->kernels += 3 + (want_grad ? 1 : 0) + ((want_grad && grad) ? 1 : 0);
+    return s;
+  }
   saa_status s = cuda_status(launch_prologue(p, K, X, prec, ws, ctx->err, st), "prologue launch");
   if (s != SAA_OK) return s;
   const bool prof = ctx->prof_on && !la.t_dev && ctx->prof_n < 256;
@@ -480,6 +493,7 @@ saa_status saa_generate(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64
   if (i0 < 0 || n < 0 || i0 + n > prob->N) return fail(SAA_EINVAL, "scenario range outside [0, N)");
   if (!z_out) return fail(SAA_EINVAL, "z_out is NULL");
   if (xi_out && !s_out) return fail(SAA_EINVAL, "xi_out needs s_out");
+  if (xi_out && !prob->chol) return fail(SAA_EUNSUPPORTED, "xi_out needs a dense chol");
   if (n == 0) return SAA_OK;
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(SAA_ECUDA, "cudaSetDevice failed");

@@ -49,12 +49,18 @@ def instance(d: int, seed: int = 0) -> Instance:
     return Instance(d, mu, sigma, np.ascontiguousarray(chol))
 
 
-def paper_instance(d: int, seed: int = 0) -> Instance:
-    """Sec. 4.1 asset setup: mu_i ~ U(-1,1), sigma_i ~ U(0,0.025), independent assets."""
+def paper_assets(d: int, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Sec. 4.1 asset setup as (mu, sd): mu_i ~ U(-1,1), sigma_i ~ U(0,0.025),
+    independent assets (Sigma = diag(sd^2)); no d x d matrix is formed."""
     rng = np.random.default_rng([seed, d, 2])
     mu = rng.uniform(-1.0, 1.0, size=d)
     sd = rng.uniform(0.0, 0.025, size=d)
-    sd = np.maximum(sd, 1e-6)
+    return mu, np.maximum(sd, 1e-6)
+
+
+def paper_instance(d: int, seed: int = 0) -> Instance:
+    """The assets of :func:`paper_assets` with dense Sigma and C."""
+    mu, sd = paper_assets(d, seed)
     return Instance(d, mu, np.diag(sd * sd), np.diag(sd))
 
 

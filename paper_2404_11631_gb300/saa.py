@@ -45,6 +45,7 @@ class _CProblem(C.Structure):
         ("epoch", C.c_uint32),
         ("mu", C.c_void_p),
         ("chol", C.c_void_p),
+        ("sd", C.c_void_p),
     ]
 
 
@@ -197,14 +198,16 @@ class Problem:
     """Law of the samples R_i = mu + s_i C zhat_i (Sec. 3.1) and estimator options.
 
     mu   -- [d] float64 CUDA tensor, the mean of R
-    chol -- [d, d] float64 CUDA tensor, lower Cholesky factor C of Sigma
+    chol -- [d, d] float64 CUDA tensor, lower Cholesky factor C of Sigma, or
+            None with ``sd`` -- [d] float64 CUDA tensor: Sigma = diag(sd^2),
+            the independent assets of Sec. 4.1 at any dimension (FP32, K <= 4)
     N    -- samples per resample; law -- LAW_*; nu -- t-law degrees of freedom
     lam  -- weight of the variance term (0.5 reproduces Eq. 3)
     seed, instance, epoch -- Philox key and counter words
     """
 
     mu: torch.Tensor
-    chol: torch.Tensor
+    chol: torch.Tensor | None
     N: int
     law: int = LAW_GAUSS
     nu: int = 4
@@ -212,6 +215,7 @@ class Problem:
     seed: int = 0
     instance: int = 0
     epoch: int = 0
+    sd: torch.Tensor | None = None
 
     @property
     def d(self) -> int:
@@ -222,13 +226,18 @@ class Problem:
         return self.mu.device
 
     def c_struct(self) -> _CProblem:
-        for name, t in (("mu", self.mu), ("chol", self.chol)):
-            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        for name, t in (("mu", self.mu), ("chol", self.chol), ("sd", self.sd)):
+            if t is not None and not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
                 raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
-        if self.chol.shape != (self.d, self.d):
+        if self.chol is None and self.sd is None:
+            raise ValueError("give chol, or sd for a diagonal covariance")
+        if self.chol is not None and self.chol.shape != (self.d, self.d):
             raise ValueError("chol must be [d, d]")
+        if self.sd is not None and self.sd.shape != (self.d,):
+            raise ValueError("sd must be [d]")
         return _CProblem(self.d, self.law, self.N, self.nu, 0, self.lam, self.seed, self.instance, self.epoch,
-                         self.mu.data_ptr(), self.chol.data_ptr())
+                         self.mu.data_ptr(), None if self.chol is None else self.chol.data_ptr(),
+                         None if self.sd is None else self.sd.data_ptr())
 
 
 def _prec(prec) -> int:

@@ -18,10 +18,9 @@ from paper_2404_11631_gb300 import inputs
 @pytest.mark.parametrize("prec", [32, 64])
 def test_diagonal_branch_is_the_dense_one(law, prec):
     d, N, K = 37, 3000, 3
-    inst = inputs.paper_instance(d, 1)
-    sd = np.diag(inst.chol).copy()
-    dense = oracle.make_problem(d, N, inst.mu, np.diag(sd), law=law, seed=5)
-    diag = oracle.make_problem(d, N, inst.mu, None, law=law, seed=5, sd=sd)
+    mu, sd = inputs.paper_assets(d, 1)
+    dense = oracle.make_problem(d, N, mu, np.diag(sd), law=law, seed=5)
+    diag = oracle.make_problem(d, N, mu, None, law=law, seed=5, sd=sd)
     W = inputs.decisions(K, d, seed=2)
     a = oracle.saa(dense, prec, W, grad=True)
     b = oracle.saa(diag, prec, W, grad=True)
@@ -34,14 +33,13 @@ def test_diagonal_branch_is_the_dense_one(law, prec):
 
 def test_large_dimension_variance_is_unbiased():
     d, N, E = 20_000, 64, 60
-    inst = inputs.paper_instance(d, 3)
-    sd = np.diag(inst.chol).copy()
+    mu, sd = inputs.paper_assets(d, 3)
     w = inputs.decisions(1, d, seed=3)[0] / d
     truth = float(np.sum(sd ** 2 * w ** 2))
-    v = np.array([oracle.saa(oracle.make_problem(d, N, inst.mu, None, seed=11, epoch=e, sd=sd), 64, w)["var"][0]
+    v = np.array([oracle.saa(oracle.make_problem(d, N, mu, None, seed=11, epoch=e, sd=sd), 64, w)["var"][0]
                   for e in range(E)])
     # the sample variance of N normals: Var[V] = 2 truth^2 / (N - 1)
     se = truth * np.sqrt(2.0 / (N - 1) / E)
     assert abs(v.mean() - truth) < 5 * se
     with pytest.raises(ValueError):
-        oracle.generate(oracle.make_problem(d, N, inst.mu, None, sd=sd), 64, 0, 4, want_xi=True)
+        oracle.generate(oracle.make_problem(d, N, mu, None, sd=sd), 64, 0, 4, want_xi=True)
