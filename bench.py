@@ -420,15 +420,30 @@ def run_large_d(args, dev, world, rank, flush, stream):
         saa.saa_ctx_sync(dev.index)
         res_k[name] = (sum(a.elapsed_time(b) for a, b in ev) / 1e3 / steps, main_ms / 1e3 / max(1, main_n),
                        launched / steps)
+    # the same call drawing the samples twice (no sample store), for comparison
+    saa.saa_ctx_set_sample_store(0, dev.index)
+    ws_r = torch.empty(saa.workspace_size(prob, 1, "fp32", 1), dtype=torch.uint8, device=dev)
+    saa.saa_grad(prob, X, "fp32", ws=ws_r)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        saa.saa_grad(prob, X, "fp32", ws=ws_r)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    saa.saa_ctx_set_sample_store(1 << 35, dev.index)
+    redraw_ms = e0.elapsed_time(e1) / 3
+    del ws_r
     step_s, kern_s, launches = res_k["grad"]
     fwd_s = res_k["value"][1]
     normals = float(N) * d
     peaks, _ = _peaks()
     peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    # lane-ops: the forward and the adjoint each draw every normal and spend
-    # one multiply-add on it (the adjoint also its m~ sum)
+    # lane-ops: one draw per normal and a multiply-add in each pass (the
+    # adjoint also its m~ sum); the adjoint reads the stored normals back
     ops_fwd = normals * (GEN_INST_GAUSS + 1.0)
-    ops = normals * (2.0 * GEN_INST_GAUSS + 3.0)
+    ops = normals * (GEN_INST_GAUSS + 3.0)
+    store_bytes = float(N) * ((d + 3) // 4 * 4) * 4
     fw = {}
     for tag, dd, M, T in (("d100000", d, LD_WORKLOAD["M"], LD_WORKLOAD["T"]),
                           ("d5000", LD_WORKLOAD["d_small"], LD_WORKLOAD["M_small"], LD_WORKLOAD["T_small"])):
@@ -451,10 +466,14 @@ def run_large_d(args, dev, world, rank, flush, stream):
     res = {"metric": "normals/s (portfolio value and gradient, diagonal Sigma)", "value": world * normals / step_s,
            "unit": "normals/s", "ms_per_step": 1e3 * step_s, "steps": steps, "kernels_ms": 1e3 * kern_s,
            "forward_kernel_ms": 1e3 * fwd_s, "value_only_ms_per_step": 1e3 * res_k["value"][0],
+           "adjoint_kernel_ms": 1e3 * (kern_s - fwd_s), "redraw_ms_per_step": redraw_ms,
            "gpu_launches_per_step": launches,
            "roofline": {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                         "frac": ops / kern_s / 1e12 / peak, "forward_frac": ops_fwd / fwd_s / 1e12 / peak,
-                        "note": "lane-ops: two draws per normal (forward, adjoint) + 3 per normal; forward + adjoint"},
+                        "adjoint_hbm_frac": store_bytes / max(1e-9, kern_s - fwd_s) / 1e9 / peaks["hbm_gbs"],
+                        "note": "lane-ops: one draw per normal + 3 per normal; forward + adjoint.  The forward "
+                                "writes the FP32 normals, the adjoint reads them (adjoint_hbm_frac: that read "
+                                "against the measured HBM copy bandwidth)"},
            "fw": fw,
            "config": {"workload": LD_WORKLOAD["name"], "d": d, "N": N, "K": 1, "law": "Gaussian",
                       "sigma": "diag, U(0, 0.025)", "prec": "fp32", "l2": "flushed between timed steps"}}

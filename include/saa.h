@@ -200,6 +200,15 @@ saa_status saa_eval_batched(saa_ctx* ctx, int32_t B, const saa_problem* probs, c
                             double* const* var, void* ws, size_t ws_bytes, void* stream);
 saa_status saa_ctx_set_autotune(saa_ctx* ctx, int enable);
 
+/* Sample store of the diagonal-covariance gradient (saa_problem.chol NULL):
+ * when its FP32 samples, N * round_up(d, 4) * 4 bytes, take at most
+ * max_bytes, the forward pass writes them to the workspace and the adjoint
+ * pass reads them back instead of drawing them again (the results are
+ * bitwise the same either way).  The default is 2^35 bytes (32 GiB), which
+ * holds Sec. 4.1's 10^5 assets at N = 2^16; 0 always draws twice.  The
+ * workspace size follows the setting, so query it after changing it. */
+saa_status saa_ctx_set_sample_store(saa_ctx* ctx, size_t max_bytes);
+
 /* A ragged batch planned once and replayed as a CUDA graph.  Same problems,
  * decisions and value outputs as saa_eval_batched; with `grad` non-NULL
  * (host [B] array of device [K_b*d_b] outputs) it also writes each problem's

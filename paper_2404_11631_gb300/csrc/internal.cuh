@@ -54,6 +54,7 @@ struct Workspace {
   float* s_dev;       // diagonal path: [N] scales s_i
   double* part_gd;    // diagonal path: [slices][K][d] adjoint partials of G
   double* part_md;    // diagonal path: [slices][d] adjoint partials of m~
+  float* zs;          // diagonal path, sample store: [N][round_up(d, 4)] FP32 normals
   size_t bytes;       // total
 };
 
@@ -69,6 +70,7 @@ struct Plan {
   int diag;       // diagonal covariance path (chol NULL, sd given)
   int nsplit;     // diagonal path: scenario slices of the adjoint
   int ablk;       // diagonal path: adjoint blocks over the dimensions
+  int keep;       // diagonal path: the forward pass stores the normals for the adjoint
 };
 
 }  // namespace saa
@@ -92,6 +94,7 @@ struct saa_ctx {
   size_t stage_bytes;
   cudaEvent_t stage_ready;       // the last upload from `stage` has completed
   int autotune;                  // time candidate tile shapes on a new batch shape
+  size_t store_cap;              // diagonal path: most bytes of kept FP32 samples
 };
 
 namespace saa {

@@ -12,10 +12,14 @@
 //            each block's FP32 dot product into a float-float sum; Q_ik = s_i (sum) and s_i go to HBM, S1 and S2 to the CTA's
 //            FP64 partials.
 //   adjoint  (gradient only) one thread per 4-dimension block over a slice
-//            of the scenarios: it draws its block again and keeps
-//            Kahan-compensated FP32 sums of a_ij Q_ik (G) and a_ij (m~),
-//            written per slice in FP64.  Drawing twice keeps nothing of size
-//            N x d in memory.
+//            of the scenarios keeps Kahan-compensated FP32 sums of a_ij Q_ik
+//            (G) and a_ij (m~), written per slice in FP64.  It takes its
+//            normals from the sample store, [N][round_up(d, 4)] FP32 that the
+//            forward pass wrote (26 GB at d = 10^5, N = 2^16: the write
+//            hides under the generator's ALU time and the read is a plain
+//            HBM stream), or, when the store is off or too small, draws its
+//            block again (nothing of size N x d in memory).  Both give the
+//            same bits.
 //   finalize S1, S2 and the slices added in fixed order (FP64), then p_bar,
 //            V, f_hat and grad = sd o [lambda 2/(N-1) (G - S1 m) - m] - mu.
 // Every sum has a fixed order: results are bitwise deterministic.
@@ -75,7 +79,7 @@ template <int KT>
 __global__ void __launch_bounds__(kLdThreads) k_ld_fwd(LawArgs la, int K, const float* __restrict__ y,
                                                        float* __restrict__ Q, float* __restrict__ S,
                                                        double* __restrict__ part_s1, double* __restrict__ part_s2,
-                                                       int64_t tiles) {
+                                                       int64_t tiles, float* __restrict__ zs, int dp) {
   constexpr int kLdChunk = kLdChunkFloats / KT;
   __shared__ __align__(16) float ys[KT][kLdChunk];
   __shared__ double red[kLdWarps][2][KT];
@@ -115,6 +119,8 @@ __global__ void __launch_bounds__(kLdThreads) k_ld_fwd(LawArgs la, int K, const 
 #pragma unroll
           for (int e = 0; e < 4; ++e)
             if (4 * bc + e >= dc) z[e] = 0.0f;   // the chunk's ragged tail (ys is zero there too)
+          if (zs)   // the sample store: row i, dimensions j0 + 4 bc .. + 3 (< dp, 16-byte aligned)
+            __stcs(reinterpret_cast<float4*>(zs + (size_t)i * dp + j0 + 4 * bc), make_float4(z[0], z[1], z[2], z[3]));
           // the block's 4-term FP32 dot product, then one float-float add: the
           // error stays at the FP32 rounding of each block's partial
 #pragma unroll
@@ -175,9 +181,51 @@ __global__ void __launch_bounds__(kLdThreads) k_ld_fwd(LawArgs la, int K, const 
   }
 }
 
-// Adjoint: thread t of block (x, slice) owns the 4-dimension block
-// b = 256 x + t and adds, over the slice's scenarios, a_ij Q_ik (G) and
-// a_ij (m~) with Kahan compensation; the slice's sums go to part_g / part_m.
+// Adjoint accumulation of one scenario into a thread's 4-dimension block:
+// a = s_i zhat_ij; m~_j += a and G_kj += a Q_ik, Kahan-compensated (the
+// compensation carries the lost low part).  Both adjoint kernels use it, so
+// the stored and the redrawn samples give the same bits.
+template <int KT>
+__device__ __forceinline__ void ld_adj_add(const float z[4], float s, const float qk[KT], float ms[4], float mc[4],
+                                           float gs[KT][4], float gc[KT][4]) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float a = z[e] * s;
+    {
+      const float yv = a - mc[e];
+      const float t = ms[e] + yv;
+      mc[e] = (t - ms[e]) - yv;
+      ms[e] = t;
+    }
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      const float yv = a * qk[k] - gc[k][e];
+      const float t = gs[k][e] + yv;
+      gc[k][e] = (t - gs[k][e]) - yv;
+      gs[k][e] = t;
+    }
+  }
+}
+
+// The slice's sums of block b to part_m [slice][d] and part_g [slice][K][d].
+template <int KT>
+__device__ __forceinline__ void ld_adj_write(int b, int d, int K, int sl, const float ms[4], const float mc[4],
+                                             const float gs[KT][4], const float gc[KT][4], double* part_g,
+                                             double* part_m) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int j = 4 * b + e;
+    if (j < d) {
+      part_m[(size_t)sl * d + j] = (double)ms[e] - (double)mc[e];
+#pragma unroll
+      for (int k = 0; k < KT; ++k)
+        if (k < K) part_g[((size_t)sl * K + k) * d + j] = (double)gs[k][e] - (double)gc[k][e];
+    }
+  }
+}
+
+// Adjoint drawing its samples again: thread t of block (x, slice) owns the
+// 4-dimension block b = 256 x + t over the slice's scenarios.
 template <int KT>
 __global__ void __launch_bounds__(kLdThreads) k_ld_adj(LawArgs la, int K, int64_t per_slice,
                                                        const float* __restrict__ Q, const float* __restrict__ S,
@@ -200,43 +248,69 @@ __global__ void __launch_bounds__(kLdThreads) k_ld_adj(LawArgs la, int K, int64_
 #pragma unroll
     for (int k = 0; k < KT; ++k) gs[k][e] = gc[k][e] = 0.0f;
   }
-  if (b < nb) {
-    for (int64_t i = i0; i < i1; ++i) {
-      float z[4];
-      gen::Gen<float>::block(st, (uint32_t)b, (uint32_t)i, gen::is_lognormal(la.law, (uint32_t)i, half), z);
-      const float s = tlaw ? S[i] : 1.0f;
-      float qk[KT];
+  if (b >= nb) return;
+  for (int64_t i = i0; i < i1; ++i) {
+    float z[4];
+    gen::Gen<float>::block(st, (uint32_t)b, (uint32_t)i, gen::is_lognormal(la.law, (uint32_t)i, half), z);
+    float qk[KT];
 #pragma unroll
-      for (int k = 0; k < KT; ++k) qk[k] = k < K ? Q[(size_t)i * K + k] : 0.0f;
+    for (int k = 0; k < KT; ++k) qk[k] = k < K ? Q[(size_t)i * K + k] : 0.0f;
+    ld_adj_add<KT>(z, tlaw ? S[i] : 1.0f, qk, ms, mc, gs, gc);
+  }
+  ld_adj_write<KT>(b, d, K, sl, ms, mc, gs, gc, part_g, part_m);
+}
+
+// Adjoint reading the sample store: the same sums from zs [N][dp], four
+// scenarios' loads issued ahead of their arithmetic (an HBM stream).
+template <int KT>
+__global__ void __launch_bounds__(kLdThreads) k_ld_adj_kept(LawArgs la, int K, int64_t per_slice,
+                                                            const float* __restrict__ zs, int dp,
+                                                            const float* __restrict__ Q, const float* __restrict__ S,
+                                                            double* __restrict__ part_g,
+                                                            double* __restrict__ part_m) {
+  constexpr int U = 4;
+  const int d = la.d;
+  const int nb = (d + 3) / 4;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sl = blockIdx.y;
+  const bool tlaw = la.law == SAA_LAW_STUDENT_T;
+  const int64_t i0 = (int64_t)sl * per_slice;
+  const int64_t i1 = min((int64_t)la.N, i0 + per_slice);
+  float gs[KT][4], gc[KT][4], ms[4], mc[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float a = z[e] * s;
-        {   // Kahan: the compensation carries the lost low part
-          const float yv = a - mc[e];
-          const float t = ms[e] + yv;
-          mc[e] = (t - ms[e]) - yv;
-          ms[e] = t;
-        }
+  for (int e = 0; e < 4; ++e) {
+    ms[e] = mc[e] = 0.0f;
 #pragma unroll
-        for (int k = 0; k < KT; ++k) {
-          const float yv = a * qk[k] - gc[k][e];
-          const float t = gs[k][e] + yv;
-          gc[k][e] = (t - gs[k][e]) - yv;
-          gs[k][e] = t;
-        }
-      }
+    for (int k = 0; k < KT; ++k) gs[k][e] = gc[k][e] = 0.0f;
+  }
+  if (b >= nb) return;
+  const float* col = zs + 4 * (size_t)b;
+  int64_t i = i0;
+  for (; i + U <= i1; i += U) {
+    float4 zz[U];
+    float sv[U], qk[U][KT];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      zz[u] = __ldcs(reinterpret_cast<const float4*>(col + (size_t)(i + u) * dp));
+      sv[u] = tlaw ? __ldg(S + i + u) : 1.0f;
+#pragma unroll
+      for (int k = 0; k < KT; ++k) qk[u][k] = k < K ? __ldg(Q + (size_t)(i + u) * K + k) : 0.0f;
     }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int j = 4 * b + e;
-      if (j < d) {
-        part_m[(size_t)sl * d + j] = (double)ms[e] - (double)mc[e];
-#pragma unroll
-        for (int k = 0; k < KT; ++k)
-          if (k < K) part_g[((size_t)sl * K + k) * d + j] = (double)gs[k][e] - (double)gc[k][e];
-      }
+    for (int u = 0; u < U; ++u) {
+      const float z[4] = {zz[u].x, zz[u].y, zz[u].z, zz[u].w};
+      ld_adj_add<KT>(z, sv[u], qk[u], ms, mc, gs, gc);
     }
   }
+  for (; i < i1; ++i) {
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(col + (size_t)i * dp));
+    const float z[4] = {v.x, v.y, v.z, v.w};
+    float qk[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) qk[k] = k < K ? __ldg(Q + (size_t)i * K + k) : 0.0f;
+    ld_adj_add<KT>(z, tlaw ? __ldg(S + i) : 1.0f, qk, ms, mc, gs, gc);
+  }
+  ld_adj_write<KT>(b, d, K, sl, ms, mc, gs, gc, part_g, part_m);
 }
 
 // One warp per decision: S1, S2 over the forward CTAs (lane-strided, fixed
@@ -291,14 +365,18 @@ __global__ void k_ld_grad_out(int nsl, int K, int d, double N, double lambda, co
 template <int KT>
 cudaError_t launch_ld_kt(const LawArgs& la, int K, int want_grad, const Plan& plan, const Workspace& w,
                          cudaStream_t st) {
+  const int dp = (la.d + 3) & ~3;
+  float* zs = (want_grad && plan.keep) ? w.zs : nullptr;
   k_ld_fwd<KT><<<plan.grid, kLdThreads, 0, st>>>(la, K, (const float*)w.Y, w.q_dev, w.s_dev, w.part_s1, w.part_s2,
-                                                 plan.tiles);
+                                                 plan.tiles, zs, dp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !want_grad) return e;
   const int64_t per = (la.N + plan.nsplit - 1) / plan.nsplit;
-  k_ld_adj<KT><<<dim3((unsigned)plan.ablk, (unsigned)plan.nsplit), kLdThreads, 0, st>>>(la, K, per, w.q_dev,
-                                                                                        w.s_dev, w.part_gd,
-                                                                                        w.part_md);
+  const dim3 ag((unsigned)plan.ablk, (unsigned)plan.nsplit);
+  if (zs)
+    k_ld_adj_kept<KT><<<ag, kLdThreads, 0, st>>>(la, K, per, zs, dp, w.q_dev, w.s_dev, w.part_gd, w.part_md);
+  else
+    k_ld_adj<KT><<<ag, kLdThreads, 0, st>>>(la, K, per, w.q_dev, w.s_dev, w.part_gd, w.part_md);
   return cudaGetLastError();
 }
 
@@ -321,6 +399,8 @@ saa_status diag_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec p
   const int nb = (p->d + 3) / 4;
   plan->ablk = (nb + kLdThreads - 1) / kLdThreads;
   if (want_grad) {
+    const size_t store = (size_t)p->N * (size_t)((p->d + 3) & ~3) * sizeof(float);
+    plan->keep = store <= ctx->store_cap;
     // enough slices for about four CTAs per SM, each at least 256 scenarios
     int64_t ns = (4 * (int64_t)ctx->sm_count + plan->ablk - 1) / plan->ablk;
     const int64_t most = (p->N + 255) / 256;
@@ -351,6 +431,7 @@ size_t diag_carve(const saa_problem* p, int K, const Plan& plan, int want_grad, 
   if (want_grad) {
     w.part_gd = (double*)take((size_t)plan.nsplit * k * d * 8);
     w.part_md = (double*)take((size_t)plan.nsplit * d * 8);
+    if (plan.keep) w.zs = (float*)take(n * ((d + 3) & ~(size_t)3) * 4);
   }
   if (want_grad == 2) {
     w.f_tmp = (double*)take(k * 8);

@@ -269,6 +269,7 @@ saa_status saa_ctx_create(saa_ctx** out, int device) {
     return s;
   }
   c->autotune = 1;
+  c->store_cap = (size_t)1 << 35;
   *out = c;
   return SAA_OK;
 }
@@ -315,6 +316,12 @@ saa_status saa_selftest_timeout(saa_ctx* ctx, uint32_t budget_us, void* stream) 
 saa_status saa_ctx_set_autotune(saa_ctx* ctx, int enable) {
   if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
   ctx->autotune = enable ? 1 : 0;
+  return SAA_OK;
+}
+
+saa_status saa_ctx_set_sample_store(saa_ctx* ctx, size_t max_bytes) {
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  ctx->store_cap = max_bytes;
   return SAA_OK;
 }
 

@@ -156,6 +156,8 @@ def lib():
             L.saa_selftest_timeout.restype = C.c_int
             L.saa_ctx_set_autotune.argtypes = [vp, C.c_int]
             L.saa_ctx_set_autotune.restype = C.c_int
+            L.saa_ctx_set_sample_store.argtypes = [vp, sz]
+            L.saa_ctx_set_sample_store.restype = C.c_int
             L.saa_max_dim.argtypes = [C.c_int]
             L.saa_max_dim.restype = C.c_int32
             L.saa_status_string.argtypes = [C.c_int]
@@ -690,6 +692,12 @@ def saa_ctx_sync(device: int | None = None):
     _check(lib().saa_ctx_sync(context(dev.index), _stream(dev)))
 
 
+def saa_ctx_set_sample_store(max_bytes: int, device: int | None = None):
+    """Most bytes of FP32 samples the diagonal-covariance gradient keeps
+    between its forward and adjoint passes (0: draw them twice)."""
+    _check(lib().saa_ctx_set_sample_store(context(device), int(max_bytes)))
+
+
 def saa_profile_enable(enable: bool = True, device: int | None = None):
     """Starts / stops event timing of the main sample kernel (see saa.h)."""
     _check(lib().saa_profile_enable(context(device), int(enable)))
@@ -715,4 +723,4 @@ EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_
             "saa_moments_workspace_size", "saa_moments", "saa_eval_moments_workspace_size", "saa_eval_moments",
             "saa_eval_samples_workspace_size", "saa_eval_samples", "saa_solve_adaptive_workspace_size",
             "saa_solve_adaptive", "saa_logistic_pitch", "saa_logistic_generate", "saa_logistic_workspace_size",
-            "saa_logistic_eval"]
+            "saa_logistic_eval", "saa_ctx_set_sample_store"]

@@ -2,8 +2,9 @@
 independent assets of Sec. 4.1) against the oracle's diagonal branch: value
 and gradient over dimensions that cross the kernels' staging chunks (8192 /
 K dimensions) with ragged ends, up to Sec. 4.1's largest d = 10^5, every law
-and K = 1..4; Algorithm 1 teacher-forced at d = 5000, resumed bitwise and run
-with an adaptive sample size; a bad spread reported on the device.
+and K = 1..4; the adjoint's sample store bitwise equal to drawing again;
+Algorithm 1 teacher-forced at d = 5000, resumed bitwise and run with an
+adaptive sample size; a bad spread reported on the device.
 
 Tolerances are the FP32 path's (relative 1e-6): each 4-dimension block's
 dot product rounds once in FP32 before a float-float sum, and the decision
@@ -85,6 +86,25 @@ def test_deterministic_and_unsupported_forms():
     with pytest.raises(saa.SAAError) as e:
         saa.saa_eval(gp, torch.tensor(inputs.decisions(5, 3000, seed=1), device="cuda"))
     assert e.value.status in (saa.SAA_EINVAL, saa.SAA_EUNSUPPORTED) and "K <= 4" in str(e.value)
+
+
+@pytest.mark.parametrize("d,N,K,law", [(7, 3001, 1, oracle.LAW_STUDENT_T), (2051, 999, 3, oracle.LAW_MIX),
+                                       (9000, 517, 2, oracle.LAW_GAUSS)])
+def test_sample_store_matches_redraw_bitwise(d, N, K, law):
+    # the adjoint's normals from the store (forward pass) or drawn again: same bits
+    from paper_2404_11631_gb300 import saa
+    gp, op, mu = _make(d, N, law=law, seed=13)
+    X = torch.tensor(inputs.decisions(K, d, seed=2) / d, device="cuda")
+    kept = saa.saa_grad(gp, X)
+    saa.saa_ctx_set_sample_store(0)
+    try:
+        assert saa.workspace_size(gp, K, "fp32", 1) < 4 * N * d
+        redrawn = saa.saa_grad(gp, X)
+    finally:
+        saa.saa_ctx_set_sample_store(1 << 35)
+    saa.saa_ctx_sync()
+    assert saa.workspace_size(gp, K, "fp32", 1) >= 4 * N * d
+    assert torch.equal(kept["grad"], redrawn["grad"]) and torch.equal(kept["f"], redrawn["f"])
 
 
 def test_bad_spread_is_flagged():
