@@ -974,6 +974,8 @@ def main():
     ap.add_argument("--streamed-only", action="store_true", help="run only the streamed-samples workload")
     ap.add_argument("--no-large-d", action="store_true", help="skip the 10^5-asset diagonal portfolio workload")
     ap.add_argument("--large-d-only", action="store_true", help="run only the 10^5-asset diagonal portfolio workload")
+    ap.add_argument("--ld-d", type=int, default=None, help="override the diagonal portfolio's dimension (profiling)")
+    ap.add_argument("--ld-N", type=int, default=None, help="override the diagonal portfolio's sample count (profiling)")
     ap.add_argument("--nv-n", type=int, default=None, help="override the newsvendor product count")
     ap.add_argument("--fw-N", type=int, default=None, help="override the Algorithm 1 scenario count")
     ap.add_argument("--fw-T", type=int, default=None, help="override the Algorithm 1 iteration count")
@@ -1001,6 +1003,10 @@ def main():
         FW_WORKLOAD["name"] += f"_T{args.fw_T}"
     if args.gen_only:
         return run_gen(args)
+    if args.ld_d or args.ld_N:
+        LD_WORKLOAD["d"] = args.ld_d or LD_WORKLOAD["d"]
+        LD_WORKLOAD["N"] = args.ld_N or LD_WORKLOAD["N"]
+        LD_WORKLOAD["name"] = f"portfolio_diag_d{LD_WORKLOAD['d']}_N{LD_WORKLOAD['N']}"
     if args.nv_n:
         NV_WORKLOAD["n"] = args.nv_n
         NV_WORKLOAD["name"] = f"newsvendor_n{args.nv_n}_S{NV_WORKLOAD['S']}_K1"

@@ -6,7 +6,7 @@
 //
 // With C = diag(sd): w'R_i = c + s_i zhat_i'y, c = mu'w, y = sd o w.  Per
 // call (FP32 normals, the generator of every other path, bit-exact):
-//   forward  tiles of 32 scenarios, one warp per 4 of them; the decisions y
+//   forward  tiles of 8 scenarios, one warp each; the decisions y
 //            are staged through shared memory 8192 / K dimensions at a time, so
 //            a tile reads y once; lanes draw 4-dimension blocks and add
 //            each block's FP32 dot product into a float-float sum; Q_ik = s_i (sum) and s_i go to HBM, S1 and S2 to the CTA's
@@ -35,8 +35,8 @@ namespace {
 
 constexpr int kLdThreads = 256;
 constexpr int kLdWarps = kLdThreads / 32;
-constexpr int kLdSPW = 4;                       // scenarios per warp in a forward tile
-constexpr int kLdTile = kLdWarps * kLdSPW;     // 32 scenarios per forward tile
+constexpr int kLdSPW = 1;                       // scenarios per warp in a forward tile
+constexpr int kLdTile = kLdWarps * kLdSPW;     // 8 scenarios per forward tile (fine-grained rounds)
 constexpr int kLdChunkFloats = 8192;            // y staged per pass: 8192 / K dimensions (32 KB)
 constexpr int kLdMaxK = 4;
 
@@ -116,18 +116,22 @@ __global__ void __launch_bounds__(kLdThreads) k_ld_fwd(LawArgs la, int K, const 
         for (int bc = lane; bc < nbc; bc += 32) {
           float z[4];
           gen::Gen<float>::block(st, (uint32_t)((j0 >> 2) + bc), (uint32_t)i, logn, z);
+          if (4 * bc + 4 > dc) {   // the chunk's ragged tail (ys is zero there too)
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (4 * bc + e >= dc) z[e] = 0.0f;   // the chunk's ragged tail (ys is zero there too)
+            for (int e = 0; e < 4; ++e)
+              if (4 * bc + e >= dc) z[e] = 0.0f;
+          }
           if (zs)   // the sample store: row i, dimensions j0 + 4 bc .. + 3 (< dp, 16-byte aligned)
             __stcs(reinterpret_cast<float4*>(zs + (size_t)i * dp + j0 + 4 * bc), make_float4(z[0], z[1], z[2], z[3]));
           // the block's 4-term FP32 dot product, then one float-float add: the
           // error stays at the FP32 rounding of each block's partial
 #pragma unroll
           for (int k = 0; k < KT; ++k) {
-            float p = z[0] * ys[k][4 * bc];
-#pragma unroll
-            for (int e = 1; e < 4; ++e) p = fmaf(z[e], ys[k][4 * bc + e], p);
+            const float4 yv = *reinterpret_cast<const float4*>(&ys[k][4 * bc]);   // one 16-byte shared load
+            float p = z[0] * yv.x;
+            p = fmaf(z[1], yv.y, p);
+            p = fmaf(z[2], yv.z, p);
+            p = fmaf(z[3], yv.w, p);
             ld_ff_add(hi[q][k], lo[q][k], p);
           }
         }
@@ -380,6 +384,31 @@ cudaError_t launch_ld_kt(const LawArgs& la, int K, int want_grad, const Plan& pl
   return cudaGetLastError();
 }
 
+// Resident CTAs per SM of the forward (which = 0) or adjoint (1, from the
+// store when kept) kernel for K decisions; 2 if the query fails.
+int ld_occupancy(int which, int K, int kept) {
+  int occ = 0;
+  cudaError_t e;
+  const int kt = K == 1 ? 1 : K == 2 ? 2 : 4;
+  if (which == 0)
+    e = kt == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ld_fwd<1>, kLdThreads, 0)
+      : kt == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ld_fwd<2>, kLdThreads, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ld_fwd<4>, kLdThreads, 0);
+  else if (kept)
+    e = kt == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ld_adj_kept<1>, kLdThreads, 0)
+      : kt == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ld_adj_kept<2>, kLdThreads, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ld_adj_kept<4>, kLdThreads, 0);
+  else
+    e = kt == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ld_adj<1>, kLdThreads, 0)
+      : kt == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ld_adj<2>, kLdThreads, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ld_adj<4>, kLdThreads, 0);
+  if (e != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    return 2;
+  }
+  return occ;
+}
+
 }  // namespace
 
 saa_status diag_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec prec, int want_grad, Plan* plan) {
@@ -393,16 +422,20 @@ saa_status diag_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec p
   }
   plan->prec = prec;
   plan->diag = 1;
+  // forward: as many CTAs as fit on the SMs at once (the tiles are small,
+  // so the last round is a small part of the work)
   plan->tiles = (p->N + kLdTile - 1) / kLdTile;
-  const int64_t cap = 2 * (int64_t)ctx->sm_count;
+  const int64_t cap = (int64_t)ld_occupancy(0, K, 0) * ctx->sm_count;
   plan->grid = (int)(plan->tiles < cap ? plan->tiles : cap);
   const int nb = (p->d + 3) / 4;
   plan->ablk = (nb + kLdThreads - 1) / kLdThreads;
   if (want_grad) {
     const size_t store = (size_t)p->N * (size_t)((p->d + 3) & ~3) * sizeof(float);
     plan->keep = store <= ctx->store_cap;
-    // enough slices for about four CTAs per SM, each at least 256 scenarios
-    int64_t ns = (4 * (int64_t)ctx->sm_count + plan->ablk - 1) / plan->ablk;
+    // adjoint: scenario slices for one full wave of CTAs (all equal work),
+    // each slice at least 256 scenarios
+    const int64_t slots = (int64_t)ld_occupancy(1, K, plan->keep) * ctx->sm_count;
+    int64_t ns = slots / plan->ablk;
     const int64_t most = (p->N + 255) / 256;
     if (ns > most) ns = most;
     plan->nsplit = (int)(ns < 1 ? 1 : ns);
