@@ -440,6 +440,15 @@ saa_status saa_eval_static(const saa_problem* prob, int32_t K, const double* X, 
  * clears it, and the context stays usable.  No fault, trap or hang. */
 saa_status saa_selftest_timeout(saa_ctx* ctx, uint32_t budget_us, void* stream);
 
+/* Arithmetic self-test of the FP32 generator: for every one of its 2^23
+ * uniforms u = (2k + 1) 2^-24 it compares the LOG's quotient (m - 1)/(m + 1)
+ * and the Box-Muller root sqrt(-2 LOG(u)), which the generator forms by
+ * Markstein's correction of the hardware approximations, with the IEEE
+ * round-to-nearest division and square root.  mismatches: device [2]
+ * (quotient, root), zeroed and then filled asynchronously on `stream`; both
+ * are 0 when the generator's results are the IEEE ones bit for bit. */
+saa_status saa_selftest_arith(saa_ctx* ctx, unsigned long long* mismatches, void* stream);
+
 /* Kernel timing (tracing).  While enabled, every saa_eval / saa_grad call
  * records a CUDA event pair on its stream around its main sample kernel (the
  * generation + contraction + epilogue kernel) and counts the kernels it

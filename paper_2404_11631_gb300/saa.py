@@ -154,6 +154,8 @@ def lib():
             L.saa_batch_destroy.restype = None
             L.saa_selftest_timeout.argtypes = [vp, C.c_uint32, vp]
             L.saa_selftest_timeout.restype = C.c_int
+            L.saa_selftest_arith.argtypes = [vp, vp, vp]
+            L.saa_selftest_arith.restype = C.c_int
             L.saa_ctx_set_autotune.argtypes = [vp, C.c_int]
             L.saa_ctx_set_autotune.restype = C.c_int
             L.saa_ctx_set_sample_store.argtypes = [vp, sz]
@@ -680,6 +682,16 @@ def saa_grad_batched(problems: list, Xs: list, prec="fp32") -> dict:
     return out
 
 
+def saa_selftest_arith(device: int | None = None) -> tuple[int, int]:
+    """(quotient, root) mismatch counts of the generator's Markstein-corrected
+    arithmetic against IEEE over all 2^23 FP32 uniforms (both 0 when exact)."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    out = torch.empty(2, dtype=torch.int64, device=dev)
+    _check(lib().saa_selftest_arith(context(dev.index), _ptr(out), _stream(dev)))
+    c = out.cpu()
+    return int(c[0]), int(c[1])
+
+
 def saa_selftest_timeout(budget_us: int = 1000, device: int | None = None):
     """Runs the bounded-wait self-test (see saa.h); saa_ctx_sync then raises SAA_ETIMEOUT."""
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -723,4 +735,4 @@ EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_
             "saa_moments_workspace_size", "saa_moments", "saa_eval_moments_workspace_size", "saa_eval_moments",
             "saa_eval_samples_workspace_size", "saa_eval_samples", "saa_solve_adaptive_workspace_size",
             "saa_solve_adaptive", "saa_logistic_pitch", "saa_logistic_generate", "saa_logistic_workspace_size",
-            "saa_logistic_eval", "saa_ctx_set_sample_store"]
+            "saa_logistic_eval", "saa_ctx_set_sample_store", "saa_selftest_arith"]

@@ -39,3 +39,23 @@ def test_generate_full_range_sampled_rows():
         out = saa.saa_generate(gp, i0, 5, "fp32")
         z_or, s_or, _ = oracle.generate(op, 32, i0, 5)
         assert np.array_equal(out["z"].cpu().numpy(), z_or.astype(np.float32))
+
+
+def test_generator_arithmetic_is_ieee_on_its_whole_domain():
+    # the LOG quotient and the Box-Muller root, formed by Markstein's
+    # correction of the hardware approximations, against the IEEE
+    # round-to-nearest results for all 2^23 FP32 uniforms
+    from paper_2404_11631_gb300 import saa
+    assert saa.saa_selftest_arith() == (0, 0)
+
+
+def test_generate_many_rows_bit_exact():
+    # 2^16 scenarios x 4 dimensions: 2^17 Box-Muller pairs through the
+    # shortened arithmetic, every law, against the oracle
+    from paper_2404_11631_gb300 import saa
+    for law in (oracle.LAW_GAUSS, oracle.LAW_MIX, oracle.LAW_STUDENT_T):
+        gp, op, inst = make(4, 1 << 16, law=law, nu=8, seed=99)
+        out = saa.saa_generate(gp, 0, 1 << 16, "fp32")
+        z_or, s_or, _ = oracle.generate(op, 32, 0, 1 << 16)
+        assert np.array_equal(out["z"].cpu().numpy().view(np.uint32), z_or.astype(np.float32).view(np.uint32))
+        assert np.array_equal(out["s"].cpu().numpy(), s_or.astype(np.float32))
