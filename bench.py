@@ -140,13 +140,13 @@ def oracle_sample(d, K, law, n_target_s=12.0, N_full=1 << 20, rank=0):
 # Per-normal work of the scenario generator (the roofline's per-unit figure):
 # thread-instructions per normal of the generator-only kernel
 # (saa_generate_moments, FP32 mode, d = 128), counted by ncu
-# (smsp__thread_inst_executed.sum / normals): 48.95 for a Gaussian normal and
-# 64.20 for a standardised lognormal one, with the LOG quotient and the
+# (smsp__thread_inst_executed.sum / normals): 46.45 for a Gaussian normal and
+# 61.70 for a standardised lognormal one, with the LOG quotient and the
 # Box-Muller root formed by Markstein's corrections (57.15 and 72.65 with the
 # IEEE divide and square-root sequences).  That kernel adds one add and one
 # fma per normal to the draw.
-GEN_INST_GAUSS = 48.95
-GEN_INST_LOGN = 64.20 - 48.95
+GEN_INST_GAUSS = 46.45
+GEN_INST_LOGN = 61.70 - 46.45
 # The stricter count from the generator's specification, each IEEE
 # add/sub/mul/fma/div/sqrt, integer op, fused 3-input xor or 32x32->64
 # multiply being one operation: Philox4x32-10 10, uniforms 3, log 10.5,
