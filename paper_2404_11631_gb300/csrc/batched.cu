@@ -797,6 +797,7 @@ extern "C" size_t saa_workspace_size_batched(const saa_ctx* ctx, int32_t B, cons
 extern "C" saa_status saa_eval_batched(saa_ctx* ctx, int32_t B, const saa_problem* probs, const int32_t* K,
                                        const double* const* X, saa_prec prec, double* const* f, double* const* pbar,
                                        double* const* var, void* ws, size_t ws_bytes, void* stream) {
+  saa::NvtxRange nvtx_range("saa_eval_batched");
   if (!ctx) {
     set_error("ctx is NULL");
     return SAA_EINVAL;
@@ -826,6 +827,7 @@ extern "C" saa_status saa_batch_create(saa_ctx* ctx, int32_t B, const saa_proble
                                        const double* const* X, saa_prec prec, double* const* f, double* const* pbar,
                                        double* const* var, double* const* grad, void* ws, size_t ws_bytes,
                                        void* stream, saa_batch** out) {
+  saa::NvtxRange nvtx_range("saa_batch_create");
   if (!ctx || !out) {
     set_error("saa_batch_create: ctx and out must be non-NULL");
     return SAA_EINVAL;
@@ -890,6 +892,7 @@ extern "C" saa_status saa_batch_create(saa_ctx* ctx, int32_t B, const saa_proble
 }
 
 extern "C" saa_status saa_batch_launch(saa_batch* batch, void* stream) {
+  saa::NvtxRange nvtx_range("saa_batch_launch");
   if (!batch) {
     set_error("saa_batch_launch: batch is NULL");
     return SAA_EINVAL;

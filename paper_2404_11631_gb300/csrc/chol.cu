@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(256) k_chol_update(int d, int jb, double* A) {
 using namespace saa;
 
 extern "C" saa_status saa_cholesky(saa_ctx* ctx, int32_t d, const double* Sigma, double* chol, void* stream) {
+  saa::NvtxRange nvtx_range("saa_cholesky");
   if (!ctx) {
     set_error("saa_cholesky: ctx is NULL");
     return SAA_EINVAL;

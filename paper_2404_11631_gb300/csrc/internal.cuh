@@ -2,6 +2,7 @@
 // units (not part of the public ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -98,6 +99,16 @@ struct saa_ctx {
 };
 
 namespace saa {
+
+// NVTX range over one entry-point call (host side).  The NVTX v3 headers
+// load no library unless a profiler injects one, so without a tool this is
+// a pair of cheap no-op calls.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 void set_error(const std::string& msg);
 saa_status cuda_status(cudaError_t e, const char* what);

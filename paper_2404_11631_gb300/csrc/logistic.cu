@@ -494,6 +494,7 @@ extern "C" int32_t saa_logistic_pitch(int32_t n) { return n < 1 ? 0 : lg_pitch(n
 
 extern "C" saa_status saa_logistic_generate(saa_ctx* ctx, const saa_logistic* prob, int64_t i0, int64_t rows,
                                             uint32_t* X, uint8_t* z, void* stream) {
+  saa::NvtxRange nvtx_range("saa_logistic_generate");
   if (!ctx || !prob) {
     set_error("saa_logistic_generate: ctx and prob must be non-NULL");
     return SAA_EINVAL;
@@ -534,6 +535,7 @@ extern "C" saa_status saa_logistic_eval(saa_ctx* ctx, int32_t n, int64_t N, cons
                                         const int64_t* idx, int64_t b, int32_t K, const double* W, const double* V,
                                         double* F, double* grad, double* hvp, void* ws, size_t ws_bytes,
                                         void* stream) {
+  saa::NvtxRange nvtx_range("saa_logistic_eval");
   if (!idx) b = N;
   saa_status s = lg_check(ctx, n, N, b, K);
   if (s != SAA_OK) return s;

@@ -170,6 +170,7 @@ extern "C" size_t saa_generate_moments_workspace_size(const saa_ctx* ctx, const 
 extern "C" saa_status saa_generate_moments(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n,
                                            saa_prec prec, double* sum, double* sumsq, void* ws, size_t ws_bytes,
                                            void* stream) {
+  saa::NvtxRange nvtx_range("saa_generate_moments");
   saa_status s = check_args(ctx, prob, i0, n, prec);
   if (s != SAA_OK) return s;
   if (!sum || !ws) {

@@ -123,6 +123,7 @@ extern "C" size_t saa_newsvendor_workspace_size(const saa_newsvendor* prob, int3
 
 extern "C" saa_status saa_newsvendor_grad(saa_ctx* ctx, const saa_newsvendor* prob, int32_t K, const double* X,
                                           double* grad, void* ws, size_t ws_bytes, void* stream) {
+  saa::NvtxRange nvtx_range("saa_newsvendor_grad");
   if (!ctx) {
     set_error("saa_newsvendor: ctx is NULL");
     return SAA_EINVAL;

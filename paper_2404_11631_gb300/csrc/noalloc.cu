@@ -59,6 +59,7 @@ using namespace saa;
 
 extern "C" saa_status saa_eval_static(const saa_problem* prob, int32_t K, const double* X, saa_prec prec, double* f,
                                       double* pbar, double* var, void* stream) {
+  saa::NvtxRange nvtx_range("saa_eval_static");
   if (!prob || prob->d < 1 || prob->N < 2 || prob->N > 0xffffffffll || prob->law < SAA_LAW_GAUSS ||
       prob->law > SAA_LAW_MIX || (prob->law == SAA_LAW_STUDENT_T && (prob->nu < 2 || (prob->nu & 1) || prob->nu > 64)) ||
       prob->reserved != 0 || !prob->mu || !prob->chol) {

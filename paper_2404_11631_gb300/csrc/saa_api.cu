@@ -410,17 +410,20 @@ static saa_status eval_impl(saa_ctx* ctx, const saa_problem* prob, int32_t K, co
 
 saa_status saa_eval(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec, double* f,
                     double* pbar, double* var, void* ws, size_t ws_bytes, void* stream) {
+  saa::NvtxRange nvtx_range("saa_eval");
   return eval_impl(ctx, prob, K, X, prec, 0, f, pbar, var, nullptr, ws, ws_bytes, stream);
 }
 
 saa_status saa_grad(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec, double* f,
                     double* grad, void* ws, size_t ws_bytes, void* stream) {
+  saa::NvtxRange nvtx_range("saa_grad");
   return eval_impl(ctx, prob, K, X, prec, 1, f, nullptr, nullptr, grad, ws, ws_bytes, stream);
 }
 
 saa_status saa_solve(saa_ctx* ctx, const saa_problem* prob, const double* w0, int32_t T, int32_t M, int64_t t0,
                      saa_prec prec, double* w_out, double* f_trace, double* gap_trace, void* ws, size_t ws_bytes,
                      void* stream) {
+  saa::NvtxRange nvtx_range("saa_solve");
   if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
   saa_status s = check_problem(prob);
   if (s != SAA_OK) return s;
@@ -454,6 +457,7 @@ size_t saa_solve_adaptive_workspace_size(const saa_ctx* ctx, const saa_problem* 
 saa_status saa_solve_adaptive(saa_ctx* ctx, const saa_problem* prob, const double* w0, const int64_t* N_sched,
                               int32_t n_epochs, int32_t M, int32_t k0, saa_prec prec, double* w_out,
                               double* f_trace, double* gap_trace, void* ws, size_t ws_bytes, void* stream) {
+  saa::NvtxRange nvtx_range("saa_solve_adaptive");
   if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
   if (!N_sched || n_epochs < 1 || M < 1 || k0 < 0) return fail(SAA_EINVAL, "need N_sched, n_epochs >= 1, M >= 1, k0 >= 0");
   if (!w0 || !w_out) return fail(SAA_EINVAL, "w0 and w_out must be device pointers");
@@ -493,6 +497,7 @@ saa_status saa_solve_adaptive(saa_ctx* ctx, const saa_problem* prob, const doubl
 
 saa_status saa_generate(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, saa_prec prec, void* z_out,
                         void* s_out, void* xi_out, void* stream) {
+  saa::NvtxRange nvtx_range("saa_generate");
   if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
   saa_status s = check_problem(prob);
   if (s != SAA_OK) return s;

@@ -437,6 +437,7 @@ extern "C" size_t saa_moments_workspace_size(const saa_ctx* ctx, const saa_probl
 
 extern "C" saa_status saa_moments(saa_ctx* ctx, const saa_problem* prob, saa_prec prec, double* M, double* mt,
                                   void* ws, size_t ws_bytes, void* stream) {
+  saa::NvtxRange nvtx_range("saa_moments");
   saa_status s = gram_check(ctx, prob, prec);
   if (s != SAA_OK) return s;
   if (!M || !mt || !ws || (((uintptr_t)ws) & 255u)) {
@@ -490,6 +491,7 @@ extern "C" size_t saa_eval_moments_workspace_size(const saa_problem* prob, int32
 extern "C" saa_status saa_eval_moments(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X,
                                        const double* M, const double* mt, double* f, double* pbar, double* var,
                                        double* grad, void* ws, size_t ws_bytes, void* stream) {
+  saa::NvtxRange nvtx_range("saa_eval_moments");
   if (!ctx || !prob || prob->d < 1 || prob->d > tc::kQD || prob->N < 2 || !prob->mu || !prob->chol) {
     set_error("saa_eval_moments: need ctx, and a problem with 1 <= d <= 128, N >= 2, device mu, chol");
     return SAA_EINVAL;

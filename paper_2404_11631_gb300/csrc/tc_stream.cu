@@ -587,6 +587,7 @@ extern "C" saa_status saa_eval_samples(saa_ctx* ctx, int64_t N, int32_t d, const
                                        const double* sigma, int32_t K, const double* X, double lambda,
                                        saa_prec prec, double* f, double* pbar, double* var, void* ws,
                                        size_t ws_bytes, void* stream) {
+  saa::NvtxRange nvtx_range("saa_eval_samples");
   saa_status s = stream_check(ctx, N, d, K, prec);
   if (s != SAA_OK) return s;
   if (!R || (((uintptr_t)R) & 15u) || !X || !ws || (((uintptr_t)ws) & 255u)) {
