@@ -43,3 +43,22 @@ def test_large_dimension_variance_is_unbiased():
     assert abs(v.mean() - truth) < 5 * se
     with pytest.raises(ValueError):
         oracle.generate(oracle.make_problem(d, N, mu, None, sd=sd), 64, 0, 4, want_xi=True)
+
+
+def test_gradient_expectation_is_the_closed_form():
+    # E[grad f_hat] = 2 lambda Sigma w - mu with Sigma = diag(sd^2): the sample
+    # covariance is unbiased and R_bar has mean mu; checked per component
+    # against the spread of independent resamples (Gaussian law)
+    d, N, E, lam = 200, 400, 120, 0.5
+    rng = np.random.default_rng(5)
+    mu = rng.uniform(-1.0, 1.0, d)
+    sd = rng.uniform(0.5, 1.5, d)
+    w = rng.uniform(0.0, 1.0, d) / d
+    g = np.array([oracle.saa(oracle.make_problem(d, N, mu, None, lam=lam, seed=7, epoch=e, sd=sd), 64, w,
+                             grad=True)["grad"][0] for e in range(E)])
+    truth = 2.0 * lam * sd ** 2 * w - mu
+    se = g.std(axis=0, ddof=1) / np.sqrt(E)
+    assert np.all(np.abs(g.mean(axis=0) - truth) <= 5.0 * se)
+    # and the spread is the one the sample mean alone would give (the variance
+    # term's noise is of order lambda sd_j sigma_p / sqrt(N), far smaller here)
+    assert np.allclose(g.std(axis=0, ddof=1), sd / np.sqrt(N), rtol=0.35)
