@@ -6,11 +6,12 @@
 //
 // With C = diag(sd): w'R_i = c + s_i zhat_i'y, c = mu'w, y = sd o w.  Per
 // call (FP32 normals, the generator of every other path, bit-exact):
-//   forward  tiles of 8 scenarios, one warp each; the decisions y
-//            are staged through shared memory 8192 / K dimensions at a time, so
-//            a tile reads y once; lanes draw 4-dimension blocks and add
-//            each block's FP32 dot product into a float-float sum; Q_ik = s_i (sum) and s_i go to HBM, S1 and S2 to the CTA's
-//            FP64 partials.
+//   forward  tiles of 8 scenarios, one warp each; the decisions y are
+//            staged through shared memory 8192 / K dimensions at a time, so
+//            a tile reads y once; lanes draw 4-dimension blocks and add each
+//            block's FP32 dot product into a float-float sum; Q_ik = s_i
+//            (sum) and s_i go to HBM, S1 and S2 to the CTA's FP64 partials;
+//            with the sample store on, every normal is written out too.
 //   adjoint  (gradient only) one thread per 4-dimension block over a slice
 //            of the scenarios keeps Kahan-compensated FP32 sums of a_ij Q_ik
 //            (G) and a_ij (m~), written per slice in FP64.  It takes its
