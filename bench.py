@@ -465,6 +465,26 @@ def run_large_d(args, dev, world, rank, flush, stream):
                    "s_for_1500_iterations": 1.5 * ms / T, "f_first_last": [float(out["f_trace"][0]),
                                                                           float(out["f_trace"][-1])],
                    "gap_last": float(out["gap_trace"][-1])}
+    # Sec. 4.1's asset sizes: Algorithm 1 per iteration at each (T = 20 timed
+    # iterations after 2; M = 25, 50 at 10^5 as the paper samples)
+    sweep = {}
+    if not args.ld_d:
+        for dd in (500, 5000, 10_000, 50_000, 100_000):
+            pr = problem(dd)
+            w0 = torch.tensor(inputs.fw_start(dd), device=dev)
+            M = 50 if dd == 100_000 else 25
+            wsf = torch.empty(saa.workspace_size(pr, 1, "fp32", 2), dtype=torch.uint8, device=dev)
+            saa.saa_solve(pr, w0, T=2, M=M, ws=wsf)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            saa.saa_solve(pr, w0, T=20, M=M, ws=wsf)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            saa.saa_ctx_sync(dev.index)
+            sweep[str(dd)] = {"ms_per_iteration": e0.elapsed_time(e1) / 20,
+                              "s_for_1500_iterations": 1.5 * e0.elapsed_time(e1) / 20, "M": M}
+            del wsf
     res = {"metric": "normals/s (portfolio value and gradient, diagonal Sigma)", "value": world * normals / step_s,
            "unit": "normals/s", "ms_per_step": 1e3 * step_s, "steps": steps, "kernels_ms": 1e3 * kern_s,
            "forward_kernel_ms": 1e3 * fwd_s, "value_only_ms_per_step": 1e3 * res_k["value"][0],
@@ -476,7 +496,7 @@ def run_large_d(args, dev, world, rank, flush, stream):
                         "note": "lane-ops: one draw per normal + 3 per normal; forward + adjoint.  The forward "
                                 "writes the FP32 normals, the adjoint reads them (adjoint_hbm_frac: that read "
                                 "against the measured HBM copy bandwidth)"},
-           "fw": fw,
+           "fw": fw, "fw_size_sweep_N65536": sweep,
            "config": {"workload": LD_WORKLOAD["name"], "d": d, "N": N, "K": 1, "law": "Gaussian",
                       "sigma": "diag, U(0, 0.025)", "prec": "fp32", "l2": "flushed between timed steps"}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -602,13 +622,31 @@ def run_newsvendor(args, dev, world, rank, flush, stream):
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = 152 * 128 * mhz * 1e6 / 1e12
     ops = samples * (GEN_INST_GAUSS + 2.0 * K)   # generator per normal + compare and count per decision
+    # Sec. 4.1's inventory sizes, 10^2 .. 10^6 products (same S): one gradient each
+    sweep = {}
+    for nn in (100, 1000, 10_000, 100_000, 1_000_000):
+        p2 = saa.Newsvendor(**{a: torch.tensor(x[:nn], device=dev) for a, x in arrs.items()}, S=S, seed=0,
+                            instance=rank)
+        X2 = X[:, :nn].contiguous()
+        for _ in range(2):
+            saa.saa_newsvendor_grad(p2, X2)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            saa.saa_newsvendor_grad(p2, X2)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sweep[str(nn)] = {"ms_per_gradient": e0.elapsed_time(e1) / 10}
+    saa.saa_ctx_sync(dev.index)
     return {"metric": "demand samples/s (newsvendor MC gradient)", "value": world * samples * steps / total_s,
             "unit": "samples/s", "ms_per_step": 1e3 * total_s / steps, "steps": steps,
             "config": {"workload": NV_WORKLOAD["name"], "n": n, "S": S, "K": K, "prec": "fp32 normals, exact counts",
                        "l2": "flushed between timed steps"},
             "roofline": {"bound": "alu", "achieved": ops * steps / total_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": ops * steps / total_s / 1e12 / peak,
-                         "note": "generator-only kernel's instructions per normal + 2 per sample and decision"}}
+                         "note": "generator-only kernel's instructions per normal + 2 per sample and decision"},
+            "size_sweep": sweep}
 
 
 def run_covariance(args, dev, world, rank, flush, stream):
