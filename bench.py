@@ -194,9 +194,10 @@ def roofline(prec, d, N, K, law, kern_s, peaks, peak_src):
                  "+ contraction/epilogue per pair"}
     if prec in ("bf16x3", "f16x3"):
         # ncu dram__bytes_read.sum + dram__bytes_write.sum of the tensor kernel
-        # (F16, d = 128, K = 256): the per-launch operand image, independent of N
+        # (F16, d = 128, K = 256, full size, one-pass capture): the per-launch
+        # operand image, independent of N
         if prec == "f16x3" and d == 128 and K == 256:
-            r["traffic"] = 188928
+            r["traffic"] = 187136
         tflops = 3 * 2.0 * N * d * K / kern_s / 1e12
         r["tensor"] = {"achieved": tflops, "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
                        "frac": tflops / float(peaks["bf16_tflops"]), "peak_source": f"{peak_src} bf16 dense (burst)"}
@@ -222,7 +223,7 @@ def grad_roofline(prec, d, N, K, law, kern_s, peaks):
     # ncu DRAM bytes of the F16 kernel at d = 1024, K = 64, N = 2^17 (the
     # per-tile flush of the gradient partials), scaled by N: it grows with
     # the number of tiles per CTA
-    traffic = 456862208.0 * N / (1 << 17) if (prec == "f16x3" and d == 1024 and K == 64) else None
+    traffic = 447954944.0 * N / (1 << 17) if (prec == "f16x3" and d == 1024 and K == 64) else None
     return {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
             "frac": ops / kern_s / 1e12 / peak, "traffic": traffic, "kernel_ms": kern_s * 1e3,
             "frac_spec_count": ops_spec / kern_s / 1e12 / peak,
