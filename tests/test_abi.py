@@ -86,3 +86,47 @@ def test_binding_argtypes_match_the_header():
             assert is_ptr == (kind == "ptr"), (name, t, kind)
         checked += 1
     assert checked >= 12
+
+
+def _c_layout(struct, fields):
+    # sizeof and offsetof of a header struct, from a C compiler
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    body = "".join(f'printf("%zu ", offsetof({struct}, {f}));' for f in fields)
+    src = (f'#include <stdio.h>\n#include <stddef.h>\n#include "saa.h"\n'
+           f'int main(void) {{ printf("%zu ", sizeof({struct})); {body} return 0; }}\n')
+    with tempfile.TemporaryDirectory() as td:
+        c, exe = os.path.join(td, "l.c"), os.path.join(td, "l")
+        with open(c, "w") as fh:
+            fh.write(src)
+        subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()]
+    return vals[0], vals[1:]
+
+
+@pytest.mark.parametrize("struct,mirror", [("saa_problem", "_CProblem"), ("saa_newsvendor", "_CNewsvendor"),
+                                           ("saa_logistic", "_CLogistic")])
+def test_binding_structs_match_the_header_layout(struct, mirror):
+    # the ctypes mirrors of the header's host structs: same size, same field offsets
+    from paper_2404_11631_gb300 import saa
+    cls = getattr(saa, mirror)
+    names = [f[0] for f in cls._fields_]
+    cnames = ["lambda" if n == "lam" else n for n in names]
+    size, offs = _c_layout(struct, cnames)
+    assert C.sizeof(cls) == size
+    assert [getattr(cls, n).offset for n in names] == offs
+
+
+def test_problem_validation_on_the_host():
+    # argument checks of the binding that run before any device call
+    import torch
+    from paper_2404_11631_gb300 import saa
+    mu = torch.zeros(4, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        saa.Problem(mu=mu, chol=None, N=10).c_struct()     # neither chol nor sd, and CPU tensors
+    with pytest.raises(ValueError):
+        saa.Problem(mu=mu, chol=torch.eye(4, dtype=torch.float64), N=10).c_struct()   # not on a GPU
