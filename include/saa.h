@@ -60,7 +60,7 @@ typedef enum {
     SAA_ECUDA = 3,        /* CUDA runtime error */
     SAA_ETIMEOUT = 4,     /* a bounded device wait gave up */
     SAA_EDEVICE = 5,      /* a device-side check flagged an error */
-    SAA_EUNSUPPORTED = 6  /* size or precision outside what this build supports */
+    SAA_EUNSUPPORTED = 6  /* size or precision outside what the library supports */
 } saa_status;
 
 typedef enum {
@@ -459,7 +459,7 @@ saa_status saa_selftest_arith(saa_ctx* ctx, unsigned long long* mismatches, void
 saa_status saa_profile_enable(saa_ctx* ctx, int enable);
 saa_status saa_profile_read(saa_ctx* ctx, double* main_ms, int64_t* main_launches, int64_t* kernels_launched);
 
-/* Largest d supported by `prec` in this build. */
+/* Largest d that `prec` supports. */
 int32_t saa_max_dim(saa_prec prec);
 
 const char* saa_status_string(saa_status s);

@@ -522,7 +522,7 @@ const char* saa_status_string(saa_status s) {
     case SAA_ECUDA: return "SAA_ECUDA: CUDA runtime error";
     case SAA_ETIMEOUT: return "SAA_ETIMEOUT: bounded device wait gave up";
     case SAA_EDEVICE: return "SAA_EDEVICE: device-side check failed";
-    case SAA_EUNSUPPORTED: return "SAA_EUNSUPPORTED: not supported by this build";
+    case SAA_EUNSUPPORTED: return "SAA_EUNSUPPORTED: not supported by libsaa";
   }
   return "unknown saa_status";
 }
