@@ -123,3 +123,23 @@ def test_bad_arguments():
         saa.saa_logistic_eval(torch.zeros(10, saa.lib().saa_logistic_pitch(60_000), dtype=torch.int32, device="cuda"),
                               torch.zeros(10, dtype=torch.uint8, device="cuda"), 60_000,
                               torch.zeros(1, 60_000, dtype=torch.float64, device="cuda"))
+
+
+def test_sqn_on_the_device_follows_the_oracle():
+    # Algorithm 3 with the device's mini-batch gradients and Hessian products
+    # against the same run with the oracle's (same sample draws)
+    from paper_2404_11631_gb300 import saa
+    from paper_2404_11631_gb300.sqn import device_callables, sqn
+    n, N, L = 100, 3000, 10
+    wstar = inputs.logistic_weights(n, 4)
+    gpu = saa.saa_logistic_generate(n, N, torch.tensor(wstar, device="cuda"), seed=4)
+    op = oracle.make_logistic(n, N, wstar, seed=4)
+    g_dev, h_dev = device_callables(gpu["X"], gpu["z"], n)
+    g_or = lambda w, idx: oracle.logistic_eval(op, w[None], idx=idx, want=("F", "grad"))["grad"][0]
+    h_or = lambda w, v, idx: oracle.logistic_eval(op, w[None], V=v[None], idx=idx, want=("F", "hvp"))["hvp"][0]
+    a = sqn(g_dev, h_dev, np.zeros(n), N, iters=6 * L, L=L, rng=np.random.default_rng(1))
+    b = sqn(g_or, h_or, np.zeros(n), N, iters=6 * L, L=L, rng=np.random.default_rng(1))
+    assert a.pairs_used == b.pairs_used >= 3
+    assert np.linalg.norm(a.w - b.w) <= 1e-2 * np.linalg.norm(b.w)
+    F = float(oracle.logistic_eval(op, a.w[None], want=("F",))["F"][0])
+    assert F < 0.8 * np.log(2.0)
