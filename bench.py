@@ -466,6 +466,17 @@ def run_large_d(args, dev, world, rank, flush, stream):
                    "s_for_1500_iterations": 1.5 * ms / T, "f_first_last": [float(out["f_trace"][0]),
                                                                           float(out["f_trace"][-1])],
                    "gap_last": float(out["gap_trace"][-1])}
+        try:   # Table 2's accuracy measure against the exact optimum (host arithmetic only)
+            from paper_2404_11631_gb300.reporting import diag_optimum, rse
+            mu_np, sd_np = inputs.paper_assets(dd, 0)
+            _, f_star = diag_optimum(mu_np, sd_np)
+            ft = out["f_trace"].cpu().numpy()
+            w_fin = out["w"].cpu().numpy()
+            fw[tag]["f_star"] = f_star
+            fw[tag]["f_exact_last"] = float(0.5 * np.sum(sd_np ** 2 * w_fin ** 2) - mu_np @ w_fin)
+            fw[tag]["rse_pct"] = {str(t): float(rse(ft[t - 1], f_star)) for t in (50, 100, 500, 1000) if t <= T}
+        except Exception as exc:   # a reporting extra never stops the bench
+            fw[tag]["rse_error"] = repr(exc)
     # Sec. 4.1's asset sizes: Algorithm 1 per iteration at each (T = 20 timed
     # iterations after 2; M = 25, 50 at 10^5 as the paper samples)
     sweep = {}
