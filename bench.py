@@ -474,7 +474,8 @@ def run_large_d(args, dev, world, rank, flush, stream):
             w_fin = out["w"].cpu().numpy()
             fw[tag]["f_star"] = f_star
             fw[tag]["f_exact_last"] = float(0.5 * np.sum(sd_np ** 2 * w_fin ** 2) - mu_np @ w_fin)
-            fw[tag]["rse_pct"] = {str(t): float(rse(ft[t - 1], f_star)) for t in (50, 100, 500, 1000) if t <= T}
+            vals = {str(t): float(rse(ft[t - 1], f_star)) for t in (50, 100, 500, 1000) if t <= T}
+            fw[tag]["rse_pct"] = {t: (v if np.isfinite(v) else None) for t, v in vals.items()}
         except Exception as exc:   # a reporting extra never stops the bench
             fw[tag]["rse_error"] = repr(exc)
     # Sec. 4.1's asset sizes: Algorithm 1 per iteration at each (T = 20 timed
