@@ -71,3 +71,12 @@ def test_algorithm_2_reaches_the_optimum():
                    bounds=[(0, None)] * n, constraints=cons, options={"ftol": 1e-12, "maxiter": 500})
     f_star, f = res.fun, _cost(x, mu, sigma, k, h, v)
     assert f >= f_star - 1e-6 and (f - f_star) <= 2e-2 * abs(f_star)
+
+
+def test_lmo_edge_cases():
+    A, C = np.array([[1.0, 2.0, 4.0]]), np.array([8.0])
+    assert np.array_equal(lmo(np.array([0.0, 1.0, 2.0]), A, C), np.zeros(3))     # nothing pays: s = 0
+    # the best cost per unit of resource: -1/1 vs -3/2 vs -4/4 -> product 1, at C / a_1
+    assert np.array_equal(lmo(np.array([-1.0, -3.0, -4.0]), A, C), np.array([0.0, 4.0, 0.0]))
+    # equal ratios: the first index
+    assert np.array_equal(lmo(np.array([-1.0, -2.0, -4.0]), A, C), np.array([8.0, 0.0, 0.0]))

@@ -50,3 +50,19 @@ def test_sqn_lowers_the_objective():
     f = [F(w) for w in res.w_trace]
     assert F(res.w) < 0.8 * F(w0)            # F(0) = log 2
     assert f[-1] < f[1]                      # still descending after the SGD phase
+
+
+def test_sqn_keeps_the_last_M_pairs_and_skips_flat_curvature():
+    n = 6
+    calls = {"h": 0}
+
+    def grad(w, idx):
+        return w - 1.0   # F = |w - 1|^2 / 2
+
+    def hvp(w, v, idx):
+        calls["h"] += 1
+        return v if calls["h"] % 3 else 0.0 * v   # every third pair has s'y = 0
+
+    res = sqn(grad, hvp, np.zeros(n), 100, iters=200, L=5, M=4, beta=1.0, rng=np.random.default_rng(0))
+    assert res.pairs_used <= 4 and res.skipped_pairs >= 1
+    assert np.allclose(res.w, 1.0, atol=5e-2)
