@@ -134,6 +134,11 @@ def lib():
             L.oracle_saa_explicit.restype = C.c_int
             L.oracle_saa.argtypes = [pp, C.c_int, C.c_uint32, C.c_int, dp, dp, dp, dp, dp]
             L.oracle_saa.restype = C.c_int
+            L.oracle_partials.argtypes = [pp, C.c_int, C.c_uint32, C.c_int64, C.c_int64, C.c_int, dp, C.c_int, dp]
+            L.oracle_partials.restype = C.c_int
+            L.oracle_finalize_partials.argtypes = [C.c_int64, C.c_int, C.c_int, dp, dp, C.c_double, dp, dp, dp, dp,
+                                                   dp]
+            L.oracle_finalize_partials.restype = C.c_int
             L.oracle_fw_step.argtypes = [C.c_int, dp, dp, C.c_int64, dp, dp]
             L.oracle_fw_step.restype = C.c_int
             L.oracle_fw.argtypes = [pp, C.c_int, dp, C.c_int, C.c_int, C.c_int64, dp, dp, dp, dp]
@@ -275,6 +280,35 @@ def saa(prob, prec, W, grad=False, epoch=None):
     g = np.empty((K, P.d)) if grad else None
     ep = P.epoch if epoch is None else epoch
     _check(lib().oracle_saa(C.byref(P), prec, ep, K, _p(W), _p(f), _p(pb), _p(var), _p(g)), "saa")
+    out = {"f": f, "pbar": pb, "var": var}
+    if grad:
+        out["grad"] = g
+    return out
+
+
+def partials(prob, prec, i0, n, W, grad=False, epoch=None):
+    """Partial sums over scenarios [i0, i0 + n) with D_i = R_i - mu and
+    p_ik = w_k'D_i: [P1 = sum p (K) | P2 = sum p^2 (K) | P3 = sum D (d) |
+    P4 = sum D p (K*d, with grad)], float64."""
+    P, keep = prob
+    W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
+    K, d = W.shape[0], P.d
+    out = np.empty(2 * K + d + (K * d if grad else 0))
+    ep = P.epoch if epoch is None else epoch
+    _check(lib().oracle_partials(C.byref(P), prec, ep, i0, n, K, _p(W), int(grad), _p(out)), "partials")
+    return out
+
+
+def finalize_partials(N, W, mu, lam, part, grad=False):
+    """Eq. 4, Eq. 5 (and the gradient) from the whole sample's partial sums."""
+    W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    part = np.ascontiguousarray(part, dtype=np.float64)
+    K, d = W.shape
+    f, pb, var = np.empty(K), np.empty(K), np.empty(K)
+    g = np.empty((K, d)) if grad else None
+    _check(lib().oracle_finalize_partials(N, d, K, _p(W), _p(mu), lam, _p(part), _p(f), _p(pb), _p(var), _p(g)),
+           "finalize_partials")
     out = {"f": f, "pbar": pb, "var": var}
     if grad:
         out["grad"] = g

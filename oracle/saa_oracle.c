@@ -17,7 +17,9 @@
  *      file's own LOG / SIN2PI / COS2PI / EXP, and the law transforms.
  *   3. The SAA estimator of Eq. 4 with the sample mean of Eq. 5, written out
  *      directly: R_bar first, then the sum of squared projections of the
- *      centred samples, and the gradient of Eq. 4 in w.
+ *      centred samples, and the gradient of Eq. 4 in w.  Also the same sums
+ *      split by scenario range (partial sums that add across ranges) and the
+ *      estimate finalized from their totals.
  *   4. Frank-Wolfe, Algorithm 1 (resample every M iterations, LMO over
  *      W = {w >= 0, 1'w <= 1}, step 2/(kM+m+2)).
  *   5. The relative squared error of Table 2's notes.
@@ -845,6 +847,124 @@ int oracle_saa(const oracle_problem* p, int prec, uint32_t epoch, int K, const d
     int rc = saa_core(&S, K, W, p->lambda, f, pbar, var, grad);
     free(Ct);
     return rc;
+}
+
+/* Partial sums of Eq. 4 / Eq. 5 over the scenario range [i0, i0 + n): the
+ * sums over i of Sec. 3.1 split by scenario, so that disjoint ranges (one
+ * per device) add up to the whole sample.  With D_i = R_i - mu (the samples
+ * centred at the law's mean) and p_ik = w_k'D_i, part holds, in order,
+ *   P1 [K]    sum_i p_ik
+ *   P2 [K]    sum_i p_ik^2
+ *   P3 [d]    sum_i D_i
+ *   P4 [K*d]  sum_i D_i p_ik   (row k, only when want_grad)
+ * R_i is formed exactly as oracle_saa forms it; each sum is Neumaier-
+ * compensated over a fixed partition of the range. */
+int oracle_partials(const oracle_problem* p, int prec, uint32_t epoch, int64_t i0, int64_t n, int K, const double* W,
+                    int want_grad, double* part)
+{
+    if (check_problem(p) != OR_OK || (prec != 32 && prec != 64) || K < 1 || !W || !part) return OR_EINVAL;
+    if (i0 < 0 || n < 1 || i0 + n > p->N) return OR_EINVAL;
+    const int d = p->d;
+    double* Ct = NULL;
+    if (p->chol) {
+        Ct = transpose_chol(p);
+        if (!Ct) return OR_ENOMEM;
+    }
+    sample_src S;
+    memset(&S, 0, sizeof(S));
+    S.p = p;
+    S.prec = prec;
+    S.epoch = epoch;
+    S.Ct = Ct;
+    S.N = p->N;
+    S.d = d;
+    const int nch = (int)(n < MAX_CHUNKS ? n : MAX_CHUNKS);
+    const int64_t width = 2 * (int64_t)K + d + (want_grad ? (int64_t)K * d : 0);
+    nsum* acc = (nsum*)calloc((size_t)nch * (size_t)width, sizeof(nsum));
+    if (!acc) {
+        free(Ct);
+        return OR_ENOMEM;
+    }
+    int err = OR_OK;
+#pragma omp parallel
+    {
+        sample_buf B = {(float*)malloc(sizeof(float) * (size_t)d), (double*)malloc(sizeof(double) * (size_t)d)};
+        double* D = (double*)malloc(sizeof(double) * (size_t)d);
+        if (!B.zf || !B.zd || !D) {
+#pragma omp atomic write
+            err = OR_ENOMEM;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int c = 0; c < nch; ++c) {
+                const int64_t a = i0 + n * c / nch, e = i0 + n * (c + 1) / nch;
+                nsum* ac = acc + (int64_t)c * width;
+                for (int64_t i = a; i < e; ++i) {
+                    get_sample(&S, &B, i, D);
+                    for (int j = 0; j < d; ++j) D[j] = D[j] - p->mu[j]; /* R_i - mu */
+                    for (int j = 0; j < d; ++j) nadd(&ac[2 * K + j], D[j]);
+                    for (int k = 0; k < K; ++k) {
+                        const double* wk = W + (int64_t)k * d;
+                        double pk = 0.0;
+                        for (int j = 0; j < d; ++j) pk = pk + wk[j] * D[j];
+                        nadd(&ac[k], pk);
+                        nadd(&ac[K + k], pk * pk);
+                        if (want_grad) {
+                            nsum* g = ac + 2 * K + d + (int64_t)k * d;
+                            for (int j = 0; j < d; ++j) nadd(&g[j], D[j] * pk);
+                        }
+                    }
+                }
+            }
+        }
+        free(B.zf); free(B.zd); free(D);
+    }
+    if (err == OR_OK) {
+        for (int64_t e = 0; e < width; ++e) {
+            nsum t = {0.0, 0.0};
+            for (int c = 0; c < nch; ++c) {
+                nadd(&t, acc[(int64_t)c * width + e].s);
+                nadd(&t, acc[(int64_t)c * width + e].c);
+            }
+            part[e] = nval(&t);
+        }
+    }
+    free(acc);
+    free(Ct);
+    return err;
+}
+
+/* Eq. 4, Eq. 5 and the gradient of Eq. 4 from the partial sums of the whole
+ * sample (the element-wise total of oracle_partials over ranges covering
+ * [0, N)): with R_bar = mu + P3/N,
+ *   pbar_k = w_k'mu + P1_k/N
+ *   V_k    = (P2_k - P1_k^2/N) / (N-1)
+ *   f_k    = lambda V_k - pbar_k
+ *   grad_k = lambda (2/(N-1)) (P4_k - P1_k P3/N) - R_bar
+ * because sum_i (R_i - R_bar)(R_i - R_bar)'w_k = P4_k - P3 P1_k/N. */
+int oracle_finalize_partials(int64_t N, int d, int K, const double* W, const double* mu, double lambda,
+                             const double* part, double* f, double* pbar, double* var, double* grad)
+{
+    if (N < 2 || d < 1 || K < 1 || !W || !mu || !part) return OR_EINVAL;
+    const double* P1 = part;
+    const double* P2 = part + K;
+    const double* P3 = part + 2 * K;
+    const double* P4 = part + 2 * K + d;
+    const double Nd = (double)N;
+    for (int k = 0; k < K; ++k) {
+        const double* wk = W + (int64_t)k * d;
+        double c = 0.0;
+        for (int j = 0; j < d; ++j) c = c + wk[j] * mu[j];
+        const double pb = c + P1[k] / Nd;
+        const double V = (P2[k] - P1[k] * P1[k] / Nd) / (Nd - 1.0);
+        if (f) f[k] = lambda * V - pb;
+        if (pbar) pbar[k] = pb;
+        if (var) var[k] = V;
+        if (grad)
+            for (int j = 0; j < d; ++j)
+                grad[(int64_t)k * d + j] = lambda * (2.0 / (Nd - 1.0)) * (P4[(int64_t)k * d + j] - P1[k] * P3[j] / Nd) -
+                                           (mu[j] + P3[j] / Nd);
+    }
+    return OR_OK;
 }
 
 /* ------------------------------------------------------------------------- */
