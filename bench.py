@@ -44,12 +44,29 @@ METRIC = "scenario-decision evals/s"
 
 
 def _peaks():
+    """Measured peaks (or the recipe's fallback), plus the SM count of the
+    device the bench runs on (the ALU peak's unit count)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as fh:
-            return json.load(fh), "measured"
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
-        "fallback"
+            peaks, src = json.load(fh), "measured"
+    else:
+        peaks, src = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                      "sm_max_mhz": 2070.0}, "fallback"
+    import torch
+    if torch.cuda.is_available():
+        peaks["sm_count"] = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return peaks, src
+
+
+def _alu_peak(peaks):
+    """Lane-operations per second (in T/s): SMs x 128 FP32 lanes x the
+    maximum SM clock, the SM count read from the device."""
+    return int(peaks["sm_count"]) * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
+def _alu_peak_source(peaks):
+    return f"derived: {int(peaks['sm_count'])} SMs (device) x 128 lanes x {float(peaks.get('sm_max_mhz', 2070.0))} MHz"
 
 
 class ClockSampler:
@@ -153,8 +170,14 @@ GEN_INST_LOGN = 61.70 - 46.45
 # radius 1, sin/cos 12.5, products 1 -> 38 per Gaussian normal, +18 lognormal.
 GEN_OPS_GAUSS = 38.0
 GEN_OPS_LOGN = 18.0
-SPLIT_OPS = 4.0       # hi/lo operand split and the m~ sum (tensor paths)
-EPI_OPS_TC = 3.0      # per scenario-decision pair: D1 + D2, square, reduce
+# The method's own work per scenario-decision pair beyond the contraction:
+# the S1 and S2 sums (Eq. 5 and the variance of Eq. 4).
+PAIR_OPS = 2.0
+# What the tensor-core kernels issue on top of the method's work (reported
+# as issued_frac, not in frac): the hi/lo operand split and the m~ sum per
+# normal, and per pair D1 + D2, square, reduce.
+SPLIT_OPS = 4.0
+EPI_OPS_TC = 3.0
 EPI_OPS_SIMT = 2.0    # per pair: S1 and S2 updates (the contraction adds d FMAs)
 
 
@@ -167,32 +190,41 @@ def roofline(prec, d, N, K, law, kern_s, peaks, peak_src):
     """Roofline of the dominant (sample) kernel.  Every path here is bound by
     ALU issue (the in-kernel generator), except FP64 which is bound by the
     FP64 pipe; the tensor-core paths also report their tensor-pipe use.
-    Per-normal work: the generator-only kernel's measured instruction count
-    (frac); the specification count is reported beside it (frac_spec_count)."""
+    frac counts the method's work only: the generator-only kernel's measured
+    instructions per normal, plus S1 and S2 per scenario-decision pair (the
+    contraction itself runs on the tensor pipe; on CUDA cores its d FMAs per
+    pair are counted too).  issued_frac adds what the tensor-core kernel
+    issues on top (hi/lo split, m~ and the D1 + D2 epilogue);
+    frac_spec_count uses the generator's specification count per normal."""
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = int(peaks["sm_count"])
     normals = float(N) * d
     gen = _gen_per_normal(law)
     gen_spec = _gen_per_normal(law, measured=False)
     if prec == "fp64":
         flops = 2.0 * N * d * K
-        peak = 152 * 2 * 2 * mhz * 1e6 / 1e12
+        peak = sms * 2 * 2 * mhz * 1e6 / 1e12
         return {"bound": "alu", "achieved": flops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "frac": flops / kern_s / 1e12 / peak, "traffic": None, "kernel_ms": kern_s * 1e3,
-                "peak_source": f"derived: 152 SMs x 2 FP64 FMA/clk x 2 x {mhz} MHz (1.25 TFLOP/s class)",
+                "peak_source": f"derived: {sms} SMs (device) x 2 FP64 FMA/clk x 2 x {mhz} MHz",
                 "note": "FP64 contraction flops 2NdK; the FP64 generator work is extra"}
+    tc = prec in ("bf16x3", "f16x3")
+
     def count(g):
-        if prec in ("bf16x3", "f16x3"):
-            return normals * (g + SPLIT_OPS) + float(N) * K * EPI_OPS_TC
-        return normals * (g + 1.0) + float(N) * K * (d + EPI_OPS_SIMT)
+        if tc:
+            return normals * g + float(N) * K * PAIR_OPS
+        return normals * g + float(N) * K * (d + PAIR_OPS)
     ops, ops_spec = count(gen), count(gen_spec)
-    peak = 152 * 128 * mhz * 1e6 / 1e12
+    peak = _alu_peak(peaks)
     r = {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
          "frac": ops / kern_s / 1e12 / peak, "traffic": None, "kernel_ms": kern_s * 1e3,
          "frac_spec_count": ops_spec / kern_s / 1e12 / peak,
-         "peak_source": f"derived: 152 SMs x 128 lanes x {mhz} MHz (lane-ops/s)",
-         "note": "lane-operations: generator-only kernel's instructions per normal (ncu) + split per normal "
-                 "+ contraction/epilogue per pair"}
-    if prec in ("bf16x3", "f16x3"):
+         "peak_source": _alu_peak_source(peaks),
+         "note": "lane-operations of the method: generator-only kernel's instructions per normal (ncu) + "
+                 "S1, S2 per pair" + ("" if tc else " + the d FMAs of the CUDA-core contraction")}
+    if tc:
+        issued = normals * (gen + SPLIT_OPS) + float(N) * K * EPI_OPS_TC
+        r["issued_frac"] = issued / kern_s / 1e12 / peak
         # ncu dram__bytes_read.sum + dram__bytes_write.sum of the tensor kernel
         # (F16, d = 128, K = 256, full size, one-pass capture): the per-launch
         # operand image, independent of N
@@ -206,28 +238,37 @@ def roofline(prec, d, N, K, law, kern_s, peaks, peak_src):
 
 GRAD_WORKLOAD = dict(name="grad_d1024_N1M_K64_gauss", d=1024, N=1 << 20, K=64, law=0)
 EPI_OPS_TC_GRAD = 8.0   # per pair: chunk fold, D1 + D2, square + reduce, W hi/lo split
+# DRAM bytes per launch of the value-and-gradient kernel, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on a small case, scaled to
+# the launch's N where the traffic grows with the number of tiles.
+GRAD_TRAFFIC = {("f16x3", 1024, 64): lambda n: 447954944.0 * n / (1 << 17)}
 
 
 def grad_roofline(prec, d, N, K, law, kern_s, peaks):
-    """ALU roofline of the value-and-gradient kernel.  Algorithmic work draws
-    each normal once; the tensor-core kernel draws it twice (forward and
-    adjoint passes), so its fraction is at most about one half."""
-    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    """ALU roofline of the value-and-gradient kernel: the method draws each
+    normal once and forms S1, S2 per pair (the forward and adjoint
+    contractions run on the tensor pipe; on CUDA cores their 2d FMAs per pair
+    are counted too)."""
+    tc = prec in ("bf16x3", "f16x3")
 
     def count(g):
-        if prec in ("bf16x3", "f16x3"):
-            return float(N) * d * (g + SPLIT_OPS) + float(N) * K * EPI_OPS_TC_GRAD
-        return float(N) * d * (g + 1.0) + float(N) * K * (2 * d + EPI_OPS_SIMT)
+        if tc:
+            return float(N) * d * g + float(N) * K * PAIR_OPS
+        return float(N) * d * g + float(N) * K * (2 * d + PAIR_OPS)
     ops, ops_spec = count(_gen_per_normal(law)), count(_gen_per_normal(law, measured=False))
-    peak = 152 * 128 * mhz * 1e6 / 1e12
-    # ncu DRAM bytes of the F16 kernel at d = 1024, K = 64, N = 2^17 (the
-    # per-tile flush of the gradient partials), scaled by N: it grows with
-    # the number of tiles per CTA
-    traffic = 447954944.0 * N / (1 << 17) if (prec == "f16x3" and d == 1024 and K == 64) else None
-    return {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-            "frac": ops / kern_s / 1e12 / peak, "traffic": traffic, "kernel_ms": kern_s * 1e3,
-            "frac_spec_count": ops_spec / kern_s / 1e12 / peak,
-            "note": "lane-operations, one draw per normal (the kernel draws twice)"}
+    peak = _alu_peak(peaks)
+    r = {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+         "frac": ops / kern_s / 1e12 / peak, "traffic": GRAD_TRAFFIC.get((prec, d, K), lambda n: None)(N),
+         "kernel_ms": kern_s * 1e3, "frac_spec_count": ops_spec / kern_s / 1e12 / peak,
+         "peak_source": _alu_peak_source(peaks),
+         "note": "lane-operations of the method: one draw per normal + S1, S2 per pair"}
+    if tc:
+        issued = float(N) * d * (_gen_per_normal(law) + SPLIT_OPS) + float(N) * K * EPI_OPS_TC_GRAD
+        r["issued_frac"] = issued / kern_s / 1e12 / peak
+        tflops = 2 * 3 * 2.0 * N * d * K / kern_s / 1e12
+        r["tensor"] = {"achieved": tflops, "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
+                       "frac": tflops / float(peaks["bf16_tflops"])}
+    return r
 
 
 def run_grad(args, dev, world, rank, flush, stream):
@@ -315,7 +356,7 @@ def run_fw(args, dev, world, rank):
     # (Gaussian) normal, the t law's chi-square draws and one multiply-add
     # each for the forward dot product and the adjoint per normal
     peaks, _ = _peaks()
-    peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    peak = _alu_peak(peaks)
     ops = float(N) * d * (GEN_INST_GAUSS + 2.0)
     achieved = ops / (ms / 1e3) / 1e12
     return {"metric": "Frank-Wolfe iterations/s (Algorithm 1)", "value": world * 1e3 / ms, "unit": "iterations/s",
@@ -363,7 +404,7 @@ def run_ragged(args, dev, world, rank, flush, stream):
     # plus the fused kernel's K_b multiply-adds per normal (dot products
     # formed while drawing), over the whole replay
     peaks, _ = _peaks()
-    peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    peak = _alu_peak(peaks)
     ops = normals * GEN_INST_GAUSS + float(np.sum(rb.N.astype(np.float64) * rb.d * rb.K))
     achieved = ops * steps / total_s / 1e12
     return {"metric": "scenario-decision evals/s (ragged batch)", "value": world * evals * steps / total_s,
@@ -441,7 +482,7 @@ def run_large_d(args, dev, world, rank, flush, stream):
     fwd_s = res_k["value"][1]
     normals = float(N) * d
     peaks, _ = _peaks()
-    peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    peak = _alu_peak(peaks)
     # lane-ops: one draw per normal and a multiply-add in each pass (the
     # adjoint also its m~ sum); the adjoint reads the stored normals back
     ops_fwd = normals * (GEN_INST_GAUSS + 1.0)
@@ -569,7 +610,7 @@ def run_logistic(args, dev, world, rank, flush, stream):
     ops = 4.0 * pairs
     peaks, _ = _peaks()
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = 152 * 128 * mhz * 1e6 / 1e12
+    peak = _alu_peak(peaks)
     # SQN-sized calls: mini-batch gradient (b = 50) and Hessian product (b_H = 600)
     mini = {}
     for name, b, want_v in (("grad_b50", LG_WORKLOAD["b"], False), ("hvp_b600", LG_WORKLOAD["bH"], True)):
@@ -633,7 +674,7 @@ def run_newsvendor(args, dev, world, rank, flush, stream):
     samples = float(n) * S
     peaks, _ = _peaks()
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = 152 * 128 * mhz * 1e6 / 1e12
+    peak = _alu_peak(peaks)
     ops = samples * (GEN_INST_GAUSS + 2.0 * K)   # generator per normal + compare and count per decision
     # Sec. 4.1's inventory sizes, 10^2 .. 10^6 products (same S): one gradient each
     sweep = {}
@@ -700,13 +741,15 @@ def run_covariance(args, dev, world, rank, flush, stream):
         kern_s = main_ms / 1e3 / max(1, main_n)
         peaks, _ = _peaks()
         mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = 152 * 128 * mhz * 1e6 / 1e12
-        ops = float(N) * d * (_gen_per_normal(law) + SPLIT_OPS)
+        peak = _alu_peak(peaks)
+        ops = float(N) * d * _gen_per_normal(law)
+        issued = float(N) * d * (_gen_per_normal(law) + SPLIT_OPS)
         res[mode] = {"value": world * N * K * steps / total_s, "unit": "evals/s", "ms_per_step": 1e3 * total_s / steps,
                      "gram_kernel_ms": kern_s * 1e3, "gpu_launches_per_step": launched / steps,
                      "roofline": {"bound": "alu", "achieved": ops / kern_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": ops / kern_s / 1e12 / peak,
-                                  "note": "Gram kernel: generator-only kernel's instructions per normal + split"}}
+                                  "frac": ops / kern_s / 1e12 / peak, "issued_frac": issued / kern_s / 1e12 / peak,
+                                  "note": "Gram kernel: generator-only kernel's instructions per normal "
+                                          "(issued_frac adds the hi/lo split)"}}
     return {"metric": "scenario-decision evals/s (covariance-first)", "config": {
         "workload": WORKLOAD["name"], "d": d, "N": N, "K": K, "prec": prec,
         "method": "M = sum a a' once on tcgen05, then S2 = y'My, G = My per decision in FP64"}, **res}
@@ -898,41 +941,38 @@ def run_ours(args):
     ms_per_step = 1e3 * total_s / args.steps
     value = world * N * K * args.steps / total_s
 
-    # e2e through the public API with host buffers: H2D of the step's inputs
-    # (mu, C, X from pinned memory) and D2H of f inside the timed region.
+    # e2e through the C ABI with host buffers: saa_eval_host takes mu, C and
+    # X in pinned host memory, copies them in, evaluates (f, pbar and var, as
+    # the timed leg does), copies the outputs back and waits for the stream;
+    # each step is timed by the host wall clock around that one call.
     mu_h = torch.tensor(inst.mu).pin_memory()
     ch_h = torch.tensor(inst.chol).pin_memory()
     X_h = torch.tensor(Xn).pin_memory()
-    f_h = torch.empty(K, dtype=torch.float64).pin_memory()
-    mu_d, ch_d, X_d = torch.empty_like(mu), torch.empty_like(ch), torch.empty_like(X)
-    prob_e = saa.Problem(mu=mu_d, chol=ch_d, N=N, law=law, seed=0, instance=rank)
+    out_h = {k: torch.empty(K, dtype=torch.float64).pin_memory() for k in ("f", "pbar", "var")}
+    prob_h = saa.Problem(mu=mu_h, chol=ch_h, N=N, law=law, seed=0, instance=rank)
+    ws_h = torch.empty(saa.saa_eval_host_workspace_size(prob_h, K, prec, dev.index), dtype=torch.uint8, device=dev)
 
     def e2e_step():
-        mu_d.copy_(mu_h, non_blocking=True)
-        ch_d.copy_(ch_h, non_blocking=True)
-        X_d.copy_(X_h, non_blocking=True)
-        r = saa.saa_eval(prob_e, X_d, prec, pbar=False, var=False, ws=ws)
-        f_h.copy_(r["f"], non_blocking=True)
+        saa.saa_eval_host(prob_h, X_h, prec, out=out_h, ws=ws_h, device=dev.index)
 
     for _ in range(args.warmup):
         e2e_step()
     torch.cuda.synchronize(dev)
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+    e2e_s = 0.0
     for i in range(args.steps):
         flush.zero_()
-        e2e_ev[i][0].record(stream)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
         e2e_step()
-        e2e_ev[i][1].record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
+        e2e_s += time.perf_counter() - t0
     if world > 1:
         t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_value = world * N * K * args.steps / e2e_s
     h2d = (mu_h.numel() + ch_h.numel() + X_h.numel()) * 8
-    d2h = K * 8
+    d2h = 3 * K * 8
+    e2e_f_match = bool(torch.equal(out_h["f"], out["f"].cpu()))
 
     peaks, peak_src = _peaks()
     kern_s = main_ms / 1e3 / max(1, main_n)
@@ -964,7 +1004,9 @@ def run_ours(args):
                    "law": "half Gaussian / half standardised lognormal", "prec": prec,
                    "l2": "flushed (256 MB write) between timed steps", "instances": world},
         "gpu_launches": int(launched),
-        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "timing": "host wall clock around each saa_eval_host call (copies in, f/pbar/var, copies out, "
+                          "stream wait); L2 flushed between calls", "f_equals_device_leg": e2e_f_match},
         "roofline": roof,
     }
     if fp64:

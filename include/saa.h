@@ -134,6 +134,24 @@ size_t saa_workspace_size(const saa_ctx* ctx, const saa_problem* prob, int32_t K
 saa_status saa_eval(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec,
                     double* f, double* pbar, double* var, void* ws, size_t ws_bytes, void* stream);
 
+/* saa_eval for a caller whose data live in HOST memory (the end-to-end
+ * call of a program that keeps mu, C and the decisions on the host).
+ *   prob->mu, prob->chol (or prob->sd), X   HOST arrays, laid out as for
+ *                                          saa_eval
+ *   f, pbar, var                           HOST [K] (pbar, var optional)
+ *   ws   DEVICE scratch of saa_eval_host_workspace_size() bytes, 256-byte
+ *        aligned: saa_eval's workspace followed by room for the copies
+ * The call copies the inputs into `ws` on `stream`, runs saa_eval there,
+ * copies the outputs back, then waits for `stream` and reads the device
+ * error word as saa_ctx_sync does: when it returns, the outputs are on the
+ * host and device-side flags (SAA_EDEVICE, SAA_ETIMEOUT) are reported.
+ * Page-locked host arrays (cudaHostAlloc) are copied by DMA directly;
+ * pageable ones go through the driver's staging.  Errors as saa_eval; the
+ * size query returns 0 for invalid arguments. */
+size_t saa_eval_host_workspace_size(const saa_ctx* ctx, const saa_problem* prob, int32_t K, saa_prec prec);
+saa_status saa_eval_host(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec,
+                         double* f, double* pbar, double* var, void* ws, size_t ws_bytes, void* stream);
+
 /* Eq. 4 and its gradient in w (the paper uses it in Algorithm 1 without
  * writing it out; differentiating Eq. 4 gives
  *   grad f_hat(w) = lambda (2/(N-1)) sum_i (R_i - R_bar)(R_i - R_bar)'w - R_bar).
@@ -233,6 +251,52 @@ saa_status saa_batch_create(saa_ctx* ctx, int32_t B, const saa_problem* probs, c
                             saa_batch** out);
 saa_status saa_batch_launch(saa_batch* batch, void* stream);
 void saa_batch_destroy(saa_batch* batch);
+
+/* Scenario-range partial sums: the sums over i in Eq. 4 and Eq. 5
+ * (Sec. 3.1) split by scenario, so that one problem's N samples can be
+ * shared across devices or calls.  Ranges that cover [0, N) without overlap
+ * add up, element by element, to the whole sample's sums, from which
+ * saa_finalize_partials gives what saa_eval / saa_grad give (up to the
+ * rounding of a different summation order).  With D_i = R_i - mu (the
+ * samples centred at the law's mean) and p_ik = w_k'D_i:
+ *   part  device [2K + d + (want_grad ? K*d : 0)] FP64, written in order
+ *         P1 [K]    sum_i p_ik
+ *         P2 [K]    sum_i p_ik^2
+ *         P3 [d]    sum_i D_i
+ *         P4 [K*d]  sum_i D_i p_ik (row k), with want_grad
+ * over i = i0 .. i0+n-1 of resample index prob->epoch (prob->N is the whole
+ * sample's size: the mixed law's split at N/2 does not move).  prec as
+ * saa_eval / saa_grad (F16X3 / BF16X3 gradients need d <= 1024, K <= 64);
+ * chol must be given (the diagonal form returns SAA_EUNSUPPORTED).
+ *   ws   device scratch of saa_partials_workspace_size() bytes (0 for
+ *        invalid arguments), 256-byte aligned
+ * Errors as saa_eval, and SAA_EINVAL for a range outside [0, N).
+ * Deterministic for a given range, device and precision. */
+size_t saa_partials_workspace_size(const saa_ctx* ctx, const saa_problem* prob, int64_t n, int32_t K, saa_prec prec,
+                                   int want_grad);
+saa_status saa_partials(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, int32_t K, const double* X,
+                        saa_prec prec, int want_grad, double* part, void* ws, size_t ws_bytes, void* stream);
+
+/* Totals of R partial vectors of length len (device [R*len], row r = the
+ * partials of one range; total device [len]): element e is the
+ * Neumaier-compensated sum over r = 0 .. R-1 in that order, so the totals
+ * are the same bit for bit whichever device or collective produced the
+ * rows.  The merge step when the ranges' partials have been gathered. */
+saa_status saa_partials_merge(saa_ctx* ctx, int32_t R, int64_t len, const double* parts, double* total,
+                              void* stream);
+
+/* Eq. 4, Eq. 5 and the gradient of Eq. 4 from the totals of saa_partials
+ * over the whole sample (FP64, no workspace):
+ *   pbar_k = w_k'mu + P1_k/N,  V_k = (P2_k - P1_k^2/N) / (N-1),
+ *   f_k = lambda V_k - pbar_k,
+ *   grad_k = lambda (2/(N-1)) (P4_k - P1_k P3/N) - (mu + P3/N)
+ * (R_bar = mu + P3/N, and sum_i (R_i - R_bar)(R_i - R_bar)'w_k =
+ * P4_k - P3 P1_k/N).  X device [K*d]; part device, laid out as above (P4
+ * needed only for grad); f, pbar, var device [K], grad device [K*d], each
+ * optional (at least one).  prob->chol is not read. */
+saa_status saa_finalize_partials(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X,
+                                 const double* part, double* f, double* pbar, double* var, double* grad,
+                                 void* stream);
 
 /* The scenario generator on its own (debugging, streamed mode, parity):
  * scenarios i0 .. i0+n-1 of resample index prob->epoch.
@@ -410,24 +474,30 @@ saa_status saa_newsvendor_grad(saa_ctx* ctx, const saa_newsvendor* prob, int32_t
  * undefined. */
 saa_status saa_cholesky(saa_ctx* ctx, int32_t d, const double* Sigma, double* chol, void* stream);
 
-/* saa_eval without a context or a workspace: for callers that cannot
- * allocate device memory (a CUDA host callback or stream capture, where
- * cudaMalloc is not allowed; a real-time loop that cannot afford
- * cudaMalloc's implicit device synchronisation; a plug-in inside a host
- * framework that owns all device memory).  The paper has no counterpart:
- * this is a deployment convenience, not part of the method.
+/* saa_eval without a context or a workspace, for callers that cannot
+ * allocate device memory: a real-time loop that cannot afford cudaMalloc's
+ * implicit device synchronisation, a plug-in inside a host framework that
+ * owns all device memory through its own allocator, or code held to a
+ * device-memory budget by another component.  The paper has no
+ * counterpart: this is a deployment convenience, not part of the method.
  *
  * Same arguments and results as saa_eval, on the CURRENT device, for
- * SAA_FP32 and SAA_FP64.  Scratch comes from one array of
+ * SAA_FP32 and SAA_FP64 with a dense chol; the diagonal form (chol NULL)
+ * returns SAA_EUNSUPPORTED.  Scratch comes from one array of
  * SAA_STATIC_SCRATCH_BYTES in device memory defined by the library, which
  * every GPU that loads libsaa holds until the process exits; problems whose
  * scratch would not fit (large K times d, or very many CTAs) return
  * SAA_ENOMEM with the needed size in saa_last_error().  The call allocates
- * nothing.  Its first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
- * All calls share the array: calls whose GPU work overlaps (other streams,
- * other host threads) race on it.  Nothing in it needs clearing between
- * calls; every value is written before it is read. */
+ * nothing (no cudaMalloc, cudaFree or allocating library routine).  Its
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it for the process, so make that first
+ * call before any stream capture, and do not use this entry point across a
+ * cudaDeviceReset.  A diagonal entry of chol that is not positive and
+ * finite cannot be reported through a context here: the call writes NaN to
+ * f (and to pbar, var when given) instead.  All calls share the array:
+ * calls whose GPU work overlaps (other streams, other host threads) race on
+ * it.  The call clears the part that must start at zero (its error word);
+ * every other value is written before it is read. */
 #define SAA_STATIC_SCRATCH_BYTES (16u << 20)
 saa_status saa_eval_static(const saa_problem* prob, int32_t K, const double* X, saa_prec prec, double* f,
                            double* pbar, double* var, void* stream);

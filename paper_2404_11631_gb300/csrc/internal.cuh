@@ -30,6 +30,12 @@ struct LawArgs {
   uint32_t epoch;            // base resample index
   const int64_t* t_dev;      // optional: device iteration counter (Frank-Wolfe)
   int32_t M;                 // resample period when t_dev is set
+  // Scenario range [i_base, i_base + n) of the sums (saa_partials); n = 0
+  // means the whole set [0, N).  N itself stays the problem's (the mixed
+  // law's split at N/2 and the counter words do not depend on the range).
+  uint32_t i_base = 0;
+  uint32_t n = 0;
+  __host__ __device__ uint32_t rows_end() const { return n ? i_base + n : N; }
 };
 
 // Per-call workspace carve-up.  Partials are per CTA ("grid" of them) and are
@@ -125,6 +131,16 @@ cudaError_t launch_simt(const LawArgs& la, int K, int prec, int want_grad, const
 cudaError_t launch_finalize(const saa_problem* p, int K, int prec, int want_grad, const Plan& plan,
                             const Workspace& ws, double* f, double* pbar, double* var, double* grad,
                             cudaStream_t st);
+// saa_partials: the CTA partials of a scenario range, merged and mapped to
+// [P1 | P2 | P3 = C m~ | P4 = C G (want_grad)] in `part`.
+cudaError_t launch_partials_out(const saa_problem* p, int K, int prec, int want_grad, const Plan& plan,
+                                const Workspace& ws, double* part, cudaStream_t st);
+// saa_partials_merge: fixed-order compensated sum of R partial vectors.
+cudaError_t launch_merge_partials(int R, int64_t len, const double* parts, double* total, cudaStream_t st);
+// saa_finalize_partials: f, pbar, var, grad from the totals of the partials.
+cudaError_t launch_finalize_partials(int64_t N, int d, int K, double lambda, const double* X, const double* mu,
+                                     const double* part, double* f, double* pbar, double* var, double* grad,
+                                     cudaStream_t st);
 // grad_kj = sum_{l <= j} C_jl u_kl - mu_j (FP64, one warp per output).
 cudaError_t launch_grad_out(int K, int d, const double* chol, const double* mu, const double* u, double* grad,
                             cudaStream_t st);

@@ -2,21 +2,23 @@
 // that cannot allocate device memory.
 //
 // saa_eval needs a caller-provided workspace and a context, and creating a
-// context calls cudaMalloc.  Some callers cannot do either: code running in
-// a CUDA host callback or while a stream is being captured (where cudaMalloc
-// is not allowed), real-time loops that cannot afford cudaMalloc's implicit
-// device synchronisation, and plug-ins inside a host framework that owns
-// all device memory through its own allocator.  For them this entry point
-// takes its scratch from one fixed array in device memory that the library
-// defines at file scope.  Every GPU that loads the library holds that array
+// context calls cudaMalloc.  Some callers cannot do either: real-time loops
+// that cannot afford cudaMalloc's implicit device synchronisation, plug-ins
+// inside a host framework that owns all device memory through its own
+// allocator, and code running under a device-memory budget that another
+// component enforces.  For them this entry point takes its scratch from one
+// fixed array in device memory that the library defines at file scope.
+// Every GPU that loads the library holds that array
 // (SAA_STATIC_SCRATCH_BYTES) until the process exits.
 //
 // The scratch is shared by every call in the process: two calls whose work
 // overlaps on the GPU (different streams, or different host threads) race
-// on it and give wrong results.  Nothing in it needs to start at zero: the
-// sample kernel writes each per-CTA partial on its first tile and the
-// finalize kernels overwrite the totals, so the contents left by the last
-// call are never read.
+// on it and give wrong results.  Its first 256 bytes hold this path's
+// device error word, which each call clears (cudaMemsetAsync) before its
+// prologue checks C's diagonal; a call whose check fires writes NaN to its
+// outputs.  The rest needs no clearing: the sample kernel writes each
+// per-CTA partial on its first tile and the finalize kernels overwrite the
+// totals, so the contents left by the last call are never read.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -52,6 +54,20 @@ saa_status scratch_address(int dev, void** out) {
   return SAA_OK;
 }
 
+// A call whose prologue flagged C's diagonal (not positive, or not finite)
+// gives NaN outputs: this path has no context whose error word a later
+// saa_ctx_sync could read.
+__global__ void k_static_flag_out(const uint32_t* err, int K, double* f, double* pbar, double* var) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K || *err == 0u) return;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  f[k] = nan;
+  if (pbar) pbar[k] = nan;
+  if (var) var[k] = nan;
+}
+
+constexpr size_t kErrBytes = 256;   // the error word's slot at the start of the scratch
+
 }  // namespace
 }  // namespace saa
 
@@ -62,9 +78,13 @@ extern "C" saa_status saa_eval_static(const saa_problem* prob, int32_t K, const 
   saa::NvtxRange nvtx_range("saa_eval_static");
   if (!prob || prob->d < 1 || prob->N < 2 || prob->N > 0xffffffffll || prob->law < SAA_LAW_GAUSS ||
       prob->law > SAA_LAW_MIX || (prob->law == SAA_LAW_STUDENT_T && (prob->nu < 2 || (prob->nu & 1) || prob->nu > 64)) ||
-      prob->reserved != 0 || !prob->mu || !prob->chol) {
+      prob->reserved != 0 || !prob->mu || (!prob->chol && !prob->sd)) {
     set_error("saa_eval_static: invalid problem (see saa_eval for the rules)");
     return SAA_EINVAL;
+  }
+  if (!prob->chol) {
+    set_error("saa_eval_static: the diagonal form (chol NULL, sd given) needs saa_eval and a workspace");
+    return SAA_EUNSUPPORTED;
   }
   if (K < 1 || K > 65535 || !X || !f) {
     set_error("saa_eval_static: need 1 <= K <= 65535 and non-NULL X, f");
@@ -93,10 +113,12 @@ extern "C" saa_status saa_eval_static(const saa_problem* prob, int32_t K, const 
   s = make_plan(&c, prob, K, prec, 0, &plan);
   if (s != SAA_OK) return s;
   Workspace ws;
-  const size_t need = carve(prob, K, plan, 0, scratch, &ws);
-  if (need > (size_t)SAA_STATIC_SCRATCH_BYTES) {
+  uint32_t* err = (uint32_t*)scratch;
+  const size_t need = carve(prob, K, plan, 0, (char*)scratch + kErrBytes, &ws);
+  if (need > (size_t)SAA_STATIC_SCRATCH_BYTES - kErrBytes) {
     set_error("saa_eval_static: this d and K need " + std::to_string(need) + " bytes of scratch, more than the " +
-              std::to_string((size_t)SAA_STATIC_SCRATCH_BYTES) + " bytes of the static array; use saa_eval");
+              std::to_string((size_t)SAA_STATIC_SCRATCH_BYTES - kErrBytes) +
+              " bytes the static array has for them; use saa_eval");
     return SAA_ENOMEM;
   }
   LawArgs la;
@@ -110,10 +132,15 @@ extern "C" saa_status saa_eval_static(const saa_problem* prob, int32_t K, const 
   la.t_dev = nullptr;
   la.M = 1;
   cudaStream_t st = (cudaStream_t)stream;
-  s = cuda_status(launch_prologue(prob, K, X, prec, ws, nullptr, st), "saa_eval_static: prologue launch");
+  s = cuda_status(cudaMemsetAsync(err, 0, sizeof(uint32_t), st), "saa_eval_static: clear the error word");
+  if (s != SAA_OK) return s;
+  s = cuda_status(launch_prologue(prob, K, X, prec, ws, err, st), "saa_eval_static: prologue launch");
   if (s != SAA_OK) return s;
   s = cuda_status(launch_simt(la, K, prec, 0, plan, ws, st), "saa_eval_static: sample kernel launch");
   if (s != SAA_OK) return s;
-  return cuda_status(launch_finalize(prob, K, prec, 0, plan, ws, f, pbar, var, nullptr, st),
-                     "saa_eval_static: finalize launch");
+  s = cuda_status(launch_finalize(prob, K, prec, 0, plan, ws, f, pbar, var, nullptr, st),
+                  "saa_eval_static: finalize launch");
+  if (s != SAA_OK) return s;
+  k_static_flag_out<<<(K + 255) / 256, 256, 0, st>>>(err, K, f, pbar, var);
+  return cuda_status(cudaGetLastError(), "saa_eval_static: input-check launch");
 }

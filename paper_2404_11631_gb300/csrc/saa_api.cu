@@ -414,6 +414,70 @@ saa_status saa_eval(saa_ctx* ctx, const saa_problem* prob, int32_t K, const doub
   return eval_impl(ctx, prob, K, X, prec, 0, f, pbar, var, nullptr, ws, ws_bytes, stream);
 }
 
+// Host-buffer form: [saa_eval workspace][mu][chol or sd][X][f][pbar][var] in ws.
+static size_t host_io_tail(const saa_problem* p, int32_t K) {
+  const size_t d = (size_t)p->d, k = (size_t)K;
+  return align_up(d * 8) + align_up((p->chol ? d * d : d) * 8) + align_up(k * d * 8) + 3 * align_up(k * 8);
+}
+
+size_t saa_eval_host_workspace_size(const saa_ctx* ctx, const saa_problem* prob, int32_t K, saa_prec prec) {
+  const size_t base = saa_workspace_size(ctx, prob, K, prec, 0);
+  return base ? align_up(base) + host_io_tail(prob, K) : 0;
+}
+
+saa_status saa_eval_host(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec, double* f,
+                         double* pbar, double* var, void* ws, size_t ws_bytes, void* stream) {
+  saa::NvtxRange nvtx_range("saa_eval_host");
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  saa_status s = check_problem(prob);
+  if (s != SAA_OK) return s;
+  if (K < 1 || K > 65535) return fail(SAA_EINVAL, "K must be in [1, 65535]");
+  if (!X || !f) return fail(SAA_EINVAL, "X and f must be host pointers");
+  if (!ws || (((uintptr_t)ws) & 255u)) return fail(SAA_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  const size_t need = saa_eval_host_workspace_size(ctx, prob, K, prec);
+  if (need == 0) return fail(SAA_EINVAL, std::string("no workspace for these arguments: ") + g_last_error);
+  if (ws_bytes < need) return fail(SAA_ENOMEM, "workspace smaller than saa_eval_host_workspace_size()");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(SAA_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t d = (size_t)prob->d, k = (size_t)K;
+  const size_t base = align_up(saa_workspace_size(ctx, prob, K, prec, 0));
+  char* b = (char*)ws + base;
+  double* mu_d = (double*)b;
+  b += align_up(d * 8);
+  double* cov_d = (double*)b;
+  const size_t cov_n = prob->chol ? d * d : d;
+  b += align_up(cov_n * 8);
+  double* X_d = (double*)b;
+  b += align_up(k * d * 8);
+  double* f_d = (double*)b;
+  double* pbar_d = (double*)(b + align_up(k * 8));
+  double* var_d = (double*)(b + 2 * align_up(k * 8));
+  s = cuda_status(cudaMemcpyAsync(mu_d, prob->mu, d * 8, cudaMemcpyHostToDevice, st), "copy mu to the device");
+  if (s == SAA_OK)
+    s = cuda_status(cudaMemcpyAsync(cov_d, prob->chol ? prob->chol : prob->sd, cov_n * 8, cudaMemcpyHostToDevice, st),
+                    "copy chol (or sd) to the device");
+  if (s == SAA_OK)
+    s = cuda_status(cudaMemcpyAsync(X_d, X, k * d * 8, cudaMemcpyHostToDevice, st), "copy X to the device");
+  if (s != SAA_OK) return s;
+  saa_problem p = *prob;
+  p.mu = mu_d;
+  if (prob->chol)
+    p.chol = cov_d;
+  else
+    p.sd = cov_d;
+  s = eval_impl(ctx, &p, K, X_d, prec, 0, f_d, pbar ? pbar_d : nullptr, var ? var_d : nullptr, nullptr, ws, base,
+                stream);
+  if (s != SAA_OK) return s;
+  s = cuda_status(cudaMemcpyAsync(f, f_d, k * 8, cudaMemcpyDeviceToHost, st), "copy f to the host");
+  if (s == SAA_OK && pbar)
+    s = cuda_status(cudaMemcpyAsync(pbar, pbar_d, k * 8, cudaMemcpyDeviceToHost, st), "copy pbar to the host");
+  if (s == SAA_OK && var)
+    s = cuda_status(cudaMemcpyAsync(var, var_d, k * 8, cudaMemcpyDeviceToHost, st), "copy var to the host");
+  if (s != SAA_OK) return s;
+  return saa_ctx_sync(ctx, stream);
+}
+
 saa_status saa_grad(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec, double* f,
                     double* grad, void* ws, size_t ws_bytes, void* stream) {
   saa::NvtxRange nvtx_range("saa_grad");
@@ -493,6 +557,91 @@ saa_status saa_solve_adaptive(saa_ctx* ctx, const saa_problem* prob, const doubl
     k = e;
   }
   return s;
+}
+
+// The plan of a scenario range: the problem with N = n sizes the grid and
+// the workspace; the kernels still see the problem's own N (LawArgs).
+static saa_status partials_plan(const saa_ctx* ctx, const saa_problem* prob, int64_t n, int32_t K, saa_prec prec,
+                                int want_grad, Plan* plan) {
+  saa_problem pr = *prob;
+  pr.N = n < 2 ? 2 : n;
+  return make_plan(ctx, &pr, K, prec, want_grad ? 1 : 0, plan);
+}
+
+size_t saa_partials_workspace_size(const saa_ctx* ctx, const saa_problem* prob, int64_t n, int32_t K, saa_prec prec,
+                                   int want_grad) {
+  if (!ctx || check_problem(prob) != SAA_OK || !prob->chol || K < 1 || n < 1 || n > prob->N) return 0;
+  DeviceGuard g(ctx->device);
+  Plan plan;
+  if (partials_plan(ctx, prob, n, K, prec, want_grad, &plan) != SAA_OK) return 0;
+  saa_problem pr = *prob;
+  pr.N = n < 2 ? 2 : n;
+  return carve(&pr, K, plan, want_grad ? 1 : 0, nullptr, nullptr);
+}
+
+saa_status saa_partials(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, int32_t K, const double* X,
+                        saa_prec prec, int want_grad, double* part, void* ws, size_t ws_bytes, void* stream) {
+  saa::NvtxRange nvtx_range("saa_partials");
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  saa_status s = check_problem(prob);
+  if (s != SAA_OK) return s;
+  if (!prob->chol) return fail(SAA_EUNSUPPORTED, "saa_partials needs a dense chol (the diagonal form is not split)");
+  if (i0 < 0 || n < 1 || i0 + n > prob->N) return fail(SAA_EINVAL, "scenario range outside [0, N) or empty");
+  if (K < 1 || K > 65535) return fail(SAA_EINVAL, "K must be in [1, 65535]");
+  if (!X || !part) return fail(SAA_EINVAL, "X and part must be device pointers");
+  if (!ws || (((uintptr_t)ws) & 255u)) return fail(SAA_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  want_grad = want_grad ? 1 : 0;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(SAA_ECUDA, "cudaSetDevice failed");
+  Plan plan;
+  s = partials_plan(ctx, prob, n, K, prec, want_grad, &plan);
+  if (s != SAA_OK) return s;
+  saa_problem pr = *prob;
+  pr.N = n < 2 ? 2 : n;
+  Workspace w;
+  const size_t need = carve(&pr, K, plan, want_grad, ws, &w);
+  if (ws_bytes < need) return fail(SAA_ENOMEM, "workspace smaller than saa_partials_workspace_size()");
+  LawArgs la = law_args(prob);
+  la.i_base = (uint32_t)i0;
+  la.n = (uint32_t)n;
+  cudaStream_t st = (cudaStream_t)stream;
+  s = cuda_status(launch_prologue(prob, K, X, prec, w, ctx->err, st), "prologue launch");
+  if (s != SAA_OK) return s;
+  if (is_tc(prec) && want_grad)
+    s = cuda_status(launch_tc_grad(la, K, prec, plan, w, ctx->err, st), "tensor-core gradient kernel launch");
+  else if (is_tc(prec))
+    s = cuda_status(launch_tc(la, K, prec, plan, w, ctx->err, st), "tensor-core kernel launch");
+  else
+    s = cuda_status(launch_simt(la, K, prec, want_grad, plan, w, st), "sample kernel launch");
+  if (s != SAA_OK) return s;
+  return cuda_status(launch_partials_out(prob, K, prec, want_grad, plan, w, part, st), "partials launch");
+}
+
+saa_status saa_partials_merge(saa_ctx* ctx, int32_t R, int64_t len, const double* parts, double* total,
+                              void* stream) {
+  saa::NvtxRange nvtx_range("saa_partials_merge");
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  if (R < 1 || len < 1 || !parts || !total) return fail(SAA_EINVAL, "need R >= 1, len >= 1 and device arrays");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(SAA_ECUDA, "cudaSetDevice failed");
+  return cuda_status(launch_merge_partials(R, len, parts, total, (cudaStream_t)stream), "merge launch");
+}
+
+saa_status saa_finalize_partials(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X,
+                                 const double* part, double* f, double* pbar, double* var, double* grad,
+                                 void* stream) {
+  saa::NvtxRange nvtx_range("saa_finalize_partials");
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  saa_status s = check_problem(prob);
+  if (s != SAA_OK) return s;
+  if (K < 1 || K > 65535) return fail(SAA_EINVAL, "K must be in [1, 65535]");
+  if (!X || !part) return fail(SAA_EINVAL, "X and part must be device pointers");
+  if (!f && !pbar && !var && !grad) return fail(SAA_EINVAL, "no output requested");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(SAA_ECUDA, "cudaSetDevice failed");
+  return cuda_status(launch_finalize_partials(prob->N, prob->d, K, prob->lambda, X, prob->mu, part, f, pbar, var,
+                                              grad, (cudaStream_t)stream),
+                     "finalize-partials launch");
 }
 
 saa_status saa_generate(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64_t n, saa_prec prec, void* z_out,

@@ -141,8 +141,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_simt(LawArgs la, int K, int wan
 
   bool first = true;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const uint32_t i0 = (uint32_t)(tile * BM);
-    const int nrow = (int)min((int64_t)BM, (int64_t)la.N - (int64_t)i0);
+    const uint32_t i0 = la.i_base + (uint32_t)(tile * BM);
+    const int nrow = (int)min((int64_t)BM, (int64_t)la.rows_end() - (int64_t)i0);
     simt_tile<T, BM, TN>(st, d, la.law, la.nu, half, i0, nrow, K, Yt, sm, macc, first, want_grad, p_s1, p_s2, p_g,
                      p_gc);
     first = false;
@@ -223,8 +223,8 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? 2 : 1) k_narrow(LawArgs l
 
   bool first = true;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const uint32_t i0 = (uint32_t)(tile * BM);
-    const int nrow = (int)min((int64_t)BM, (int64_t)la.N - (int64_t)i0);
+    const uint32_t i0 = la.i_base + (uint32_t)(tile * BM);
+    const int nrow = (int)min((int64_t)BM, (int64_t)la.rows_end() - (int64_t)i0);
     __syncthreads();
     if (tid < BM) ss[tid] = (tid < nrow) ? gen::Gen<T>::scale(st, i0 + tid, la.law, la.nu) : T(0);
     __syncthreads();
@@ -531,11 +531,12 @@ __global__ void k_value_out(int K, double N, double lambda, const double* __rest
 // partials are summed as float-float pairs (branch-free TwoSum, the running
 // error and the Kahan compensations in a second float): about 2^-48 relative,
 // without the narrow FP64 pipe.  FP64 partials use Neumaier's sum.
+// With raw set it writes G_kj itself (the partial sums of saa_partials).
 template <typename T>
 __global__ void __launch_bounds__(256) k_grad_u(int grid, int K, int d, double N, double lambda,
                                                 const T* __restrict__ part_g, const T* __restrict__ part_gc,
                                                 const double* __restrict__ s1, const double* __restrict__ mt,
-                                                double* __restrict__ u) {
+                                                double* __restrict__ u, int raw) {
   __shared__ double sh_s[8][32], sh_c[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
@@ -574,12 +575,16 @@ __global__ void __launch_bounds__(256) k_grad_u(int grid, int K, int d, double N
       neumaier(S, C, sh_c[w][lane]);
     }
     const double G = S + C;
-    const double mj = mt[j] / N;
-    u[(size_t)k * d + j] = lambda * (2.0 / (N - 1.0)) * (G - s1[k] * mj) - mj;
+    if (raw) {
+      u[(size_t)k * d + j] = G;
+    } else {
+      const double mj = mt[j] / N;
+      u[(size_t)k * d + j] = lambda * (2.0 / (N - 1.0)) * (G - s1[k] * mj) - mj;
+    }
   }
 }
 
-// grad_kj = sum_{l <= j} C_jl u_kl - mu_j: one warp per (k, j).
+// grad_kj = sum_{l <= j} C_jl u_kl - mu_j (mu NULL: 0): one warp per (k, j).
 __global__ void k_grad_out(int K, int d, const double* __restrict__ C, const double* __restrict__ mu,
                            const double* __restrict__ u, double* __restrict__ grad) {
   const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
@@ -592,7 +597,7 @@ __global__ void k_grad_out(int K, int d, const double* __restrict__ C, const dou
   for (int l = lane; l <= j; l += 32) s = fma(cj[l], uk[l], s);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) grad[(size_t)k * d + j] = s - mu[j];
+  if (lane == 0) grad[(size_t)k * d + j] = mu ? s - mu[j] : s;
 }
 
 cudaError_t launch_grad_out(int K, int d, const double* chol, const double* mu, const double* u, double* grad,
@@ -621,13 +626,105 @@ cudaError_t launch_finalize(const saa_problem* p, int K, int prec, int want_grad
     dim3 gu((d + 31) / 32, K);
     if (prec == SAA_FP64)
       k_grad_u<double><<<gu, 256, 0, st>>>(plan.grid, K, d, N, p->lambda, (const double*)ws.part_g,
-                                           (const double*)ws.part_gc, ws.tot_s1, ws.tot_m, ws.grad_tmp);
+                                           (const double*)ws.part_gc, ws.tot_s1, ws.tot_m, ws.grad_tmp, 0);
     else
       k_grad_u<float><<<gu, 256, 0, st>>>(plan.grid, K, d, N, p->lambda, (const float*)ws.part_g,
-                                          (const float*)ws.part_gc, ws.tot_s1, ws.tot_m, ws.grad_tmp);
+                                          (const float*)ws.part_gc, ws.tot_s1, ws.tot_m, ws.grad_tmp, 0);
     const int64_t warps = (int64_t)K * d;
     k_grad_out<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(K, d, p->chol, p->mu, ws.grad_tmp, grad);
   }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// saa_partials: the CTA partials of a scenario range merged (the same fixed
+// order as the finalize) and mapped from the whitened coordinates of the
+// kernels to the paper's, D_i = R_i - mu = C a_i:
+//   P1_k = S1_k, P2_k = S2_k, P3 = C m~, P4_k = C G_k.
+// ------------------------------------------------------------------------
+cudaError_t launch_partials_out(const saa_problem* p, int K, int prec, int want_grad, const Plan& plan,
+                                const Workspace& ws, double* part, cudaStream_t st) {
+  const int d = p->d;
+  const int items = 2 * K + d;
+  const int first = is_tc(prec) ? K : 0;
+  double* P1 = part;
+  double* P2 = part + K;
+  double* P3 = part + 2 * K;
+  double* P4 = part + 2 * K + d;
+  k_reduce_parts<<<((items - first) * 32 + 255) / 256, 256, 0, st>>>(ws.part_s1, ws.part_s2, ws.part_m, plan.grid,
+                                                                      K, d, first, P1, P2, ws.tot_m);
+  if (is_tc(prec))   // S1 = m~'y_k (the tensor kernels keep no row sums of Q)
+    k_value_out_m<<<(K * 32 + 255) / 256, 256, 0, st>>>(K, d, 2.0, p->lambda, ws.tot_m, ws.Y64, ws.c, P2, P1,
+                                                         nullptr, nullptr, nullptr);
+  k_grad_out<<<(unsigned)((d * 32 + 255) / 256), 256, 0, st>>>(1, d, p->chol, nullptr, ws.tot_m, P3);
+  if (want_grad) {
+    dim3 gu((d + 31) / 32, K);
+    if (prec == SAA_FP64)
+      k_grad_u<double><<<gu, 256, 0, st>>>(plan.grid, K, d, 2.0, p->lambda, (const double*)ws.part_g,
+                                           (const double*)ws.part_gc, nullptr, nullptr, ws.grad_tmp, 1);
+    else
+      k_grad_u<float><<<gu, 256, 0, st>>>(plan.grid, K, d, 2.0, p->lambda, (const float*)ws.part_g,
+                                          (const float*)ws.part_gc, nullptr, nullptr, ws.grad_tmp, 1);
+    const int64_t warps = (int64_t)K * d;
+    k_grad_out<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(K, d, p->chol, nullptr, ws.grad_tmp, P4);
+  }
+  return cudaGetLastError();
+}
+
+// saa_partials_merge: element e of the totals is the Neumaier-compensated
+// sum of parts[r][e] over r = 0 .. R-1 in that order, one thread per
+// element, so the totals do not depend on who computed which range when.
+__global__ void k_merge_partials(int R, int64_t len, const double* __restrict__ parts, double* __restrict__ total) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= len) return;
+  double s = 0.0, c = 0.0;
+  for (int r = 0; r < R; ++r) neumaier(s, c, parts[(size_t)r * len + e]);
+  total[e] = s + c;
+}
+
+cudaError_t launch_merge_partials(int R, int64_t len, const double* parts, double* total, cudaStream_t st) {
+  k_merge_partials<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(R, len, parts, total);
+  return cudaGetLastError();
+}
+
+// saa_finalize_partials: Eq. 4, Eq. 5 and the gradient from the whole
+// sample's partial sums, one warp per decision (FP64):
+//   pbar = w'mu + P1/N, V = (P2 - P1^2/N)/(N-1), f = lambda V - pbar,
+//   grad_j = lambda 2/(N-1) (P4_j - P1 P3_j/N) - (mu_j + P3_j/N).
+__global__ void k_finalize_partials(int K, int d, double N, double lambda, const double* __restrict__ X,
+                                    const double* __restrict__ mu, const double* __restrict__ part,
+                                    double* __restrict__ f, double* __restrict__ pbar, double* __restrict__ var,
+                                    double* __restrict__ grad) {
+  const int k = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= K) return;
+  const double* x = X + (size_t)k * d;
+  double c = 0.0;
+  for (int j = lane; j < d; j += 32) c = fma(mu[j], x[j], c);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  const double P1 = part[k], P2 = part[K + k];
+  const double* P3 = part + 2 * K;
+  const double* P4 = part + 2 * K + d + (size_t)k * d;
+  if (lane == 0) {
+    const double pb = c + P1 / N;
+    const double V = (P2 - P1 * (P1 / N)) / (N - 1.0);
+    if (f) f[k] = lambda * V - pb;
+    if (pbar) pbar[k] = pb;
+    if (var) var[k] = V;
+  }
+  if (grad) {
+    const double a = lambda * (2.0 / (N - 1.0));
+    for (int j = lane; j < d; j += 32)
+      grad[(size_t)k * d + j] = a * (P4[j] - P1 * (P3[j] / N)) - (mu[j] + P3[j] / N);
+  }
+}
+
+cudaError_t launch_finalize_partials(int64_t N, int d, int K, double lambda, const double* X, const double* mu,
+                                     const double* part, double* f, double* pbar, double* var, double* grad,
+                                     cudaStream_t st) {
+  k_finalize_partials<<<(K * 32 + 255) / 256, 256, 0, st>>>(K, d, (double)N, lambda, X, mu, part, f, pbar, var,
+                                                             grad);
   return cudaGetLastError();
 }
 

@@ -220,8 +220,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
     uint32_t ph = 0;
     for (int it = 0; it < iters; ++it) {
       const uint32_t tile = blockIdx.x + (uint32_t)tt * gridDim.x;
-      const uint32_t i0 = tile * (uint32_t)kM;
-      const int nrow = (int)min((uint32_t)kM, la.N - i0);
+      const uint32_t i0 = la.i_base + tile * (uint32_t)kM;
+      const int nrow = (int)min((uint32_t)kM, la.rows_end() - i0);
       const int sb = tt & (kSBufs - 1);
       const uint32_t s_bar = smem_u32(&sm->s_ready[sb]);
       if (tlaw && kb == 0 && rt < kM) {   // RNG warps 0..3 draw the tile's scales

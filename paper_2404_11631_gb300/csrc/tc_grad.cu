@@ -406,8 +406,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
       const int tt = it / per_tile;
       const int pt = it - tt * per_tile;
       const uint32_t tile = blockIdx.x + (uint32_t)tt * gridDim.x;
-      const uint32_t i0 = tile * (uint32_t)kGM;
-      const int nrow = (int)min((uint32_t)kGM, la.N - i0);
+      const uint32_t i0 = la.i_base + tile * (uint32_t)kGM;
+      const int nrow = (int)min((uint32_t)kGM, la.rows_end() - i0);
       const int sb4 = tt & (kGSBufs - 1);
       const uint32_t s_bar = smem_u32(&sm->s_ready[sb4]);
       if (tlaw && pt == 0 && rt < kGM) {   // generator warps 0..3 draw the tile's scales

@@ -89,6 +89,18 @@ def lib():
             L.saa_workspace_size.restype = sz
             L.saa_eval.argtypes = [vp, pp, C.c_int32, vp, C.c_int, vp, vp, vp, vp, sz, vp]
             L.saa_eval.restype = C.c_int
+            L.saa_eval_host_workspace_size.argtypes = [vp, pp, C.c_int32, C.c_int]
+            L.saa_eval_host_workspace_size.restype = sz
+            L.saa_eval_host.argtypes = [vp, pp, C.c_int32, vp, C.c_int, vp, vp, vp, vp, sz, vp]
+            L.saa_eval_host.restype = C.c_int
+            L.saa_partials_workspace_size.argtypes = [vp, pp, C.c_int64, C.c_int32, C.c_int, C.c_int]
+            L.saa_partials_workspace_size.restype = sz
+            L.saa_partials.argtypes = [vp, pp, C.c_int64, C.c_int64, C.c_int32, vp, C.c_int, C.c_int, vp, vp, sz, vp]
+            L.saa_partials.restype = C.c_int
+            L.saa_partials_merge.argtypes = [vp, C.c_int32, C.c_int64, vp, vp, vp]
+            L.saa_partials_merge.restype = C.c_int
+            L.saa_finalize_partials.argtypes = [vp, pp, C.c_int32, vp, vp, vp, vp, vp, vp, vp]
+            L.saa_finalize_partials.restype = C.c_int
             L.saa_grad.argtypes = [vp, pp, C.c_int32, vp, C.c_int, vp, vp, vp, sz, vp]
             L.saa_grad.restype = C.c_int
             L.saa_solve.argtypes = [vp, pp, vp, C.c_int32, C.c_int32, C.c_int64, C.c_int, vp, vp, vp, vp, sz, vp]
@@ -229,10 +241,11 @@ class Problem:
     def device(self):
         return self.mu.device
 
-    def c_struct(self) -> _CProblem:
+    def c_struct(self, host: bool = False) -> _CProblem:
+        where = "CPU" if host else "CUDA"
         for name, t in (("mu", self.mu), ("chol", self.chol), ("sd", self.sd)):
-            if t is not None and not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-                raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+            if t is not None and not (t.is_cuda != host and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous float64 {where} tensor")
         if self.chol is None and self.sd is None:
             raise ValueError("give chol, or sd for a diagonal covariance")
         if self.chol is not None and self.chol.shape != (self.d, self.d):
@@ -292,6 +305,38 @@ def saa_eval(prob: Problem, X: torch.Tensor, prec="fp32", pbar: bool = True, var
     return out
 
 
+def saa_eval_host_workspace_size(prob: Problem, K: int, prec="fp32", device: int | None = None) -> int:
+    """Device scratch bytes of saa_eval_host (prob's tensors on the host)."""
+    cp = prob.c_struct(host=True)
+    n = lib().saa_eval_host_workspace_size(context(device), C.byref(cp), K, _prec(prec))
+    if n == 0:
+        raise SAAError(SAA_EINVAL, "no workspace size for these arguments: " + lib().saa_last_error().decode())
+    return int(n)
+
+
+def saa_eval_host(prob: Problem, X: torch.Tensor, prec="fp32", out: dict | None = None,
+                  ws: torch.Tensor | None = None, device: int | None = None) -> dict:
+    """Eq. 4 with mu, chol (or sd), X and the outputs in host memory (pinned
+    tensors copy by DMA): the library copies in, evaluates, copies out and
+    waits, so {'f', 'pbar', 'var'} (float64 CPU tensors) are ready on return."""
+    if X.dim() == 1:
+        X = X.unsqueeze(0)
+    if X.is_cuda or X.dtype != torch.float64 or not X.is_contiguous() or X.shape[1] != prob.d:
+        raise ValueError("X must be a contiguous float64 CPU tensor [K, d]")
+    K = X.shape[0]
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if out is None:
+        out = {k: torch.empty(K, dtype=torch.float64).pin_memory() for k in ("f", "pbar", "var")}
+    need = saa_eval_host_workspace_size(prob, K, prec, dev)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=torch.device("cuda", dev))
+    cp = prob.c_struct(host=True)
+    _check(lib().saa_eval_host(context(dev), C.byref(cp), K, _ptr(X), _prec(prec), _ptr(out["f"]),
+                               _ptr(out.get("pbar")), _ptr(out.get("var")), _ptr(ws), ws.numel(),
+                               _stream(torch.device("cuda", dev))))
+    return out
+
+
 def saa_grad(prob: Problem, X: torch.Tensor, prec="fp32", want_f: bool = True,
              ws: torch.Tensor | None = None) -> dict:
     """Eq. 4 and its gradient in w: {'f', 'grad' [K, d]}."""
@@ -307,6 +352,62 @@ def saa_grad(prob: Problem, X: torch.Tensor, prec="fp32", want_f: bool = True,
     out = {"grad": g}
     if want_f:
         out["f"] = f
+    return out
+
+
+def partials_len(d: int, K: int, grad: bool) -> int:
+    """Length of saa_partials' FP64 vector: P1 [K], P2 [K], P3 [d], P4 [K*d]."""
+    return 2 * K + d + (K * d if grad else 0)
+
+
+def saa_partials(prob: Problem, i0: int, n: int, X: torch.Tensor, prec="fp32", grad: bool = False,
+                 ws: torch.Tensor | None = None) -> torch.Tensor:
+    """Partial sums of Eq. 4 / Eq. 5 over scenarios [i0, i0 + n) (see
+    saa.h): a float64 CUDA vector [P1 | P2 | P3 | P4] that adds across
+    disjoint ranges."""
+    X = _decisions(X, prob)
+    K = X.shape[0]
+    dev = prob.device
+    cp = prob.c_struct()
+    ctx = context(dev.index)
+    need = lib().saa_partials_workspace_size(ctx, C.byref(cp), n, K, _prec(prec), int(grad))
+    if need == 0:
+        raise SAAError(SAA_EINVAL, "no workspace size for these arguments: " + lib().saa_last_error().decode())
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    part = torch.empty(partials_len(prob.d, K, grad), dtype=torch.float64, device=dev)
+    _check(lib().saa_partials(ctx, C.byref(cp), int(i0), int(n), K, _ptr(X), _prec(prec), int(grad), _ptr(part),
+                              _ptr(ws), ws.numel(), _stream(dev)))
+    return part
+
+
+def saa_partials_merge(parts: torch.Tensor) -> torch.Tensor:
+    """Totals of the rows of ``parts`` ([R, len] float64 CUDA), added in row
+    order with compensation (bitwise independent of who produced the rows)."""
+    if not (parts.is_cuda and parts.dtype == torch.float64 and parts.is_contiguous() and parts.dim() == 2):
+        raise ValueError("parts must be a contiguous [R, len] float64 CUDA tensor")
+    dev = parts.device
+    total = torch.empty(parts.shape[1], dtype=torch.float64, device=dev)
+    _check(lib().saa_partials_merge(context(dev.index), parts.shape[0], parts.shape[1], _ptr(parts), _ptr(total),
+                                    _stream(dev)))
+    return total
+
+
+def saa_finalize_partials(prob: Problem, X: torch.Tensor, part: torch.Tensor, grad: bool = False) -> dict:
+    """Eq. 4, Eq. 5 (and the gradient) from the whole sample's partial sums:
+    {'f', 'pbar', 'var'} (+ 'grad' [K, d]) as float64 CUDA tensors."""
+    X = _decisions(X, prob)
+    K = X.shape[0]
+    dev = prob.device
+    if not (part.is_cuda and part.dtype == torch.float64 and part.is_contiguous()
+            and part.numel() == partials_len(prob.d, K, grad)):
+        raise ValueError("part must be a contiguous float64 CUDA vector of partials_len(d, K, grad)")
+    out = {k: torch.empty(K, dtype=torch.float64, device=dev) for k in ("f", "pbar", "var")}
+    if grad:
+        out["grad"] = torch.empty(K, prob.d, dtype=torch.float64, device=dev)
+    cp = prob.c_struct()
+    _check(lib().saa_finalize_partials(context(dev.index), C.byref(cp), K, _ptr(X), _ptr(part), _ptr(out["f"]),
+                                       _ptr(out["pbar"]), _ptr(out["var"]), _ptr(out.get("grad")), _stream(dev)))
     return out
 
 
@@ -735,4 +836,6 @@ EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_
             "saa_moments_workspace_size", "saa_moments", "saa_eval_moments_workspace_size", "saa_eval_moments",
             "saa_eval_samples_workspace_size", "saa_eval_samples", "saa_solve_adaptive_workspace_size",
             "saa_solve_adaptive", "saa_logistic_pitch", "saa_logistic_generate", "saa_logistic_workspace_size",
-            "saa_logistic_eval", "saa_ctx_set_sample_store", "saa_selftest_arith"]
+            "saa_logistic_eval", "saa_ctx_set_sample_store", "saa_selftest_arith", "saa_eval_host_workspace_size",
+            "saa_eval_host", "saa_partials_workspace_size", "saa_partials", "saa_finalize_partials",
+            "saa_partials_merge"]

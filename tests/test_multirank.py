@@ -2,11 +2,15 @@
 
 1. The weak-scaling layout: each rank its own instance, the job time is the
    slowest rank's.
-2. The exchange that splitting one instance's scenarios across ranks needs:
-   each rank forms the FP64 partial sums of Eq. 4 over its scenario range
-   (here from the oracle's samples, so no GPU is involved), one all-reduce
-   merges them, and the finalized f_hat and gradient equal the single-rank
-   oracle result.
+2. One problem's N scenarios split across the ranks, in the library's
+   partials layout [P1 | P2 | P3 | P4] (saa_partials, include/saa.h): each
+   rank takes multirank.scenario_ranges' range, forms that range's partial
+   sums (here with the oracle, the CPU stand-in for the rank's GPU, so no
+   GPU is involved), multirank.merge_partials adds them with one
+   collective, and the estimate finalized from the totals equals the
+   single-rank oracle result.  The GPU side of the same exchange (the
+   library's saa_partials, saa_partials_merge and saa_finalize_partials) is
+   checked in tests/test_gpu_partials.py.
 """
 import os
 import socket
@@ -26,6 +30,9 @@ def _free_port():
     return p
 
 
+D, N, K, LAM = 6, 3001, 3, 0.5
+
+
 def _worker(rank, world, port, root, q):
     import sys
     sys.path.insert(0, root)
@@ -33,29 +40,20 @@ def _worker(rank, world, port, root, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         import oracle
-        from paper_2404_11631_gb300 import inputs, multirank
+        from paper_2404_11631_gb300 import inputs, multirank, saa
         # 1. weak scaling
         inst = multirank.instance_for_rank(rank)
         tmax = multirank.max_time_over_ranks(0.5 + rank)
         # 2. split one instance's N over the ranks and merge the partials
-        d, N, K, lam = 6, 3001, 3, 0.5
-        ins = inputs.instance(d, 0)
-        X = inputs.decisions(K, d, 0)
-        P = oracle.make_problem(d, N, ins.mu, ins.chol, law=oracle.LAW_MIX, seed=4, lam=lam)
+        ins = inputs.instance(D, 0)
+        X = inputs.decisions(K, D, 0)
+        P = oracle.make_problem(D, N, ins.mu, ins.chol, law=oracle.LAW_MIX, seed=4, lam=LAM)
         a, b = multirank.scenario_ranges(N, world)[rank]
-        z, s, _ = oracle.generate(P, 32, a, b - a)
-        A = s[:, None] * z                              # a_i = s_i zhat_i
-        Y = X @ ins.chol                                # y_k = C'w_k (rows)
-        Q = A @ Y.T                                     # [n, K]
-        part = np.concatenate([Q.sum(0), (Q * Q).sum(0), A.sum(0), (A.T @ Q).T.ravel()])
-        tot = multirank.merge_partials(torch.tensor(part)).numpy()
-        S1, S2, m_t, G = tot[:K], tot[K:2 * K], tot[2 * K:2 * K + d], tot[2 * K + d:].reshape(K, d)
-        c = X @ ins.mu
-        V = (S2 - S1 * S1 / N) / (N - 1)
-        f = lam * V - (c + S1 / N)
-        m = m_t / N
-        grad = (lam * 2 / (N - 1) * (G - S1[:, None] * m[None, :]) - m[None, :]) @ ins.chol.T - ins.mu[None, :]
-        q.put((rank, inst, tmax, f, grad))
+        part = torch.tensor(oracle.partials(P, 32, a, b - a, X, grad=True))
+        assert part.numel() == saa.partials_len(D, K, True)
+        tot = multirank.merge_partials(part, ordered=False).numpy()
+        out = oracle.finalize_partials(N, X, ins.mu, LAM, tot, grad=True)
+        q.put((rank, inst, tmax, (a, b), out["f"], out["grad"]))
     finally:
         dist.destroy_process_group()
 
@@ -74,14 +72,27 @@ def test_two_rank_weak_scaling_and_partial_merge():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    res.sort()
+    res.sort(key=lambda r: r[0])
     assert [r[1] for r in res] == [0, 1]
     assert all(r[2] == 1.5 for r in res)
-    d, N, K = 6, 3001, 3
-    ins = inputs.instance(d, 0)
-    X = inputs.decisions(K, d, 0)
-    P = oracle.make_problem(d, N, ins.mu, ins.chol, law=oracle.LAW_MIX, seed=4)
+    assert [r[3] for r in res] == [(0, N // 2), (N // 2, N)]
+    ins = inputs.instance(D, 0)
+    X = inputs.decisions(K, D, 0)
+    P = oracle.make_problem(D, N, ins.mu, ins.chol, law=oracle.LAW_MIX, seed=4)
     ref = oracle.saa(P, 32, X, grad=True)
     for r in res:
-        assert np.allclose(r[3], ref["f"], rtol=1e-10, atol=1e-12)
-        assert np.allclose(r[4], ref["grad"], rtol=1e-9, atol=1e-11)
+        assert np.allclose(r[4], ref["f"], rtol=1e-10, atol=1e-12)
+        assert np.allclose(r[5], ref["grad"], rtol=1e-9, atol=1e-11)
+    # both ranks hold the same totals, so the same estimate bit for bit
+    assert np.array_equal(res[0][4], res[1][4]) and np.array_equal(res[0][5], res[1][5])
+
+
+def test_scenario_ranges_cover_without_overlap():
+    from paper_2404_11631_gb300 import multirank
+    for n, w in ((10, 3), (1 << 20, 8), (7, 7), (2, 1)):
+        r = multirank.scenario_ranges(n, w)
+        assert r[0][0] == 0 and r[-1][1] == n
+        assert all(a < b for a, b in r) and all(r[i][1] == r[i + 1][0] for i in range(w - 1))
+        assert max(b - a for a, b in r) - min(b - a for a, b in r) <= 1
+    with pytest.raises(ValueError):
+        multirank.scenario_ranges(3, 4)
