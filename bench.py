@@ -240,8 +240,9 @@ GRAD_WORKLOAD = dict(name="grad_d1024_N1M_K64_gauss", d=1024, N=1 << 20, K=64, l
 EPI_OPS_TC_GRAD = 8.0   # per pair: chunk fold, D1 + D2, square + reduce, W hi/lo split
 # DRAM bytes per launch of the value-and-gradient kernel, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on a small case, scaled to
-# the launch's N where the traffic grows with the number of tiles.
-GRAD_TRAFFIC = {("f16x3", 1024, 64): lambda n: 447954944.0 * n / (1 << 17)}
+# the launch's N where the traffic grows with the number of tiles; absent
+# until taken on the current kernel.
+GRAD_TRAFFIC = {}
 
 
 def grad_roofline(prec, d, N, K, law, kern_s, peaks):
@@ -1053,6 +1054,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the FP64 GPU comparator")
     ap.add_argument("--no-grad", action="store_true", help="skip the value-and-gradient workload")
     ap.add_argument("--grad-N", type=int, default=None, help="override the gradient workload's scenario count")
+    ap.add_argument("--grad-only", action="store_true", help="run only the value-and-gradient workload")
     ap.add_argument("--gen-only", action="store_true", help="time the bare generator (per-normal figure)")
     ap.add_argument("--no-fw", action="store_true", help="skip the Algorithm 1 (Frank-Wolfe) workload")
     ap.add_argument("--fw-only", action="store_true", help="run only the Algorithm 1 workload")
@@ -1105,6 +1107,12 @@ def main():
     if args.nv_n:
         NV_WORKLOAD["n"] = args.nv_n
         NV_WORKLOAD["name"] = f"newsvendor_n{args.nv_n}_S{NV_WORKLOAD['S']}_K1"
+    if args.grad_only:
+        import torch
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps(run_grad(args, dev, 1, 0, flush, torch.cuda.current_stream(dev))), flush=True)
+        return 0
     if args.cov_only:
         import torch
         dev = torch.device("cuda", 0)

@@ -529,6 +529,13 @@ saa_status saa_selftest_arith(saa_ctx* ctx, unsigned long long* mismatches, void
 saa_status saa_profile_enable(saa_ctx* ctx, int enable);
 saa_status saa_profile_read(saa_ctx* ctx, double* main_ms, int64_t* main_launches, int64_t* kernels_launched);
 
+/* Launch shape that saa_eval (want_grad = 0) or saa_grad (1) would use for
+ * this problem: CTAs of the main kernel (grid), CTAs per thread-block
+ * cluster (1 unless the path splits the dimensions across a cluster) and
+ * scenario tiles.  Any output may be NULL.  For tracing and tuning. */
+saa_status saa_plan_info(const saa_ctx* ctx, const saa_problem* prob, int32_t K, saa_prec prec, int want_grad,
+                         int32_t* grid, int32_t* cluster, int64_t* tiles);
+
 /* Largest d that `prec` supports. */
 int32_t saa_max_dim(saa_prec prec);
 

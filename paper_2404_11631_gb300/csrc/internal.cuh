@@ -78,6 +78,7 @@ struct Plan {
   int nsplit;     // diagonal path: scenario slices of the adjoint
   int ablk;       // diagonal path: adjoint blocks over the dimensions
   int keep;       // diagonal path: the forward pass stores the normals for the adjoint
+  int cluster;    // tensor-core gradient: CTAs per thread-block cluster (grid counts clusters)
 };
 
 }  // namespace saa

@@ -376,6 +376,23 @@ int32_t saa_max_dim(saa_prec prec) {
   }
 }
 
+saa_status saa_plan_info(const saa_ctx* ctx, const saa_problem* prob, int32_t K, saa_prec prec, int want_grad,
+                         int32_t* grid, int32_t* cluster, int64_t* tiles) {
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  saa_status s = check_problem(prob);
+  if (s != SAA_OK) return s;
+  if (K < 1 || K > 65535) return fail(SAA_EINVAL, "K must be in [1, 65535]");
+  DeviceGuard g(ctx->device);
+  Plan plan;
+  s = make_plan(ctx, prob, K, prec, want_grad ? 1 : 0, &plan);
+  if (s != SAA_OK) return s;
+  const int c = plan.cluster > 0 ? plan.cluster : 1;
+  if (grid) *grid = plan.grid * c;
+  if (cluster) *cluster = c;
+  if (tiles) *tiles = plan.tiles;
+  return SAA_OK;
+}
+
 size_t saa_workspace_size(const saa_ctx* ctx, const saa_problem* prob, int32_t K, saa_prec prec, int want_grad) {
   if (!ctx || check_problem(prob) != SAA_OK || K < 1) return 0;
   if (want_grad == 2) K = 1;

@@ -1,44 +1,62 @@
 // tc_grad.cu -- tcgen05 tensor-core path of the SAA estimate together with
-// its gradient in w (Eq. 4 with Eq. 5, Sec. 3.1), for d <= 1024, K <= 64.
+// its gradient in w (Eq. 4 with Eq. 5, Sec. 3.1), for d <= 1024, K <= 64,
+// drawing every normal once.
 //
 // With a_i = s_i zhat_i (the whitened samples), y_k = C'w_k and
 // Q_ik = a_i'y_k, the gradient needs, per decision k, the d-vector
-// G_k = sum_i a_i Q_ik besides S1_k, S2_k and m~ = sum_i a_i.  Per CTA (one
-// per SM, persistent over 128-scenario tiles), per tile:
-//   forward   the generator warps write the tile of a_i, 64 dimensions per
-//             stage (K-major, 128-byte swizzle), while bulk TMA brings the
-//             matching 64-dimension slice of the decision operand into the
-//             same stage; one thread issues hi*hi and hi*lo + lo*hi (the
-//             split-precision forward of the value kernel, FP16 or BF16).
-//   epilogue  four warps read Q, keep S2_k in FP64 registers and write
-//             W = Q 2^-f_k (2^f_k > |y_k|_2 in operand units, so |W_ik| <=
-//             |a_i|_2) as hi/lo of the operand type into shared memory,
-//             K-major over the tile's scenarios: the adjoint's second operand.
-//   adjoint   the generator warps draw the same tile again, transposed: 128
-//             dimensions x 128 scenarios per stage; the MMA thread issues
-//             G += A' W (hi/lo, three products, hi*hi into G1 and the
-//             corrections into G2) into one of two TMEM buffer pairs, and the
-//             epilogue folds each 128-dimension block into the CTA's
-//             Kahan-carried FP32 partial of G in global memory.  The same
-//             stage also yields the CTA's partial of m~.
-// The tensor core rounds every update of an accumulator with a bias toward
-// zero, so a running sum over T k steps loses about T/2 of its low-order
-// units in the last place: at d = 1024 (64 steps) that is 2e-6 of Q.  The
-// hi*hi products therefore go, 8 k steps (128 dimensions) at a time, into
-// one of two chunk accumulators that the epilogue folds into a running Q in
-// TMEM with round-to-nearest FP32 additions; the small corrections keep one
-// accumulator per tile.  The bias then stays near 4 units in the last
-// place whatever d is.
-// Drawing each tile twice costs a second pass of the generator but keeps
-// A out of shared memory (a 128 x 1024 tile in hi/lo would need 512 KB).
-// The adjoint's representation error changes sign and size from scenario to
-// scenario, so it shrinks like sqrt(d / N) relative to G: FP16 hi/lo (2^-22
-// per product) keeps it below 1e-6 from N ~ d upwards, where BF16 hi/lo
-// (2^-17) would not.
+// G_k = sum_i a_i Q_ik besides S2_k = sum_i Q_ik^2 and m~ = sum_i a_i.  G
+// needs the whole Q_ik (all d dimensions) before any a_i can be folded into
+// it, and a tile of 128 scenarios x 1024 dimensions in hi/lo takes 512 KB,
+// more than one SM's shared memory.  So the dimensions are split across a
+// thread-block cluster of C = ceil(d / 128) CTAs (at most 8): CTA r of a
+// cluster owns dimensions 128 r .. 128 r + 127, and every CTA of the cluster
+// works on the same 128-scenario tile at the same time.  Per tile:
+//   draw      the generator warps of CTA r write a_i for its 128 dimensions
+//             as hi/lo halves (K-major, 128-byte swizzle) into a 64 KB stage;
+//             the stage is the operand of both contractions below.
+//   forward   one thread issues Q^(r) = A^(r) Y^(r) over the CTA's 128
+//             dimensions, with its slice of the decision operand resident in
+//             shared memory: A_hi [Y_hi; Y_lo] as one MMA of N = 2 Kp (hi*hi
+//             and hi*lo side by side in TMEM), then A_lo Y_hi into the hi*lo
+//             columns.
+//   exchange  the epilogue warps put Q^(r) (FP32, transposed) into shared
+//             memory; once every CTA of the cluster has, CTA r adds the C
+//             partials of its own rows in rank order through distributed
+//             shared memory (a reduce-scatter: 128 / C rows each, 16-byte
+//             loads of 8 rows of one column, every peer's in flight at
+//             once), keeps S2 of those rows, and writes W = Q 2^-f_k as
+//             hi/lo into the W buffer of every CTA of the cluster, one 16-byte
+//             unit of 8 scenarios at a time (2^f_k > |y_k|_2 in operand
+//             units, so |W_ik| <= |a_i|_2).
+//   adjoint   with all rows of W in place, the thread issues
+//             G^(r) = A^(r)' W for the tile, reading the same stage as an
+//             MN-major operand (the dimensions of a 64-dimension chunk are
+//             contiguous) against [W_hi; W_lo] and A_lo' W_hi.  The epilogue
+//             adds each tile's block (hi*hi + corrections) into a
+//             Kahan-compensated running sum held in TMEM, so G never leaves
+//             the SM until the end.
+// The draw of tile t + 1 overlaps the forward, exchange and adjoint of tile
+// t (two stages); the exchange moves 2 x 32 KB of distributed shared memory
+// per tile and CTA.
+//
+// Accuracy.  The tensor core rounds every update of an accumulator with a
+// bias toward zero, so a running sum over T k steps loses about T/2 units in
+// the last place.  The forward runs 8 k steps per CTA and the C partials are
+// added with round-to-nearest FP32 additions; the adjoint's blocks run 8 k
+// steps per tile before their compensated fold, so the bias stays near 4
+// units in the last place of a tile's block.  The adjoint's representation
+// error changes sign and size from scenario to scenario, so it shrinks like
+// sqrt(d / N) relative to G: FP16 hi/lo (2^-22 per product) keeps it below
+// 1e-6 from N ~ d upwards, where BF16 hi/lo (2^-17) would not.
+//
 // Every mbarrier wait is clock-bounded: on expiry the kernel raises the error
-// word, drains its MMAs and copies, frees its TMEM and returns.
+// word and falls through to the end; every thread of every CTA still reaches
+// the closing cluster barriers (no CTA leaves while a peer may touch its
+// shared memory), MMAs and copies are drained and TMEM is freed.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "gen.cuh"
 #include "internal.cuh"
@@ -47,515 +65,490 @@
 namespace saa {
 namespace tc {
 
-constexpr int kGM = 128;               // scenarios per tile (MMA M of the forward)
-constexpr int kGKB = 64;               // dimensions per forward stage
-constexpr int kGMB = 128;              // dimensions per adjoint stage (MMA M of the adjoint)
-constexpr int kGStages = 3;
-constexpr int kGStageBytes = 65536;    // forward: A hi+lo 32 KB + B slice <= 16 KB; adjoint: A' hi+lo 64 KB
-constexpr int kGSubBytes = kGMB * 128; // adjoint: one [128 dims][64 scenarios] bf16 block
-constexpr int kGEpiWarps = 4;
-constexpr int kGMmaWarp = 4;           // warps 0..3 epilogue, 4 MMA, 5.. generator
+constexpr int kGM = 128;                   // scenarios per tile (forward MMA M, adjoint MMA K)
+constexpr int kGDims = 128;                // dimensions per CTA (adjoint MMA M)
+constexpr int kGStages = 2;
+constexpr int kGChunkBytes = kGM * 128;    // [128 rows][64 dims] of one half: 16 KB
+constexpr int kGStageBytes = 4 * kGChunkBytes;   // [chunk 0: hi, lo][chunk 1: hi, lo]
+constexpr int kGEpiWarps = 4;              // one per TMEM lane quadrant
+constexpr int kGEpiThreads = 32 * kGEpiWarps;
+constexpr int kGMmaWarp = kGEpiWarps;      // warps 0..7 epilogue, 8 forward MMA, 9.. generator
 constexpr int kGRngWarps = 16;
-constexpr int kGThreads = 32 * (5 + kGRngWarps);
+constexpr int kGThreads = 32 * (kGEpiWarps + 1 + kGRngWarps);
 constexpr int kGRngThreads = 32 * kGRngWarps;
-constexpr int kGMaxKp = 64;
-constexpr int kGMaxDim = 1024;
-constexpr int kGSBufs = 4;
-constexpr int kGChunkStages = 2;       // forward stages (8 k steps) per hi*hi chunk accumulator
-static_assert(kGRngThreads == 512, "adjoint stage mapping assumes 512 generator threads");
+constexpr int kGKp = 64;                   // decision columns (K <= 64; unused ones are zero)
+constexpr int kGMaxCluster = 8;
+constexpr int kGMaxDim = kGDims * kGMaxCluster;
+static_assert(kGRngThreads == 512, "stage mapping assumes 512 generator threads");
 
 struct GArgs {
   LawArgs la;
-  int K, Kp, nkb, nmb;
+  int K, C;
   int64_t tiles;
-  const uint8_t* bimage;   // [nkb][hi, lo][Kp][128 B], swizzled
+  const uint8_t* bimage;   // [2C blocks of 64 dims][hi, lo][64][128 B], swizzled
   const double* gaux;      // [2K]: 2^(e_k + f_k) (G at true scale), then 2^-f_k (W)
   const double* scale2;    // [K] 4^e_k  (S2 at true scale)
-  double* part_s2;         // [grid][K]
-  double* part_m;          // [grid][d]
-  float* part_g;           // [grid][K][d]
-  float* part_gc;          // [grid][K][d] Kahan compensation (true sum = part_g - part_gc)
+  double* part_s2;         // [clusters][K]
+  double* part_m;          // [clusters][d]
+  float* part_g;           // [clusters][K][d]
+  float* part_gc;          // [clusters][K][d] (true sum = part_g - part_gc)
   uint32_t* err;
 };
 
 struct GSmem {
-  uint64_t a_full[kGStages];    // generator warps' stores into the stage
-  uint64_t a_empty[kGStages];   // MMAs reading the stage done
-  uint64_t b_full[kGStages];    // decision-operand slice landed (forward stages)
-  uint64_t s_ready[kGSBufs];    // t-law scales of a tile
-  uint64_t c_full[2], c_empty[2];   // hi*hi chunk accumulators
-  uint64_t q_full, q_empty, w_full, w_empty;
-  uint64_t g_full[2], g_empty[2];
-  uint64_t drain;
+  uint64_t a_full[kGStages][2];  // generator warps' stores into each 64-dimension chunk of the stage
+  uint64_t a_empty[kGStages];  // both contractions of the stage done
+  uint64_t s_ready[2];         // t-law scales of a tile
+  uint64_t y_full;             // decision-operand slice landed
+  uint64_t q_full, q_empty;    // forward accumulators
+  uint64_t x_full;             // every CTA's partial rows are in this CTA's inbox (4 C arrivals)
+  uint64_t w_full;             // every CTA's rows of W are in this CTA's W (4 C arrivals)
+  uint64_t w_free;             // every CTA's adjoint of the tile is done (C multicast commits)
+  uint64_t g_full, g_empty;    // per-tile block of G
+  uint64_t drain, drain_adj;   // forward / adjoint MMAs complete (end of kernel)
   uint32_t tmem_base;
   uint32_t abort_flag;
-  float s_buf[kGSBufs][kGM];
-  float gsc_f[kGMaxKp];   // 2^(e_k + f_k)
-  float wsc_f[kGMaxKp];   // 2^-f_k
+  float s_buf[2][kGM];
+  float gsc_f[kGKp];   // 2^(e_k + f_k)
+  float wsc_f[kGKp];   // 2^-f_k
 };
 
-// Layout: [stages][W: 2 scenario blocks x hi/lo x Kp rows x 128 B][GSmem]; 1024-byte aligned base.
-size_t grad_smem_bytes(int Kp) { return (size_t)kGStages * kGStageBytes + (size_t)4 * Kp * 128 + sizeof(GSmem); }
+// Layout (1024-byte aligned base):
+//   [stages: 2 x 64 KB]
+//   [Y slice: 2 chunks of 64 dims x (hi, lo) x 64 decisions x 128 B]     32 KB, K-major
+//   [W: (hi, lo) x 128 scenarios x 64 decisions (128 B)]                 32 KB, MN-major
+//   [inbox: C sources x (128 / C) rows x 64 FP32]                       32 KB
+//   [GSmem]
+constexpr int kGOpBytes = 2 * 2 * kGKp * 128;
+size_t grad_smem_bytes() { return (size_t)kGStages * kGStageBytes + (size_t)3 * kGOpBytes + sizeof(GSmem); }
 
-// D8: d is a multiple of 8, so every unit below d is whole and the
-// per-element guards drop out.
+// Float offset in the inbox of column k of row l (of the owner's rows) from
+// source CTA p: 16-byte units XOR-swizzled by the row, so a warp's stores
+// (32 rows, one unit each) and the owner's 16-byte reads are free of bank
+// conflicts.
+__device__ __forceinline__ uint32_t inbox_off(int p, int nr, int l, int k) {
+  return (uint32_t)((p * nr + l) * kGKp + ((((k >> 2) ^ l) & 15) << 2) + (k & 3));
+}
+
+// D8: d is a multiple of 8, so every 8-dimension unit below d is whole and
+// the per-element guards drop out.
 template <bool F16, bool D8>
 __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t base = smem_u32(smem_raw);
-  if (base & 1023u) {
+  if (base & 1023u) {   // identical in every CTA: the whole cluster leaves together
     if (threadIdx.x == 0) atomicOr(a.err, kErrBounds);
     return;
   }
-  const int Kp = a.Kp;
+  const int C = a.C, nr = kGM / C;    // CTAs of the cluster; rows of the tile each one reduces
+  const uint32_t rank = cluster_rank();
+  const uint32_t cl = cluster_id(), ncl = cluster_count();
   uint8_t* ring = smem_raw;
-  uint8_t* wbuf = smem_raw + kGStages * kGStageBytes;
-  GSmem* sm = reinterpret_cast<GSmem*>(wbuf + 4 * Kp * 128);
-  const uint32_t sRing = base, sW = base + (uint32_t)(kGStages * kGStageBytes);
+  uint8_t* ybuf = ring + kGStages * kGStageBytes;
+  uint8_t* wbuf = ybuf + kGOpBytes;
+  float* inbox = reinterpret_cast<float*>(wbuf + kGOpBytes);
+  GSmem* sm = reinterpret_cast<GSmem*>(wbuf + 2 * kGOpBytes);
+  const uint32_t sRing = base, sY = smem_u32(ybuf), sW = smem_u32(wbuf), sIn = smem_u32(inbox);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const LawArgs& la = a.la;
   const int d = la.d;
-  const uint32_t bslice = (uint32_t)(2 * Kp * 128);   // one forward slice of the decision operand
+  constexpr uint32_t bslice = 2 * kGKp * 128;   // one 64-dimension block of the decision operand
+  constexpr uint32_t wchunk = kGM * 128;        // W: the hi (or lo) half, 128 scenarios x 64 decisions
   volatile uint32_t* abort_flag = &sm->abort_flag;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kGStages; ++s) {
-      mbar_init(smem_u32(&sm->a_full[s]), kGRngWarps);
+      mbar_init(smem_u32(&sm->a_full[s][0]), kGRngWarps / 2);
+      mbar_init(smem_u32(&sm->a_full[s][1]), kGRngWarps / 2);
       mbar_init(smem_u32(&sm->a_empty[s]), 1);
-      mbar_init(smem_u32(&sm->b_full[s]), 1);
     }
-    for (int s = 0; s < kGSBufs; ++s) mbar_init(smem_u32(&sm->s_ready[s]), kGM / 32);
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(smem_u32(&sm->c_full[b]), 1);
-      mbar_init(smem_u32(&sm->c_empty[b]), kGEpiWarps);
-    }
+    for (int s = 0; s < 2; ++s) mbar_init(smem_u32(&sm->s_ready[s]), kGM / 32);
+    mbar_init(smem_u32(&sm->y_full), 1);
     mbar_init(smem_u32(&sm->q_full), 1);
     mbar_init(smem_u32(&sm->q_empty), kGEpiWarps);
-    mbar_init(smem_u32(&sm->w_full), kGEpiWarps);
-    mbar_init(smem_u32(&sm->w_empty), 1);
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(smem_u32(&sm->g_full[b]), 1);
-      mbar_init(smem_u32(&sm->g_empty[b]), kGEpiWarps);
-    }
+    mbar_init(smem_u32(&sm->x_full), kGEpiWarps * C);
+    mbar_init(smem_u32(&sm->w_full), kGEpiWarps * C);
+    mbar_init(smem_u32(&sm->w_free), C);
+    mbar_init(smem_u32(&sm->g_full), 1);
+    mbar_init(smem_u32(&sm->g_empty), kGEpiWarps);
     mbar_init(smem_u32(&sm->drain), 1);
+    mbar_init(smem_u32(&sm->drain_adj), 1);
     sm->abort_flag = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int k = threadIdx.x; k < kGMaxKp; k += blockDim.x) {
+  for (int k = threadIdx.x; k < kGKp; k += blockDim.x) {
     sm->gsc_f[k] = (k < a.K) ? (float)a.gaux[k] : 0.0f;
     sm->wsc_f[k] = (k < a.K) ? (float)a.gaux[a.K + k] : 0.0f;
   }
-  // TMEM, Kp columns each: two hi*hi chunk accumulators, the running Q, the
-  // corrections D2, and two (G1, G2) pairs
-  const uint32_t ncols = (8 * Kp <= 256) ? 256u : 512u;
+  // TMEM, 64 columns each: Q hi*hi, Q corrections, the tile's G hi*hi and
+  // corrections, G's running sum, its Kahan compensation
+  constexpr uint32_t ncols = 512u;
   if (warp == kGMmaWarp) tmem_alloc(smem_u32(&sm->tmem_base), ncols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  cluster_sync();   // every CTA's barriers are initialised before any peer arrives on them
   const uint32_t tmem = sm->tmem_base;
-  const uint32_t tq = tmem + 2u * Kp, td2 = tmem + 3u * Kp;
-  const int nchunk = (a.nkb + kGChunkStages - 1) / kGChunkStages;
-  const int my_tiles = (int)((a.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
-  const int per_tile = a.nkb + a.nmb;
-  double s2acc[kGMaxKp / 32];
+  const uint32_t tq1 = tmem, td2 = tmem + 64u, tg1 = tmem + 128u, tg2 = tmem + 192u;
+  const uint32_t tgs = tmem + 256u, tgc = tmem + 320u;
+  const int my_tiles = (cl < (uint32_t)a.tiles) ? (int)((a.tiles - cl + ncl - 1) / ncl) : 0;
+  const uint16_t cmask = (uint16_t)((1u << C) - 1u);
+  float s2h[8], s2l[8];           // epilogue: S2 of this thread's 8 columns (float-float)
+  float mh[8], ml[8];             // generator: m~ of this thread's 8 dimensions (float-float)
+#pragma unroll
+  for (int q = 0; q < 8; ++q) mh[q] = ml[q] = s2h[q] = s2l[q] = 0.0f;
 
   if (warp == kGMmaWarp) {
     // ------------------------------------------------------------ MMA ---
     if (lane == 0) {
-      bool ok = true;
-      const uint32_t idf = idesc_f16(kGM, Kp, F16);
-      const uint32_t ida = idesc_f16(kGMB, Kp, F16);
-      int st = 0, gcount = 0, ccount = 0;
-      uint32_t ph = 0, bph = 0;   // bph: bit s = phase parity of b_full[s]
+      // this CTA's two 64-dimension blocks of the decision operand, resident
+      const uint32_t yb = smem_u32(&sm->y_full);
+      mbar_expect_tx(yb, 2 * bslice);
+      bulk_g2s(sY, a.bimage + (size_t)(2 * rank) * bslice, 2 * bslice, yb);
+      bool ok = mbar_wait(yb, 0, abort_flag, a.err);
+      // hi and lo halves of the second operand are stacked along N, so
+      // A_hi [B_hi, B_lo] is one MMA of N = 128 (hi*hi in columns 0..63,
+      // hi*lo in 64..127) and A_lo B_hi adds into the latter.  This thread
+      // issues only the forward; the adjoint is issued by the epilogue
+      // once W is in place, so the next tile's forward never waits on it.
+      const uint32_t idf2 = idesc_f16(kGM, 2 * kGKp, F16), idf1 = idesc_f16(kGM, kGKp, F16);
+      int st = 0;
+      uint32_t ph = 0;
       for (int tt = 0; ok && tt < my_tiles; ++tt) {
-        if (tt > 0) ok = mbar_wait(smem_u32(&sm->q_empty), (uint32_t)((tt - 1) & 1), abort_flag, a.err);
-        for (int kb = 0; ok && kb < a.nkb; ++kb) {
-          const int cb = ccount & 1;
-          const bool c_first = (kb % kGChunkStages) == 0;
-          const bool c_last = (kb % kGChunkStages) == kGChunkStages - 1 || kb == a.nkb - 1;
-          if (c_first) {
-            ok = mbar_wait(smem_u32(&sm->c_empty[cb]), (uint32_t)(((ccount >> 1) & 1) ^ 1), abort_flag, a.err);
-            if (!ok) break;
-          }
-          const uint32_t tc1 = tmem + (uint32_t)(cb * Kp);
-          ok = mbar_wait(smem_u32(&sm->a_full[st]), ph, abort_flag, a.err) &&
-               mbar_wait(smem_u32(&sm->b_full[st]), (bph >> st) & 1u, abort_flag, a.err);
-          if (!ok) break;
-          bph ^= 1u << st;
-          tc_fence_after();
-          const uint32_t a_hi = sRing + (uint32_t)(st * kGStageBytes);
-          const uint32_t a_lo = a_hi + kGM * 128;
-          const uint32_t b_hi = a_hi + 2 * kGM * 128;
-          const uint32_t b_lo = b_hi + (uint32_t)(Kp * 128);
+        ok = tt == 0 || mbar_wait(smem_u32(&sm->q_empty), (uint32_t)((tt - 1) & 1), abort_flag, a.err);
+        if (!ok) break;
+        const uint32_t stage = sRing + (uint32_t)(st * kGStageBytes);
+        // forward: Q^(r) over this CTA's 128 dimensions, 16 per k step, each
+        // 64-dimension chunk as soon as it is drawn
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {   // 16 dimensions per k step
+        for (int c = 0; c < 2; ++c) {
+          ok = mbar_wait(smem_u32(&sm->a_full[st][c]), ph, abort_flag, a.err);
+          if (!ok) break;
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
             const uint32_t o = (uint32_t)(kk * 32);
-            mma_bf16(tc1, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idf, (c_first && kk == 0) ? 0u : 1u);
-            mma_bf16(td2, desc_sw128(a_hi + o), desc_sw128(b_lo + o), idf, (kb == 0 && kk == 0) ? 0u : 1u);
-            mma_bf16(td2, desc_sw128(a_lo + o), desc_sw128(b_hi + o), idf, 1u);
+            const uint32_t a_hi = stage + (uint32_t)(c * 2 * kGChunkBytes) + o, a_lo = a_hi + kGChunkBytes;
+            const uint32_t b_hi = sY + (uint32_t)c * bslice + o;
+            mma_bf16(tq1, desc_sw128(a_hi), desc_sw128(b_hi), idf2, (c == 0 && kk == 0) ? 0u : 1u);
+            mma_bf16(td2, desc_sw128(a_lo), desc_sw128(b_hi), idf1, 1u);
           }
-          mma_commit(smem_u32(&sm->a_empty[st]));
-          if (c_last) {
-            mma_commit(smem_u32(&sm->c_full[cb]));
-            ++ccount;
-          }
-          if (++st == kGStages) { st = 0; ph ^= 1u; }
         }
         if (!ok) break;
         mma_commit(smem_u32(&sm->q_full));
-        ok = mbar_wait(smem_u32(&sm->w_full), (uint32_t)(tt & 1), abort_flag, a.err);
-        for (int mb = 0; ok && mb < a.nmb; ++mb, ++gcount) {
-          const int gb = gcount & 1;
-          const uint32_t tg1 = tmem + (uint32_t)((4 + 2 * gb) * Kp), tg2 = tg1 + (uint32_t)Kp;
-          ok = mbar_wait(smem_u32(&sm->g_empty[gb]), (uint32_t)(((gcount >> 1) & 1) ^ 1), abort_flag, a.err) &&
-               mbar_wait(smem_u32(&sm->a_full[st]), ph, abort_flag, a.err);
-          if (!ok) break;
-          tc_fence_after();
-          const uint32_t stage = sRing + (uint32_t)(st * kGStageBytes);
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {   // 16 scenarios per k step
-            const int sb = kk >> 2;
-            const uint32_t o = (uint32_t)((kk & 3) * 32);
-            const uint32_t at_hi = stage + (uint32_t)((sb * 2 + 0) * kGSubBytes) + o;
-            const uint32_t at_lo = stage + (uint32_t)((sb * 2 + 1) * kGSubBytes) + o;
-            const uint32_t w_hi = sW + (uint32_t)((sb * 2 + 0) * Kp * 128) + o;
-            const uint32_t w_lo = sW + (uint32_t)((sb * 2 + 1) * Kp * 128) + o;
-            const uint32_t acc0 = (kk == 0) ? 0u : 1u;
-            mma_bf16(tg1, desc_sw128(at_hi), desc_sw128(w_hi), ida, acc0);
-            mma_bf16(tg2, desc_sw128(at_hi), desc_sw128(w_lo), ida, acc0);
-            mma_bf16(tg2, desc_sw128(at_lo), desc_sw128(w_hi), ida, 1u);
-          }
-          mma_commit(smem_u32(&sm->a_empty[st]));
-          mma_commit(smem_u32(&sm->g_full[gb]));
-          if (++st == kGStages) { st = 0; ph ^= 1u; }
-        }
-        if (!ok) break;
-        mma_commit(smem_u32(&sm->w_empty));
+        if (++st == kGStages) { st = 0; ph ^= 1u; }
       }
-      // every MMA issued above completes before TMEM is released
+      // every forward MMA and the operand copy complete before TMEM and the stages are released
       mma_commit(smem_u32(&sm->drain));
       uint32_t never = 0u;
       mbar_wait(smem_u32(&sm->drain), 0, &never, a.err);
+      mbar_wait(yb, 0, &never, a.err);
     }
     __syncwarp();
   } else if (warp < kGEpiWarps) {
     // ------------------------------------------------------- epilogue ---
+    // Warp w reads TMEM lane quadrant w (rows / dimensions 32 w .. 32 w + 31).
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-#pragma unroll
-    for (int g = 0; g < kGMaxKp / 32; ++g) s2acc[g] = 0.0;
-    const int row = warp * 32 + lane;          // forward: scenario of this TMEM lane
-    const int wsb = row >> 6, wil = row & 63;  // its 64-scenario block and position
-    uint8_t* w_hi = wbuf + wsb * 2 * Kp * 128;
-    uint8_t* w_lo = w_hi + Kp * 128;
-    int gcount = 0, ccount = 0;
-    for (int tt = 0; tt < my_tiles; ++tt) {
-      // fold the hi*hi chunks into the running Q (round to nearest)
-      bool cok = true;
-      for (int c = 0; c < nchunk; ++c, ++ccount) {
-        const int cb = ccount & 1;
-        if (!warp_wait(smem_u32(&sm->c_full[cb]), (uint32_t)((ccount >> 1) & 1), abort_flag, a.err)) {
-          cok = false;
-          break;
-        }
-        tc_fence_after();
-#pragma unroll 1
-        for (int c0 = 0; c0 < Kp; c0 += 16) {
-          uint32_t ra[16], rq[16];
-          tmem_ld16(tmem + (uint32_t)(cb * Kp + c0) + lane_base, ra);
-          if (c > 0) tmem_ld16(tq + (uint32_t)c0 + lane_base, rq);
-          tmem_wait_ld();
-          if (c > 0) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) ra[i] = __float_as_uint(__uint_as_float(ra[i]) + __uint_as_float(rq[i]));
-          }
-          tmem_st16(tq + (uint32_t)c0 + lane_base, ra);
-          tmem_wait_st();
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&sm->c_empty[cb]));
-      }
-      if (!cok) break;
+    const int row = warp * 32 + lane;                // forward: scenario of this TMEM lane; adjoint: dimension
+    const int own = row / nr, lrow = row - own * nr;  // CTA that reduces this row, and its place there
+    const int e = threadIdx.x;                       // 0 .. 127
+    const int kq = e & 7;                            // reduce: this thread's columns 8 kq .. 8 kq + 7
+    const int r0 = (int)rank * nr;                   // reduce: this CTA's rows r0 .. r0 + nr - 1
+    const bool issuer = (threadIdx.x == 0);          // issues the adjoint MMAs
+    const uint32_t ida2 = idesc_f16(kGDims, 2 * kGKp, F16) | kIdescAMajorMN | kIdescBMajorMN;
+    const uint32_t ida1 = idesc_f16(kGDims, kGKp, F16) | kIdescAMajorMN | kIdescBMajorMN;
+    bool adj_issued = false;
+    int tt = 0;
+    for (; tt < my_tiles; ++tt) {
+      // ---- this CTA's partial Q of every row into the inbox of the row's owner
       if (!warp_wait(smem_u32(&sm->q_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
-      if (tt > 0 && !warp_wait(smem_u32(&sm->w_empty), (uint32_t)((tt - 1) & 1), abort_flag, a.err)) break;
+      if (tt > 0 && !warp_wait_cluster(smem_u32(&sm->w_full), (uint32_t)((tt - 1) & 1), abort_flag, a.err)) break;
       tc_fence_after();
 #pragma unroll 1
-      for (int pc = 0; pc < Kp / 16; ++pc) {
-        const uint32_t c0 = (uint32_t)(16 * pc);
-        uint32_t r1[16], r2[16];
-        tmem_ld16(tq + lane_base + c0, r1);
-        tmem_ld16(td2 + lane_base + c0, r2);
+      for (uint32_t c0 = 0; c0 < (uint32_t)kGKp; c0 += 16) {
+        uint32_t r1v[16], r2v[16];
+        tmem_ld16(tq1 + lane_base + c0, r1v);
+        tmem_ld16(td2 + lane_base + c0, r2v);
         tmem_wait_ld();
-        float v[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float q = __uint_as_float(r1[i]) + __uint_as_float(r2[i]);
-          const int k = (int)c0 + i;
-          // element (k, row) of W: row k of the operand, 16-byte unit wil/8 swizzled by k
-          const float wq = q * sm->wsc_f[k];   // power of two: exact
-          const uint32_t hp = pack2<F16>(wq, 0.0f);
-          const uint32_t lp = pack2<F16>(wq - unpack2<F16>(hp).x, 0.0f);
-          const uint32_t off = (uint32_t)(k * 128 + (((wil >> 3) ^ (k & 7)) << 4) + (wil & 7) * 2);
-          *reinterpret_cast<uint16_t*>(w_hi + off) = (uint16_t)(hp & 0xffffu);
-          *reinterpret_cast<uint16_t*>(w_lo + off) = (uint16_t)(lp & 0xffffu);
-          v[i] = q * q;
+        for (int u = 0; u < 4; ++u) {
+          float4 q;
+          q.x = __uint_as_float(r1v[4 * u + 0]) + __uint_as_float(r2v[4 * u + 0]);
+          q.y = __uint_as_float(r1v[4 * u + 1]) + __uint_as_float(r2v[4 * u + 1]);
+          q.z = __uint_as_float(r1v[4 * u + 2]) + __uint_as_float(r2v[4 * u + 2]);
+          q.w = __uint_as_float(r1v[4 * u + 3]) + __uint_as_float(r2v[4 * u + 3]);
+          const uint32_t off = inbox_off((int)rank, nr, lrow, (int)c0 + 4 * u);
+          if (C == 1)
+            *reinterpret_cast<float4*>(inbox + off) = q;
+          else
+            st_cluster_v4(mapa(sIn + 4u * off, (uint32_t)own),
+                          make_uint4(__float_as_uint(q.x), __float_as_uint(q.y), __float_as_uint(q.z),
+                                     __float_as_uint(q.w)));
         }
-        // reduce-scatter over the warp's 32 rows: lanes l and l + 16 end with column c0 + (l & 15)
-#pragma unroll
-        for (int w = 8; w >= 1; w >>= 1) {
-          const bool upper = (lane & w) != 0;
-#pragma unroll
-          for (int i = 0; i < w; ++i) {
-            const float send = upper ? v[i] : v[i + w];
-            const float keep = upper ? v[i + w] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-          }
-        }
-        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
-        // lane l keeps column 32 g + l of s2acc[g]
-#pragma unroll
-        for (int h = 0; h < kGMaxKp / 32; ++h)
-          if (h == (pc >> 1) && (lane >> 4) == (pc & 1)) s2acc[h] += (double)v[0];
       }
-      fence_proxy_async();   // W: generic-proxy stores -> the MMA's async-proxy reads
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(smem_u32(&sm->w_full));
-        mbar_arrive(smem_u32(&sm->q_empty));
-      }
-      // fold each adjoint block into the CTA's partial of G
-      bool ok = true;
-      for (int mb = 0; mb < a.nmb; ++mb, ++gcount) {
-        const int gb = gcount & 1;
-        const uint32_t tg1 = tmem + (uint32_t)((4 + 2 * gb) * Kp), tg2 = tg1 + (uint32_t)Kp;
-        if (!warp_wait(smem_u32(&sm->g_full[gb]), (uint32_t)((gcount >> 1) & 1), abort_flag, a.err)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const int j = mb * kGMB + warp * 32 + lane;   // dimension of this TMEM lane
+      if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty));
+      if (lane < C) mbar_arrive_remote(mapa(smem_u32(&sm->x_full), (uint32_t)lane));
+      // ---- reduce this CTA's rows: the C partials in rank order, S2, and W into every CTA
+      if (!warp_wait_cluster(smem_u32(&sm->x_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
+      if (tt > 0 && !warp_wait_cluster(smem_u32(&sm->w_free), (uint32_t)((tt - 1) & 1), abort_flag, a.err)) break;
+      float s2t[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s2t[q] = 0.0f;
 #pragma unroll 1
-        for (int c0 = 0; c0 < Kp; c0 += 16) {
-          uint32_t r1[16], r2[16];
-          tmem_ld16(tg1 + lane_base + (uint32_t)c0, r1);
-          tmem_ld16(tg2 + lane_base + (uint32_t)c0, r2);
-          tmem_wait_ld();
-          const int kn = a.K - c0;   // valid columns of this batch (may be <= 0)
-          if (j < d && kn > 0) {
-            float gv[16];
+      for (int it = e; it < nr * 8; it += kGEpiThreads) {
+        const int l = it >> 3;
+        float q[8];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) gv[i] = (__uint_as_float(r1[i]) + __uint_as_float(r2[i])) * sm->gsc_f[c0 + i];
-            const size_t e0 = ((size_t)blockIdx.x * a.K + c0) * d + j;
-            if (tt == 0) {
+        for (int j = 0; j < 8; ++j) q[j] = 0.0f;
+#pragma unroll 1
+        for (int p = 0; p < C; ++p) {   // rank order: the sum does not depend on timing
+          const float4 va = *reinterpret_cast<const float4*>(inbox + inbox_off(p, nr, l, 8 * kq));
+          const float4 vb = *reinterpret_cast<const float4*>(inbox + inbox_off(p, nr, l, 8 * kq + 4));
+          q[0] += va.x; q[1] += va.y; q[2] += va.z; q[3] += va.w;
+          q[4] += vb.x; q[5] += vb.y; q[6] += vb.z; q[7] += vb.w;
+        }
+        uint4 hv, lv;
+        uint32_t* hp = &hv.x;
+        uint32_t* lp = &lv.x;
 #pragma unroll
-              for (int i = 0; i < 16; ++i)
-                if (i < kn) {
-                  a.part_g[e0 + (size_t)i * d] = gv[i];
-                  a.part_gc[e0 + (size_t)i * d] = 0.0f;
-                }
-            } else {
+        for (int u = 0; u < 4; ++u) {
+          s2t[2 * u] = fmaf(q[2 * u], q[2 * u], s2t[2 * u]);
+          s2t[2 * u + 1] = fmaf(q[2 * u + 1], q[2 * u + 1], s2t[2 * u + 1]);
+          const float wa = q[2 * u] * sm->wsc_f[8 * kq + 2 * u];   // powers of two: exact
+          const float wb = q[2 * u + 1] * sm->wsc_f[8 * kq + 2 * u + 1];
+          hp[u] = pack2<F16>(wa, wb);
+          const float2 h = unpack2<F16>(hp[u]);
+          lp[u] = pack2<F16>(wa - h.x, wb - h.y);
+        }
+        // decisions 8 kq .. 8 kq + 7 of scenario i: one 16-byte unit of W's row i, swizzled by i
+        const int i = r0 + l;
+        const uint32_t woff = (uint32_t)(i * 128 + ((kq ^ (i & 7)) << 4));
+        if (C == 1) {
+          *reinterpret_cast<uint4*>(wbuf + woff) = hv;
+          *reinterpret_cast<uint4*>(wbuf + wchunk + woff) = lv;
+        } else {
+#pragma unroll 1
+          for (int p = 0; p < C; ++p) {
+            st_cluster_v4(mapa(sW + woff, (uint32_t)p), hv);
+            st_cluster_v4(mapa(sW + wchunk + woff, (uint32_t)p), lv);
+          }
+        }
+      }
 #pragma unroll
-              for (int hb = 0; hb < 16; hb += 8) {   // two halves: 16 loads in flight, fewer live registers
-                float ps[8], pc[8];
+      for (int q = 0; q < 8; ++q) ff_add(s2h[q], s2l[q], s2t[q]);
+      fence_proxy_async_cluster();   // W: generic stores -> the MMAs' async-proxy reads
+      __syncwarp();
+      if (lane < C) mbar_arrive_remote(mapa(smem_u32(&sm->w_full), (uint32_t)lane));
+      // ---- adjoint: G^(r) = A^(r)' W of the tile, once every row of W is in place and the
+      // last tile's block is folded; the stage is read as an MN-major A (dimensions
+      // contiguous, 64-dimension chunks 32 KB apart), W as an MN-major B (decisions
+      // contiguous, the hi and lo halves 16 KB apart)
+      if (issuer) {
+        bool ok = mbar_wait_cluster(smem_u32(&sm->w_full), (uint32_t)(tt & 1), abort_flag, a.err) &&
+                  (tt == 0 || mbar_wait(smem_u32(&sm->g_empty), (uint32_t)((tt - 1) & 1), abort_flag, a.err));
+        if (ok) {
+          tc_fence_after();
+          const uint32_t stage = sRing + (uint32_t)((tt % kGStages) * kGStageBytes);
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                  if (hb + i < kn) {
-                    ps[i] = a.part_g[e0 + (size_t)(hb + i) * d];
-                    pc[i] = a.part_gc[e0 + (size_t)(hb + i) * d];
-                  }
+          for (int kk = 0; kk < 8; ++kk) {   // 16 scenarios per k step
+            const uint32_t at_hi = stage + (uint32_t)(kk * 2048), at_lo = at_hi + kGChunkBytes;
+            const uint64_t bw = desc_mn_sw128(sW + (uint32_t)(kk * 2048), wchunk, 1024);
+            mma_bf16(tg1, desc_mn_sw128(at_hi, 2 * kGChunkBytes, 1024), bw, ida2, kk == 0 ? 0u : 1u);
+            mma_bf16(tg2, desc_mn_sw128(at_lo, 2 * kGChunkBytes, 1024), bw, ida1, 1u);
+          }
+          mma_commit(smem_u32(&sm->a_empty[tt % kGStages]));
+          mma_commit(smem_u32(&sm->g_full));
+          mma_commit_multicast(smem_u32(&sm->w_free), cmask);
+          adj_issued = true;
+        }
+      }
+      __syncwarp();
+      // ---- fold the tile's block of G (hi*hi + corrections) into the running sum (Kahan)
+      if (!warp_wait(smem_u32(&sm->g_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
+      tc_fence_after();
+#pragma unroll 1
+      for (uint32_t c0 = 0; c0 < (uint32_t)kGKp; c0 += 8) {
+        uint32_t rg[8], rh[8], rs[8], rc[8];
+        tmem_ld8(tg1 + lane_base + c0, rg);
+        tmem_ld8(tg2 + lane_base + c0, rh);
+        if (tt > 0) {
+          tmem_ld8(tgs + lane_base + c0, rs);
+          tmem_ld8(tgc + lane_base + c0, rc);
+        }
+        tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                  if (hb + i < kn) {
-                    const float y = gv[hb + i] - pc[i];
-                    const float t = ps[i] + y;
-                    a.part_gc[e0 + (size_t)(hb + i) * d] = (t - ps[i]) - y;
-                    a.part_g[e0 + (size_t)(hb + i) * d] = t;
-                  }
-              }
+        for (int q = 0; q < 8; ++q) {
+          const float g = __uint_as_float(rg[q]) + __uint_as_float(rh[q]);
+          if (tt == 0) {
+            rc[q] = 0u;
+            rg[q] = __float_as_uint(g);
+          } else {
+            const float s = __uint_as_float(rs[q]), c = __uint_as_float(rc[q]);
+            const float y = g - c;
+            const float t = s + y;
+            rc[q] = __float_as_uint((t - s) - y);
+            rg[q] = __float_as_uint(t);
+          }
+        }
+        tmem_st8(tgs + lane_base + c0, rg);
+        tmem_st8(tgc + lane_base + c0, rc);
+        tmem_wait_st();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&sm->g_empty));
+    }
+    if (issuer && adj_issued) {   // every adjoint MMA complete before TMEM and the stages are released
+      mma_commit(smem_u32(&sm->drain_adj));
+      uint32_t never = 0u;
+      mbar_wait(smem_u32(&sm->drain_adj), 0, &never, a.err);
+    }
+    // ---- this CTA's dimensions of G: running sum and its compensation
+    const int j = (int)rank * kGDims + row;
+    if (tt == my_tiles && my_tiles > 0) {
+      tc_fence_after();
+#pragma unroll 1
+      for (uint32_t c0 = 0; c0 < (uint32_t)kGKp; c0 += 8) {
+        uint32_t rs[8], rc[8];
+        tmem_ld8(tgs + lane_base + c0, rs);
+        tmem_ld8(tgc + lane_base + c0, rc);
+        tmem_wait_ld();
+        if (j < d) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int k = (int)c0 + q;
+            if (k < a.K) {
+              const size_t o = ((size_t)cl * a.K + k) * d + j;
+              const float g = sm->gsc_f[k];   // power of two: exact
+              a.part_g[o] = __uint_as_float(rs[q]) * g;
+              a.part_gc[o] = __uint_as_float(rc[q]) * g;
             }
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&sm->g_empty[gb]));
       }
-      if (!ok) break;
+    } else if (my_tiles == 0 && j < d) {
+      for (int k = 0; k < a.K; ++k) {
+        const size_t o = ((size_t)cl * a.K + k) * d + j;
+        a.part_g[o] = 0.0f;
+        a.part_gc[o] = 0.0f;
+      }
     }
   } else {
     // ------------------------------------------------------------ RNG ---
     const int rt = threadIdx.x - 32 * (kGMmaWarp + 1);   // 0 .. 511
+    const int ch = rt >> 8;                               // 64-dimension chunk: warps 0..7 chunk 0, 8..15 chunk 1
+    const int cu = rt & 7;                                // 16-byte unit (8 dimensions) of the chunk
+    const int rbase = (rt >> 3) & 31;                     // rows rbase, rbase + 32, rbase + 64, rbase + 96
+    const int j0 = (int)rank * kGDims + ch * 64 + cu * 8; // first dimension of this thread's unit
     uint32_t epoch = la.epoch;
     if (la.t_dev) epoch += (uint32_t)(*la.t_dev / la.M);
     const gen::Stream gs = gen::make_stream(la.seed, epoch, la.instance);
     const uint32_t half = la.N / 2u;
     const bool tlaw = la.law == SAA_LAW_STUDENT_T;
-    // forward stage: 16-byte unit cu (8 dimensions) of rows rt/8 and rt/8 + 64
-    const int cu = rt & 7;
-    // adjoint stage: dimensions 4 b4 .. 4 b4 + 3 of the block, scenarios 8 g8 .. 8 g8 + 7,
-    // written one scenario pair (4 bytes) at a time; the pair order is staggered by
-    // lane group so that each store instruction covers all 32 banks once
-    const int b4 = rt >> 4, g8 = rt & 15;
-    const int asb = g8 >> 3, au = g8 & 7;
-    const int pfirst = lane >> 3;
+    const bool live_unit = j0 < d;
     int st = 0;
     uint32_t ph = 0;
-    uint32_t bissued = 0, bpar = 0;   // copy issuer: stages with copies, parity of the next copy per stage
-    const int iters = my_tiles * per_tile;
-    for (int it = 0; it < iters; ++it) {
-      const int tt = it / per_tile;
-      const int pt = it - tt * per_tile;
-      const uint32_t tile = blockIdx.x + (uint32_t)tt * gridDim.x;
+    for (int tt = 0; tt < my_tiles; ++tt) {
+      const uint32_t tile = cl + (uint32_t)tt * ncl;
       const uint32_t i0 = la.i_base + tile * (uint32_t)kGM;
       const int nrow = (int)min((uint32_t)kGM, la.rows_end() - i0);
-      const int sb4 = tt & (kGSBufs - 1);
-      const uint32_t s_bar = smem_u32(&sm->s_ready[sb4]);
-      if (tlaw && pt == 0 && rt < kGM) {   // generator warps 0..3 draw the tile's scales
-        sm->s_buf[sb4][rt] = (rt < nrow) ? gen::t_scale_f(gs, i0 + (uint32_t)rt, la.nu) : 0.0f;
+      const int sb = tt & 1;
+      const uint32_t s_bar = smem_u32(&sm->s_ready[sb]);
+      if (!warp_wait(smem_u32(&sm->a_empty[st]), ph ^ 1u, abort_flag, a.err)) break;
+      // Past this wait every generator warp has finished tile tt - 2, the
+      // last user of this scale buffer, so two buffers suffice.
+      if (tlaw && rt < kGM) {   // generator warps 0..3 draw the tile's scales
+        sm->s_buf[sb][rt] = (rt < nrow) ? gen::t_scale_f(gs, i0 + (uint32_t)rt, la.nu) : 0.0f;
         __syncwarp();
         if (lane == 0) mbar_arrive(s_bar);
       }
-      if (!warp_wait(smem_u32(&sm->a_empty[st]), ph ^ 1u, abort_flag, a.err)) break;
-      if (tlaw && !warp_wait(s_bar, (uint32_t)((tt >> 2) & 1), abort_flag, a.err)) break;
-      uint8_t* stage = ring + st * kGStageBytes;
-      if (pt < a.nkb) {
-        // ---- forward stage: dimensions 64 kb .. 64 kb + 63 of the tile
-        const int kb = pt;
-        if (rt == 0) {
-          const uint32_t bb = smem_u32(&sm->b_full[st]);
-          mbar_expect_tx(bb, bslice);
-          bulk_g2s(sRing + (uint32_t)(st * kGStageBytes) + 2u * kGM * 128u, a.bimage + (size_t)kb * bslice, bslice,
-                   bb);
-          bissued |= 1u << st;
-          bpar ^= 1u << st;
-        }
-        const int j0 = kb * kGKB + cu * 8;
+      if (tlaw && !warp_wait(s_bar, (uint32_t)((tt >> 1) & 1), abort_flag, a.err)) break;
+      uint8_t* chunk = ring + st * kGStageBytes + ch * 2 * kGChunkBytes;
+      float msum[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) msum[q] = 0.0f;
 #pragma unroll 1
-        for (int r = rt >> 3; r < kGM; r += kGRngThreads / 8) {
-          float v[8];
+      for (int r = rbase; r < kGM; r += 32) {
+        float v[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) v[e] = 0.0f;
-          if (r < nrow && j0 < d) {
-            const uint32_t i = i0 + (uint32_t)r;
-            const bool logn = gen::is_lognormal(la.law, i, half);
-            float z[4];
-            gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2), i, logn, z);
+        for (int q = 0; q < 8; ++q) v[q] = 0.0f;
+        if (r < nrow && live_unit) {
+          const uint32_t i = i0 + (uint32_t)r;
+          const bool logn = gen::is_lognormal(la.law, i, half);
+          float z[4];
+          gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2), i, logn, z);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) v[e] = (D8 || j0 + e < d) ? z[e] : 0.0f;
-            if (D8 || j0 + 4 < d) {
-              gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2) + 1u, i, logn, z);
+          for (int q = 0; q < 4; ++q) v[q] = (D8 || j0 + q < d) ? z[q] : 0.0f;
+          if (D8 || j0 + 4 < d) {
+            gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2) + 1u, i, logn, z);
 #pragma unroll
-              for (int e = 0; e < 4; ++e) v[4 + e] = (D8 || j0 + 4 + e < d) ? z[e] : 0.0f;
-            }
-            if (tlaw) {
-              const float s = sm->s_buf[sb4][r];
-#pragma unroll
-              for (int e = 0; e < 8; ++e) v[e] *= s;
-            }
+            for (int q = 0; q < 4; ++q) v[4 + q] = (D8 || j0 + 4 + q < d) ? z[q] : 0.0f;
           }
-          uint32_t hi[4], lo[4];
+          if (tlaw) {
+            const float s = sm->s_buf[sb][r];
 #pragma unroll
-          for (int e = 0; e < 8; e += 2) {
-            hi[e / 2] = pack2<F16>(v[e], v[e + 1]);
-            const float2 h = unpack2<F16>(hi[e / 2]);
-            lo[e / 2] = pack2<F16>(v[e] - h.x, v[e + 1] - h.y);
-          }
-          const uint32_t off = sw_off(r, cu);
-          *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<uint4*>(stage + kGM * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-        }
-      } else {
-        // ---- adjoint stage: dimensions 128 mb .. 128 mb + 127, transposed
-        const int mb = pt - a.nkb;
-        const int jb = mb * kGMB + 4 * b4;   // first of this thread's 4 dimensions
-        float msum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 1
-        for (int p = 0; p < 4; ++p) {
-          const int pq = (p + pfirst) & 3;   // scenarios 8 g8 + 2 pq, + 1
-          const int r0 = 8 * g8 + 2 * pq;
-          float z0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, z1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-          if (jb < d) {
-            if (r0 < nrow) {
-              const uint32_t i = i0 + (uint32_t)r0;
-              gen::Gen<float>::block(gs, (uint32_t)(jb >> 2), i, gen::is_lognormal(la.law, i, half), z0);
-              if (tlaw) {
-                const float s0 = sm->s_buf[sb4][r0];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) z0[e] *= s0;
-              }
-#pragma unroll
-              for (int e = 0; e < 4; ++e) z0[e] = (D8 || jb + e < d) ? z0[e] : 0.0f;
-            }
-            if (r0 + 1 < nrow) {
-              const uint32_t i = i0 + (uint32_t)r0 + 1u;
-              gen::Gen<float>::block(gs, (uint32_t)(jb >> 2), i, gen::is_lognormal(la.law, i, half), z1);
-              if (tlaw) {
-                const float s1 = sm->s_buf[sb4][r0 + 1];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) z1[e] *= s1;
-              }
-#pragma unroll
-              for (int e = 0; e < 4; ++e) z1[e] = (D8 || jb + e < d) ? z1[e] : 0.0f;
-            }
-          }
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            msum[e] += z0[e] + z1[e];
-            const int jr = 4 * b4 + e;   // row of the stage
-            const uint32_t h = pack2<F16>(z0[e], z1[e]);
-            const float2 f = unpack2<F16>(h);
-            const uint32_t l = pack2<F16>(z0[e] - f.x, z1[e] - f.y);
-            const uint32_t off = (uint32_t)(jr * 128 + ((au ^ (jr & 7)) << 4) + pq * 4);
-            *reinterpret_cast<uint32_t*>(stage + (asb * 2 + 0) * kGSubBytes + off) = h;
-            *reinterpret_cast<uint32_t*>(stage + (asb * 2 + 1) * kGSubBytes + off) = l;
+            for (int q = 0; q < 8; ++q) v[q] *= s;
           }
         }
-        // m~: fold the 16 lanes that share these dimensions; lane g8 == 0 owns
-        // them for the whole kernel, so its additions reach part_m in program order
+        uint32_t hi[4], lo[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-#pragma unroll
-          for (int o = 1; o < 16; o <<= 1) msum[e] += __shfl_xor_sync(0xffffffffu, msum[e], o);
+        for (int q = 0; q < 8; q += 2) {
+          msum[q] += v[q];
+          msum[q + 1] += v[q + 1];
+          hi[q / 2] = pack2<F16>(v[q], v[q + 1]);
+          const float2 h = unpack2<F16>(hi[q / 2]);
+          lo[q / 2] = pack2<F16>(v[q] - h.x, v[q + 1] - h.y);
         }
-        if (g8 == 0) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (jb + e < d) {
-              double* pm = a.part_m + (size_t)blockIdx.x * d + jb + e;
-              if (tt == 0)
-                *pm = (double)msum[e];
-              else
-                atomicAdd(pm, (double)msum[e]);
-            }
-        }
+        const uint32_t off = sw_off(r, cu);
+        *reinterpret_cast<uint4*>(chunk + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(chunk + kGChunkBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
       }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) ff_add(mh[q], ml[q], msum[q]);
       fence_proxy_async();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sm->a_full[st]));
+      if (lane == 0) mbar_arrive(smem_u32(&sm->a_full[st][ch]));
       if (++st == kGStages) { st = 0; ph ^= 1u; }
-    }
-    if (rt == 0) {
-      // the last copy into each stage has landed before the CTA moves on (after an abort too)
-      uint32_t never = 0u;
-      for (int s = 0; s < kGStages; ++s)
-        if ((bissued >> s) & 1u) mbar_wait(smem_u32(&sm->b_full[s]), ((bpar >> s) & 1u) ^ 1u, &never, a.err);
     }
   }
 
   // ----------------------------------------------------- CTA reductions ---
-  __syncthreads();   // MMAs and copies drained: the stages are free
-  double* red_s2 = reinterpret_cast<double*>(ring);   // [kGEpiWarps][kGMaxKp]
-  if (warp < kGEpiWarps) {
+  __syncthreads();   // MMAs and the copy drained, TMEM reads done: the stages are free
+  double* red_m = reinterpret_cast<double*>(ring);        // [32 row groups][128 dims]
+  double* red_s2 = red_m + 32 * kGDims;                   // [128 epilogue threads][8 columns]
+  double* s2loc = red_s2 + kGEpiThreads * 8;              // [64]
+  if (warp > kGMmaWarp) {
+    const int rt = threadIdx.x - 32 * (kGMmaWarp + 1);
+    const int jl = (rt >> 8) * 64 + (rt & 7) * 8;
 #pragma unroll
-    for (int g = 0; g < kGMaxKp / 32; ++g)
-      if (32 * g < Kp) red_s2[warp * kGMaxKp + 32 * g + lane] = s2acc[g];
+    for (int q = 0; q < 8; ++q) red_m[((rt >> 3) & 31) * kGDims + jl + q] = (double)mh[q] + (double)ml[q];
+  } else if (warp < kGEpiWarps) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) red_s2[threadIdx.x * 8 + q] = (double)s2h[q] + (double)s2l[q];
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
+  if (threadIdx.x < kGDims) {   // m~ of this CTA's dimensions, row groups added in order
+    const int j = (int)rank * kGDims + threadIdx.x;
     double s = 0.0;
-    for (int w = 0; w < kGEpiWarps; ++w) s += red_s2[w * kGMaxKp + k];
-    a.part_s2[(size_t)blockIdx.x * a.K + k] = s * a.scale2[k];
+    for (int g = 0; g < 32; ++g) s += red_m[g * kGDims + threadIdx.x];
+    if (j < d) a.part_m[(size_t)cl * d + j] = s;
   }
+  if (threadIdx.x < kGKp) {     // S2 of this CTA's rows: the 16 threads of column k, in order
+    const int kq = threadIdx.x >> 3, q = threadIdx.x & 7;
+    double s = 0.0;
+    for (int m = 0; m < kGEpiThreads / 8; ++m) s += red_s2[(kq + 8 * m) * 8 + q];
+    s2loc[threadIdx.x] = s;
+  }
+  cluster_sync();   // every CTA's S2 is in place and every peer is done with this CTA's buffers
+  if (rank == 0 && threadIdx.x < a.K) {   // the cluster's S2, CTAs added in rank order
+    const uint32_t o = smem_u32(s2loc + threadIdx.x);
+    double s = 0.0;
+    for (int p = 0; p < C; ++p) s += ld_cluster_f64(mapa(o, (uint32_t)p));
+    a.part_s2[(size_t)cl * a.K + threadIdx.x] = s * a.scale2[threadIdx.x];
+  }
+  cluster_sync();   // rank 0 has read every peer's S2
   if (warp == kGMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, ncols);
@@ -564,26 +557,69 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
 
 }  // namespace tc
 
-bool tc_grad_supported(const saa_problem* p, int K) { return p->d <= tc::kGMaxDim && K <= tc::kGMaxKp; }
+bool tc_grad_supported(const saa_problem* p, int K) { return p->d <= tc::kGMaxDim && K <= tc::kGKp; }
 
-static size_t grad_image_bytes(int K, int d) {
-  const int Kp = (K + 31) / 32 * 32;
-  const int nkb = (d + tc::kGKB - 1) / tc::kGKB;
-  return (size_t)nkb * 2 * Kp * 128;
+// CTAs per cluster: the dimensions in 128-wide slices, rounded up to a power
+// of two so that the 128 rows of a tile split evenly among them (a CTA whose
+// slice lies past d draws nothing).
+static int grad_cluster(int d) {
+  const int c = (d + tc::kGDims - 1) / tc::kGDims;
+  return c <= 1 ? 1 : c <= 2 ? 2 : c <= 4 ? 4 : 8;
+}
+
+// The decision operand in 64-dimension blocks, two per CTA of the cluster
+// (blocks past d are zero), 64 decision rows each.
+static size_t grad_image_bytes(int d) { return (size_t)(2 * grad_cluster(d)) * 2 * tc::kGKp * 128; }
+
+template <bool F16, bool D8>
+static const void* grad_kernel() {
+  return (const void*)tc::k_tc_grad<F16, D8>;
+}
+
+// Clusters of C CTAs that fit on the device at once (one CTA per SM), per
+// (device, C): the persistent grid.  Queried once and cached.
+static int grad_max_clusters(const saa_ctx* ctx, int C, int smem) {
+  static std::mutex mu;
+  static int cache[64][tc::kGMaxCluster + 1];
+  std::lock_guard<std::mutex> lock(mu);
+  int& slot = cache[ctx->device & 63][C];
+  if (slot > 0) return slot;
+  int best = ctx->sm_count / C;
+  const void* kern = grad_kernel<true, true>();
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(tc::kGThreads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0) best = n;
+  }
+  cudaGetLastError();   // a failed query leaves no sticky error
+  slot = best;
+  return best;
 }
 
 saa_status tc_grad_plan(const saa_ctx* ctx, const saa_problem* p, int K, Plan* plan) {
-  const int Kp = (K + 31) / 32 * 32;
+  const int C = grad_cluster(p->d);
   plan->bm = tc::kGM;
+  plan->cluster = C;
   plan->tiles = (p->N + tc::kGM - 1) / tc::kGM;
-  plan->grid = (int)(plan->tiles < ctx->sm_count ? plan->tiles : ctx->sm_count);
-  plan->smem = (int)tc::grad_smem_bytes(Kp);
-  // operand image, then scale2[K], gaux[2K]
-  plan->tc_bytes = grad_image_bytes(K, p->d) + (size_t)24 * K;
+  plan->smem = (int)tc::grad_smem_bytes();
   if (plan->smem > ctx->smem_optin) {
     set_error("tensor-core gradient tile does not fit in shared memory");
     return SAA_EUNSUPPORTED;
   }
+  const int64_t cl = grad_max_clusters(ctx, C, plan->smem);
+  plan->grid = (int)(plan->tiles < cl ? plan->tiles : cl);   // clusters; the partial slots are per cluster
+  // operand image, then scale2[K], gaux[2K]
+  plan->tc_bytes = grad_image_bytes(p->d) + (size_t)24 * K;
   return SAA_OK;
 }
 
@@ -593,12 +629,10 @@ cudaError_t launch_tc_grad(const LawArgs& la, int K, int prec, const Plan& plan,
   tc::GArgs a;
   a.la = la;
   a.K = K;
-  a.Kp = (K + 31) / 32 * 32;
-  a.nkb = (la.d + tc::kGKB - 1) / tc::kGKB;
-  a.nmb = (la.d + tc::kGMB - 1) / tc::kGMB;
+  a.C = plan.cluster;
   a.tiles = plan.tiles;
   uint8_t* img = (uint8_t*)ws.tc;
-  double* scale2 = (double*)(img + grad_image_bytes(K, la.d));
+  double* scale2 = (double*)(img + grad_image_bytes(la.d));
   double* gaux = scale2 + K;
   a.bimage = img;
   a.gaux = gaux;
@@ -608,15 +642,27 @@ cudaError_t launch_tc_grad(const LawArgs& la, int K, int prec, const Plan& plan,
   a.part_g = (float*)ws.part_g;
   a.part_gc = (float*)ws.part_gc;
   a.err = err;
-  cudaError_t e = launch_tc_image(la.d, K, a.Kp, a.nkb, f16, ws.Y64, scale2, gaux, img, st);
+  cudaError_t e = launch_tc_image(la.d, K, tc::kGKp, 2 * a.C, f16, ws.Y64, scale2, gaux, img, st);
   if (e != cudaSuccess) return e;
   const bool d8 = (la.d & 7) == 0;
-  auto kern = f16 ? (d8 ? tc::k_tc_grad<true, true> : tc::k_tc_grad<true, false>)
-                  : (d8 ? tc::k_tc_grad<false, true> : tc::k_tc_grad<false, false>);
+  const void* kern = f16 ? (d8 ? grad_kernel<true, true>() : grad_kernel<true, false>())
+                         : (d8 ? grad_kernel<false, true>() : grad_kernel<false, false>());
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
   if (e != cudaSuccess) return e;
-  kern<<<plan.grid, tc::kGThreads, plan.smem, st>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(plan.grid * a.C));
+  cfg.blockDim = dim3(tc::kGThreads);
+  cfg.dynamicSmemBytes = (size_t)plan.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)a.C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  void* args[] = {&a};
+  return cudaLaunchKernelExC(&cfg, kern, args);
 }
 
 }  // namespace saa

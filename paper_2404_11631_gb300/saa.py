@@ -172,6 +172,9 @@ def lib():
             L.saa_ctx_set_autotune.restype = C.c_int
             L.saa_ctx_set_sample_store.argtypes = [vp, sz]
             L.saa_ctx_set_sample_store.restype = C.c_int
+            L.saa_plan_info.argtypes = [vp, pp, C.c_int32, C.c_int, C.c_int, C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
+            L.saa_plan_info.restype = C.c_int
             L.saa_max_dim.argtypes = [C.c_int]
             L.saa_max_dim.restype = C.c_int32
             L.saa_status_string.argtypes = [C.c_int]
@@ -823,6 +826,15 @@ def saa_profile_read(device: int | None = None) -> tuple[float, int, int]:
     return ms.value, n.value, k.value
 
 
+def saa_plan_info(prob: Problem, K: int, prec="fp32", want_grad: bool = False) -> dict:
+    """Launch shape of saa_eval / saa_grad for this problem: {'grid', 'cluster', 'tiles'}."""
+    g, c, t = C.c_int32(), C.c_int32(), C.c_int64()
+    cp = prob.c_struct()
+    _check(lib().saa_plan_info(context(prob.device.index), C.byref(cp), K, _prec(prec), int(want_grad), C.byref(g),
+                               C.byref(c), C.byref(t)))
+    return {"grid": g.value, "cluster": c.value, "tiles": t.value}
+
+
 def max_dim(prec) -> int:
     return int(lib().saa_max_dim(_prec(prec)))
 
@@ -838,4 +850,4 @@ EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_
             "saa_solve_adaptive", "saa_logistic_pitch", "saa_logistic_generate", "saa_logistic_workspace_size",
             "saa_logistic_eval", "saa_ctx_set_sample_store", "saa_selftest_arith", "saa_eval_host_workspace_size",
             "saa_eval_host", "saa_partials_workspace_size", "saa_partials", "saa_finalize_partials",
-            "saa_partials_merge"]
+            "saa_partials_merge", "saa_plan_info"]
