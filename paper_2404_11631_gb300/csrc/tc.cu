@@ -75,7 +75,7 @@ struct Smem {
   uint64_t a_full[kStages];
   uint64_t a_empty[kStages];
   uint64_t s_ready[kSBufs];
-  uint64_t q_full, q_empty, b_full, drain;
+  uint64_t q_full[2], q_empty[2], b_full, drain;   // accumulator buffers (one when K blocks > 2)
   uint32_t tmem_base;
   uint32_t abort_flag;
   float s_buf[kSBufs][kM];
@@ -90,6 +90,7 @@ size_t smem_bytes(int Kp, int nkb) {
 // the per-element guards drop out.
 template <bool F16, int NKB, bool D8>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
+  constexpr bool ONE = NKB <= 2;   // one accumulator per tile, double-buffered (see the MMA role)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // The 128-byte swizzle is address based: operands need a 1024-byte aligned base.
   const uint32_t base = smem_u32(smem_raw);
@@ -113,8 +114,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
       mbar_init(smem_u32(&sm->a_empty[s]), 1);
     }
     for (int s = 0; s < kSBufs; ++s) mbar_init(smem_u32(&sm->s_ready[s]), kM / 32);
-    mbar_init(smem_u32(&sm->q_full), 1);
-    mbar_init(smem_u32(&sm->q_empty), kEpiWarps);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&sm->q_full[b]), 1);
+      mbar_init(smem_u32(&sm->q_empty[b]), kEpiWarps);
+    }
     mbar_init(smem_u32(&sm->b_full), 1);
     mbar_init(smem_u32(&sm->drain), 1);
     sm->abort_flag = 0u;
@@ -147,32 +150,83 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
       const bool b_landed = ok;
       const uint32_t idesc = idesc_f16(kM, a.Kp, F16);
       const uint32_t hl_b = (uint32_t)(a.Kp * 128);
-      int tt = 0, kb = 0, st = 0;
-      uint32_t ph = 0;
-      for (int it = 0; ok && it < iters; ++it) {
-        if (kb == 0 && tt > 0) {
-          ok = mbar_wait(smem_u32(&sm->q_empty), (uint32_t)((tt - 1) & 1), abort_flag, a.err);
+      if constexpr (ONE) {
+        // One accumulator per tile, two buffers: the small corrections
+        // hi*lo + lo*hi of every K block go in first, then hi*hi, so the
+        // running sum is large for only the 4 nkb hi*hi updates (the bias
+        // of the two-accumulator scheme) and the epilogue of tile t runs
+        // under the MMAs of tile t + 1.  The tile's K blocks (at most two
+        // of the three stages) stay resident until its MMAs complete.
+        int st = 0;
+        uint32_t ph = 0;
+        for (int tt = 0; ok && tt < my_tiles; ++tt) {
+          const int buf = tt & 1;
+          if (tt >= 2) {
+            ok = mbar_wait(smem_u32(&sm->q_empty[buf]), (uint32_t)(((tt - 2) >> 1) & 1), abort_flag, a.err);
+            if (!ok) break;
+          }
+          int sts[2];
+          for (int kb = 0; ok && kb < a.nkb; ++kb) {
+            ok = mbar_wait(smem_u32(&sm->a_full[st]), ph, abort_flag, a.err);
+            sts[kb] = st;
+            if (++st == kStages) { st = 0; ph ^= 1u; }
+          }
           if (!ok) break;
-        }
-        ok = mbar_wait(smem_u32(&sm->a_full[st]), ph, abort_flag, a.err);
-        if (!ok) break;
-        tc_fence_after();
-        const uint32_t a_hi = sA + (uint32_t)(st * kStageBytes);
-        const uint32_t a_lo = a_hi + kM * 128;
-        const uint32_t b_hi = sB + (uint32_t)(kb * 2) * hl_b;
-        const uint32_t b_lo = b_hi + hl_b;
+          tc_fence_after();
+          const uint32_t td = tmem + (uint32_t)(buf * a.Kp);
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint32_t o = (uint32_t)(kk * 32);
-          const uint32_t acc0 = (kb == 0 && kk == 0) ? 0u : 1u;
-          mma_bf16(td1, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idesc, acc0);
-          mma_bf16(td2, desc_sw128(a_hi + o), desc_sw128(b_lo + o), idesc, acc0);
-          mma_bf16(td2, desc_sw128(a_lo + o), desc_sw128(b_hi + o), idesc, 1u);
+          for (int kb = 0; kb < NKB; ++kb) {
+            if (kb >= a.nkb) break;
+            const uint64_t dah = desc_sw128(sA + (uint32_t)(sts[kb] * kStageBytes));
+            const uint64_t dal = dah + (uint64_t)((kM * 128) >> 4);
+            const uint64_t dbh = desc_sw128(sB + (uint32_t)(kb * 2) * hl_b);
+            const uint64_t dbl = dbh + (uint64_t)(hl_b >> 4);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t o = (uint64_t)(kk * 2);   // 32 bytes in the descriptor's 16-byte units
+              mma_bf16(td, dah + o, dbl + o, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
+              mma_bf16(td, dal + o, dbh + o, idesc, 1u);
+            }
+          }
+#pragma unroll
+          for (int kb = 0; kb < NKB; ++kb) {
+            if (kb >= a.nkb) break;
+            const uint64_t dah = desc_sw128(sA + (uint32_t)(sts[kb] * kStageBytes));
+            const uint64_t dbh = desc_sw128(sB + (uint32_t)(kb * 2) * hl_b);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) mma_bf16(td, dah + (uint64_t)(kk * 2), dbh + (uint64_t)(kk * 2), idesc, 1u);
+          }
+          for (int kb = 0; kb < a.nkb; ++kb) mma_commit(smem_u32(&sm->a_empty[sts[kb]]));
+          mma_commit(smem_u32(&sm->q_full[buf]));
         }
-        mma_commit(smem_u32(&sm->a_empty[st]));
-        if (kb == a.nkb - 1) mma_commit(smem_u32(&sm->q_full));
-        if (++kb == a.nkb) { kb = 0; ++tt; }
-        if (++st == kStages) { st = 0; ph ^= 1u; }
+      } else {
+        int tt = 0, kb = 0, st = 0;
+        uint32_t ph = 0;
+        for (int it = 0; ok && it < iters; ++it) {
+          if (kb == 0 && tt > 0) {
+            ok = mbar_wait(smem_u32(&sm->q_empty[0]), (uint32_t)((tt - 1) & 1), abort_flag, a.err);
+            if (!ok) break;
+          }
+          ok = mbar_wait(smem_u32(&sm->a_full[st]), ph, abort_flag, a.err);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t a_hi = sA + (uint32_t)(st * kStageBytes);
+          const uint32_t a_lo = a_hi + kM * 128;
+          const uint32_t b_hi = sB + (uint32_t)(kb * 2) * hl_b;
+          const uint32_t b_lo = b_hi + hl_b;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t o = (uint32_t)(kk * 32);
+            const uint32_t acc0 = (kb == 0 && kk == 0) ? 0u : 1u;
+            mma_bf16(td1, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idesc, acc0);
+            mma_bf16(td2, desc_sw128(a_hi + o), desc_sw128(b_lo + o), idesc, acc0);
+            mma_bf16(td2, desc_sw128(a_lo + o), desc_sw128(b_hi + o), idesc, 1u);
+          }
+          mma_commit(smem_u32(&sm->a_empty[st]));
+          if (kb == a.nkb - 1) mma_commit(smem_u32(&sm->q_full[0]));
+          if (++kb == a.nkb) { kb = 0; ++tt; }
+          if (++st == kStages) { st = 0; ph ^= 1u; }
+        }
       }
       // every MMA issued above completes before TMEM is released; after an
       // abort, wait (bounded) for the operand copies still in flight too
@@ -188,22 +242,27 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
 #pragma unroll
     for (int g = 0; g < kMaxKp / 32; ++g) s2h[g] = s2l[g] = 0.0f;
     for (int tt = 0; tt < my_tiles; ++tt) {
-      if (!warp_wait(smem_u32(&sm->q_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
+      const int buf = ONE ? (tt & 1) : 0;
+      const uint32_t par = ONE ? (uint32_t)((tt >> 1) & 1) : (uint32_t)(tt & 1);
+      if (!warp_wait(smem_u32(&sm->q_full[buf]), par, abort_flag, a.err)) break;
       tc_fence_after();
+      const uint32_t tq = tmem + (uint32_t)(buf * a.Kp);
       // the group loop stays rolled (register pressure); the running sums
       // rotate so that group g's pair is s2h[0] / s2l[0] when it is added
 #pragma unroll 1
       for (int g = 0; g < kMaxKp / 32; ++g) {
         if (32 * g < a.Kp) {
           const uint32_t c0 = (uint32_t)(32 * g);
-          ff_add(s2h[0], s2l[0], epi_sq_colsum32(td1 + lane_base + c0, td2 + lane_base + c0, lane));
+          const float cs = ONE ? epi_sq_colsum32_1(tq + lane_base + c0, lane)
+                               : epi_sq_colsum32_x2(td1 + lane_base + c0, td2 + lane_base + c0, lane);
+          ff_add(s2h[0], s2l[0], cs);
         }
         rot_left(s2h);
         rot_left(s2l);
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty));
+      if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty[buf]));
     }
   } else {
     // ------------------------------------------------------------ RNG ---

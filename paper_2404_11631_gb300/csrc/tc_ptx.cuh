@@ -218,30 +218,39 @@ __device__ __forceinline__ int epi_col(int lane) {
   return 8 * ((lane >> 3) & 3) + 2 * (lane & 3) + ((lane >> 2) & 1);
 }
 
-// Column sums of q^2, q = D1 + D2, over a warp's 32 TMEM lanes (rows) for
-// the 32 columns at t1 / t2 (lane quadrant already in the address): lane t
-// returns column epi_col(t)'s sum.  With the 16x256b shape each thread holds
-// four rows of two columns per 8-column block (rows t/4, t/4 + 8, t/4 + 16,
-// t/4 + 24), so the rows fold in registers first; a reduce-scatter over the
-// eight row groups (lanes 4 apart) leaves one column per lane.
-__device__ __forceinline__ float epi_sq_colsum32(uint32_t t1, uint32_t t2, int lane) {
-  float v[8];   // v[2j + b]: column 8j + 2(t%4) + b over the thread's rows
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    uint32_t r1[16], r2[16];
-    tmem_ld16x256_x4(t1 + ((16u * half) << 16), r1);
-    tmem_ld16x256_x4(t2 + ((16u * half) << 16), r2);
-    tmem_wait_ld();
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const float qa = __uint_as_float(r1[4 * j + b]) + __uint_as_float(r2[4 * j + b]);
-        const float qb = __uint_as_float(r1[4 * j + 2 + b]) + __uint_as_float(r2[4 * j + 2 + b]);
-        const float sq = fmaf(qa, qa, qb * qb);
-        v[2 * j + b] = half ? v[2 * j + b] + sq : sq;
-      }
-  }
+// Packed FP32 pairs (the f32x2 forms of add / mul / fma): two adjacent
+// 32-bit values per 64-bit register, one instruction per pair.
+__device__ __forceinline__ unsigned long long f2_pack(uint32_t lo, uint32_t hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+  uint32_t a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(a), "=r"(b) : "l"(v));
+  lo = __uint_as_float(a);
+  hi = __uint_as_float(b);
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Reduce-scatter of eight 4-row column sums over the eight row groups of
+// the 16x256b shape (lanes 4 apart): lane t is left with column epi_col(t).
+__device__ __forceinline__ float epi_rows_reduce(float (&v)[8], int lane) {
 #pragma unroll
   for (int w = 16; w >= 4; w >>= 1) {
     const bool upper = (lane & w) != 0;
@@ -254,6 +263,57 @@ __device__ __forceinline__ float epi_sq_colsum32(uint32_t t1, uint32_t t2, int l
     }
   }
   return v[0];
+}
+
+// Column sums of q^2, q = D1 + D2, over a warp's 32 TMEM lanes (rows) for
+// the 32 columns at t1 / t2 (lane quadrant already in the address): lane t
+// returns column epi_col(t)'s sum.  With the 16x256b shape each thread holds
+// four rows of two adjacent columns per 8-column block (rows t/4, t/4 + 8,
+// t/4 + 16, t/4 + 24); the adjacent columns are natural f32x2 pairs, so the
+// rows fold in packed registers before the reduce-scatter.
+__device__ __forceinline__ float epi_sq_colsum32_x2(uint32_t t1, uint32_t t2, int lane) {
+  unsigned long long vp[4];
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    uint32_t r1[16], r2[16];
+    tmem_ld16x256_x4(t1 + ((16u * half) << 16), r1);
+    tmem_ld16x256_x4(t2 + ((16u * half) << 16), r2);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned long long qa = f2_add(f2_pack(r1[4 * j], r1[4 * j + 1]), f2_pack(r2[4 * j], r2[4 * j + 1]));
+      const unsigned long long qb =
+          f2_add(f2_pack(r1[4 * j + 2], r1[4 * j + 3]), f2_pack(r2[4 * j + 2], r2[4 * j + 3]));
+      const unsigned long long sq = f2_fma(qa, qa, f2_mul(qb, qb));
+      vp[j] = half ? f2_add(vp[j], sq) : sq;
+    }
+  }
+  float v[8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) f2_unpack(vp[j], v[2 * j], v[2 * j + 1]);
+  return epi_rows_reduce(v, lane);
+}
+
+// The same for a single accumulator q = D.
+__device__ __forceinline__ float epi_sq_colsum32_1(uint32_t t, int lane) {
+  unsigned long long vp[4];
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    uint32_t r[16];
+    tmem_ld16x256_x4(t + ((16u * half) << 16), r);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned long long qa = f2_pack(r[4 * j], r[4 * j + 1]);
+      const unsigned long long qb = f2_pack(r[4 * j + 2], r[4 * j + 3]);
+      vp[j] = f2_fma(qa, qa, half ? vp[j] : f2_mul(qb, qb));
+      if (half) vp[j] = f2_fma(qb, qb, vp[j]);
+    }
+  }
+  float v[8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) f2_unpack(vp[j], v[2 * j], v[2 * j + 1]);
+  return epi_rows_reduce(v, lane);
 }
 
 // Rotates a register array left by one (a[i] = a[i + 1], the first value

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
         for (int g = gb + g0; g < ge; g += kSEpiStride) {
           if (32 * g < a.Kp) {
             const uint32_t c = (uint32_t)(32 * g - 128 * h);
-            ff_add(s2h[0], s2l[0], epi_sq_colsum32(d1 + c, d2 + c, lane));
+            ff_add(s2h[0], s2l[0], epi_sq_colsum32_x2(d1 + c, d2 + c, lane));
           }
           rot_left(s2h);
           rot_left(s2l);
