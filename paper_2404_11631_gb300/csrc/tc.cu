@@ -7,6 +7,10 @@
 // over N, so FP16 (2 x 11 bits, ~2^-22) is the 1e-6 variant and BF16
 // (2 x 8 bits, ~2^-16) the 1e-4 variant.
 //
+// Two kernels: k_tc_value1 for d <= 128 (described above its definition:
+// one double-buffered accumulator per tile, the MMAs issued by an epilogue
+// thread) and k_tc_value for 128 < d <= 256, below.
+//
 // Per CTA (one per SM, persistent over 128-scenario tiles):
 //   RNG warps   regenerate the tile of a_i = s_i zhat_i (Sec. 3.1 samples)
 //               64 dimensions at a time, split each value into bf16 hi + lo
@@ -90,7 +94,6 @@ size_t smem_bytes(int Kp, int nkb) {
 // the per-element guards drop out.
 template <bool F16, int NKB, bool D8>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
-  constexpr bool ONE = NKB <= 2;   // one accumulator per tile, double-buffered (see the MMA role)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // The 128-byte swizzle is address based: operands need a 1024-byte aligned base.
   const uint32_t base = smem_u32(smem_raw);
@@ -150,83 +153,32 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
       const bool b_landed = ok;
       const uint32_t idesc = idesc_f16(kM, a.Kp, F16);
       const uint32_t hl_b = (uint32_t)(a.Kp * 128);
-      if constexpr (ONE) {
-        // One accumulator per tile, two buffers: the small corrections
-        // hi*lo + lo*hi of every K block go in first, then hi*hi, so the
-        // running sum is large for only the 4 nkb hi*hi updates (the bias
-        // of the two-accumulator scheme) and the epilogue of tile t runs
-        // under the MMAs of tile t + 1.  The tile's K blocks (at most two
-        // of the three stages) stay resident until its MMAs complete.
-        int st = 0;
-        uint32_t ph = 0;
-        for (int tt = 0; ok && tt < my_tiles; ++tt) {
-          const int buf = tt & 1;
-          if (tt >= 2) {
-            ok = mbar_wait(smem_u32(&sm->q_empty[buf]), (uint32_t)(((tt - 2) >> 1) & 1), abort_flag, a.err);
-            if (!ok) break;
-          }
-          int sts[2];
-          for (int kb = 0; ok && kb < a.nkb; ++kb) {
-            ok = mbar_wait(smem_u32(&sm->a_full[st]), ph, abort_flag, a.err);
-            sts[kb] = st;
-            if (++st == kStages) { st = 0; ph ^= 1u; }
-          }
+      int tt = 0, kb = 0, st = 0;
+      uint32_t ph = 0;
+      for (int it = 0; ok && it < iters; ++it) {
+        if (kb == 0 && tt > 0) {
+          ok = mbar_wait(smem_u32(&sm->q_empty[0]), (uint32_t)((tt - 1) & 1), abort_flag, a.err);
           if (!ok) break;
-          tc_fence_after();
-          const uint32_t td = tmem + (uint32_t)(buf * a.Kp);
-#pragma unroll
-          for (int kb = 0; kb < NKB; ++kb) {
-            if (kb >= a.nkb) break;
-            const uint64_t dah = desc_sw128(sA + (uint32_t)(sts[kb] * kStageBytes));
-            const uint64_t dal = dah + (uint64_t)((kM * 128) >> 4);
-            const uint64_t dbh = desc_sw128(sB + (uint32_t)(kb * 2) * hl_b);
-            const uint64_t dbl = dbh + (uint64_t)(hl_b >> 4);
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t o = (uint64_t)(kk * 2);   // 32 bytes in the descriptor's 16-byte units
-              mma_bf16(td, dah + o, dbl + o, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
-              mma_bf16(td, dal + o, dbh + o, idesc, 1u);
-            }
-          }
-#pragma unroll
-          for (int kb = 0; kb < NKB; ++kb) {
-            if (kb >= a.nkb) break;
-            const uint64_t dah = desc_sw128(sA + (uint32_t)(sts[kb] * kStageBytes));
-            const uint64_t dbh = desc_sw128(sB + (uint32_t)(kb * 2) * hl_b);
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) mma_bf16(td, dah + (uint64_t)(kk * 2), dbh + (uint64_t)(kk * 2), idesc, 1u);
-          }
-          for (int kb = 0; kb < a.nkb; ++kb) mma_commit(smem_u32(&sm->a_empty[sts[kb]]));
-          mma_commit(smem_u32(&sm->q_full[buf]));
         }
-      } else {
-        int tt = 0, kb = 0, st = 0;
-        uint32_t ph = 0;
-        for (int it = 0; ok && it < iters; ++it) {
-          if (kb == 0 && tt > 0) {
-            ok = mbar_wait(smem_u32(&sm->q_empty[0]), (uint32_t)((tt - 1) & 1), abort_flag, a.err);
-            if (!ok) break;
-          }
-          ok = mbar_wait(smem_u32(&sm->a_full[st]), ph, abort_flag, a.err);
-          if (!ok) break;
-          tc_fence_after();
-          const uint32_t a_hi = sA + (uint32_t)(st * kStageBytes);
-          const uint32_t a_lo = a_hi + kM * 128;
-          const uint32_t b_hi = sB + (uint32_t)(kb * 2) * hl_b;
-          const uint32_t b_lo = b_hi + hl_b;
+        ok = mbar_wait(smem_u32(&sm->a_full[st]), ph, abort_flag, a.err);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t a_hi = sA + (uint32_t)(st * kStageBytes);
+        const uint32_t a_lo = a_hi + kM * 128;
+        const uint32_t b_hi = sB + (uint32_t)(kb * 2) * hl_b;
+        const uint32_t b_lo = b_hi + hl_b;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t o = (uint32_t)(kk * 32);
-            const uint32_t acc0 = (kb == 0 && kk == 0) ? 0u : 1u;
-            mma_bf16(td1, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idesc, acc0);
-            mma_bf16(td2, desc_sw128(a_hi + o), desc_sw128(b_lo + o), idesc, acc0);
-            mma_bf16(td2, desc_sw128(a_lo + o), desc_sw128(b_hi + o), idesc, 1u);
-          }
-          mma_commit(smem_u32(&sm->a_empty[st]));
-          if (kb == a.nkb - 1) mma_commit(smem_u32(&sm->q_full[0]));
-          if (++kb == a.nkb) { kb = 0; ++tt; }
-          if (++st == kStages) { st = 0; ph ^= 1u; }
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t o = (uint32_t)(kk * 32);
+          const uint32_t acc0 = (kb == 0 && kk == 0) ? 0u : 1u;
+          mma_bf16(td1, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idesc, acc0);
+          mma_bf16(td2, desc_sw128(a_hi + o), desc_sw128(b_lo + o), idesc, acc0);
+          mma_bf16(td2, desc_sw128(a_lo + o), desc_sw128(b_hi + o), idesc, 1u);
         }
+        mma_commit(smem_u32(&sm->a_empty[st]));
+        if (kb == a.nkb - 1) mma_commit(smem_u32(&sm->q_full[0]));
+        if (++kb == a.nkb) { kb = 0; ++tt; }
+        if (++st == kStages) { st = 0; ph ^= 1u; }
       }
       // every MMA issued above completes before TMEM is released; after an
       // abort, wait (bounded) for the operand copies still in flight too
@@ -242,27 +194,22 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
 #pragma unroll
     for (int g = 0; g < kMaxKp / 32; ++g) s2h[g] = s2l[g] = 0.0f;
     for (int tt = 0; tt < my_tiles; ++tt) {
-      const int buf = ONE ? (tt & 1) : 0;
-      const uint32_t par = ONE ? (uint32_t)((tt >> 1) & 1) : (uint32_t)(tt & 1);
-      if (!warp_wait(smem_u32(&sm->q_full[buf]), par, abort_flag, a.err)) break;
+      if (!warp_wait(smem_u32(&sm->q_full[0]), (uint32_t)(tt & 1), abort_flag, a.err)) break;
       tc_fence_after();
-      const uint32_t tq = tmem + (uint32_t)(buf * a.Kp);
       // the group loop stays rolled (register pressure); the running sums
       // rotate so that group g's pair is s2h[0] / s2l[0] when it is added
 #pragma unroll 1
       for (int g = 0; g < kMaxKp / 32; ++g) {
         if (32 * g < a.Kp) {
           const uint32_t c0 = (uint32_t)(32 * g);
-          const float cs = ONE ? epi_sq_colsum32_1(tq + lane_base + c0, lane)
-                               : epi_sq_colsum32_x2(td1 + lane_base + c0, td2 + lane_base + c0, lane);
-          ff_add(s2h[0], s2l[0], cs);
+          ff_add(s2h[0], s2l[0], epi_sq_colsum32_x2(td1 + lane_base + c0, td2 + lane_base + c0, lane));
         }
         rot_left(s2h);
         rot_left(s2l);
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty[buf]));
+      if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty[0]));
     }
   } else {
     // ------------------------------------------------------------ RNG ---
@@ -384,6 +331,290 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
     a.part_s2[(size_t)blockIdx.x * a.K + k] = s * a.scale2[k];
   }
   if (warp == kMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
+// ------------------------------------------------------------------------
+// k_tc_value1: the same estimate for d <= 128 (one or two K blocks of 64
+// dimensions per tile), without a dedicated MMA warp: thread 0 of the
+// epilogue issues each tile's MMAs once the tile's stages are drawn, then
+// the four epilogue warps reduce the previous tile.  Fewer warps leave each
+// thread up to 96 registers (no spills).  The three products go to
+// one accumulator per tile, the small corrections hi*lo + lo*hi of every K
+// block first and hi*hi last, so the running sum is large for only 4 nkb
+// updates (the same rounding bias as a separate hi*hi accumulator); two
+// accumulator buffers let the epilogue of one tile run under the MMAs of
+// the next.  The tile's K blocks (at most two of the three stages) stay
+// resident until its MMAs complete.
+// ------------------------------------------------------------------------
+constexpr int kThreads1 = 32 * (kEpiWarps + kRngWarps);
+
+template <bool F16, int NKB, bool D8>
+__global__ void __launch_bounds__(kThreads1, 1) k_tc_value1(Args a) {
+  static_assert(NKB <= 2, "a tile's K blocks must fit in the stage ring with one to spare");
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const uint32_t base = smem_u32(smem_raw);
+  if (base & 1023u) {
+    if (threadIdx.x == 0) atomicOr(a.err, kErrBounds);
+    return;
+  }
+  const int bbytes = a.nkb * 2 * a.Kp * 128;
+  uint8_t* As = smem_raw;
+  Smem* sm = reinterpret_cast<Smem*>(smem_raw + kStages * kStageBytes + bbytes);
+  const uint32_t sA = base, sB = base + (uint32_t)(kStages * kStageBytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const LawArgs& la = a.la;
+  const int d = la.d;
+  volatile uint32_t* abort_flag = &sm->abort_flag;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&sm->a_full[s]), kRngWarps);
+      mbar_init(smem_u32(&sm->a_empty[s]), 1);
+    }
+    for (int s = 0; s < kSBufs; ++s) mbar_init(smem_u32(&sm->s_ready[s]), kM / 32);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&sm->q_full[b]), 1);
+      mbar_init(smem_u32(&sm->q_empty[b]), kEpiWarps);
+    }
+    mbar_init(smem_u32(&sm->b_full), 1);
+    mbar_init(smem_u32(&sm->drain), 1);
+    sm->abort_flag = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const uint32_t ncols = (2 * a.Kp <= 32) ? 32u : (2 * a.Kp <= 64) ? 64u : (2 * a.Kp <= 128) ? 128u
+                       : (2 * a.Kp <= 256) ? 256u : 512u;
+  if (warp == 0) tmem_alloc(smem_u32(&sm->tmem_base), ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm->tmem_base;
+  const int my_tiles = (int)((a.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+  const int iters = my_tiles * a.nkb;
+  float macc[NKB][8];                          // generator: per-dimension sums of a_i
+  float s2h[kMaxKp / 32], s2l[kMaxKp / 32];    // epilogue: S2 of column 32 g + epi_col(lane)
+
+  if (warp < kEpiWarps) {
+    // ------------------------------------------- MMA issue + epilogue ---
+    const bool issuer = threadIdx.x == 0;
+    const uint32_t bb = smem_u32(&sm->b_full);
+    bool mma_ok = true, b_landed = false;
+    if (issuer) {
+      mbar_expect_tx(bb, (uint32_t)bbytes);
+      for (int off = 0; off < bbytes; off += 32768) {
+        const int n = min(32768, bbytes - off);
+        bulk_g2s(sB + (uint32_t)off, a.bimage + off, (uint32_t)n, bb);
+      }
+      mma_ok = b_landed = mbar_wait(bb, 0, abort_flag, a.err);
+    }
+    const uint32_t idesc = idesc_f16(kM, a.Kp, F16);
+    const uint32_t hl_b = (uint32_t)(a.Kp * 128);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+    for (int g = 0; g < kMaxKp / 32; ++g) s2h[g] = s2l[g] = 0.0f;
+    int st = 0;
+    uint32_t ph = 0;
+    for (int tt = 0; tt <= my_tiles; ++tt) {
+      if (issuer && mma_ok && tt < my_tiles) {
+        // ---- the MMAs of tile tt into accumulator buffer tt & 1
+        const int buf = tt & 1;
+        if (tt >= 2)
+          mma_ok = mbar_wait(smem_u32(&sm->q_empty[buf]), (uint32_t)(((tt - 2) >> 1) & 1), abort_flag, a.err);
+        int sts[NKB];
+#pragma unroll
+        for (int kb = 0; kb < NKB; ++kb) {
+          if (kb < a.nkb && mma_ok) {
+            mma_ok = mbar_wait(smem_u32(&sm->a_full[st]), ph, abort_flag, a.err);
+            sts[kb] = st;
+            if (++st == kStages) { st = 0; ph ^= 1u; }
+          }
+        }
+        if (mma_ok) {
+          tc_fence_after();
+          const uint32_t td = tmem + (uint32_t)(buf * a.Kp);
+#pragma unroll
+          for (int kb = 0; kb < NKB; ++kb) {
+            if (kb < a.nkb) {
+              const uint64_t dah = desc_sw128(sA + (uint32_t)(sts[kb] * kStageBytes));
+              const uint64_t dal = dah + (uint64_t)((kM * 128) >> 4);
+              const uint64_t dbh = desc_sw128(sB + (uint32_t)(kb * 2) * hl_b);
+              const uint64_t dbl = dbh + (uint64_t)(hl_b >> 4);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t o = (uint64_t)(kk * 2);   // 32 bytes in the descriptor's 16-byte units
+                mma_bf16(td, dah + o, dbl + o, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
+                mma_bf16(td, dal + o, dbh + o, idesc, 1u);
+              }
+            }
+          }
+#pragma unroll
+          for (int kb = 0; kb < NKB; ++kb) {
+            if (kb < a.nkb) {
+              const uint64_t dah = desc_sw128(sA + (uint32_t)(sts[kb] * kStageBytes));
+              const uint64_t dbh = desc_sw128(sB + (uint32_t)(kb * 2) * hl_b);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                mma_bf16(td, dah + (uint64_t)(kk * 2), dbh + (uint64_t)(kk * 2), idesc, 1u);
+            }
+          }
+#pragma unroll
+          for (int kb = 0; kb < NKB; ++kb)
+            if (kb < a.nkb) mma_commit(smem_u32(&sm->a_empty[sts[kb]]));
+          mma_commit(smem_u32(&sm->q_full[buf]));
+        }
+      }
+      __syncwarp();
+      if (tt == 0) continue;
+      // ---- S2 of tile tt - 1
+      const int te = tt - 1, buf = te & 1;
+      if (!warp_wait(smem_u32(&sm->q_full[buf]), (uint32_t)((te >> 1) & 1), abort_flag, a.err)) break;
+      tc_fence_after();
+      const uint32_t tq = tmem + (uint32_t)(buf * a.Kp) + lane_base;
+      // the group loop stays rolled (register pressure); the running sums
+      // rotate so that group g's pair is s2h[0] / s2l[0] when it is added
+#pragma unroll 1
+      for (int g = 0; g < kMaxKp / 32; ++g) {
+        if (32 * g < a.Kp) ff_add(s2h[0], s2l[0], epi_sq_colsum32_1(tq + (uint32_t)(32 * g), lane));
+        rot_left(s2h);
+        rot_left(s2l);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty[buf]));
+    }
+    if (issuer) {
+      // every MMA issued above completes before TMEM is released; after an
+      // abort, wait (bounded) for the operand copies still in flight too
+      mma_commit(smem_u32(&sm->drain));
+      uint32_t never = 0u;
+      mbar_wait(smem_u32(&sm->drain), 0, &never, a.err);
+      if (!b_landed) mbar_wait(bb, 0, &never, a.err);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ RNG ---
+    const int rt = threadIdx.x - 32 * kEpiWarps;       // 0 .. kRngThreads-1
+    const int cu = rt & 7;                             // 16-byte unit (8 dims) within the K block
+    const int r0 = rt >> 3;                            // this thread's rows r0, r0 + kRngThreads / 8, ...
+    const gen::Stream gs = gen::make_stream(la.seed, la.epoch, la.instance);
+    const uint32_t half = la.N / 2u;
+    const bool tlaw = la.law == SAA_LAW_STUDENT_T;
+#pragma unroll
+    for (int b = 0; b < NKB; ++b)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) macc[b][e] = 0.0f;
+    int tt = 0, kb = 0, st = 0;
+    uint32_t ph = 0;
+    for (int it = 0; it < iters; ++it) {
+      const uint32_t tile = blockIdx.x + (uint32_t)tt * gridDim.x;
+      const uint32_t i0 = la.i_base + tile * (uint32_t)kM;
+      const int nrow = (int)min((uint32_t)kM, la.rows_end() - i0);
+      const int sb = tt & (kSBufs - 1);
+      const uint32_t s_bar = smem_u32(&sm->s_ready[sb]);
+      if (tlaw && kb == 0 && rt < kM) {   // generator warps 0..3 draw the tile's scales
+        sm->s_buf[sb][rt] = (rt < nrow) ? gen::t_scale_f(gs, i0 + (uint32_t)rt, la.nu) : 0.0f;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(s_bar);
+      }
+      if (!warp_wait(smem_u32(&sm->a_empty[st]), ph ^ 1u, abort_flag, a.err)) break;
+      if (tlaw && !warp_wait(s_bar, (uint32_t)((tt >> 2) & 1), abort_flag, a.err)) break;
+      uint8_t* stage = As + st * kStageBytes;
+      const int j0 = kb * kKB + cu * 8;   // first dimension of this unit
+      float vs[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) vs[e] = 0.0f;
+      const bool unit_ok = j0 < d;
+#pragma unroll 1
+      for (int r = r0; r < kM; r += kRngThreads / 8) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0.0f;
+        if (r < nrow && unit_ok) {
+          const uint32_t i = i0 + (uint32_t)r;
+          const bool logn = gen::is_lognormal(la.law, i, half);
+          float z[4];
+          gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2), i, logn, z);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[e] = (D8 || j0 + e < d) ? z[e] : 0.0f;
+          if (D8 || j0 + 4 < d) {
+            gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2) + 1u, i, logn, z);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[4 + e] = (D8 || j0 + 4 + e < d) ? z[e] : 0.0f;
+          }
+          if (tlaw) {
+            const float sv = sm->s_buf[sb][r];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] *= sv;
+          }
+        }
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+          hi[e / 2] = pack2<F16>(v[e], v[e + 1]);
+          const float2 h = unpack2<F16>(hi[e / 2]);
+          lo[e / 2] = pack2<F16>(v[e] - h.x, v[e + 1] - h.y);
+        }
+        const uint32_t off = sw_off(r, cu);
+        *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(stage + kM * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) vs[e] += v[e];
+      }
+#pragma unroll
+      for (int b = 0; b < NKB; ++b)
+        if (b == kb)
+#pragma unroll
+          for (int e = 0; e < 8; ++e) macc[b][e] += vs[e];
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&sm->a_full[st]));
+      if (++kb == a.nkb) { kb = 0; ++tt; }
+      if (++st == kStages) { st = 0; ph ^= 1u; }
+    }
+    // lanes with equal rt & 7 hold the same unit: fold them (lanes 0..7 keep the sums)
+#pragma unroll
+    for (int b = 0; b < NKB; ++b)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        float v = macc[b][e];
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        macc[b][e] = v;
+      }
+  }
+
+  // ----------------------------------------------------- CTA reductions ---
+  __syncthreads();   // MMAs drained: the A stages are free for the reductions
+  const int dpad = a.nkb * kKB;
+  double* red_s2 = reinterpret_cast<double*>(As);      // [kEpiWarps][Kp]
+  float* red_m = reinterpret_cast<float*>(red_s2 + kEpiWarps * a.Kp);   // [kRngWarps][dpad]
+  if (warp >= kEpiWarps && lane < 8) {
+    const int rw = warp - kEpiWarps;
+#pragma unroll
+    for (int b = 0; b < NKB; ++b)
+      if (b < a.nkb)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) red_m[rw * dpad + b * kKB + lane * 8 + e] = macc[b][e];
+  }
+  if (warp < kEpiWarps) {
+#pragma unroll
+    for (int g = 0; g < kMaxKp / 32; ++g)
+      if (32 * g < a.Kp) red_s2[warp * a.Kp + 32 * g + epi_col(lane)] = (double)s2h[g] + (double)s2l[g];
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    double s = 0.0;
+    for (int rw = 0; rw < kRngWarps; ++rw) s += (double)red_m[rw * dpad + j];
+    a.part_m[(size_t)blockIdx.x * d + j] = s;
+  }
+  for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < kEpiWarps; ++w) s += red_s2[w * a.Kp + k];
+    a.part_s2[(size_t)blockIdx.x * a.K + k] = s * a.scale2[k];
+  }
+  if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, ncols);
   }
@@ -540,17 +771,22 @@ cudaError_t launch_tc(const LawArgs& la, int K, int prec, const Plan& plan, cons
   cudaError_t e = launch_tc_image(la.d, K, a.Kp, a.nkb, f16, ws.Y64, scale2, nullptr, img, st);
   if (e != cudaSuccess) return e;
   const bool d8 = (la.d & 7) == 0;
-  auto kern = f16 ? (d8 ? (a.nkb == 1 ? tc::k_tc_value<true, 1, true> : a.nkb == 2 ? tc::k_tc_value<true, 2, true>
-                                                                                  : tc::k_tc_value<true, 4, true>)
-                        : (a.nkb == 1 ? tc::k_tc_value<true, 1, false> : a.nkb == 2 ? tc::k_tc_value<true, 2, false>
-                                                                                   : tc::k_tc_value<true, 4, false>))
-                  : (d8 ? (a.nkb == 1 ? tc::k_tc_value<false, 1, true> : a.nkb == 2 ? tc::k_tc_value<false, 2, true>
-                                                                                   : tc::k_tc_value<false, 4, true>)
-                        : (a.nkb == 1 ? tc::k_tc_value<false, 1, false>
-                                      : a.nkb == 2 ? tc::k_tc_value<false, 2, false> : tc::k_tc_value<false, 4, false>));
+  void (*kern)(tc::Args);
+  int threads = tc::kThreads1;
+  if (a.nkb == 1)
+    kern = f16 ? (d8 ? tc::k_tc_value1<true, 1, true> : tc::k_tc_value1<true, 1, false>)
+               : (d8 ? tc::k_tc_value1<false, 1, true> : tc::k_tc_value1<false, 1, false>);
+  else if (a.nkb == 2)
+    kern = f16 ? (d8 ? tc::k_tc_value1<true, 2, true> : tc::k_tc_value1<true, 2, false>)
+               : (d8 ? tc::k_tc_value1<false, 2, true> : tc::k_tc_value1<false, 2, false>);
+  else {
+    kern = f16 ? (d8 ? tc::k_tc_value<true, 4, true> : tc::k_tc_value<true, 4, false>)
+               : (d8 ? tc::k_tc_value<false, 4, true> : tc::k_tc_value<false, 4, false>);
+    threads = tc::kThreadsTc;
+  }
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
   if (e != cudaSuccess) return e;
-  kern<<<plan.grid, tc::kThreadsTc, plan.smem, st>>>(a);
+  kern<<<plan.grid, threads, plan.smem, st>>>(a);
   return cudaGetLastError();
 }
 
