@@ -76,7 +76,14 @@ typedef enum {
     SAA_BF16X3 = 2, /* FP32 normals, BF16 hi/lo split contraction on tcgen05 tensor cores
                        (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM), FP64 reduction;
                        relative error of the estimates within 5e-5 */
-    SAA_FP8X = 3,   /* reserved: FP8 E4M3 scaled contraction with hi/lo refinement */
+    SAA_FP8X = 3,   /* streamed mode only (saa_eval_samples): E4M3 contraction, samples split
+                       hi + lo, decisions in three terms, four products (A1 B1 + A1 B2 +
+                       A2 B1 + A1 B3) on kind::f8f6f4, power-of-two column and decision
+                       scales, FP32 accumulation in TMEM; centred and scaled samples
+                       required.  The sample-side rounding (2^-8 per element) averages over
+                       the scenarios: relative error of the estimates within 1e-4 from
+                       N of a few thousand; every other entry point returns
+                       SAA_EUNSUPPORTED for it */
     SAA_F16X3 = 4   /* as SAA_BF16X3 with FP16 hi/lo operands and a power-of-two scale per
                        decision: relative error of the estimates within 1e-6 */
 } saa_prec;
@@ -325,13 +332,16 @@ saa_status saa_generate(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64
  *   sigma    device [d] FP64 or NULL (1): per-column spreads; column j is
  *            multiplied by 2^-a_j and x_kj by 2^a_j, 2^(a_j-1) < sigma_j <=
  *            2^a_j (exact), so the split products stay in range.  At
- *            SAA_F16X3 every |R_ij - c_j| 2^-a_j must be below 2^15
- *            (violations and sigma_j outside [2^-100, 2^100] or not finite
- *            are reported by the next saa_ctx_sync as SAA_EDEVICE)
+ *            SAA_F16X3 every |R_ij - c_j| 2^-a_j must be below 2^15, at
+ *            SAA_FP8X at most 448 (E4M3's largest finite value); violations
+ *            and sigma_j outside [2^-100, 2^100] or not finite are reported
+ *            by the next saa_ctx_sync as SAA_EDEVICE
  *   X        device [K*d] FP64 decisions w_k (the scenario vector already
  *            holds the returns: no mu or C is applied)
  *   lambda   risk weight of Eq. 2
- *   prec     SAA_F16X3 or SAA_BF16X3 (operand type of the hi/lo products)
+ *   prec     SAA_F16X3, SAA_BF16X3 (operand type of the hi/lo products) or
+ *            SAA_FP8X (E4M3 products; center and sigma must then both be
+ *            given, else SAA_EINVAL)
  *   f, pbar, var  device [K] FP64, each optional: lambda V - pbar, the
  *            sample mean of R_i'x_k, and its unbiased sample variance
  *   ws       device scratch of saa_eval_samples_workspace_size() bytes,

@@ -59,6 +59,8 @@ saa_status make_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec p
       return fail(SAA_EUNSUPPORTED, "tensor-core path: this d/K/gradient combination is not built");
     return tc_plan(ctx, p, K, plan);
   }
+  if (prec == SAA_FP8X)
+    return fail(SAA_EUNSUPPORTED, "SAA_FP8X runs in the streamed mode only (saa_eval_samples)");
   if (prec != SAA_FP32 && prec != SAA_FP64) return fail(SAA_EUNSUPPORTED, "precision not built");
   if (p->d > kMaxDimSimt) return fail(SAA_EUNSUPPORTED, "d exceeds saa_max_dim for this precision");
   plan->bm = simt_bm(prec, p->d);

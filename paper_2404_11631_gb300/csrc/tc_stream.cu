@@ -97,8 +97,12 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int 
       : "memory");
 }
 
-template <bool F16, int NKB>
+// P: 0 BF16 hi/lo, 1 FP16 hi/lo (three products each), 2 E4M3 (samples
+// split hi/lo, decisions in three terms, four products).
+template <int P, int NKB>
 __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __grid_constant__ CUtensorMap tmap) {
+  constexpr bool F16 = P == 1;
+  constexpr bool F8 = P == 2;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t base = smem_u32(smem_raw);
   if (base & 1023u) {
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sm->tmem_base;
-  const int nh = a.Kp > 128 ? 2 : 1;   // column halves per tile
+  const int nh = (!F8 && a.Kp > 128) ? 2 : 1;   // column halves per tile (E4M3: one accumulator, whole tile)
   const int my_tiles = (int)((a.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
   const int iters = my_tiles * a.nkb;
   float s2h[kSMaxKp / 32 / kSEpiStride], s2l[kSMaxKp / 32 / kSEpiStride];   // epilogue: S2 (float-float)
@@ -163,8 +167,8 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
       }
       bool ok = mbar_wait(bb, 0, abort_flag, a.err);
       const bool b_landed = ok;
-      const uint32_t idesc0 = idesc_f16(kSM, nh == 2 ? 128 : a.Kp, F16);
-      const uint32_t idesc1 = idesc_f16(kSM, nh == 2 ? a.Kp - 128 : a.Kp, F16);
+      const uint32_t idesc0 = F8 ? idesc_e4m3(kSM, a.Kp) : idesc_f16(kSM, nh == 2 ? 128 : a.Kp, F16);
+      const uint32_t idesc1 = F8 ? idesc0 : idesc_f16(kSM, nh == 2 ? a.Kp - 128 : a.Kp, F16);
       const uint32_t hl_b = (uint32_t)(a.Kp * 128);
       int tt = 0, kb = 0, st = 0;
       uint32_t ph = 0;
@@ -194,13 +198,29 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
           const uint32_t d1 = tmem + 256u * (uint32_t)sl, d2 = d1 + 128u;
           const uint32_t bo = (uint32_t)h * (128u * 128u);   // decision rows 128 h ..
           const uint32_t idesc = h == 0 ? idesc0 : idesc1;
+          if constexpr (F8) {
+            // A rows [A1 | A2], decision planes [B1 | B1] (b_hi) and
+            // [B2 | B3] (b_lo), 64 dimensions per half, 32 per step:
+            // A1 B3 + A1 B2, then A1 B1 + A2 B1 over the whole row
+            const uint32_t acc0 = kb == 0 ? 0u : 1u;
+            mma_e4m3(d1, desc_sw128(a_hi), desc_sw128(b_lo + 64u), idesc, acc0);
+            mma_e4m3(d1, desc_sw128(a_hi + 32u), desc_sw128(b_lo + 96u), idesc, 1u);
+            mma_e4m3(d1, desc_sw128(a_hi), desc_sw128(b_lo), idesc, 1u);
+            mma_e4m3(d1, desc_sw128(a_hi + 32u), desc_sw128(b_lo + 32u), idesc, 1u);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t o = (uint32_t)(kk * 32);
-            const uint32_t acc0 = (kb == 0 && kk == 0) ? 0u : 1u;
-            mma_bf16(d1, desc_sw128(a_hi + o), desc_sw128(b_hi + bo + o), idesc, acc0);
-            mma_bf16(d2, desc_sw128(a_hi + o), desc_sw128(b_lo + bo + o), idesc, acc0);
-            mma_bf16(d2, desc_sw128(a_lo + o), desc_sw128(b_hi + bo + o), idesc, 1u);
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t o = (uint32_t)(kk * 32);
+              mma_e4m3(d1, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idesc, 1u);
+            }
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t o = (uint32_t)(kk * 32);
+              const uint32_t acc0 = (kb == 0 && kk == 0) ? 0u : 1u;
+              mma_bf16(d1, desc_sw128(a_hi + o), desc_sw128(b_hi + bo + o), idesc, acc0);
+              mma_bf16(d2, desc_sw128(a_hi + o), desc_sw128(b_lo + bo + o), idesc, acc0);
+              mma_bf16(d2, desc_sw128(a_lo + o), desc_sw128(b_hi + bo + o), idesc, 1u);
+            }
           }
           if (kb == a.nkb - 1) mma_commit(smem_u32(&sm->q_full[sl]));
         }
@@ -267,7 +287,10 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
         for (int g = gb + g0; g < ge; g += kSEpiStride) {
           if (32 * g < a.Kp) {
             const uint32_t c = (uint32_t)(32 * g - 128 * h);
-            ff_add(s2h[0], s2l[0], epi_sq_colsum32_x2(d1 + c, d2 + c, lane));
+            if constexpr (F8)
+              ff_add(s2h[0], s2l[0], epi_sq_colsum32_1(d1 + c, lane));
+            else
+              ff_add(s2h[0], s2l[0], epi_sq_colsum32_x2(d1 + c, d2 + c, lane));
           }
           rot_left(s2h);
           rot_left(s2l);
@@ -317,7 +340,35 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
       for (int e = 0; e < 16; ++e) {
         v[e] = row_ok ? v[e] : 0.0f;
         if constexpr (F16) in_range = in_range && fabsf(v[e]) < 32768.0f;
+        if constexpr (F8) in_range = in_range && fabsf(v[e]) <= 448.0f;
       }
+      if constexpr (F8) {
+        // E4M3 hi + lo of each value; the row's 128 bytes become [A1 | A2]:
+        // this thread's 16 dimensions 16 q .. 16 q + 15 are unit q of A1 and
+        // unit 4 + q of A2 (v[] holds their two 8-column halves swapped when
+        // hsw is set)
+        uint32_t h8[4], l8[4];   // byte quads: dims (of v) 4 w .. 4 w + 3
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          uint32_t hq = 0u, lq = 0u;
+#pragma unroll
+          for (int t = 0; t < 4; t += 2) {
+            const int e = 4 * w + t;
+            const uint32_t hp = e4m3x2(v[e], v[e + 1]);
+            const float2 hf = e4m3x2_to_f2(hp);
+            const uint32_t lp = e4m3x2(v[e] - hf.x, v[e + 1] - hf.y);
+            hq |= hp << (8 * t);
+            lq |= lp << (8 * t);
+          }
+          h8[w] = hq;
+          l8[w] = lq;
+        }
+        __syncwarp();   // every thread of these rows has read its FP32 values
+        const uint4 hu = hsw ? make_uint4(h8[2], h8[3], h8[0], h8[1]) : make_uint4(h8[0], h8[1], h8[2], h8[3]);
+        const uint4 lu = hsw ? make_uint4(l8[2], l8[3], l8[0], l8[1]) : make_uint4(l8[0], l8[1], l8[2], l8[3]);
+        *reinterpret_cast<uint4*>(stage + sw_off(r, q)) = hu;
+        *reinterpret_cast<uint4*>(stage + sw_off(r, 4 + q)) = lu;
+      } else {
       uint32_t hi[8], lo[8];
 #pragma unroll
       for (int e = 0; e < 16; e += 2) {
@@ -333,6 +384,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
       *reinterpret_cast<uint4*>(hrow + sw_off(r, ub)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
       *reinterpret_cast<uint4*>(lrow + sw_off(r, ua)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
       *reinterpret_cast<uint4*>(lrow + sw_off(r, ub)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+      }
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sm->a_full[st]));
@@ -440,6 +492,70 @@ __global__ void k_stream_prep(int K, int d, int dpad, const double* __restrict__
     int e = sigma ? spread_exp(sigma[j]) : 0;
     if (e == -1000) e = 0;
     Xs[u] = ldexp(X[u], e);
+  }
+}
+
+// Decision operand image for the E4M3 products, one block per padded
+// decision row n: e_n with max_j |x'_nj| 2^-e_n in [1, 2) (0 for a zero row),
+// y = x'_n 2^(7 - e_n) (largest entry in [128, 256), inside E4M3's 448),
+// split in FP64 into three E4M3 terms, y = B1 + B2 + B3 + r with |r| about
+// 2^-12 |y| (each residual is exact in FP64), scale2[n] = 4^(e_n - 7).  Per
+// K block two planes of Kp rows x 128 B in the 128-byte-swizzled K-major
+// order: rows [B1 | B1] and [B2 | B3], 64 dimensions in each half, so that
+// one pass over a sample row [A1 | A2] against the first plane gives
+// A1 B1 + A2 B1.  Rows n >= K and dimensions j >= d are zero.
+__global__ void __launch_bounds__(64) k_stream_image8(int d, int K, int Kp, int nkb, const double* __restrict__ Y64,
+                                                      double* __restrict__ scale2, uint8_t* __restrict__ img) {
+  __shared__ double wmax[2];
+  const int n = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  double m = 0.0;
+  if (n < K)
+    for (int j = threadIdx.x; j < d; j += blockDim.x) m = fmax(m, fabs(Y64[(size_t)n * d + j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = fmax(wmax[0], wmax[1]);
+  const int e = (m > 0.0) ? ilogb(m) : 0;
+  const double sc = ldexp(1.0, 7 - e);   // exact
+  if (threadIdx.x == 0 && n < K) scale2[n] = ldexp(1.0, 2 * (e - 7));
+  for (int grp = threadIdx.x; grp < nkb * 4; grp += blockDim.x) {
+    const int kb = grp >> 2, g = grp & 3;   // dimensions 64 kb + 16 g .. + 15
+    uint32_t w1[4], w2[4], w3[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      uint32_t b1 = 0u, b2 = 0u, b3 = 0u;
+#pragma unroll
+      for (int t = 0; t < 4; t += 2) {
+        double y[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int j = kb * tc::kSKB + 16 * g + 4 * w + t + u;
+          y[u] = (n < K && j < d) ? Y64[(size_t)n * d + j] * sc : 0.0;
+        }
+        const uint32_t p1 = tc::e4m3x2((float)y[0], (float)y[1]);
+        const float2 f1 = tc::e4m3x2_to_f2(p1);
+        const double r0 = y[0] - (double)f1.x, r1 = y[1] - (double)f1.y;
+        const uint32_t p2 = tc::e4m3x2((float)r0, (float)r1);
+        const float2 f2 = tc::e4m3x2_to_f2(p2);
+        const uint32_t p3 = tc::e4m3x2((float)(r0 - (double)f2.x), (float)(r1 - (double)f2.y));
+        b1 |= p1 << (8 * t);
+        b2 |= p2 << (8 * t);
+        b3 |= p3 << (8 * t);
+      }
+      w1[w] = b1;
+      w2[w] = b2;
+      w3[w] = b3;
+    }
+    const size_t blk = (size_t)kb * 2 * Kp * 128;
+    const uint32_t o_a = (uint32_t)(n * 128 + ((g ^ (n & 7)) << 4));
+    const uint32_t o_b = (uint32_t)(n * 128 + (((4 + g) ^ (n & 7)) << 4));
+    const uint4 u1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    *reinterpret_cast<uint4*>(img + blk + o_a) = u1;
+    *reinterpret_cast<uint4*>(img + blk + o_b) = u1;
+    *reinterpret_cast<uint4*>(img + blk + (size_t)Kp * 128 + o_a) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+    *reinterpret_cast<uint4*>(img + blk + (size_t)Kp * 128 + o_b) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
   }
 }
 
@@ -560,8 +676,8 @@ saa_status stream_check(const saa_ctx* ctx, int64_t N, int d, int K, saa_prec pr
     set_error("saa_eval_samples: need 2 <= N < 2^31, d >= 4 a multiple of 4 (16-byte rows for TMA), K >= 1");
     return SAA_EINVAL;
   }
-  if (!is_tc(prec)) {
-    set_error("saa_eval_samples: streamed samples run at SAA_F16X3 or SAA_BF16X3");
+  if (!is_tc(prec) && prec != SAA_FP8X) {
+    set_error("saa_eval_samples: streamed samples run at SAA_F16X3, SAA_BF16X3 or SAA_FP8X");
     return SAA_EUNSUPPORTED;
   }
   const SPlan p = stream_plan(ctx, N, d, K);
@@ -592,6 +708,10 @@ extern "C" saa_status saa_eval_samples(saa_ctx* ctx, int64_t N, int32_t d, const
   if (s != SAA_OK) return s;
   if (!R || (((uintptr_t)R) & 15u) || !X || !ws || (((uintptr_t)ws) & 255u)) {
     set_error("saa_eval_samples: R (16-byte aligned), X and a 256-byte aligned ws are required");
+    return SAA_EINVAL;
+  }
+  if (prec == SAA_FP8X && (!center || !sigma)) {
+    set_error("saa_eval_samples: SAA_FP8X needs center and sigma (E4M3 keeps 1e-4 only on centred, scaled samples)");
     return SAA_EINVAL;
   }
   const SPlan p = stream_plan(ctx, N, d, K);
@@ -636,11 +756,19 @@ extern "C" saa_status saa_eval_samples(saa_ctx* ctx, int64_t N, int32_t d, const
   double* tot_m = (double*)(w + p.tots);
   cudaStream_t st = (cudaStream_t)stream;
   const bool f16 = prec == SAA_F16X3;
+  const bool f8 = prec == SAA_FP8X;
   const int64_t nprep = p.dpad + (int64_t)K * d;
   k_stream_prep<<<(unsigned)((nprep + 255) / 256), 256, 0, st>>>(K, d, p.dpad, center, sigma, X, cf, isf, ncs,
                                                                 Xs, ctx->err);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_tc_image(d, K, p.Kp, p.nkb, f16, Xs, scale2, nullptr, img, st);
+  if (e == cudaSuccess) {
+    if (f8) {
+      k_stream_image8<<<p.Kp, 64, 0, st>>>(d, K, p.Kp, p.nkb, Xs, scale2, img);
+      e = cudaGetLastError();
+    } else {
+      e = launch_tc_image(d, K, p.Kp, p.nkb, f16, Xs, scale2, nullptr, img, st);
+    }
+  }
   tc::SArgs a;
   a.d = d;
   a.K = K;
@@ -656,10 +784,9 @@ extern "C" saa_status saa_eval_samples(saa_ctx* ctx, int64_t N, int32_t d, const
   a.part_s2 = part_s2;
   a.part_m = part_m;
   a.err = ctx->err;
-  auto kern = f16 ? (p.nkb == 1 ? tc::k_tc_stream<true, 1> : p.nkb == 2 ? tc::k_tc_stream<true, 2>
-                                                                        : tc::k_tc_stream<true, 4>)
-                  : (p.nkb == 1 ? tc::k_tc_stream<false, 1> : p.nkb == 2 ? tc::k_tc_stream<false, 2>
-                                                                         : tc::k_tc_stream<false, 4>);
+  auto kern = f8 ? (p.nkb == 1 ? tc::k_tc_stream<2, 1> : p.nkb == 2 ? tc::k_tc_stream<2, 2> : tc::k_tc_stream<2, 4>)
+            : f16 ? (p.nkb == 1 ? tc::k_tc_stream<1, 1> : p.nkb == 2 ? tc::k_tc_stream<1, 2> : tc::k_tc_stream<1, 4>)
+                  : (p.nkb == 1 ? tc::k_tc_stream<0, 1> : p.nkb == 2 ? tc::k_tc_stream<0, 2> : tc::k_tc_stream<0, 4>);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
   const bool prof = ctx->prof_on && ctx->prof_n < 256;
   if (e == cudaSuccess) {

@@ -659,7 +659,8 @@ def saa_eval_samples(R: torch.Tensor, X: torch.Tensor, lam: float, prec="f16x3",
     float64.  ``center`` [d] float64 (e.g. the samples' mean) is subtracted
     before the split-precision contraction and ``sigma`` [d] float64 (e.g.
     per-column standard deviations) sets the exact power-of-two column
-    scaling; neither changes the result beyond rounding."""
+    scaling; neither changes the result beyond rounding.  ``prec`` "fp8x"
+    (E4M3 products) needs both."""
     if not (R.is_cuda and R.dtype == torch.float32 and R.is_contiguous() and R.dim() == 2):
         raise ValueError("R must be a contiguous float32 CUDA tensor [N, d]")
     N, d = int(R.shape[0]), int(R.shape[1])
