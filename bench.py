@@ -756,6 +756,13 @@ def run_covariance(args, dev, world, rank, flush, stream):
         "method": "M = sum a a' once on tcgen05, then S2 = y'My, G = My per decision in FP64"}, **res}
 
 
+# DRAM bytes (read + write) per launch of the streamed kernel on the bench's
+# workload (d = 128, N = 2^20, K = 256), from one ncu capture at full size
+# (dram__bytes_read.sum + dram__bytes_write.sum): the algorithmic N d 4 =
+# 536,870,912 B of samples plus the decision image and the partials.
+STREAM_TRAFFIC = {("fp8x", 128, 1 << 20, 256): 537204736.0}
+
+
 def run_streamed(args, dev, world, rank, flush, stream):
     """Streamed mode on the value workload's shape (d = 128, N = 2^20,
     K = 256): the N samples R_i are materialised once in HBM as FP32 rows
@@ -806,6 +813,7 @@ def run_streamed(args, dev, world, rank, flush, stream):
             roof = {"bound": "hbm", "achieved": hbm_bytes / kern_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": hbm_bytes / kern_s / 1e9 / peaks["hbm_gbs"]}
         roof["peak_source"] = {"hbm": src, "tensor": tc_src}
+        roof["traffic"] = STREAM_TRAFFIC.get((pr, d, N, K))
         roof["hbm"] = {"achieved_gbs": hbm_bytes / kern_s / 1e9, "frac": hbm_bytes / kern_s / 1e9 / peaks["hbm_gbs"]}
         roof["tensor"] = {"achieved_tflops": tc_flops / kern_s / 1e12, "frac": tc_flops / kern_s / 1e12 / tc_peak,
                           "products": products}
