@@ -101,8 +101,8 @@ struct GSmem {
   uint64_t s_ready[2];         // t-law scales of a tile
   uint64_t y_full;             // decision-operand slice landed
   uint64_t q_full, q_empty;    // forward accumulators
-  uint64_t x_full;             // every CTA's partial rows are in this CTA's inbox (4 C arrivals)
-  uint64_t w_full;             // every CTA's rows of W are in this CTA's W (4 C arrivals)
+  uint64_t x_full;             // every CTA's partial rows are in this CTA's inbox (4 arrivals + bytes)
+  uint64_t w_full;             // every CTA's rows of W are in this CTA's W (4 arrivals + bytes)
   uint64_t w_free;             // every CTA's adjoint of the tile is done (C multicast commits)
   uint64_t g_full, g_empty;    // per-tile block of G
   uint64_t drain, drain_adj;   // forward / adjoint MMAs complete (end of kernel)
@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
     mbar_init(smem_u32(&sm->y_full), 1);
     mbar_init(smem_u32(&sm->q_full), 1);
     mbar_init(smem_u32(&sm->q_empty), kGEpiWarps);
-    mbar_init(smem_u32(&sm->x_full), kGEpiWarps * C);
-    mbar_init(smem_u32(&sm->w_full), kGEpiWarps * C);
+    mbar_init(smem_u32(&sm->x_full), kGEpiWarps);
+    mbar_init(smem_u32(&sm->w_full), kGEpiWarps);
     mbar_init(smem_u32(&sm->w_free), C);
     mbar_init(smem_u32(&sm->g_full), 1);
     mbar_init(smem_u32(&sm->g_empty), kGEpiWarps);
@@ -260,10 +260,14 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
     bool adj_issued = false;
     int tt = 0;
     for (; tt < my_tiles; ++tt) {
-      // ---- this CTA's partial Q of every row into the inbox of the row's owner
+      // ---- this CTA's partial Q of every row: its own rows straight into its
+      // inbox, every other owner's rows staged in W (free: this CTA's last
+      // adjoint is done) in the inbox's layout, then one bulk copy per half
+      // block into the owner's inbox, completing bytes of its x_full
       if (!warp_wait(smem_u32(&sm->q_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
       if (tt > 0 && !warp_wait_cluster(smem_u32(&sm->w_full), (uint32_t)((tt - 1) & 1), abort_flag, a.err)) break;
       tc_fence_after();
+      const uint32_t half = (uint32_t)nr * 128u;   // bytes of half an owner's block
 #pragma unroll 1
       for (uint32_t c0 = 0; c0 < (uint32_t)kGKp; c0 += 16) {
         uint32_t r1v[16], r2v[16];
@@ -277,28 +281,47 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
           q.y = __uint_as_float(r1v[4 * u + 1]) + __uint_as_float(r2v[4 * u + 1]);
           q.z = __uint_as_float(r1v[4 * u + 2]) + __uint_as_float(r2v[4 * u + 2]);
           q.w = __uint_as_float(r1v[4 * u + 3]) + __uint_as_float(r2v[4 * u + 3]);
-          const uint32_t off = inbox_off((int)rank, nr, lrow, (int)c0 + 4 * u);
-          if (C == 1)
-            *reinterpret_cast<float4*>(inbox + off) = q;
-          else
-            st_cluster_v4(mapa(sIn + 4u * off, (uint32_t)own),
-                          make_uint4(__float_as_uint(q.x), __float_as_uint(q.y), __float_as_uint(q.z),
-                                     __float_as_uint(q.w)));
+          const uint32_t off = inbox_off(0, nr, lrow, (int)c0 + 4 * u);   // float offset in the block
+          if (own == (int)rank) {
+            *reinterpret_cast<float4*>(inbox + (uint32_t)(own * nr * kGKp) + off) = q;
+          } else {
+            const uint32_t bo = 4u * off;
+            const uint32_t so = bo < half ? (uint32_t)own * half + bo : wchunk + (uint32_t)own * half + (bo - half);
+            *reinterpret_cast<float4*>(wbuf + so) = q;
+          }
         }
       }
       tc_fence_before();
+      fence_proxy_async();   // staged partials: generic stores -> the bulk copies' reads
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sm->q_empty));
-      if (lane < C) mbar_arrive_remote(mapa(smem_u32(&sm->x_full), (uint32_t)lane));
+      // This warp's 32 rows are whole halves of the blocks of one or two
+      // owners (nr / 2 <= 32 rows per half): one lane per half copies it into
+      // that owner's inbox.  Each warp then arrives on this CTA's x_full with
+      // a quarter of the bytes the other C - 1 CTAs will send.
+      if (C > 1 && lane < 2 * ((32 + nr - 1) / nr) && lane * (nr / 2) < 32) {
+        const int hrow = warp * 32 + lane * (nr / 2);   // first row of this half
+        const int q = hrow / nr, hs = (hrow - q * nr) / (nr / 2);   // its owner and which half
+        if (q != (int)rank) {
+          const uint32_t src = hs == 0 ? sW + (uint32_t)q * half : sW + wchunk + (uint32_t)q * half;
+          const uint32_t dst = sIn + 4u * (uint32_t)((int)rank * nr * kGKp) + (uint32_t)hs * half;
+          bulk_s2cluster(mapa(dst, (uint32_t)q), src, half, mapa(smem_u32(&sm->x_full), (uint32_t)q));
+        }
+      }
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&sm->q_empty));
+        mbar_expect_tx(smem_u32(&sm->x_full), (uint32_t)(C - 1) * (uint32_t)nr * 64u);
+      }
+      __syncwarp();
       // ---- reduce this CTA's rows: the C partials in rank order, S2, and W into every CTA
       if (!warp_wait_cluster(smem_u32(&sm->x_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
-      if (tt > 0 && !warp_wait_cluster(smem_u32(&sm->w_free), (uint32_t)((tt - 1) & 1), abort_flag, a.err)) break;
       float s2t[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) s2t[q] = 0.0f;
+      // warp w reduces rows w nr / 4 .. (w + 1) nr / 4 - 1 of this CTA's
+      // (contiguous, so that it can copy its rows of W by itself)
+      const int rpw = nr / kGEpiWarps;   // rows per warp: 32 / C
 #pragma unroll 1
-      for (int it = e; it < nr * 8; it += kGEpiThreads) {
-        const int l = it >> 3;
+      for (int l = warp * rpw + (lane >> 3); l < (warp + 1) * rpw; l += 4) {
         float q[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) q[j] = 0.0f;
@@ -323,24 +346,31 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
           lp[u] = pack2<F16>(wa - h.x, wb - h.y);
         }
         // decisions 8 kq .. 8 kq + 7 of scenario i: one 16-byte unit of W's row i, swizzled by i
+        // (this CTA's own rows; the other CTAs' copies of them follow by bulk copy)
         const int i = r0 + l;
         const uint32_t woff = (uint32_t)(i * 128 + ((kq ^ (i & 7)) << 4));
-        if (C == 1) {
-          *reinterpret_cast<uint4*>(wbuf + woff) = hv;
-          *reinterpret_cast<uint4*>(wbuf + wchunk + woff) = lv;
-        } else {
-#pragma unroll 1
-          for (int p = 0; p < C; ++p) {
-            st_cluster_v4(mapa(sW + woff, (uint32_t)p), hv);
-            st_cluster_v4(mapa(sW + wchunk + woff, (uint32_t)p), lv);
-          }
-        }
+        *reinterpret_cast<uint4*>(wbuf + woff) = hv;
+        *reinterpret_cast<uint4*>(wbuf + wchunk + woff) = lv;
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) ff_add(s2h[q], s2l[q], s2t[q]);
-      fence_proxy_async_cluster();   // W: generic stores -> the MMAs' async-proxy reads
+      fence_proxy_async();   // W: generic stores -> the MMAs' and the bulk copies' reads
       __syncwarp();
-      if (lane < C) mbar_arrive_remote(mapa(smem_u32(&sm->w_full), (uint32_t)lane));
+      // this warp's rows of W into every other CTA's W (lane p: CTA p), once
+      // every CTA's adjoint of the last tile is done (the rows there also
+      // held that CTA's staged partial for this CTA, read by now: x_full is
+      // complete); then this warp's quarter of the bytes this CTA receives
+      if (C > 1 && tt > 0 &&
+          !warp_wait_cluster(smem_u32(&sm->w_free), (uint32_t)((tt - 1) & 1), abort_flag, a.err))
+        break;
+      if (C > 1 && lane < C && lane != (int)rank) {
+        const uint32_t wo = (uint32_t)(r0 + warp * rpw) * 128u, wbytes = (uint32_t)rpw * 128u;
+        const uint32_t wb = mapa(smem_u32(&sm->w_full), (uint32_t)lane);
+        bulk_s2cluster(mapa(sW + wo, (uint32_t)lane), sW + wo, wbytes, wb);
+        bulk_s2cluster(mapa(sW + wchunk + wo, (uint32_t)lane), sW + wchunk + wo, wbytes, wb);
+      }
+      if (lane == 0) mbar_expect_tx(smem_u32(&sm->w_full), (uint32_t)(C - 1) * (uint32_t)nr * 64u);
+      __syncwarp();
       // ---- adjoint: G^(r) = A^(r)' W of the tile, once every row of W is in place and the
       // last tile's block is folded; the stage is read as an MN-major A (dimensions
       // contiguous, 64-dimension chunks 32 KB apart), W as an MN-major B (decisions
@@ -399,6 +429,14 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sm->g_empty));
+    }
+    if (tt < my_tiles && C > 1) {
+      // the loop was abandoned (a bounded wait ran out): the bulk copies
+      // already issued by the CTAs of the cluster carry no completion this
+      // CTA can wait for, so give them a bounded pause to land
+      const long long t0 = clock64();
+      while (clock64() - t0 < 400000ll) {
+      }
     }
     if (issuer && adj_issued) {   // every adjoint MMA complete before TMEM and the stages are released
       mma_commit(smem_u32(&sm->drain_adj));
