@@ -258,6 +258,42 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
     const uint32_t ida2 = idesc_f16(kGDims, 2 * kGKp, F16) | kIdescAMajorMN | kIdescBMajorMN;
     const uint32_t ida1 = idesc_f16(kGDims, kGKp, F16) | kIdescAMajorMN | kIdescBMajorMN;
     bool adj_issued = false;
+    // Kahan fold of tile tf's block of G (hi*hi + corrections) into the
+    // running sum; then the block's TMEM is free for the next adjoint
+    auto fold = [&](int tf) {
+      tc_fence_after();
+#pragma unroll 1
+      for (uint32_t c0 = 0; c0 < (uint32_t)kGKp; c0 += 8) {
+        uint32_t rg[8], rh[8], rs[8], rc[8];
+        tmem_ld8(tg1 + lane_base + c0, rg);
+        tmem_ld8(tg2 + lane_base + c0, rh);
+        if (tf > 0) {
+          tmem_ld8(tgs + lane_base + c0, rs);
+          tmem_ld8(tgc + lane_base + c0, rc);
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float g = __uint_as_float(rg[q]) + __uint_as_float(rh[q]);
+          if (tf == 0) {
+            rc[q] = 0u;
+            rg[q] = __float_as_uint(g);
+          } else {
+            const float s = __uint_as_float(rs[q]), c = __uint_as_float(rc[q]);
+            const float y = g - c;
+            const float t = s + y;
+            rc[q] = __float_as_uint((t - s) - y);
+            rg[q] = __float_as_uint(t);
+          }
+        }
+        tmem_st8(tgs + lane_base + c0, rg);
+        tmem_st8(tgc + lane_base + c0, rc);
+        tmem_wait_st();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&sm->g_empty));
+    };
     int tt = 0;
     for (; tt < my_tiles; ++tt) {
       // ---- this CTA's partial Q of every row: its own rows straight into its
@@ -266,6 +302,9 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
       // block into the owner's inbox, completing bytes of its x_full
       if (!warp_wait(smem_u32(&sm->q_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
       if (tt > 0 && !warp_wait_cluster(smem_u32(&sm->w_full), (uint32_t)((tt - 1) & 1), abort_flag, a.err)) break;
+      // the last tile's adjoint is done: W is free for the staging below, and
+      // that tile's block of G is folded while the other CTAs' copies travel
+      if (tt > 0 && !warp_wait(smem_u32(&sm->g_full), (uint32_t)((tt - 1) & 1), abort_flag, a.err)) break;
       tc_fence_after();
       const uint32_t half = (uint32_t)nr * 128u;   // bytes of half an owner's block
 #pragma unroll 1
@@ -312,6 +351,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         mbar_expect_tx(smem_u32(&sm->x_full), (uint32_t)(C - 1) * (uint32_t)nr * 64u);
       }
       __syncwarp();
+      if (tt > 0) fold(tt - 1);
       // ---- reduce this CTA's rows: the C partials in rank order, S2, and W into every CTA
       if (!warp_wait_cluster(smem_u32(&sm->x_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
       float s2t[8];
@@ -395,40 +435,12 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         }
       }
       __syncwarp();
-      // ---- fold the tile's block of G (hi*hi + corrections) into the running sum (Kahan)
-      if (!warp_wait(smem_u32(&sm->g_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
-      tc_fence_after();
-#pragma unroll 1
-      for (uint32_t c0 = 0; c0 < (uint32_t)kGKp; c0 += 8) {
-        uint32_t rg[8], rh[8], rs[8], rc[8];
-        tmem_ld8(tg1 + lane_base + c0, rg);
-        tmem_ld8(tg2 + lane_base + c0, rh);
-        if (tt > 0) {
-          tmem_ld8(tgs + lane_base + c0, rs);
-          tmem_ld8(tgc + lane_base + c0, rc);
-        }
-        tmem_wait_ld();
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float g = __uint_as_float(rg[q]) + __uint_as_float(rh[q]);
-          if (tt == 0) {
-            rc[q] = 0u;
-            rg[q] = __float_as_uint(g);
-          } else {
-            const float s = __uint_as_float(rs[q]), c = __uint_as_float(rc[q]);
-            const float y = g - c;
-            const float t = s + y;
-            rc[q] = __float_as_uint((t - s) - y);
-            rg[q] = __float_as_uint(t);
-          }
-        }
-        tmem_st8(tgs + lane_base + c0, rg);
-        tmem_st8(tgc + lane_base + c0, rc);
-        tmem_wait_st();
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sm->g_empty));
+    }
+    bool folded = false;   // every tile's block is in the running sum
+    if (tt == my_tiles && my_tiles > 0 &&
+        warp_wait(smem_u32(&sm->g_full), (uint32_t)((my_tiles - 1) & 1), abort_flag, a.err)) {
+      fold(my_tiles - 1);
+      folded = true;
     }
     if (tt < my_tiles && C > 1) {
       // the loop was abandoned (a bounded wait ran out): the bulk copies
@@ -445,7 +457,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
     }
     // ---- this CTA's dimensions of G: running sum and its compensation
     const int j = (int)rank * kGDims + row;
-    if (tt == my_tiles && my_tiles > 0) {
+    if (folded) {
       tc_fence_after();
 #pragma unroll 1
       for (uint32_t c0 = 0; c0 < (uint32_t)kGKp; c0 += 8) {
