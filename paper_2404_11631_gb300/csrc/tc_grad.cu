@@ -16,18 +16,18 @@
 //             the stage is the operand of both contractions below.
 //   forward   one thread issues Q^(r) = A^(r) Y^(r) over the CTA's 128
 //             dimensions, with its slice of the decision operand resident in
-//             shared memory: A_hi [Y_hi; Y_lo] as one MMA of N = 2 Kp (hi*hi
-//             and hi*lo side by side in TMEM), then A_lo Y_hi into the hi*lo
-//             columns.
-//   exchange  the epilogue warps put Q^(r) (FP32, transposed) into shared
-//             memory; once every CTA of the cluster has, CTA r adds the C
-//             partials of its own rows in rank order through distributed
-//             shared memory (a reduce-scatter: 128 / C rows each, 16-byte
-//             loads of 8 rows of one column, every peer's in flight at
-//             once), keeps S2 of those rows, and writes W = Q 2^-f_k as
-//             hi/lo into the W buffer of every CTA of the cluster, one 16-byte
-//             unit of 8 scenarios at a time (2^f_k > |y_k|_2 in operand
-//             units, so |W_ik| <= |a_i|_2).
+//             shared memory, into one FP32 accumulator: the corrections
+//             A_hi Y_lo and A_lo Y_hi of both chunks first, then A_hi Y_hi.
+//   exchange  the epilogue warps write the rows of Q^(r) that CTA r reduces
+//             into its own inbox and stage every other owner's rows in the
+//             W buffer (free once the last tile's adjoint is done), in the
+//             inbox's layout; one lane per half block bulk-copies it into
+//             that owner's inbox (shared::cta -> shared::cluster, completing
+//             bytes of the owner's x_full).  CTA r then adds the C partials
+//             of its 128 / C rows in rank order, keeps S2 of those rows, and
+//             writes W = Q 2^-f_k as hi/lo into its own W buffer (2^f_k >
+//             |y_k|_2 in operand units, so |W_ik| <= |a_i|_2); each warp
+//             bulk-copies its rows of W into every other CTA's W.
 //   adjoint   with all rows of W in place, the thread issues
 //             G^(r) = A^(r)' W for the tile, reading the same stage as an
 //             MN-major operand (the dimensions of a 64-dimension chunk are
@@ -36,13 +36,15 @@
 //             Kahan-compensated running sum held in TMEM, so G never leaves
 //             the SM until the end.
 // The draw of tile t + 1 overlaps the forward, exchange and adjoint of tile
-// t (two stages); the exchange moves 2 x 32 KB of distributed shared memory
-// per tile and CTA.
+// t (two stages), and the fold of tile t overlaps the exchange of tile
+// t + 1; the exchange moves 2 x 28 KB of distributed shared memory per tile
+// and CTA at C = 8.
 //
 // Accuracy.  The tensor core rounds every update of an accumulator with a
 // bias toward zero, so a running sum over T k steps loses about T/2 units in
-// the last place.  The forward runs 8 k steps per CTA and the C partials are
-// added with round-to-nearest FP32 additions; the adjoint's blocks run 8 k
+// the last place.  The forward's accumulator takes the 16 correction steps
+// while it is still small and then the 8 hi*hi steps per CTA, and the C
+// partials are added with round-to-nearest FP32 additions; the adjoint's blocks run 8 k
 // steps per tile before their compensated fold, so the bias stays near 4
 // units in the last place of a tile's block.  The adjoint's representation
 // error changes sign and size from scenario to scenario, so it shrinks like
@@ -180,8 +182,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
     sm->gsc_f[k] = (k < a.K) ? (float)a.gaux[k] : 0.0f;
     sm->wsc_f[k] = (k < a.K) ? (float)a.gaux[a.K + k] : 0.0f;
   }
-  // TMEM, 64 columns each: Q hi*hi, Q corrections, the tile's G hi*hi and
-  // corrections, G's running sum, its Kahan compensation
+  // TMEM, 64 columns each: Q, (unused), the tile's G hi*hi and corrections,
+  // G's running sum, its Kahan compensation
   constexpr uint32_t ncols = 512u;
   if (warp == kGMmaWarp) tmem_alloc(smem_u32(&sm->tmem_base), ncols);
   tc_fence_before();
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
   tc_fence_after();
   cluster_sync();   // every CTA's barriers are initialised before any peer arrives on them
   const uint32_t tmem = sm->tmem_base;
-  const uint32_t tq1 = tmem, td2 = tmem + 64u, tg1 = tmem + 128u, tg2 = tmem + 192u;
+  const uint32_t tq1 = tmem, tg1 = tmem + 128u, tg2 = tmem + 192u;
   const uint32_t tgs = tmem + 256u, tgc = tmem + 320u;
   const int my_tiles = (cl < (uint32_t)a.tiles) ? (int)((a.tiles - cl + ncl - 1) / ncl) : 0;
   const uint16_t cmask = (uint16_t)((1u << C) - 1u);
@@ -206,12 +208,14 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
       mbar_expect_tx(yb, 2 * bslice);
       bulk_g2s(sY, a.bimage + (size_t)(2 * rank) * bslice, 2 * bslice, yb);
       bool ok = mbar_wait(yb, 0, abort_flag, a.err);
-      // hi and lo halves of the second operand are stacked along N, so
-      // A_hi [B_hi, B_lo] is one MMA of N = 128 (hi*hi in columns 0..63,
-      // hi*lo in 64..127) and A_lo B_hi adds into the latter.  This thread
-      // issues only the forward; the adjoint is issued by the epilogue
-      // once W is in place, so the next tile's forward never waits on it.
-      const uint32_t idf2 = idesc_f16(kGM, 2 * kGKp, F16), idf1 = idesc_f16(kGM, kGKp, F16);
+      // One FP32 accumulator per tile: the corrections A_hi B_lo and A_lo
+      // B_hi of both chunks first, then A_hi B_hi, so the small terms are
+      // not added to the large running sum (the accumulator's rounding is
+      // relative to it).  This thread issues only the forward; the adjoint
+      // is issued by the epilogue once W is in place, so the next tile's
+      // forward never waits on it.
+      const uint32_t idf1 = idesc_f16(kGM, kGKp, F16);
+      constexpr uint32_t bhalf = kGKp * 128;   // the lo half of a decision block follows its hi half
       int st = 0;
       uint32_t ph = 0;
       for (int tt = 0; ok && tt < my_tiles; ++tt) {
@@ -230,11 +234,19 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
             const uint32_t o = (uint32_t)(kk * 32);
             const uint32_t a_hi = stage + (uint32_t)(c * 2 * kGChunkBytes) + o, a_lo = a_hi + kGChunkBytes;
             const uint32_t b_hi = sY + (uint32_t)c * bslice + o;
-            mma_bf16(tq1, desc_sw128(a_hi), desc_sw128(b_hi), idf2, (c == 0 && kk == 0) ? 0u : 1u);
-            mma_bf16(td2, desc_sw128(a_lo), desc_sw128(b_hi), idf1, 1u);
+            mma_bf16(tq1, desc_sw128(a_hi), desc_sw128(b_hi + bhalf), idf1, (c == 0 && kk == 0) ? 0u : 1u);
+            mma_bf16(tq1, desc_sw128(a_lo), desc_sw128(b_hi), idf1, 1u);
           }
         }
         if (!ok) break;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t o = (uint32_t)(kk * 32);
+            const uint32_t a_hi = stage + (uint32_t)(c * 2 * kGChunkBytes) + o;
+            mma_bf16(tq1, desc_sw128(a_hi), desc_sw128(sY + (uint32_t)c * bslice + o), idf1, 1u);
+          }
         mma_commit(smem_u32(&sm->q_full));
         if (++st == kGStages) { st = 0; ph ^= 1u; }
       }
@@ -309,17 +321,13 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
       const uint32_t half = (uint32_t)nr * 128u;   // bytes of half an owner's block
 #pragma unroll 1
       for (uint32_t c0 = 0; c0 < (uint32_t)kGKp; c0 += 16) {
-        uint32_t r1v[16], r2v[16];
+        uint32_t r1v[16];
         tmem_ld16(tq1 + lane_base + c0, r1v);
-        tmem_ld16(td2 + lane_base + c0, r2v);
         tmem_wait_ld();
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          float4 q;
-          q.x = __uint_as_float(r1v[4 * u + 0]) + __uint_as_float(r2v[4 * u + 0]);
-          q.y = __uint_as_float(r1v[4 * u + 1]) + __uint_as_float(r2v[4 * u + 1]);
-          q.z = __uint_as_float(r1v[4 * u + 2]) + __uint_as_float(r2v[4 * u + 2]);
-          q.w = __uint_as_float(r1v[4 * u + 3]) + __uint_as_float(r2v[4 * u + 3]);
+          const float4 q = make_float4(__uint_as_float(r1v[4 * u + 0]), __uint_as_float(r1v[4 * u + 1]),
+                                       __uint_as_float(r1v[4 * u + 2]), __uint_as_float(r1v[4 * u + 3]));
           const uint32_t off = inbox_off(0, nr, lrow, (int)c0 + 4 * u);   // float offset in the block
           if (own == (int)rank) {
             *reinterpret_cast<float4*>(inbox + (uint32_t)(own * nr * kGKp) + off) = q;
