@@ -520,6 +520,24 @@ saa_status saa_eval_static(const saa_problem* prob, int32_t K, const double* X, 
  * clears it, and the context stays usable.  No fault, trap or hang. */
 saa_status saa_selftest_timeout(saa_ctx* ctx, uint32_t budget_us, void* stream);
 
+/* Index-checked build.  Compiled with SAA_BOUNDS_CHECK defined (the package
+ * builds it as libsaa_bounds.so), the tensor-core value, gradient and
+ * streamed kernels check the indices of their partial-sum writes against
+ * the workspace regions the host carved, and of their shared-memory stage
+ * stores against the stage; an index at or past its bound raises the bounds
+ * bit of the context's error word (the next saa_ctx_sync returns
+ * SAA_EDEVICE) and the access is skipped, instead of faulting.  The results
+ * of every call are otherwise the same, bit for bit, as the normal build's.
+ * saa_bounds_check_enabled returns 1 in that build, 0 in the normal one.
+ * saa_selftest_bounds launches one warp that stores, through the same
+ * check, past the declared capacity of a device array twice that size (so
+ * no build writes outside it): the checked build flags every store and
+ * skips it, and the next saa_ctx_sync returns SAA_EDEVICE; the normal build
+ * returns SAA_EUNSUPPORTED without launching.  Not in the paper: a tool for
+ * this library's own checking. */
+int32_t saa_bounds_check_enabled(void);
+saa_status saa_selftest_bounds(saa_ctx* ctx, void* stream);
+
 /* Arithmetic self-test of the FP32 generator: for every one of its 2^23
  * uniforms u = (2k + 1) 2^-24 it compares the LOG's quotient (m - 1)/(m + 1)
  * and the Box-Muller root sqrt(-2 LOG(u)), which the generator forms by

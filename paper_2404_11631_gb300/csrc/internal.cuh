@@ -19,6 +19,32 @@ constexpr int kMaxDimSimt = 1024;
 // Device error word bits (ctx->err).
 enum : uint32_t { kErrBounds = 1u, kErrTimeout = 2u, kErrInput = 4u };
 
+// Index checks of the SAA_BOUNDS_CHECK build (-DSAA_BOUNDS_CHECK; libsaa_bounds.so).
+// There an index at or past its buffer's capacity raises kErrBounds in the
+// error word and the caller skips the access, instead of faulting: a stand-in
+// for a memory checker where none can run.  In the normal build the checks
+// compile to nothing.
+#ifdef SAA_BOUNDS_CHECK
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
+// A bound that exists only in the checked build (its kernel-argument fields
+// are compiled in there alone, so the normal build's arguments and code stay
+// as they are).
+#ifdef SAA_BOUNDS_CHECK
+#define SAA_BOUND(n) (n)
+#else
+#define SAA_BOUND(n) (~(size_t)0)
+#endif
+__device__ __forceinline__ bool bc_ok(size_t i, size_t n, uint32_t* err) {
+  if (kBoundsCheck && i >= n) {
+    atomicOr(err, kErrBounds);
+    return false;
+  }
+  return true;
+}
+
 // Everything a sample-generating kernel needs to know about the law.
 struct LawArgs {
   int d;
@@ -62,6 +88,7 @@ struct Workspace {
   double* part_gd;    // diagonal path: [slices][K][d] adjoint partials of G
   double* part_md;    // diagonal path: [slices][d] adjoint partials of m~
   float* zs;          // diagonal path, sample store: [N][round_up(d, 4)] FP32 normals
+  size_t n_s2, n_m, n_g;   // elements of part_s2, part_m, part_g / part_gc (the bounds of the checked build)
   size_t bytes;       // total
 };
 

@@ -24,6 +24,7 @@ saa_status cuda_status(cudaError_t e, const char* what) {
 
 cudaError_t launch_set_i64(int64_t* p, int64_t v, cudaStream_t st);
 cudaError_t launch_selftest_timeout(uint32_t* err, uint32_t budget_us, cudaStream_t st);
+cudaError_t launch_selftest_bounds(uint32_t* err, cudaStream_t st);
 
 static saa_status fail(saa_status s, const std::string& msg) {
   set_error(msg);
@@ -109,6 +110,9 @@ size_t carve(const saa_problem* p, int K, const Plan& plan, int want_grad, void*
     w.grad_out = (double*)take(k * d * 8);
   }
   if (plan.tc_bytes) w.tc = take(plan.tc_bytes);
+  w.n_s2 = g * k;
+  w.n_m = g * d;
+  w.n_g = want_grad ? g * k * d : 0;
   w.bytes = off;
   if (ws) *ws = w;
   return off;
@@ -313,6 +317,16 @@ saa_status saa_selftest_timeout(saa_ctx* ctx, uint32_t budget_us, void* stream) 
   if (budget_us < 1 || budget_us > 100000) return fail(SAA_EINVAL, "budget must be in [1 us, 100 ms]");
   DeviceGuard g(ctx->device);
   return cuda_status(launch_selftest_timeout(ctx->err, budget_us, (cudaStream_t)stream), "self-test launch");
+}
+
+int32_t saa_bounds_check_enabled(void) { return kBoundsCheck ? 1 : 0; }
+
+saa_status saa_selftest_bounds(saa_ctx* ctx, void* stream) {
+  if (!ctx) return fail(SAA_EINVAL, "ctx is NULL");
+  if (!kBoundsCheck)
+    return fail(SAA_EUNSUPPORTED, "index checks are compiled out of this build (build with SAA_BOUNDS_CHECK)");
+  DeviceGuard g(ctx->device);
+  return cuda_status(launch_selftest_bounds(ctx->err, (cudaStream_t)stream), "self-test launch");
 }
 
 saa_status saa_ctx_set_autotune(saa_ctx* ctx, int enable) {

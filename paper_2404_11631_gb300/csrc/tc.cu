@@ -70,6 +70,9 @@ struct Args {
   double* part_s2;            // [grid][K]
   double* part_m;             // [grid][d]
   uint32_t* err;
+#ifdef SAA_BOUNDS_CHECK
+  size_t n_s2, n_m;           // elements of part_s2 and part_m
+#endif
 };
 
 // ------------------------------------------------------------- kernel ----
@@ -323,12 +326,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
   for (int j = threadIdx.x; j < d; j += blockDim.x) {
     double s = 0.0;
     for (int rw = 0; rw < kRngWarps; ++rw) s += (double)red_m[rw * dpad + j];
-    a.part_m[(size_t)blockIdx.x * d + j] = s;
+    if (bc_ok((size_t)blockIdx.x * d + j, SAA_BOUND(a.n_m), a.err)) a.part_m[(size_t)blockIdx.x * d + j] = s;
   }
   for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
     double s = 0.0;
     for (int w = 0; w < kEpiWarps; ++w) s += red_s2[w * a.Kp + k];
-    a.part_s2[(size_t)blockIdx.x * a.K + k] = s * a.scale2[k];
+    if (bc_ok((size_t)blockIdx.x * a.K + k, SAA_BOUND(a.n_s2), a.err)) a.part_s2[(size_t)blockIdx.x * a.K + k] = s * a.scale2[k];
   }
   if (warp == kMmaWarp) {
     tc_fence_after();
@@ -607,12 +610,12 @@ __global__ void __launch_bounds__(kThreads1, 1) k_tc_value1(Args a) {
   for (int j = threadIdx.x; j < d; j += blockDim.x) {
     double s = 0.0;
     for (int rw = 0; rw < kRngWarps; ++rw) s += (double)red_m[rw * dpad + j];
-    a.part_m[(size_t)blockIdx.x * d + j] = s;
+    if (bc_ok((size_t)blockIdx.x * d + j, SAA_BOUND(a.n_m), a.err)) a.part_m[(size_t)blockIdx.x * d + j] = s;
   }
   for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
     double s = 0.0;
     for (int w = 0; w < kEpiWarps; ++w) s += red_s2[w * a.Kp + k];
-    a.part_s2[(size_t)blockIdx.x * a.K + k] = s * a.scale2[k];
+    if (bc_ok((size_t)blockIdx.x * a.K + k, SAA_BOUND(a.n_s2), a.err)) a.part_s2[(size_t)blockIdx.x * a.K + k] = s * a.scale2[k];
   }
   if (warp == 0) {
     tc_fence_after();
@@ -707,6 +710,16 @@ __global__ void k_selftest_timeout(uint32_t* err, long long budget) {
   mbar_wait_budget(smem_u32(&bar), 0u, &abort_flag, err, budget);
 }
 
+// Self-test of the index checks: each thread stores through bc_ok at an
+// index at or past the declared capacity (32) of a 64-element array.  The
+// checked build raises the bounds bit and skips every store; the indices
+// stay inside the real array, so no build writes outside it.
+__device__ float g_bc_probe[64];
+__global__ void k_selftest_bounds(uint32_t* err) {
+  const size_t i = 32u + threadIdx.x;
+  if (bc_ok(i, 32u, err)) g_bc_probe[i] = 1.0f;
+}
+
 }  // namespace tc
 
 cudaError_t launch_tc_image(int d, int K, int Kp, int nkb, bool f16, const double* Y64, double* scale2,
@@ -720,6 +733,11 @@ cudaError_t launch_tc_image(int d, int K, int Kp, int nkb, bool f16, const doubl
 
 cudaError_t launch_selftest_timeout(uint32_t* err, uint32_t budget_us, cudaStream_t st) {
   tc::k_selftest_timeout<<<1, 32, 0, st>>>(err, (long long)budget_us * 2100ll);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_bounds(uint32_t* err, cudaStream_t st) {
+  tc::k_selftest_bounds<<<1, 32, 0, st>>>(err);
   return cudaGetLastError();
 }
 
@@ -767,6 +785,10 @@ cudaError_t launch_tc(const LawArgs& la, int K, int prec, const Plan& plan, cons
   a.scale2 = scale2;
   a.part_s2 = ws.part_s2;
   a.part_m = ws.part_m;
+#ifdef SAA_BOUNDS_CHECK
+  a.n_s2 = ws.n_s2;
+  a.n_m = ws.n_m;
+#endif
   a.err = err;
   cudaError_t e = launch_tc_image(la.d, K, a.Kp, a.nkb, f16, ws.Y64, scale2, nullptr, img, st);
   if (e != cudaSuccess) return e;

@@ -95,6 +95,9 @@ struct GArgs {
   float* part_g;           // [clusters][K][d]
   float* part_gc;          // [clusters][K][d] (true sum = part_g - part_gc)
   uint32_t* err;
+#ifdef SAA_BOUNDS_CHECK
+  size_t n_s2, n_m, n_g;   // elements of part_s2, part_m, part_g
+#endif
 };
 
 struct GSmem {
@@ -330,11 +333,12 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
                                        __uint_as_float(r1v[4 * u + 2]), __uint_as_float(r1v[4 * u + 3]));
           const uint32_t off = inbox_off(0, nr, lrow, (int)c0 + 4 * u);   // float offset in the block
           if (own == (int)rank) {
-            *reinterpret_cast<float4*>(inbox + (uint32_t)(own * nr * kGKp) + off) = q;
+            if (bc_ok((size_t)(own * nr * kGKp) + off + 3u, (size_t)kGM * kGKp, a.err))   // the 32 KB inbox
+              *reinterpret_cast<float4*>(inbox + (uint32_t)(own * nr * kGKp) + off) = q;
           } else {
             const uint32_t bo = 4u * off;
             const uint32_t so = bo < half ? (uint32_t)own * half + bo : wchunk + (uint32_t)own * half + (bo - half);
-            *reinterpret_cast<float4*>(wbuf + so) = q;
+            if (bc_ok(so + 15u, 2u * wchunk, a.err)) *reinterpret_cast<float4*>(wbuf + so) = q;
           }
         }
       }
@@ -397,8 +401,10 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         // (this CTA's own rows; the other CTAs' copies of them follow by bulk copy)
         const int i = r0 + l;
         const uint32_t woff = (uint32_t)(i * 128 + ((kq ^ (i & 7)) << 4));
-        *reinterpret_cast<uint4*>(wbuf + woff) = hv;
-        *reinterpret_cast<uint4*>(wbuf + wchunk + woff) = lv;
+        if (bc_ok(woff + 15u, wchunk, a.err)) {
+          *reinterpret_cast<uint4*>(wbuf + woff) = hv;
+          *reinterpret_cast<uint4*>(wbuf + wchunk + woff) = lv;
+        }
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) ff_add(s2h[q], s2l[q], s2t[q]);
@@ -480,8 +486,10 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
             if (k < a.K) {
               const size_t o = ((size_t)cl * a.K + k) * d + j;
               const float g = sm->gsc_f[k];   // power of two: exact
-              a.part_g[o] = __uint_as_float(rs[q]) * g;
-              a.part_gc[o] = __uint_as_float(rc[q]) * g;
+              if (bc_ok(o, SAA_BOUND(a.n_g), a.err)) {
+                a.part_g[o] = __uint_as_float(rs[q]) * g;
+                a.part_gc[o] = __uint_as_float(rc[q]) * g;
+              }
             }
           }
         }
@@ -489,8 +497,10 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
     } else if (my_tiles == 0 && j < d) {
       for (int k = 0; k < a.K; ++k) {
         const size_t o = ((size_t)cl * a.K + k) * d + j;
-        a.part_g[o] = 0.0f;
-        a.part_gc[o] = 0.0f;
+        if (bc_ok(o, SAA_BOUND(a.n_g), a.err)) {
+          a.part_g[o] = 0.0f;
+          a.part_gc[o] = 0.0f;
+        }
       }
     }
   } else {
@@ -560,8 +570,10 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
           lo[q / 2] = pack2<F16>(v[q] - h.x, v[q + 1] - h.y);
         }
         const uint32_t off = sw_off(r, cu);
-        *reinterpret_cast<uint4*>(chunk + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(chunk + kGChunkBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        if (bc_ok(off + 15u, (size_t)kGChunkBytes, a.err)) {   // one 16-byte unit of each half of the chunk
+          *reinterpret_cast<uint4*>(chunk + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(chunk + kGChunkBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) ff_add(mh[q], ml[q], msum[q]);
@@ -591,7 +603,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
     const int j = (int)rank * kGDims + threadIdx.x;
     double s = 0.0;
     for (int g = 0; g < 32; ++g) s += red_m[g * kGDims + threadIdx.x];
-    if (j < d) a.part_m[(size_t)cl * d + j] = s;
+    if (j < d && bc_ok((size_t)cl * d + j, SAA_BOUND(a.n_m), a.err)) a.part_m[(size_t)cl * d + j] = s;
   }
   if (threadIdx.x < kGKp) {     // S2 of this CTA's rows: the 16 threads of column k, in order
     const int kq = threadIdx.x >> 3, q = threadIdx.x & 7;
@@ -604,7 +616,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
     const uint32_t o = smem_u32(s2loc + threadIdx.x);
     double s = 0.0;
     for (int p = 0; p < C; ++p) s += ld_cluster_f64(mapa(o, (uint32_t)p));
-    a.part_s2[(size_t)cl * a.K + threadIdx.x] = s * a.scale2[threadIdx.x];
+    if (bc_ok((size_t)cl * a.K + threadIdx.x, SAA_BOUND(a.n_s2), a.err))
+      a.part_s2[(size_t)cl * a.K + threadIdx.x] = s * a.scale2[threadIdx.x];
   }
   cluster_sync();   // rank 0 has read every peer's S2
   if (warp == kGMmaWarp) {
@@ -699,6 +712,11 @@ cudaError_t launch_tc_grad(const LawArgs& la, int K, int prec, const Plan& plan,
   a.part_m = ws.part_m;
   a.part_g = (float*)ws.part_g;
   a.part_gc = (float*)ws.part_gc;
+#ifdef SAA_BOUNDS_CHECK
+  a.n_s2 = ws.n_s2;
+  a.n_m = ws.n_m;
+  a.n_g = ws.n_g;
+#endif
   a.err = err;
   cudaError_t e = launch_tc_image(la.d, K, tc::kGKp, 2 * a.C, f16, ws.Y64, scale2, gaux, img, st);
   if (e != cudaSuccess) return e;

@@ -68,6 +68,9 @@ struct SArgs {
   double* part_s2;        // [grid][K]
   double* part_m;         // [grid][dpad]
   uint32_t* err;
+#ifdef SAA_BOUNDS_CHECK
+  size_t n_s2, n_m;       // elements of part_s2 and part_m
+#endif
 };
 
 // 16-byte aligned size: the FP32 center / scale arrays that follow it are
@@ -366,8 +369,10 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
         __syncwarp();   // every thread of these rows has read its FP32 values
         const uint4 hu = hsw ? make_uint4(h8[2], h8[3], h8[0], h8[1]) : make_uint4(h8[0], h8[1], h8[2], h8[3]);
         const uint4 lu = hsw ? make_uint4(l8[2], l8[3], l8[0], l8[1]) : make_uint4(l8[0], l8[1], l8[2], l8[3]);
-        *reinterpret_cast<uint4*>(stage + sw_off(r, q)) = hu;
-        *reinterpret_cast<uint4*>(stage + sw_off(r, 4 + q)) = lu;
+        if (bc_ok(sw_off(r, 4 + q) + 15u, (size_t)kSM * 128, a.err) && bc_ok(sw_off(r, q) + 15u, (size_t)kSM * 128, a.err)) {
+          *reinterpret_cast<uint4*>(stage + sw_off(r, q)) = hu;
+          *reinterpret_cast<uint4*>(stage + sw_off(r, 4 + q)) = lu;
+        }
       } else {
       uint32_t hi[8], lo[8];
 #pragma unroll
@@ -380,10 +385,12 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
       uint8_t* hrow = stage;                    // hi over the first half
       uint8_t* lrow = stage + kSM * 128;        // lo over the second half
       const int ua = 2 * q + hsw, ub = 2 * q + 1 - hsw;   // units of v[0..7] and v[8..15]
-      *reinterpret_cast<uint4*>(hrow + sw_off(r, ua)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      *reinterpret_cast<uint4*>(hrow + sw_off(r, ub)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-      *reinterpret_cast<uint4*>(lrow + sw_off(r, ua)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-      *reinterpret_cast<uint4*>(lrow + sw_off(r, ub)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+      if (bc_ok(sw_off(r, ua) + 15u, (size_t)kSM * 128, a.err) && bc_ok(sw_off(r, ub) + 15u, (size_t)kSM * 128, a.err)) {
+        *reinterpret_cast<uint4*>(hrow + sw_off(r, ua)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(hrow + sw_off(r, ub)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+        *reinterpret_cast<uint4*>(lrow + sw_off(r, ua)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        *reinterpret_cast<uint4*>(lrow + sw_off(r, ub)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+      }
       }
       fence_proxy_async();
       __syncwarp();
@@ -438,13 +445,13 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
     double t = 0.0;
 #pragma unroll 4
     for (int w = 0; w < kSConv; ++w) t += red_m[w * dpad + j];
-    a.part_m[(size_t)blockIdx.x * dpad + j] = t;
+    if (bc_ok((size_t)blockIdx.x * dpad + j, SAA_BOUND(a.n_m), a.err)) a.part_m[(size_t)blockIdx.x * dpad + j] = t;
   }
   __syncthreads();
   for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
     double s = 0.0;
     for (int w = 0; w < 4; ++w) s += red_s2[w * a.Kp + k];
-    a.part_s2[(size_t)blockIdx.x * a.K + k] = s * a.scale2[k];
+    if (bc_ok((size_t)blockIdx.x * a.K + k, SAA_BOUND(a.n_s2), a.err)) a.part_s2[(size_t)blockIdx.x * a.K + k] = s * a.scale2[k];
   }
   if (warp == kSMma) {
     tc_fence_after();
@@ -783,6 +790,10 @@ extern "C" saa_status saa_eval_samples(saa_ctx* ctx, int64_t N, int32_t d, const
   a.scale2 = scale2;
   a.part_s2 = part_s2;
   a.part_m = part_m;
+#ifdef SAA_BOUNDS_CHECK
+  a.n_s2 = (size_t)p.grid * K;
+  a.n_m = (size_t)p.grid * p.dpad;
+#endif
   a.err = ctx->err;
   auto kern = f8 ? (p.nkb == 1 ? tc::k_tc_stream<2, 1> : p.nkb == 2 ? tc::k_tc_stream<2, 2> : tc::k_tc_stream<2, 4>)
             : f16 ? (p.nkb == 1 ? tc::k_tc_stream<1, 1> : p.nkb == 2 ? tc::k_tc_stream<1, 2> : tc::k_tc_stream<1, 4>)

@@ -70,13 +70,18 @@ _ctx: dict[int, C.c_void_p] = {}
 
 
 def lib():
-    """Loads libsaa.so (building it in-tree first if it is missing)."""
+    """Loads libsaa.so (building it in-tree first if it is missing).  With
+    SAA_BOUNDS_CHECK=1 in the environment it loads the index-checked build,
+    libsaa_bounds.so, building or refreshing it first."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
-            if not os.path.exists(path):
-                path = _build.build()
+            if os.environ.get("SAA_BOUNDS_CHECK") == "1":
+                path = _build.build(bounds=True)
+            else:
+                path = _build.LIB
+                if not os.path.exists(path):
+                    path = _build.build()
             L = C.CDLL(path)
             vp, sz = C.c_void_p, C.c_size_t
             pp = C.POINTER(_CProblem)
@@ -166,6 +171,10 @@ def lib():
             L.saa_batch_destroy.restype = None
             L.saa_selftest_timeout.argtypes = [vp, C.c_uint32, vp]
             L.saa_selftest_timeout.restype = C.c_int
+            L.saa_bounds_check_enabled.argtypes = []
+            L.saa_bounds_check_enabled.restype = C.c_int32
+            L.saa_selftest_bounds.argtypes = [vp, vp]
+            L.saa_selftest_bounds.restype = C.c_int
             L.saa_selftest_arith.argtypes = [vp, vp, vp]
             L.saa_selftest_arith.restype = C.c_int
             L.saa_ctx_set_autotune.argtypes = [vp, C.c_int]
@@ -803,6 +812,19 @@ def saa_selftest_timeout(budget_us: int = 1000, device: int | None = None):
     _check(lib().saa_selftest_timeout(context(dev.index), budget_us, _stream(dev)))
 
 
+def saa_bounds_check_enabled() -> bool:
+    """True when the loaded library is the index-checked build (see saa.h)."""
+    return bool(lib().saa_bounds_check_enabled())
+
+
+def saa_selftest_bounds(device: int | None = None):
+    """Runs the index-check self-test (see saa.h): in the checked build the
+    next saa_ctx_sync raises SAA_EDEVICE; the normal build raises
+    SAA_EUNSUPPORTED here."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    _check(lib().saa_selftest_bounds(context(dev.index), _stream(dev)))
+
+
 def saa_ctx_sync(device: int | None = None):
     """Waits for the current stream and raises if a device-side check fired."""
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -851,4 +873,4 @@ EXPORTED = ["saa_ctx_create", "saa_ctx_destroy", "saa_ctx_sync", "saa_workspace_
             "saa_solve_adaptive", "saa_logistic_pitch", "saa_logistic_generate", "saa_logistic_workspace_size",
             "saa_logistic_eval", "saa_ctx_set_sample_store", "saa_selftest_arith", "saa_eval_host_workspace_size",
             "saa_eval_host", "saa_partials_workspace_size", "saa_partials", "saa_finalize_partials",
-            "saa_partials_merge", "saa_plan_info"]
+            "saa_partials_merge", "saa_plan_info", "saa_bounds_check_enabled", "saa_selftest_bounds"]
