@@ -87,8 +87,16 @@ struct alignas(16) SSmem {
 
 static_assert(sizeof(SSmem) % 16 == 0, "the arrays after SSmem are read as float4");
 
-size_t stream_smem_bytes(int Kp, int nkb, int nst) {
-  return (size_t)nst * kSStageBytes + (size_t)nkb * 2 * Kp * 128 + sizeof(SSmem) +
+// Bytes of the decision image: per K block two planes (hi, lo) of Kp rows x
+// 128 B for the 16-bit types; for E4M3 the 3 nkb 64-dimension halves (B1 of
+// every block, then B2, then B3) packed two to a 128-byte row, half h in
+// plane h / 2 at byte (h % 2) 64.
+__host__ __device__ constexpr int img_bytes(int Kp, int nkb, bool f8) {
+  return (f8 ? (3 * nkb + 1) / 2 : 2 * nkb) * Kp * 128;
+}
+
+size_t stream_smem_bytes(int Kp, int nkb, int nst, bool f8) {
+  return (size_t)nst * kSStageBytes + (size_t)img_bytes(Kp, nkb, f8) + sizeof(SSmem) +
          2 * sizeof(float) * (size_t)nkb * kSKB;
 }
 
@@ -112,7 +120,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
     if (threadIdx.x == 0) atomicOr(a.err, kErrBounds);
     return;
   }
-  const int bbytes = a.nkb * 2 * a.Kp * 128;
+  const int bbytes = img_bytes(a.Kp, a.nkb, F8);
   uint8_t* As = smem_raw;
   const int nst = a.nst;
   SSmem* sm = reinterpret_cast<SSmem*>(smem_raw + nst * kSStageBytes + bbytes);
@@ -202,19 +210,23 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
           const uint32_t bo = (uint32_t)h * (128u * 128u);   // decision rows 128 h ..
           const uint32_t idesc = h == 0 ? idesc0 : idesc1;
           if constexpr (F8) {
-            // A rows [A1 | A2], decision planes [B1 | B1] (b_hi) and
-            // [B2 | B3] (b_lo), 64 dimensions per half, 32 per step:
-            // A1 B3 + A1 B2, then A1 B1 + A2 B1 over the whole row
+            // A rows [A1 | A2] (64 dimensions per half, 32 per step) against
+            // the image's halves B3, B2 and B1 of this block: the small
+            // products A1 B3, A1 B2, A2 B1 first, then A1 B1
             const uint32_t acc0 = kb == 0 ? 0u : 1u;
-            mma_e4m3(d1, desc_sw128(a_hi), desc_sw128(b_lo + 64u), idesc, acc0);
-            mma_e4m3(d1, desc_sw128(a_hi + 32u), desc_sw128(b_lo + 96u), idesc, 1u);
-            mma_e4m3(d1, desc_sw128(a_hi), desc_sw128(b_lo), idesc, 1u);
-            mma_e4m3(d1, desc_sw128(a_hi + 32u), desc_sw128(b_lo + 32u), idesc, 1u);
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t o = (uint32_t)(kk * 32);
-              mma_e4m3(d1, desc_sw128(a_hi + o), desc_sw128(b_hi + o), idesc, 1u);
-            }
+            const uint32_t plane = (uint32_t)(a.Kp * 128);
+            const int h1 = kb, h2 = a.nkb + kb, h3 = 2 * a.nkb + kb;
+            const uint32_t b1 = sB + (uint32_t)(h1 >> 1) * plane + (uint32_t)(h1 & 1) * 64u;
+            const uint32_t b2 = sB + (uint32_t)(h2 >> 1) * plane + (uint32_t)(h2 & 1) * 64u;
+            const uint32_t b3 = sB + (uint32_t)(h3 >> 1) * plane + (uint32_t)(h3 & 1) * 64u;
+            mma_e4m3(d1, desc_sw128(a_hi), desc_sw128(b3), idesc, acc0);
+            mma_e4m3(d1, desc_sw128(a_hi + 32u), desc_sw128(b3 + 32u), idesc, 1u);
+            mma_e4m3(d1, desc_sw128(a_hi), desc_sw128(b2), idesc, 1u);
+            mma_e4m3(d1, desc_sw128(a_hi + 32u), desc_sw128(b2 + 32u), idesc, 1u);
+            mma_e4m3(d1, desc_sw128(a_hi + 64u), desc_sw128(b1), idesc, 1u);
+            mma_e4m3(d1, desc_sw128(a_hi + 96u), desc_sw128(b1 + 32u), idesc, 1u);
+            mma_e4m3(d1, desc_sw128(a_hi), desc_sw128(b1), idesc, 1u);
+            mma_e4m3(d1, desc_sw128(a_hi + 32u), desc_sw128(b1 + 32u), idesc, 1u);
           } else {
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
@@ -506,11 +518,11 @@ __global__ void k_stream_prep(int K, int d, int dpad, const double* __restrict__
 // decision row n: e_n with max_j |x'_nj| 2^-e_n in [1, 2) (0 for a zero row),
 // y = x'_n 2^(7 - e_n) (largest entry in [128, 256), inside E4M3's 448),
 // split in FP64 into three E4M3 terms, y = B1 + B2 + B3 + r with |r| about
-// 2^-12 |y| (each residual is exact in FP64), scale2[n] = 4^(e_n - 7).  Per
-// K block two planes of Kp rows x 128 B in the 128-byte-swizzled K-major
-// order: rows [B1 | B1] and [B2 | B3], 64 dimensions in each half, so that
-// one pass over a sample row [A1 | A2] against the first plane gives
-// A1 B1 + A2 B1.  Rows n >= K and dimensions j >= d are zero.
+// 2^-12 |y| (each residual is exact in FP64), scale2[n] = 4^(e_n - 7).  The
+// 64-dimension halves of the nkb K blocks, B1 of every block, then B2, then
+// B3, are packed two to a 128-byte row (half h: plane h / 2 of Kp rows, bytes
+// (h % 2) 64 .. + 63) in the 128-byte-swizzled K-major order.  Rows n >= K
+// and dimensions j >= d are zero.
 __global__ void __launch_bounds__(64) k_stream_image8(int d, int K, int Kp, int nkb, const double* __restrict__ Y64,
                                                       double* __restrict__ scale2, uint8_t* __restrict__ img) {
   __shared__ double wmax[2];
@@ -555,14 +567,12 @@ __global__ void __launch_bounds__(64) k_stream_image8(int d, int K, int Kp, int 
       w2[w] = b2;
       w3[w] = b3;
     }
-    const size_t blk = (size_t)kb * 2 * Kp * 128;
-    const uint32_t o_a = (uint32_t)(n * 128 + ((g ^ (n & 7)) << 4));
-    const uint32_t o_b = (uint32_t)(n * 128 + (((4 + g) ^ (n & 7)) << 4));
-    const uint4 u1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-    *reinterpret_cast<uint4*>(img + blk + o_a) = u1;
-    *reinterpret_cast<uint4*>(img + blk + o_b) = u1;
-    *reinterpret_cast<uint4*>(img + blk + (size_t)Kp * 128 + o_a) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-    *reinterpret_cast<uint4*>(img + blk + (size_t)Kp * 128 + o_b) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+    auto unit = [&](int h) {   // this row's 16-byte unit g of half h
+      return (size_t)(h >> 1) * Kp * 128 + (size_t)n * 128 + (size_t)((((h & 1) * 4 + g) ^ (n & 7)) << 4);
+    };
+    *reinterpret_cast<uint4*>(img + unit(kb)) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    *reinterpret_cast<uint4*>(img + unit(nkb + kb)) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+    *reinterpret_cast<uint4*>(img + unit(2 * nkb + kb)) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
   }
 }
 
@@ -652,7 +662,8 @@ struct SPlan {
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-SPlan stream_plan(const saa_ctx* ctx, int64_t N, int d, int K) {
+SPlan stream_plan(const saa_ctx* ctx, int64_t N, int d, int K, saa_prec prec) {
+  const bool f8 = prec == SAA_FP8X;
   SPlan p;
   p.Kp = (K + 31) / 32 * 32;
   p.nkb = (d + tc::kSKB - 1) / tc::kSKB;
@@ -661,8 +672,8 @@ SPlan stream_plan(const saa_ctx* ctx, int64_t N, int d, int K) {
   p.grid = (int)(p.tiles < ctx->sm_count ? p.tiles : ctx->sm_count);
   // as many 32 KB stages as the shared memory left by the decision image holds
   p.nst = tc::kSMaxStages;
-  while (p.nst > 2 && (int)tc::stream_smem_bytes(p.Kp, p.nkb, p.nst) > ctx->smem_optin) --p.nst;
-  p.smem = (int)tc::stream_smem_bytes(p.Kp, p.nkb, p.nst);
+  while (p.nst > 2 && (int)tc::stream_smem_bytes(p.Kp, p.nkb, p.nst, f8) > ctx->smem_optin) --p.nst;
+  p.smem = (int)tc::stream_smem_bytes(p.Kp, p.nkb, p.nst, f8);
   size_t off = 0;
   p.img = off; off = a256(off + (size_t)p.nkb * 2 * p.Kp * 128 + 8 * (size_t)K);
   p.s2 = off; off = a256(off + 8 * (size_t)p.grid * K);
@@ -687,8 +698,9 @@ saa_status stream_check(const saa_ctx* ctx, int64_t N, int d, int K, saa_prec pr
     set_error("saa_eval_samples: streamed samples run at SAA_F16X3, SAA_BF16X3 or SAA_FP8X");
     return SAA_EUNSUPPORTED;
   }
-  const SPlan p = stream_plan(ctx, N, d, K);
-  if (d > 256 || p.Kp > tc::kSMaxKp || (size_t)p.nkb * 2 * p.Kp * 128 > 128 * 1024 || p.smem > ctx->smem_optin) {
+  const SPlan p = stream_plan(ctx, N, d, K, prec);
+  if (d > 256 || p.Kp > tc::kSMaxKp || tc::img_bytes(p.Kp, p.nkb, prec == SAA_FP8X) > 128 * 1024 ||
+      p.smem > ctx->smem_optin) {
     set_error("saa_eval_samples: needs d <= 256, K <= 256 and a decision image of at most 128 KB");
     return SAA_EUNSUPPORTED;
   }
@@ -703,7 +715,7 @@ using namespace saa;
 extern "C" size_t saa_eval_samples_workspace_size(const saa_ctx* ctx, int64_t N, int32_t d, int32_t K,
                                                   saa_prec prec) {
   if (stream_check(ctx, N, d, K, prec) != SAA_OK) return 0;
-  return stream_plan(ctx, N, d, K).total;
+  return stream_plan(ctx, N, d, K, prec).total;
 }
 
 extern "C" saa_status saa_eval_samples(saa_ctx* ctx, int64_t N, int32_t d, const float* R, const double* center,
@@ -721,7 +733,7 @@ extern "C" saa_status saa_eval_samples(saa_ctx* ctx, int64_t N, int32_t d, const
     set_error("saa_eval_samples: SAA_FP8X needs center and sigma (E4M3 keeps 1e-4 only on centred, scaled samples)");
     return SAA_EINVAL;
   }
-  const SPlan p = stream_plan(ctx, N, d, K);
+  const SPlan p = stream_plan(ctx, N, d, K, prec);
   if (ws_bytes < p.total) {
     set_error("saa_eval_samples: workspace smaller than saa_eval_samples_workspace_size()");
     return SAA_ENOMEM;
