@@ -760,7 +760,7 @@ def run_covariance(args, dev, world, rank, flush, stream):
 # workload (d = 128, N = 2^20, K = 256), from one ncu capture at full size
 # (dram__bytes_read.sum + dram__bytes_write.sum): the algorithmic N d 4 =
 # 536,870,912 B of samples plus the decision image and the partials.
-STREAM_TRAFFIC = {("fp8x", 128, 1 << 20, 256): 537204736.0}
+STREAM_TRAFFIC = {("fp8x", 128, 1 << 20, 256): 537204480.0}
 
 
 def run_streamed(args, dev, world, rank, flush, stream):
