@@ -751,6 +751,41 @@ def run_covariance(args, dev, world, rank, flush, stream):
                                   "frac": ops / kern_s / 1e12 / peak, "issued_frac": issued / kern_s / 1e12 / peak,
                                   "note": "Gram kernel: generator-only kernel's instructions per normal "
                                           "(issued_frac adds the hi/lo split)"}}
+    # blocked form at d = 1024 (M in 128 x 128 blocks, each block's CTAs
+    # drawing its two dimension slices): value and gradient for K = 64
+    db, Kb = 1024, 64
+    instb = inputs.instance(db, 0)
+    probb = saa.Problem(mu=torch.tensor(instb.mu, device=dev), chol=torch.tensor(instb.chol, device=dev), N=N,
+                        law=law, seed=0, instance=rank)
+    Xb = torch.tensor(inputs.decisions(Kb, db, 0), device=dev)
+    ewsb = torch.empty(1 << 26, dtype=torch.uint8, device=dev)
+
+    def stepb():
+        mom = saa.saa_moments(probb, prec, ws=mws)
+        return saa.saa_eval_moments(probb, Xb, mom, want_grad=True, ws=ewsb)
+    stepb()
+    torch.cuda.synchronize(dev)
+    saa.saa_profile_enable(True, dev.index)
+    nb_steps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nb_steps):
+        stepb()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    main_ms, main_n, _ = saa.saa_profile_read(dev.index)
+    saa.saa_profile_enable(False, dev.index)
+    saa.saa_ctx_sync(dev.index)
+    kern_s = main_ms / 1e3 / max(1, main_n)
+    nslices = (db + 127) // 128
+    ops = float(N) * db * _gen_per_normal(law)
+    res["blocked_d1024_K64_value_and_gradient"] = {
+        "ms_per_step": e0.elapsed_time(e1) / nb_steps, "gram_kernel_ms": kern_s * 1e3,
+        "value": world * N * Kb / (e0.elapsed_time(e1) / nb_steps / 1e3), "unit": "evals/s",
+        "roofline": {"bound": "alu", "frac": ops / kern_s / 1e12 / _alu_peak(_peaks()[0]),
+                     "issued_frac": nslices * ops / kern_s / 1e12 / _alu_peak(_peaks()[0]),
+                     "note": f"frac counts one draw per normal; every normal is drawn {nslices} times "
+                             "(once per block that needs its slice)"}}
     return {"metric": "scenario-decision evals/s (covariance-first)", "config": {
         "workload": WORKLOAD["name"], "d": d, "N": N, "K": K, "prec": prec,
         "method": "M = sum a a' once on tcgen05, then S2 = y'My, G = My per decision in FP64"}, **res}

@@ -417,7 +417,7 @@ saa_status saa_generate_moments(saa_ctx* ctx, const saa_problem* prob, int64_t i
                                 double* sum, double* sumsq, void* ws, size_t ws_bytes, void* stream);
 
 /* Covariance-first form (Sec. 3.1: the sample mean and covariance formed
- * once per resample), for d <= 128 on the tensor cores.  With the whitened
+ * once per resample), for d <= 1024 on the tensor cores.  With the whitened
  * samples a_i = s_i zhat_i of resample prob->epoch:
  *   saa_moments       M = sum_i a_i a_i' (device [d*d] FP64, row-major) and
  *                     mt = sum_i a_i (device [d] FP64); prec SAA_F16X3 or
@@ -430,7 +430,10 @@ saa_status saa_generate_moments(saa_ctx* ctx, const saa_problem* prob, int64_t i
  *                     all in FP64.  Scratch: saa_eval_moments_workspace_size().
  * The moments' work does not depend on K: evaluating many decisions, or
  * many iterations of Algorithm 1 on one resample, costs K d^2 FP64
- * multiply-adds each after one saa_moments.  EUNSUPPORTED for d > 128. */
+ * multiply-adds each after one saa_moments.  Above d = 128, M is formed in
+ * 128 x 128 blocks, each block's CTAs drawing the two dimension slices it
+ * needs (every normal drawn up to ceil(d/128) times at d = 1024); SAA_EINVAL
+ * for d > 1024. */
 size_t saa_moments_workspace_size(const saa_ctx* ctx, const saa_problem* prob, saa_prec prec);
 saa_status saa_moments(saa_ctx* ctx, const saa_problem* prob, saa_prec prec, double* M, double* mt, void* ws,
                        size_t ws_bytes, void* stream);

@@ -1,6 +1,6 @@
 // tc_gram.cu -- covariance-first form of the SAA estimate (Sec. 3.1: the
 // sample mean and covariance of the R_i, formed once per resample) for
-// d <= 128, on tcgen05 tensor cores.
+// d <= 1024, on tcgen05 tensor cores.
 //
 // With a_i = s_i zhat_i (whitened samples), every quantity of Eq. 4, Eq. 5
 // and the gradient follows from two sums over the scenarios:
@@ -10,18 +10,25 @@
 // decisions); saa_eval_moments then evaluates any K decisions, value and
 // gradient, in FP64 at the cost of K d^2 multiply-adds.
 //
-// Kernel (one CTA per SM, persistent over 128-scenario tiles):
-//   generator warps draw each tile transposed -- [dims][scenarios],
-//     K-major over the scenarios, hi/lo of the operand type -- into a
-//     3-stage ring, and fold their draws into the CTA's partial of m~;
-//   one thread issues A'A'^T (M = N = 128 dimensions, 8 k steps of 16
-//     scenarios): hi*hi into two chunk accumulators of 4 k steps each,
-//     hi*lo + lo*hi into a third;
-//   four epilogue warps fold each tile's (chunk + chunk) + corrections
-//     into a running FP32 sum in TMEM with round-to-nearest adds, and at
-//     the end write the CTA's partial of M.
-// TMEM: 4 x 128 columns.  The operands both change with the scenario, so
-// their hi/lo representation error averages out; the chunked hi*hi keeps the
+// M is formed in 128 x 128 blocks M[p, q], p <= q, of the nb = ceil(d / 128)
+// dimension slices (the rest by symmetry).  CTA g takes block pair
+// g mod npairs over the scenario tiles t = g / npairs, + nrange, ... (nrange
+// = the SMs the pairs leave, at least one), so that every SM works.  The
+// generator draws any (scenario, slice) on its own, so each CTA draws the
+// two slices of its pair: at d = 1024 every normal is drawn by up to 8 CTAs,
+// the price of needing no exchange between them.
+// Kernel (one CTA per SM, persistent over 64-scenario tiles):
+//   generator warps draw slices p and q of each tile transposed --
+//     [dims][scenarios], K-major over the scenarios, hi/lo of the operand
+//     type -- into a 3-stage ring (one slice on a diagonal block), and the
+//     diagonal blocks fold their draws into the CTA's partial of m~;
+//   one thread issues A_p A_q^T (M = N = 128 dimensions, 4 k steps of 16
+//     scenarios): hi*hi into one accumulator, hi*lo + lo*hi into another;
+//   four epilogue warps fold each tile's hi*hi + corrections into a running
+//     FP32 sum in TMEM with round-to-nearest adds, and at the end write the
+//     CTA's partial of its block.
+// TMEM: 3 x 128 columns.  The operands both change with the scenario, so
+// their hi/lo representation error averages out; 4 k steps per tile keep the
 // accumulator's rounding bias near two units in the last place per tile.
 // Every wait is clock-bounded.
 #include <cuda_runtime.h>
@@ -35,11 +42,12 @@
 namespace saa {
 namespace tc {
 
-constexpr int kQM = 128;                 // scenarios per tile
-constexpr int kQD = 128;                 // dimensions: MMA M and N
+constexpr int kQM = 64;                  // scenarios per tile of an off-diagonal block (diagonal: 2 kQM)
+constexpr int kQD = 128;                 // dimensions per slice: MMA M and N
+constexpr int kQMaxDim = 1024;
 constexpr int kQStages = 3;
 constexpr int kQSub = kQD * 128;         // one [128 dims][64 scenarios] 16-bit block
-constexpr int kQStageBytes = 4 * kQSub;  // [2 scenario halves][hi, lo]
+constexpr int kQStageBytes = 4 * kQSub;  // [slice p, slice q][hi, lo]
 constexpr int kQEpi = 4;
 constexpr int kQMma = 4;
 constexpr int kQRng = 16;
@@ -49,8 +57,9 @@ constexpr int kQSBufs = 4;
 struct QArgs {
   LawArgs la;
   int64_t tiles;
-  float* part_M;    // [grid][128][128] row j (TMEM lane), column l
-  double* part_m;   // [grid][d]
+  int nb, npairs, nrange;   // slices, block pairs p <= q, scenario ranges (CTA g: pair g % npairs, range g / npairs)
+  float* part_M;    // [grid][128][128] row j (TMEM lane) of slice p, column l of slice q
+  double* part_m;   // [grid][2 halves][d] (diagonal blocks: their slice's entries)
   uint32_t* err;
 };
 
@@ -61,7 +70,7 @@ struct QSmem {
   uint64_t g_full, g_empty, drain;
   uint32_t tmem_base;
   uint32_t abort_flag;
-  float s_buf[kQSBufs][kQM];
+  float s_buf[kQSBufs][2 * kQM];
 };
 
 size_t gram_smem_bytes() { return (size_t)kQStages * kQStageBytes + sizeof(QSmem); }
@@ -83,12 +92,27 @@ __global__ void __launch_bounds__(kQThreads, 1) k_tc_gram(QArgs a) {
   const int d = la.d;
   volatile uint32_t* abort_flag = &sm->abort_flag;
 
+  // this CTA's block pair (p, q), p <= q, in row order, and scenario range;
+  // a diagonal block takes 128-scenario tiles (both halves of the stage hold
+  // slice p), an off-diagonal one 64-scenario tiles (slices p and q)
+  int bp = 0, bq = (int)(blockIdx.x % (uint32_t)a.npairs);
+  while (bq >= a.nb - bp) {
+    bq -= a.nb - bp;
+    ++bp;
+  }
+  bq += bp;
+  const bool diag = bp == bq;
+  const int tm = diag ? 2 * kQM : kQM;
+  const int64_t ntiles = ((int64_t)la.N + tm - 1) / tm;
+  const int rg = (int)(blockIdx.x / (uint32_t)a.npairs);
+  const int my_tiles = (rg < ntiles) ? (int)((ntiles - rg + a.nrange - 1) / a.nrange) : 0;
+
   if (threadIdx.x == 0) {
     for (int s = 0; s < kQStages; ++s) {
       mbar_init(smem_u32(&sm->a_full[s]), kQRng);
       mbar_init(smem_u32(&sm->a_empty[s]), 1);
     }
-    for (int s = 0; s < kQSBufs; ++s) mbar_init(smem_u32(&sm->s_ready[s]), kQM / 32);
+    for (int s = 0; s < kQSBufs; ++s) mbar_init(smem_u32(&sm->s_ready[s]), tm / 32);
     mbar_init(smem_u32(&sm->g_full), 1);
     mbar_init(smem_u32(&sm->g_empty), kQEpi);
     mbar_init(smem_u32(&sm->drain), 1);
@@ -101,7 +125,7 @@ __global__ void __launch_bounds__(kQThreads, 1) k_tc_gram(QArgs a) {
   tc_fence_after();
   const uint32_t tmem = sm->tmem_base;
   const uint32_t tg1a = tmem, tg1b = tmem + 128u, tg2 = tmem + 256u, tr = tmem + 384u;
-  const int my_tiles = (int)((a.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+
 
   if (warp == kQMma) {
     // ------------------------------------------------------------ MMA ---
@@ -116,16 +140,20 @@ __global__ void __launch_bounds__(kQThreads, 1) k_tc_gram(QArgs a) {
         if (!ok) break;
         tc_fence_after();
         const uint32_t stage = smem_u32(ring) + (uint32_t)(st * kQStageBytes);
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {   // 16 scenarios per k step
-          const int sb = kk >> 2;
+        // off-diagonal: A = slice p, B = slice q, 4 k steps; diagonal: A = B,
+        // 4 k steps on each half of the stage (the two halves' hi*hi in two
+        // chunk accumulators)
+        const int nk = diag ? 8 : 4;
+        for (int kk = 0; kk < nk; ++kk) {   // 16 scenarios per k step
           const uint32_t o = (uint32_t)((kk & 3) * 32);
-          const uint32_t hi = stage + (uint32_t)((sb * 2 + 0) * kQSub) + o;
-          const uint32_t lo = stage + (uint32_t)((sb * 2 + 1) * kQSub) + o;
+          const uint32_t ha = (uint32_t)((kk >> 2) * 2 * kQSub);           // diagonal: the stage half
+          const uint32_t hb = diag ? ha : 2u * (uint32_t)kQSub;            // slice q (or the same half)
+          const uint32_t ahi = stage + ha + o, alo = stage + ha + (uint32_t)kQSub + o;
+          const uint32_t bhi = stage + hb + o, blo = stage + hb + (uint32_t)kQSub + o;
           const uint32_t g1 = (kk < 4) ? tg1a : tg1b;
-          mma_bf16(g1, desc_sw128(hi), desc_sw128(hi), idesc, (kk & 3) == 0 ? 0u : 1u);
-          mma_bf16(tg2, desc_sw128(hi), desc_sw128(lo), idesc, kk == 0 ? 0u : 1u);
-          mma_bf16(tg2, desc_sw128(lo), desc_sw128(hi), idesc, 1u);
+          mma_bf16(g1, desc_sw128(ahi), desc_sw128(bhi), idesc, (kk & 3) == 0 ? 0u : 1u);
+          mma_bf16(tg2, desc_sw128(ahi), desc_sw128(blo), idesc, kk == 0 ? 0u : 1u);
+          mma_bf16(tg2, desc_sw128(alo), desc_sw128(bhi), idesc, 1u);
         }
         mma_commit(smem_u32(&sm->a_empty[st]));
         mma_commit(smem_u32(&sm->g_full));
@@ -150,11 +178,11 @@ __global__ void __launch_bounds__(kQThreads, 1) k_tc_gram(QArgs a) {
       for (int c0 = 0; c0 < kQD; c0 += 16) {
         uint32_t x[16], y[16];
         tmem_ld16(tg1a + lane_base + (uint32_t)c0, x);
-        tmem_ld16(tg1b + lane_base + (uint32_t)c0, y);
+        if (diag) tmem_ld16(tg1b + lane_base + (uint32_t)c0, y);
         tmem_wait_ld();
         float p[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) p[i] = __uint_as_float(x[i]) + __uint_as_float(y[i]);
+        for (int i = 0; i < 16; ++i) p[i] = diag ? __uint_as_float(x[i]) + __uint_as_float(y[i]) : __uint_as_float(x[i]);
         tmem_ld16(tg2 + lane_base + (uint32_t)c0, x);
         if (tt > 0) tmem_ld16(tr + lane_base + (uint32_t)c0, y);
         tmem_wait_ld();
@@ -192,21 +220,25 @@ __global__ void __launch_bounds__(kQThreads, 1) k_tc_gram(QArgs a) {
     const gen::Stream gs = gen::make_stream(la.seed, la.epoch, la.instance);
     const uint32_t half = la.N / 2u;
     const bool tlaw = la.law == SAA_LAW_STUDENT_T;
-    // dimensions 4 b4 .. 4 b4 + 3, scenarios 8 g8 .. 8 g8 + 7 of every tile, one
-    // scenario pair (4 bytes) per store, pair order staggered by lane group
-    const int b4 = rt >> 4, g8 = rt & 15;
-    const int asb = g8 >> 3, au = g8 & 7;
-    const int pfirst = lane >> 3;
-    const int jb = 4 * b4;
+    // stage half blk: slice p (blk 0) or q (blk 1) of the tile's 64
+    // scenarios, or on a diagonal block slice p of scenarios 64 blk ..
+    // 64 blk + 63; dimensions 4 b4 .. 4 b4 + 3 of the slice, scenarios
+    // 8 g8 .. 8 g8 + 7 of the half, one scenario pair (4 bytes) per store,
+    // pair order staggered by lane group
+    const int blk = rt >> 8, b4 = (rt >> 3) & 31, g8 = rt & 7;
+    const int pfirst = (lane >> 3) & 3;
+    const int jb = 4 * b4;                                           // row of the stage (dimension within the slice)
+    const int jg = ((diag || blk == 0) ? bp : bq) * kQD + jb;        // dimension
+    const int sh = diag ? kQM * blk : 0;                             // first scenario of the half
     int st = 0;
     uint32_t ph = 0;
     for (int tt = 0; tt < my_tiles; ++tt) {
-      const uint32_t tile = blockIdx.x + (uint32_t)tt * gridDim.x;
-      const uint32_t i0 = tile * (uint32_t)kQM;
-      const int nrow = (int)min((uint32_t)kQM, la.N - i0);
+      const uint32_t tile = (uint32_t)rg + (uint32_t)tt * (uint32_t)a.nrange;
+      const uint32_t i0 = tile * (uint32_t)tm;
+      const int nrow = (int)min((uint32_t)tm, la.N - i0);
       const int sb4 = tt & (kQSBufs - 1);
       const uint32_t s_bar = smem_u32(&sm->s_ready[sb4]);
-      if (tlaw && rt < kQM) {
+      if (tlaw && rt < tm) {
         sm->s_buf[sb4][rt] = (rt < nrow) ? gen::t_scale_f(gs, i0 + (uint32_t)rt, la.nu) : 0.0f;
         __syncwarp();
         if (lane == 0) mbar_arrive(s_bar);
@@ -215,63 +247,68 @@ __global__ void __launch_bounds__(kQThreads, 1) k_tc_gram(QArgs a) {
       if (tlaw && !warp_wait(s_bar, (uint32_t)((tt >> 2) & 1), abort_flag, a.err)) break;
       uint8_t* stage = ring + st * kQStageBytes;
       float msum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      {
 #pragma unroll 1
-      for (int p = 0; p < 4; ++p) {
-        const int pq = (p + pfirst) & 3;   // scenarios 8 g8 + 2 pq, + 1
-        const int r0 = 8 * g8 + 2 * pq;
-        float z0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, z1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (jb < d) {
-          if (r0 < nrow) {
-            const uint32_t i = i0 + (uint32_t)r0;
-            gen::Gen<float>::block(gs, (uint32_t)(jb >> 2), i, gen::is_lognormal(la.law, i, half), z0);
-            if (tlaw) {
-              const float s0 = sm->s_buf[sb4][r0];
+        for (int p = 0; p < 4; ++p) {
+          const int pq = (p + pfirst) & 3;   // scenarios 8 g8 + 2 pq, + 1 of the half
+          const int r0 = sh + 8 * g8 + 2 * pq;
+          float z0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, z1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          if (jg < d) {
+            if (r0 < nrow) {
+              const uint32_t i = i0 + (uint32_t)r0;
+              gen::Gen<float>::block(gs, (uint32_t)(jg >> 2), i, gen::is_lognormal(la.law, i, half), z0);
+              if (tlaw) {
+                const float s0 = sm->s_buf[sb4][r0];
 #pragma unroll
-              for (int e = 0; e < 4; ++e) z0[e] *= s0;
+                for (int e = 0; e < 4; ++e) z0[e] *= s0;
+              }
+#pragma unroll
+              for (int e = 0; e < 4; ++e) z0[e] = (D4 || jg + e < d) ? z0[e] : 0.0f;
             }
+            if (r0 + 1 < nrow) {
+              const uint32_t i = i0 + (uint32_t)r0 + 1u;
+              gen::Gen<float>::block(gs, (uint32_t)(jg >> 2), i, gen::is_lognormal(la.law, i, half), z1);
+              if (tlaw) {
+                const float s1 = sm->s_buf[sb4][r0 + 1];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) z0[e] = (D4 || jb + e < d) ? z0[e] : 0.0f;
+                for (int e = 0; e < 4; ++e) z1[e] *= s1;
+              }
+#pragma unroll
+              for (int e = 0; e < 4; ++e) z1[e] = (D4 || jg + e < d) ? z1[e] : 0.0f;
+            }
           }
-          if (r0 + 1 < nrow) {
-            const uint32_t i = i0 + (uint32_t)r0 + 1u;
-            gen::Gen<float>::block(gs, (uint32_t)(jb >> 2), i, gen::is_lognormal(la.law, i, half), z1);
-            if (tlaw) {
-              const float s1 = sm->s_buf[sb4][r0 + 1];
 #pragma unroll
-              for (int e = 0; e < 4; ++e) z1[e] *= s1;
-            }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) z1[e] = (D4 || jb + e < d) ? z1[e] : 0.0f;
+          for (int e = 0; e < 4; ++e) {
+            msum[e] += z0[e] + z1[e];
+            const int jr = jb + e;   // row of the stage
+            const uint32_t h = pack2<F16>(z0[e], z1[e]);
+            const float2 f = unpack2<F16>(h);
+            const uint32_t l = pack2<F16>(z0[e] - f.x, z1[e] - f.y);
+            const uint32_t off = (uint32_t)(jr * 128 + ((g8 ^ (jr & 7)) << 4) + pq * 4);
+            *reinterpret_cast<uint32_t*>(stage + (blk * 2 + 0) * kQSub + off) = h;
+            *reinterpret_cast<uint32_t*>(stage + (blk * 2 + 1) * kQSub + off) = l;
           }
         }
+      }
+      // m~ (diagonal blocks): fold the 8 lanes that share these dimensions;
+      // lane g8 == 0 of each half owns them in that half's partial row
+      if (diag) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          msum[e] += z0[e] + z1[e];
-          const int jr = jb + e;   // row of the stage
-          const uint32_t h = pack2<F16>(z0[e], z1[e]);
-          const float2 f = unpack2<F16>(h);
-          const uint32_t l = pack2<F16>(z0[e] - f.x, z1[e] - f.y);
-          const uint32_t off = (uint32_t)(jr * 128 + ((au ^ (jr & 7)) << 4) + pq * 4);
-          *reinterpret_cast<uint32_t*>(stage + (asb * 2 + 0) * kQSub + off) = h;
-          *reinterpret_cast<uint32_t*>(stage + (asb * 2 + 1) * kQSub + off) = l;
+#pragma unroll
+          for (int o = 1; o < 8; o <<= 1) msum[e] += __shfl_xor_sync(0xffffffffu, msum[e], o);
         }
-      }
-      // m~: fold the 16 lanes that share these dimensions; lane g8 == 0 owns them
+        if (g8 == 0) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-#pragma unroll
-        for (int o = 1; o < 16; o <<= 1) msum[e] += __shfl_xor_sync(0xffffffffu, msum[e], o);
-      }
-      if (g8 == 0) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (jb + e < d) {
-            double* pm = a.part_m + (size_t)blockIdx.x * d + jb + e;
-            if (tt == 0)
-              *pm = (double)msum[e];
-            else
-              atomicAdd(pm, (double)msum[e]);
-          }
+          for (int e = 0; e < 4; ++e)
+            if (jg + e < d) {
+              double* pm = a.part_m + ((size_t)blockIdx.x * 2 + blk) * d + jg + e;
+              if (tt == 0)
+                *pm = (double)msum[e];
+              else
+                atomicAdd(pm, (double)msum[e]);
+            }
+        }
       }
       fence_proxy_async();
       __syncwarp();
@@ -300,20 +337,29 @@ __device__ __forceinline__ void nm_add(double& s, double& c, double x) {
   s = t;
 }
 
-// M_jl = sum over CTAs of part_M[g][j][l] (float-float pairs: branch-free
-// TwoSum), mt_j = sum of part_m[g][j] (Neumaier); one block per (row j,
-// 32 columns), warp w takes CTAs w, w + 8, ..., merged in warp order.
-__global__ void __launch_bounds__(256) k_gram_reduce(int grid, int d, const float* __restrict__ part_M,
+// M_jl = sum over the scenario ranges of block (p, q)'s partials, p = j / 128
+// and q = l / 128 (or the transposed entry of block (q, p) when p > q), as
+// float-float pairs (branch-free TwoSum); mt_j = sum over the ranges of the
+// diagonal block's two partials of m~ (Neumaier).  One block per (row j, 32
+// columns); warp w takes ranges w, w + 8, ..., merged in warp order.
+__global__ void __launch_bounds__(256) k_gram_reduce(int nb, int npairs, int nrange, int d,
+                                                     const float* __restrict__ part_M,
                                                      const double* __restrict__ part_m, double* __restrict__ M,
                                                      double* __restrict__ mt) {
   __shared__ double sh_s[8][32], sh_c[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blockIdx.y;
   const int l = blockIdx.x * 32 + lane;
+  // the block holding M_jl, and the entry's row / column within it
+  const int pj = j >> 7, pl = l >> 7;
+  const bool tr = pj > pl;
+  const int p = tr ? pl : pj, q = tr ? pj : pl;
+  const int jj = tr ? (l & 127) : (j & 127), ll = tr ? (j & 127) : (l & 127);
+  const int pair = p * nb - p * (p - 1) / 2 + (q - p);   // row-order index of (p, q), p <= q
   float S = 0.0f, E = 0.0f;
   if (l < d)
-    for (int g = warp; g < grid; g += 8) {
-      const float x = part_M[((size_t)g * 128 + j) * 128 + l];
+    for (int r = warp; r < nrange; r += 8) {
+      const float x = part_M[(((size_t)r * npairs + pair) * 128 + jj) * 128 + ll];
       const float t = __fadd_rn(S, x);
       const float bb = __fsub_rn(t, S);
       E = __fadd_rn(E, __fadd_rn(__fsub_rn(S, __fsub_rn(t, bb)), __fsub_rn(x, bb)));
@@ -330,56 +376,71 @@ __global__ void __launch_bounds__(256) k_gram_reduce(int grid, int d, const floa
     }
     M[(size_t)j * d + l] = s + c;
   }
-  if (blockIdx.x == 0 && warp == 1 && lane == 0) {
+  if (blockIdx.x == 0 && warp == 1) {
+    // lane L adds the partials of ranges L, L + 32, ... (both halves), then
+    // the lanes' sums merge by a fixed shuffle tree
+    const int dp = pj * nb - pj * (pj - 1) / 2;   // the diagonal block of j's slice
     double s = 0.0, c = 0.0;
-    for (int g = 0; g < grid; ++g) nm_add(s, c, part_m[(size_t)g * d + j]);
-    mt[j] = s + c;
+    for (int r = lane; r < nrange; r += 32)
+      for (int h = 0; h < 2; ++h) nm_add(s, c, part_m[(((size_t)r * npairs + dp) * 2 + h) * d + j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double os = __shfl_down_sync(0xffffffffu, s, o), oc = __shfl_down_sync(0xffffffffu, c, o);
+      nm_add(s, c, os);
+      c += oc;
+    }
+    if (lane == 0) mt[j] = s + c;
   }
 }
 
-// Per decision k (one block): t = M y_k, S2 = y_k't, S1 = mt'y_k; f, pbar, var;
-// with a gradient, u_k = lambda 2/(N-1) (t - S1 m) - m with m = mt/N.
-__global__ void __launch_bounds__(128) k_gram_eval(int K, int d, double N, double lambda, const double* __restrict__ M,
+// Per decision k (one block of min(256, d rounded up to 32) threads, y_k in
+// shared memory): S1 =
+// mt'y_k, then t = M y_k row by row, S2 = y_k't; f, pbar, var; with a
+// gradient, u_k = lambda 2/(N-1) (t - S1 m) - m with m = mt/N.  Sums in a
+// fixed order (per thread, then a shuffle tree, then the warps in order).
+__device__ __forceinline__ double gram_block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+__global__ void __launch_bounds__(256) k_gram_eval(int K, int d, double N, double lambda, const double* __restrict__ M,
                                                    const double* __restrict__ mt, const double* __restrict__ Y64,
                                                    const double* __restrict__ c, double* __restrict__ f,
                                                    double* __restrict__ pbar, double* __restrict__ var,
                                                    double* __restrict__ u) {
-  __shared__ double ys[128], red2[4], red1[4];
+  extern __shared__ double ys[];   // [d]
+  __shared__ double red[8];
   const int k = blockIdx.x;
-  const int j = threadIdx.x;
-  const int lane = j & 31, warp = j >> 5;
-  if (j < d) ys[j] = Y64[(size_t)k * d + j];
+  for (int j = threadIdx.x; j < d; j += blockDim.x) ys[j] = Y64[(size_t)k * d + j];
   __syncthreads();
-  double t = 0.0, p2 = 0.0, p1 = 0.0;
-  if (j < d) {
+  double p1 = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) p1 = fma(mt[j], ys[j], p1);
+  const double S1 = gram_block_sum(p1, red);
+  double p2 = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
     const double* Mj = M + (size_t)j * d;
+    double t = 0.0;
     for (int l = 0; l < d; ++l) t = fma(Mj[l], ys[l], t);
-    p2 = ys[j] * t;
-    p1 = mt[j] * ys[j];
+    p2 = fma(ys[j], t, p2);
+    if (u) {
+      const double mj = mt[j] / N;
+      u[(size_t)k * d + j] = lambda * (2.0 / (N - 1.0)) * (t - S1 * mj) - mj;
+    }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    p2 += __shfl_down_sync(0xffffffffu, p2, o);
-    p1 += __shfl_down_sync(0xffffffffu, p1, o);
-  }
-  if (lane == 0) {
-    red2[warp] = p2;
-    red1[warp] = p1;
-  }
-  __syncthreads();
-  const double S2 = (red2[0] + red2[1]) + (red2[2] + red2[3]);
-  const double S1 = (red1[0] + red1[1]) + (red1[2] + red1[3]);
-  if (j == 0) {
+  const double S2 = gram_block_sum(p2, red);
+  if (threadIdx.x == 0) {
     const double qbar = S1 / N;
     const double pb = c[k] + qbar;
     const double V = (S2 - S1 * qbar) / (N - 1.0);
     if (f) f[k] = lambda * V - pb;
     if (pbar) pbar[k] = pb;
     if (var) var[k] = V;
-  }
-  if (u && j < d) {
-    const double mj = mt[j] / N;
-    u[(size_t)k * d + j] = lambda * (2.0 / (N - 1.0)) * (t - S1 * mj) - mj;
   }
 }
 
@@ -388,10 +449,10 @@ saa_status gram_check(const saa_ctx* ctx, const saa_problem* p, saa_prec prec) {
     set_error("saa_moments: ctx and prob must be non-NULL");
     return SAA_EINVAL;
   }
-  if (p->d < 1 || p->d > tc::kQD || p->N < 2 || p->N > 0xffffffffll || p->law < SAA_LAW_GAUSS ||
+  if (p->d < 1 || p->d > tc::kQMaxDim || p->N < 2 || p->N > 0xffffffffll || p->law < SAA_LAW_GAUSS ||
       p->law > SAA_LAW_MIX || (p->law == SAA_LAW_STUDENT_T && (p->nu < 2 || (p->nu & 1) || p->nu > 64)) ||
       p->reserved != 0 || !p->mu || !p->chol) {
-    set_error("saa_moments: need 1 <= d <= 128, 2 <= N < 2^32, a known law and device mu, chol");
+    set_error("saa_moments: need 1 <= d <= 1024, 2 <= N < 2^32, a known law and device mu, chol");
     return SAA_EINVAL;
   }
   if (!is_tc(prec)) {
@@ -405,9 +466,24 @@ saa_status gram_check(const saa_ctx* ctx, const saa_problem* p, saa_prec prec) {
   return SAA_OK;
 }
 
-int gram_grid(const saa_ctx* ctx, const saa_problem* p) {
-  const int64_t tiles = (p->N + tc::kQM - 1) / tc::kQM;
-  return (int)(tiles < ctx->sm_count ? tiles : ctx->sm_count);
+// Grid of the Gram kernel: every block pair p <= q of the nb slices, times
+// as many scenario ranges as the SMs leave (at least one, at most the tiles).
+struct GramPlan {
+  int nb, npairs, nrange, grid;
+  int64_t tiles;
+};
+GramPlan gram_plan(const saa_ctx* ctx, const saa_problem* p) {
+  GramPlan g;
+  g.nb = (p->d + tc::kQD - 1) / tc::kQD;
+  g.npairs = g.nb * (g.nb + 1) / 2;
+  g.tiles = (p->N + tc::kQM - 1) / tc::kQM;
+  const int64_t dtiles = (p->N + 2 * tc::kQM - 1) / (2 * tc::kQM);   // a diagonal block's tiles
+  int64_t nr = ctx->sm_count / g.npairs;
+  if (nr < 1) nr = 1;
+  if (nr > dtiles) nr = dtiles;   // every range has a tile of every block
+  g.nrange = (int)nr;
+  g.grid = g.npairs * g.nrange;
+  return g;
 }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -431,8 +507,8 @@ using namespace saa;
 
 extern "C" size_t saa_moments_workspace_size(const saa_ctx* ctx, const saa_problem* prob, saa_prec prec) {
   if (gram_check(ctx, prob, prec) != SAA_OK) return 0;
-  const size_t g = (size_t)gram_grid(ctx, prob);
-  return al256(sizeof(float) * g * tc::kQD * tc::kQD) + al256(sizeof(double) * g * prob->d);
+  const size_t g = (size_t)gram_plan(ctx, prob).grid;
+  return al256(sizeof(float) * g * tc::kQD * tc::kQD) + al256(sizeof(double) * g * 2 * prob->d);
 }
 
 extern "C" saa_status saa_moments(saa_ctx* ctx, const saa_problem* prob, saa_prec prec, double* M, double* mt,
@@ -444,9 +520,10 @@ extern "C" saa_status saa_moments(saa_ctx* ctx, const saa_problem* prob, saa_pre
     set_error("saa_moments: M, mt and a 256-byte aligned ws are required");
     return SAA_EINVAL;
   }
-  const int grid = gram_grid(ctx, prob);
+  const GramPlan gp = gram_plan(ctx, prob);
+  const int grid = gp.grid;
   const size_t pm_off = al256(sizeof(float) * (size_t)grid * tc::kQD * tc::kQD);
-  if (ws_bytes < pm_off + al256(sizeof(double) * (size_t)grid * prob->d)) {
+  if (ws_bytes < pm_off + al256(sizeof(double) * (size_t)grid * 2 * prob->d)) {
     set_error("saa_moments: workspace smaller than saa_moments_workspace_size()");
     return SAA_ENOMEM;
   }
@@ -461,7 +538,10 @@ extern "C" saa_status saa_moments(saa_ctx* ctx, const saa_problem* prob, saa_pre
   a.la.epoch = prob->epoch;
   a.la.t_dev = nullptr;
   a.la.M = 1;
-  a.tiles = (prob->N + tc::kQM - 1) / tc::kQM;
+  a.tiles = gp.tiles;
+  a.nb = gp.nb;
+  a.npairs = gp.npairs;
+  a.nrange = gp.nrange;
   a.part_M = (float*)ws;
   a.part_m = (double*)((char*)ws + pm_off);
   a.err = ctx->err;
@@ -477,13 +557,14 @@ extern "C" saa_status saa_moments(saa_ctx* ctx, const saa_problem* prob, saa_pre
   if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], st);
   kern<<<grid, tc::kQThreads, smem, st>>>(a);
   if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n++ + 1], st);
-  k_gram_reduce<<<dim3((prob->d + 31) / 32, prob->d), 256, 0, st>>>(grid, prob->d, a.part_M, a.part_m, M, mt);
+  k_gram_reduce<<<dim3((prob->d + 31) / 32, prob->d), 256, 0, st>>>(gp.nb, gp.npairs, gp.nrange, prob->d, a.part_M,
+                                                                     a.part_m, M, mt);
   ctx->kernels += 2;
   return cuda_status(cudaGetLastError(), "saa_moments: launch");
 }
 
 extern "C" size_t saa_eval_moments_workspace_size(const saa_problem* prob, int32_t K) {
-  if (!prob || prob->d < 1 || prob->d > tc::kQD || K < 1 || K > 65535) return 0;
+  if (!prob || prob->d < 1 || prob->d > tc::kQMaxDim || K < 1 || K > 65535) return 0;
   const size_t d = (size_t)prob->d, k = (size_t)K;
   return al256(8 * k * d) + al256(8 * k) + al256(8 * k * d);
 }
@@ -492,8 +573,8 @@ extern "C" saa_status saa_eval_moments(saa_ctx* ctx, const saa_problem* prob, in
                                        const double* M, const double* mt, double* f, double* pbar, double* var,
                                        double* grad, void* ws, size_t ws_bytes, void* stream) {
   saa::NvtxRange nvtx_range("saa_eval_moments");
-  if (!ctx || !prob || prob->d < 1 || prob->d > tc::kQD || prob->N < 2 || !prob->mu || !prob->chol) {
-    set_error("saa_eval_moments: need ctx, and a problem with 1 <= d <= 128, N >= 2, device mu, chol");
+  if (!ctx || !prob || prob->d < 1 || prob->d > tc::kQMaxDim || prob->N < 2 || !prob->mu || !prob->chol) {
+    set_error("saa_eval_moments: need ctx, and a problem with 1 <= d <= 1024, N >= 2, device mu, chol");
     return SAA_EINVAL;
   }
   if (K < 1 || K > 65535 || !X || !M || !mt || !ws || (((uintptr_t)ws) & 255u) || !(f || pbar || var || grad)) {
@@ -515,8 +596,9 @@ extern "C" saa_status saa_eval_moments(saa_ctx* ctx, const saa_problem* prob, in
   // y_k = C'w_k and c_k = mu'w_k in FP64 (no contraction-precision copy)
   saa_status s = cuda_status(launch_prologue(prob, K, X, SAA_F16X3, w, ctx->err, st), "saa_eval_moments: prologue");
   if (s != SAA_OK) return s;
-  k_gram_eval<<<K, 128, 0, st>>>(K, prob->d, (double)prob->N, prob->lambda, M, mt, w.Y64, w.c, f, pbar, var,
-                                 grad ? u : nullptr);
+  const int et = (int)(d < 256 ? (d + 31) / 32 * 32 : 256);
+  k_gram_eval<<<K, et, sizeof(double) * d, st>>>(K, prob->d, (double)prob->N, prob->lambda, M, mt, w.Y64, w.c, f,
+                                                 pbar, var, grad ? u : nullptr);
   int launched = 2;
   if (grad) {
     launch_grad_out(K, prob->d, prob->chol, prob->mu, u, grad, st);

@@ -2,9 +2,10 @@
 M = sum_i a_i a_i' and mt = sum_i a_i of the whitened samples, formed once on
 the tensor cores, then Eq. 4, Eq. 5 and the gradient for any K decisions in
 FP64.  Checked against the oracle's plain definition on the same samples
-(every law, d up to 128, K up to 256), M and mt directly against sums of the
-oracle's draws, and against the direct tensor-core path at the full
-d = 128, N = 2^20, K = 256 workload."""
+(every law, d up to 128, K up to 256; d = 130 to 1024, where M is formed in
+128 x 128 blocks, on two laws), M and mt directly against sums of the
+oracle's draws (one slice and three), and against the direct tensor-core
+path at the full d = 128, N = 2^20, K = 256 workload."""
 import numpy as np
 import pytest
 import torch
@@ -39,10 +40,23 @@ def test_covariance_first_matches_oracle(d, N, K, law, prec):
     assert e_f <= TOL[prec] and e_p <= TOL[prec] and e_g <= TOL_GRAD[prec]
 
 
+@pytest.mark.parametrize("d,N,K", [(130, 5_000, 9), (256, 4_099, 17), (300, 3_000, 33), (1024, 2_500, 64)])
+@pytest.mark.parametrize("law", [oracle.LAW_GAUSS, oracle.LAW_STUDENT_T])
 @pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
-def test_moments_against_sums_of_oracle_draws(prec):
+def test_covariance_first_blocked_matches_oracle(d, N, K, law, prec):
+    out, ref, X, inst, _ = _run(d, N, K, law, prec)
+    e_f = est_err(out["f"], ref["f"], ref["var"], X, inst.mu, 0.5)
+    e_p = est_err(out["pbar"], ref["pbar"], ref["var"], X, inst.mu, 0.5)
+    e_g = grad_err(out["grad"], ref["grad"])
+    print(f"{prec} d={d} N={N} K={K} law={law}: f {e_f:.2e} pbar {e_p:.2e} grad {e_g:.2e}")
+    assert e_f <= TOL[prec] and e_p <= TOL[prec] and e_g <= TOL_GRAD[prec]
+
+
+@pytest.mark.parametrize("d", [37, 300])
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+def test_moments_against_sums_of_oracle_draws(d, prec):
     from paper_2404_11631_gb300 import saa
-    d, N = 37, 3001
+    N = 3001
     gp, op, inst = make(d, N, law=oracle.LAW_STUDENT_T, seed=2)
     mom = saa.saa_moments(gp, prec)
     saa.saa_ctx_sync()
@@ -73,7 +87,7 @@ def test_covariance_first_matches_direct_path_full_size():
 
 def test_covariance_first_limits():
     from paper_2404_11631_gb300 import saa
-    gp, op, inst = make(129, 1000)
+    gp, op, inst = make(1025, 1000)
     with pytest.raises(saa.SAAError):
         saa.saa_moments(gp, "f16x3")
     gp, op, inst = make(16, 1000)
