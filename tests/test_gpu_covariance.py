@@ -85,6 +85,22 @@ def test_covariance_first_matches_direct_path_full_size():
     assert grad_err(a["grad"][:64].cpu().numpy(), c["grad"].cpu().numpy()) <= 2e-6
 
 
+def test_covariance_first_blocked_matches_direct_path_large():
+    # d = 1024 (36 blocks of M over 4 scenario ranges), N = 2^18, against
+    # the direct tensor-core value-and-gradient path on the same scenarios
+    from paper_2404_11631_gb300 import saa
+    d, N, K = 1024, 1 << 18, 8
+    gp, op, inst = make(d, N, law=oracle.LAW_MIX, seed=1)
+    X = torch.tensor(inputs.decisions(K, d, seed=1), device="cuda")
+    mom = saa.saa_moments(gp, "f16x3")
+    a = saa.saa_eval_moments(gp, X, mom)
+    b = saa.saa_grad(gp, X, "f16x3")
+    saa.saa_ctx_sync()
+    scale = (0.5 * a["var"] + (X @ gp.mu).abs()).cpu().numpy()
+    assert np.max(np.abs((a["f"] - b["f"]).cpu().numpy()) / scale) <= 2e-6
+    assert grad_err(a["grad"].cpu().numpy(), b["grad"].cpu().numpy()) <= 2e-6
+
+
 def test_covariance_first_limits():
     from paper_2404_11631_gb300 import saa
     gp, op, inst = make(1025, 1000)
