@@ -301,11 +301,34 @@ def run_grad(args, dev, world, rank, flush, stream):
     total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     peaks, _ = _peaks()
     kern_s = main_ms / 1e3 / max(1, main_n)
+    # values only on the same workload (saa_eval: the cluster kernel without
+    # its adjoint above d = 256 at the tensor precisions)
+    vws = torch.empty(saa.workspace_size(prob, K, prec, 0), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        saa.saa_eval(prob, X, prec, ws=vws)
+    torch.cuda.synchronize(dev)
+    saa.saa_profile_enable(True, dev.index)
+    vev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        vev[i][0].record(stream)
+        saa.saa_eval(prob, X, prec, ws=vws)
+        vev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    vms, vn, _ = saa.saa_profile_read(dev.index)
+    saa.saa_profile_enable(False, dev.index)
+    vtotal = sum(a.elapsed_time(b) for a, b in vev) / 1e3
+    vkern = vms / 1e3 / max(1, vn)
+    vroof = {"bound": "alu", "frac": float(N) * d * _gen_per_normal(law) / vkern / 1e12 / _alu_peak(peaks),
+             "kernel_ms": vkern * 1e3,
+             "note": "one draw per normal (generator-only kernel's instructions per normal) over the ALU peak"}
     return {"metric": "scenario-decision evals/s with gradient", "value": world * N * K * steps / total_s,
             "unit": "evals/s", "ms_per_step": 1e3 * total_s / steps, "steps": steps,
             "config": {"workload": GRAD_WORKLOAD["name"], "d": d, "N": N, "K": K, "law": "Gaussian",
                        "prec": prec, "l2": "flushed between timed steps"},
-            "gpu_launches": int(launched), "roofline": grad_roofline(prec, d, N, K, law, kern_s, peaks)}
+            "gpu_launches": int(launched), "roofline": grad_roofline(prec, d, N, K, law, kern_s, peaks),
+            "value_only": {"value": world * N * K * steps / vtotal, "unit": "evals/s",
+                           "ms_per_step": 1e3 * vtotal / steps, "roofline": vroof}}
 
 
 FW_WORKLOAD = dict(name="fw_d1024_N4M_t4_T200", d=1024, N=1 << 22, law=2, nu=4, T=200, M=1)

@@ -567,7 +567,9 @@ saa_status saa_profile_read(saa_ctx* ctx, double* main_ms, int64_t* main_launche
 saa_status saa_plan_info(const saa_ctx* ctx, const saa_problem* prob, int32_t K, saa_prec prec, int want_grad,
                          int32_t* grid, int32_t* cluster, int64_t* tiles);
 
-/* Largest d that `prec` supports. */
+/* Largest d that `prec` supports.  For SAA_F16X3 and SAA_BF16X3 that is
+ * 1024: up to d = 256 any K <= 256 (k_tc_value), above it K <= 64 (the
+ * cluster kernel that splits the dimensions, without its adjoint for values). */
 int32_t saa_max_dim(saa_prec prec);
 
 const char* saa_status_string(saa_status s);

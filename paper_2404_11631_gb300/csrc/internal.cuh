@@ -205,6 +205,7 @@ cudaError_t launch_tc_image(int d, int K, int Kp, int nkb, bool f16, const doubl
 bool tc_grad_supported(const saa_problem* p, int K);
 saa_status tc_grad_plan(const saa_ctx* ctx, const saa_problem* p, int K, Plan* plan);
 cudaError_t launch_tc_grad(const LawArgs& la, int K, int prec, const Plan& plan, const Workspace& ws, uint32_t* err,
-                           cudaStream_t st);
+                           cudaStream_t st,
+                           bool value_only = false);
 
 }  // namespace saa

@@ -56,9 +56,10 @@ saa_status make_plan(const saa_ctx* ctx, const saa_problem* p, int K, saa_prec p
     return tc_grad_plan(ctx, p, K, plan);
   }
   if (is_tc(prec)) {
-    if (!tc_supported(p, K, want_grad))
-      return fail(SAA_EUNSUPPORTED, "tensor-core path: this d/K/gradient combination is not built");
-    return tc_plan(ctx, p, K, plan);
+    if (tc_supported(p, K, want_grad)) return tc_plan(ctx, p, K, plan);
+    // values above d = 256: the cluster kernel without its adjoint
+    if (tc_grad_supported(p, K)) return tc_grad_plan(ctx, p, K, plan);
+    return fail(SAA_EUNSUPPORTED, "tensor-core value path: needs d <= 256 (K <= 256) or d <= 1024 with K <= 64");
   }
   if (prec == SAA_FP8X)
     return fail(SAA_EUNSUPPORTED, "SAA_FP8X runs in the streamed mode only (saa_eval_samples)");
@@ -165,8 +166,9 @@ static saa_status run_estimator(saa_ctx* ctx, const saa_problem* p, int K, const
   if (s != SAA_OK) return s;
   const bool prof = ctx->prof_on && !la.t_dev && ctx->prof_n < 256;
   if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], st);
-  if (is_tc(prec) && want_grad)
-    s = cuda_status(launch_tc_grad(la, K, prec, plan, ws, ctx->err, st), "tensor-core gradient kernel launch");
+  if (is_tc(prec) && (want_grad || plan.cluster > 0))
+    s = cuda_status(launch_tc_grad(la, K, prec, plan, ws, ctx->err, st, !want_grad),
+                    "tensor-core gradient kernel launch");
   else if (is_tc(prec))
     s = cuda_status(launch_tc(la, K, prec, plan, ws, ctx->err, st), "tensor-core kernel launch");
   else
@@ -387,7 +389,7 @@ int32_t saa_max_dim(saa_prec prec) {
     case SAA_FP64:
     case SAA_FP32: return kMaxDimSimt;
     case SAA_BF16X3:
-    case SAA_F16X3: return 256;
+    case SAA_F16X3: return 1024;
     default: return 0;
   }
 }
@@ -640,8 +642,9 @@ saa_status saa_partials(saa_ctx* ctx, const saa_problem* prob, int64_t i0, int64
   cudaStream_t st = (cudaStream_t)stream;
   s = cuda_status(launch_prologue(prob, K, X, prec, w, ctx->err, st), "prologue launch");
   if (s != SAA_OK) return s;
-  if (is_tc(prec) && want_grad)
-    s = cuda_status(launch_tc_grad(la, K, prec, plan, w, ctx->err, st), "tensor-core gradient kernel launch");
+  if (is_tc(prec) && (want_grad || plan.cluster > 0))
+    s = cuda_status(launch_tc_grad(la, K, prec, plan, w, ctx->err, st, !want_grad),
+                    "tensor-core gradient kernel launch");
   else if (is_tc(prec))
     s = cuda_status(launch_tc(la, K, prec, plan, w, ctx->err, st), "tensor-core kernel launch");
   else

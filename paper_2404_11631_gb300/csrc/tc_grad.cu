@@ -137,7 +137,12 @@ __device__ __forceinline__ uint32_t inbox_off(int p, int nr, int l, int k) {
 
 // D8: d is a multiple of 8, so every 8-dimension unit below d is whole and
 // the per-element guards drop out.
-template <bool F16, bool D8>
+// VO (value only): the forward, the exchange of partial Q and S2, without W,
+// the adjoint or G; the tensor-core value path for 256 < d <= 1024, K <= 64.
+// The forward's MMAs release the stage, and w_full becomes the signal that
+// every CTA of the cluster has reduced the tile (4 C arrivals), after which
+// the inbox and the staging in W may be reused.
+template <bool F16, bool D8, bool VO>
 __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t base = smem_u32(smem_raw);
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
     mbar_init(smem_u32(&sm->q_full), 1);
     mbar_init(smem_u32(&sm->q_empty), kGEpiWarps);
     mbar_init(smem_u32(&sm->x_full), kGEpiWarps);
-    mbar_init(smem_u32(&sm->w_full), kGEpiWarps);
+    mbar_init(smem_u32(&sm->w_full), VO ? kGEpiWarps * C : kGEpiWarps);
     mbar_init(smem_u32(&sm->w_free), C);
     mbar_init(smem_u32(&sm->g_full), 1);
     mbar_init(smem_u32(&sm->g_empty), kGEpiWarps);
@@ -251,6 +256,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
             mma_bf16(tq1, desc_sw128(a_hi), desc_sw128(sY + (uint32_t)c * bslice + o), idf1, 1u);
           }
         mma_commit(smem_u32(&sm->q_full));
+        if (VO) mma_commit(smem_u32(&sm->a_empty[st]));   // no adjoint reads the stage
         if (++st == kGStages) { st = 0; ph ^= 1u; }
       }
       // every forward MMA and the operand copy complete before TMEM and the stages are released
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
       if (tt > 0 && !warp_wait_cluster(smem_u32(&sm->w_full), (uint32_t)((tt - 1) & 1), abort_flag, a.err)) break;
       // the last tile's adjoint is done: W is free for the staging below, and
       // that tile's block of G is folded while the other CTAs' copies travel
-      if (tt > 0 && !warp_wait(smem_u32(&sm->g_full), (uint32_t)((tt - 1) & 1), abort_flag, a.err)) break;
+      if (!VO && tt > 0 && !warp_wait(smem_u32(&sm->g_full), (uint32_t)((tt - 1) & 1), abort_flag, a.err)) break;
       tc_fence_after();
       const uint32_t half = (uint32_t)nr * 128u;   // bytes of half an owner's block
 #pragma unroll 1
@@ -363,7 +369,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         mbar_expect_tx(smem_u32(&sm->x_full), (uint32_t)(C - 1) * (uint32_t)nr * 64u);
       }
       __syncwarp();
-      if (tt > 0) fold(tt - 1);
+      if (!VO && tt > 0) fold(tt - 1);
       // ---- reduce this CTA's rows: the C partials in rank order, S2, and W into every CTA
       if (!warp_wait_cluster(smem_u32(&sm->x_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
       float s2t[8];
@@ -391,23 +397,34 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         for (int u = 0; u < 4; ++u) {
           s2t[2 * u] = fmaf(q[2 * u], q[2 * u], s2t[2 * u]);
           s2t[2 * u + 1] = fmaf(q[2 * u + 1], q[2 * u + 1], s2t[2 * u + 1]);
-          const float wa = q[2 * u] * sm->wsc_f[8 * kq + 2 * u];   // powers of two: exact
-          const float wb = q[2 * u + 1] * sm->wsc_f[8 * kq + 2 * u + 1];
-          hp[u] = pack2<F16>(wa, wb);
-          const float2 h = unpack2<F16>(hp[u]);
-          lp[u] = pack2<F16>(wa - h.x, wb - h.y);
         }
-        // decisions 8 kq .. 8 kq + 7 of scenario i: one 16-byte unit of W's row i, swizzled by i
-        // (this CTA's own rows; the other CTAs' copies of them follow by bulk copy)
-        const int i = r0 + l;
-        const uint32_t woff = (uint32_t)(i * 128 + ((kq ^ (i & 7)) << 4));
-        if (bc_ok(woff + 15u, wchunk, a.err)) {
-          *reinterpret_cast<uint4*>(wbuf + woff) = hv;
-          *reinterpret_cast<uint4*>(wbuf + wchunk + woff) = lv;
+        if constexpr (!VO) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float wa = q[2 * u] * sm->wsc_f[8 * kq + 2 * u];   // powers of two: exact
+            const float wb = q[2 * u + 1] * sm->wsc_f[8 * kq + 2 * u + 1];
+            hp[u] = pack2<F16>(wa, wb);
+            const float2 h = unpack2<F16>(hp[u]);
+            lp[u] = pack2<F16>(wa - h.x, wb - h.y);
+          }
+          // decisions 8 kq .. 8 kq + 7 of scenario i: one 16-byte unit of W's row i, swizzled by i
+          // (this CTA's own rows; the other CTAs' copies of them follow by bulk copy)
+          const int i = r0 + l;
+          const uint32_t woff = (uint32_t)(i * 128 + ((kq ^ (i & 7)) << 4));
+          if (bc_ok(woff + 15u, wchunk, a.err)) {
+            *reinterpret_cast<uint4*>(wbuf + woff) = hv;
+            *reinterpret_cast<uint4*>(wbuf + wchunk + woff) = lv;
+          }
         }
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) ff_add(s2h[q], s2l[q], s2t[q]);
+      if (VO) {
+        // this warp has read its rows of the inbox: tell every CTA of the cluster
+        __syncwarp();
+        if (lane < C) mbar_arrive_remote(mapa(smem_u32(&sm->w_full), (uint32_t)lane));
+        continue;
+      }
       fence_proxy_async();   // W: generic stores -> the MMAs' and the bulk copies' reads
       __syncwarp();
       // this warp's rows of W into every other CTA's W (lane p: CTA p), once
@@ -451,7 +468,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
       __syncwarp();
     }
     bool folded = false;   // every tile's block is in the running sum
-    if (tt == my_tiles && my_tiles > 0 &&
+    if (!VO && tt == my_tiles && my_tiles > 0 &&
         warp_wait(smem_u32(&sm->g_full), (uint32_t)((my_tiles - 1) & 1), abort_flag, a.err)) {
       fold(my_tiles - 1);
       folded = true;
@@ -494,7 +511,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
           }
         }
       }
-    } else if (my_tiles == 0 && j < d) {
+    } else if (!VO && my_tiles == 0 && j < d) {
       for (int k = 0; k < a.K; ++k) {
         const size_t o = ((size_t)cl * a.K + k) * d + j;
         if (bc_ok(o, SAA_BOUND(a.n_g), a.err)) {
@@ -642,9 +659,9 @@ static int grad_cluster(int d) {
 // (blocks past d are zero), 64 decision rows each.
 static size_t grad_image_bytes(int d) { return (size_t)(2 * grad_cluster(d)) * 2 * tc::kGKp * 128; }
 
-template <bool F16, bool D8>
+template <bool F16, bool D8, bool VO = false>
 static const void* grad_kernel() {
-  return (const void*)tc::k_tc_grad<F16, D8>;
+  return (const void*)tc::k_tc_grad<F16, D8, VO>;
 }
 
 // Clusters of C CTAs that fit on the device at once (one CTA per SM), per
@@ -695,7 +712,7 @@ saa_status tc_grad_plan(const saa_ctx* ctx, const saa_problem* p, int K, Plan* p
 }
 
 cudaError_t launch_tc_grad(const LawArgs& la, int K, int prec, const Plan& plan, const Workspace& ws, uint32_t* err,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool value_only) {
   const bool f16 = (prec == SAA_F16X3);
   tc::GArgs a;
   a.la = la;
@@ -721,8 +738,11 @@ cudaError_t launch_tc_grad(const LawArgs& la, int K, int prec, const Plan& plan,
   cudaError_t e = launch_tc_image(la.d, K, tc::kGKp, 2 * a.C, f16, ws.Y64, scale2, gaux, img, st);
   if (e != cudaSuccess) return e;
   const bool d8 = (la.d & 7) == 0;
-  const void* kern = f16 ? (d8 ? grad_kernel<true, true>() : grad_kernel<true, false>())
-                         : (d8 ? grad_kernel<false, true>() : grad_kernel<false, false>());
+  const void* kern =
+      value_only ? (f16 ? (d8 ? grad_kernel<true, true, true>() : grad_kernel<true, false, true>())
+                        : (d8 ? grad_kernel<false, true, true>() : grad_kernel<false, false, true>()))
+                 : (f16 ? (d8 ? grad_kernel<true, true>() : grad_kernel<true, false>())
+                        : (d8 ? grad_kernel<false, true>() : grad_kernel<false, false>()));
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};

@@ -2,7 +2,10 @@
 the oracle on the same FP32-mode samples (Eq. 4 and Eq. 5, Sec. 3.1).  Shapes cover a single
 K block, several K blocks with a ragged last one, decision counts that are
 not multiples of 32, ragged scenario tails and every law; the full d=128,
-N=2^20, K=256 workload is checked on sampled decisions."""
+N=2^20, K=256 workload is checked on sampled decisions.  Above d = 256 the
+values run on the cluster kernel without its adjoint (d <= 1024, K <= 64):
+against the oracle, and bit for bit against saa_grad's values, which take
+the same exchange."""
 import numpy as np
 import pytest
 import torch
@@ -74,11 +77,44 @@ def test_tc_full_size_sampled_decisions(prec):
     assert np.max(np.abs(v - ref["var"]) / ref["var"]) <= TOL[prec]
 
 
+@pytest.mark.parametrize("d,N,K", [(300, 5_000, 17), (512, 4_099, 64), (1000, 3_000, 5), (1024, 2_500, 64)])
+@pytest.mark.parametrize("law", [oracle.LAW_GAUSS, oracle.LAW_STUDENT_T])
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+def test_tc_value_parity_large_d(d, N, K, law, prec):
+    from paper_2404_11631_gb300 import saa
+    out, ref, X, inst = _tc(d, N, K, law=law, prec=prec)
+    e_f = est_err(out["f"], ref["f"], ref["var"], X, inst.mu, 0.5)
+    e_p = est_err(out["pbar"], ref["pbar"], ref["var"], X, inst.mu, 0.5)
+    e_v = np.max(np.abs(out["var"] - ref["var"]) / ref["var"])
+    print(f"{prec} d={d} N={N} K={K} law={law}: f {e_f:.2e} pbar {e_p:.2e} var {e_v:.2e}")
+    assert e_f <= TOL[prec] and e_p <= TOL[prec] and e_v <= TOL[prec]
+    gp, op, inst = make(d, N, law=law, seed=3)
+    g = saa.saa_grad(gp, torch.tensor(X, device="cuda"), prec)
+    saa.saa_ctx_sync()
+    assert np.array_equal(g["f"].cpu().numpy(), out["f"])
+
+
+def test_tc_value_large_d_many_tiles_sampled_decisions():
+    from paper_2404_11631_gb300 import saa
+    d, N, K = 1024, 1 << 18, 64
+    gp, op, inst = make(d, N, law=oracle.LAW_MIX, seed=0)
+    X = inputs.decisions(K, d, seed=0)
+    out = saa.saa_eval(gp, torch.tensor(X, device="cuda"), "f16x3")
+    saa.saa_ctx_sync()
+    pick = [0, 37, 63]
+    ref = oracle.saa(op, 32, X[pick])
+    f = out["f"].cpu().numpy()[pick]
+    assert est_err(f, ref["f"], ref["var"], X[pick], inst.mu, 0.5) <= TOL["f16x3"]
+
+
 def test_tc_unsupported_shapes_are_rejected():
     from paper_2404_11631_gb300 import saa
     gp, op, inst = make(1024, 1000)
     with pytest.raises(saa.SAAError):
-        saa.saa_eval(gp, torch.zeros(2, 1024, dtype=torch.float64, device="cuda"), "f16x3")
+        saa.saa_eval(gp, torch.zeros(65, 1024, dtype=torch.float64, device="cuda"), "f16x3")
+    gp, op, inst = make(1025, 1000)
+    with pytest.raises(saa.SAAError):
+        saa.saa_eval(gp, torch.zeros(2, 1025, dtype=torch.float64, device="cuda"), "f16x3")
     gp, op, inst = make(16, 1000)
     with pytest.raises(saa.SAAError):
         saa.saa_eval(gp, torch.zeros(257, 16, dtype=torch.float64, device="cuda"), "f16x3")
