@@ -161,7 +161,13 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sm->tmem_base;
-  const int nh = (!F8 && a.Kp > 128) ? 2 : 1;   // column halves per tile (E4M3: one accumulator, whole tile)
+  // One accumulator per tile (E4M3 always; the 16-bit types when the ring
+  // holds a whole tile and a stage more, nkb < nst): the corrections of
+  // every K block first, then hi*hi, in one 256-column slot.  Otherwise the
+  // 16-bit types keep hi*hi and the corrections in two accumulators, a
+  // tile's columns split over the slots at Kp > 128.
+  const bool single = F8 || a.nkb < nst;
+  const int nh = (!single && a.Kp > 128) ? 2 : 1;   // column halves per tile
   const int my_tiles = (int)((a.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
   const int iters = my_tiles * a.nkb;
   float s2h[kSMaxKp / 32 / kSEpiStride], s2l[kSMaxKp / 32 / kSEpiStride];   // epilogue: S2 (float-float)
@@ -227,6 +233,28 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
             mma_e4m3(d1, desc_sw128(a_hi + 96u), desc_sw128(b1 + 32u), idesc, 1u);
             mma_e4m3(d1, desc_sw128(a_hi), desc_sw128(b1), idesc, 1u);
             mma_e4m3(d1, desc_sw128(a_hi + 32u), desc_sw128(b1 + 32u), idesc, 1u);
+          } else if (single) {
+            // this K block's corrections now; the hi*hi of every K block of
+            // the tile once its last block is in (the tile's stages are
+            // consecutive in the ring and all still held)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t o = (uint32_t)(kk * 32);
+              mma_bf16(d1, desc_sw128(a_hi + o), desc_sw128(b_lo + o), idesc, (kb == 0 && kk == 0) ? 0u : 1u);
+              mma_bf16(d1, desc_sw128(a_lo + o), desc_sw128(b_hi + o), idesc, 1u);
+            }
+            if (kb == a.nkb - 1) {
+              for (int k2 = 0; k2 < a.nkb; ++k2) {
+                const int s2 = (st - (a.nkb - 1 - k2) + nst) % nst;
+                const uint32_t ah = sA + (uint32_t)(s2 * kSStageBytes);
+                const uint32_t bh = sB + (uint32_t)(k2 * 2) * hl_b;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                  const uint32_t o = (uint32_t)(kk * 32);
+                  mma_bf16(d1, desc_sw128(ah + o), desc_sw128(bh + o), idesc, 1u);
+                }
+              }
+            }
           } else {
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
@@ -240,7 +268,11 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
           if (kb == a.nkb - 1) mma_commit(smem_u32(&sm->q_full[sl]));
         }
         if (!ok) break;
-        mma_commit(smem_u32(&sm->a_empty[st]));
+        if (F8 || !single) {
+          mma_commit(smem_u32(&sm->a_empty[st]));
+        } else if (kb == a.nkb - 1) {   // the tile's stages, once its hi*hi are issued
+          for (int k2 = 0; k2 < a.nkb; ++k2) mma_commit(smem_u32(&sm->a_empty[(st - (a.nkb - 1 - k2) + nst) % nst]));
+        }
         if (++kb == a.nkb) { kb = 0; ++tt; }
         if (++st == nst) { st = 0; ph ^= 1u; }
       }
@@ -302,7 +334,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_tc_stream(SArgs a, const __gri
         for (int g = gb + g0; g < ge; g += kSEpiStride) {
           if (32 * g < a.Kp) {
             const uint32_t c = (uint32_t)(32 * g - 128 * h);
-            if constexpr (F8)
+            if (single)
               ff_add(s2h[0], s2l[0], epi_sq_colsum32_1(d1 + c, lane));
             else
               ff_add(s2h[0], s2l[0], epi_sq_colsum32_x2(d1 + c, d2 + c, lane));
