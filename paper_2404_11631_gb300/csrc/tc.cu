@@ -352,7 +352,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_value(Args a) {
 // the next.  The tile's K blocks (at most two of the three stages) stay
 // resident until its MMAs complete.
 // ------------------------------------------------------------------------
-constexpr int kThreads1 = 32 * (kEpiWarps + kRngWarps);
+// 16 generator warps, 96 registers: 20, 24 and 28 warps (80, 72 and 64
+// registers, no spills) each measured slower.
+constexpr int kRngWarps1 = 16;
+constexpr int kRngThreads1 = 32 * kRngWarps1;
+constexpr int kThreads1 = 32 * (kEpiWarps + kRngWarps1);
+constexpr int kRowStep1 = kRngThreads1 / 8;   // rows between a generator thread's rows in a stage
+static_assert(kRowStep1 % 8 == 0 && kM % kRowStep1 == 0,
+              "every thread draws the same rows, all with one swizzle phase");
 
 template <bool F16, int NKB, bool D8>
 __global__ void __launch_bounds__(kThreads1, 1) k_tc_value1(Args a) {
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(kThreads1, 1) k_tc_value1(Args a) {
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(smem_u32(&sm->a_full[s]), kRngWarps);
+      mbar_init(smem_u32(&sm->a_full[s]), kRngWarps1);
       mbar_init(smem_u32(&sm->a_empty[s]), 1);
     }
     for (int s = 0; s < kSBufs; ++s) mbar_init(smem_u32(&sm->s_ready[s]), kM / 32);
@@ -395,7 +402,6 @@ __global__ void __launch_bounds__(kThreads1, 1) k_tc_value1(Args a) {
   tc_fence_after();
   const uint32_t tmem = sm->tmem_base;
   const int my_tiles = (int)((a.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
-  const int iters = my_tiles * a.nkb;
   float macc[NKB][8];                          // generator: per-dimension sums of a_i
   float s2h[kMaxKp / 32], s2l[kMaxKp / 32];    // epilogue: S2 of column 32 g + epi_col(lane)
 
@@ -475,13 +481,15 @@ __global__ void __launch_bounds__(kThreads1, 1) k_tc_value1(Args a) {
       if (!warp_wait(smem_u32(&sm->q_full[buf]), (uint32_t)((te >> 1) & 1), abort_flag, a.err)) break;
       tc_fence_after();
       const uint32_t tq = tmem + (uint32_t)(buf * a.Kp) + lane_base;
-      // the group loop stays rolled (register pressure); the running sums
-      // rotate so that group g's pair is s2h[0] / s2l[0] when it is added
+      // the group loop stays rolled (register pressure; unrolled it measured
+      // slower), two groups per pass: the running sums rotate by two so that
+      // groups g, g + 1 are in s2h[0..1] / s2l[0..1] when they are added
 #pragma unroll 1
-      for (int g = 0; g < kMaxKp / 32; ++g) {
+      for (int g = 0; g < kMaxKp / 32; g += 2) {
         if (32 * g < a.Kp) ff_add(s2h[0], s2l[0], epi_sq_colsum32_1(tq + (uint32_t)(32 * g), lane));
-        rot_left(s2h);
-        rot_left(s2l);
+        if (32 * g + 32 < a.Kp) ff_add(s2h[1], s2l[1], epi_sq_colsum32_1(tq + (uint32_t)(32 * g + 32), lane));
+        rot_left2(s2h);
+        rot_left2(s2l);
       }
       tc_fence_before();
       __syncwarp();
@@ -498,84 +506,92 @@ __global__ void __launch_bounds__(kThreads1, 1) k_tc_value1(Args a) {
     __syncwarp();
   } else {
     // ------------------------------------------------------------ RNG ---
-    const int rt = threadIdx.x - 32 * kEpiWarps;       // 0 .. kRngThreads-1
+    // One pass per tile; the tile's K blocks (one stage each) in an
+    // unrolled inner loop, so each stage's m~ sums go straight to their own
+    // registers.  The sums are kept as f32x2 pairs (dimensions 2e, 2e + 1).
+    const int rt = threadIdx.x - 32 * kEpiWarps;       // 0 .. kRngThreads1-1
     const int cu = rt & 7;                             // 16-byte unit (8 dims) within the K block
-    const int r0 = rt >> 3;                            // this thread's rows r0, r0 + kRngThreads / 8, ...
+    const int r0 = rt >> 3;
     const gen::Stream gs = gen::make_stream(la.seed, la.epoch, la.instance);
     const uint32_t half = la.N / 2u;
     const bool tlaw = la.law == SAA_LAW_STUDENT_T;
+    unsigned long long mp[NKB][4];
 #pragma unroll
     for (int b = 0; b < NKB; ++b)
 #pragma unroll
-      for (int e = 0; e < 8; ++e) macc[b][e] = 0.0f;
-    int tt = 0, kb = 0, st = 0;
+      for (int e = 0; e < 4; ++e) mp[b][e] = 0ull;   // +0.0f, +0.0f
+    int st = 0;
     uint32_t ph = 0;
-    for (int it = 0; it < iters; ++it) {
+    bool ok = true;
+    for (int tt = 0; tt < my_tiles && ok; ++tt) {
       const uint32_t tile = blockIdx.x + (uint32_t)tt * gridDim.x;
       const uint32_t i0 = la.i_base + tile * (uint32_t)kM;
       const int nrow = (int)min((uint32_t)kM, la.rows_end() - i0);
       const int sb = tt & (kSBufs - 1);
       const uint32_t s_bar = smem_u32(&sm->s_ready[sb]);
-      if (tlaw && kb == 0 && rt < kM) {   // generator warps 0..3 draw the tile's scales
+      if (tlaw && rt < kM) {   // generator warps 0..3 draw the tile's scales
         sm->s_buf[sb][rt] = (rt < nrow) ? gen::t_scale_f(gs, i0 + (uint32_t)rt, la.nu) : 0.0f;
         __syncwarp();
         if (lane == 0) mbar_arrive(s_bar);
       }
-      if (!warp_wait(smem_u32(&sm->a_empty[st]), ph ^ 1u, abort_flag, a.err)) break;
-      if (tlaw && !warp_wait(s_bar, (uint32_t)((tt >> 2) & 1), abort_flag, a.err)) break;
-      uint8_t* stage = As + st * kStageBytes;
-      const int j0 = kb * kKB + cu * 8;   // first dimension of this unit
-      float vs[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) vs[e] = 0.0f;
-      const bool unit_ok = j0 < d;
+      for (int kb = 0; kb < NKB; ++kb) {
+        if (!warp_wait(smem_u32(&sm->a_empty[st]), ph ^ 1u, abort_flag, a.err)) { ok = false; break; }
+        if (kb == 0 && tlaw && !warp_wait(s_bar, (uint32_t)((tt >> 2) & 1), abort_flag, a.err)) {
+          ok = false;
+          break;
+        }
+        uint8_t* stage = As + st * kStageBytes;
+        const int j0 = kb * kKB + cu * 8;   // first dimension of this unit
+        const bool unit_ok = j0 < d;
 #pragma unroll 1
-      for (int r = r0; r < kM; r += kRngThreads / 8) {
-        float v[8];
+        for (int r = r0; r < kM; r += kRowStep1) {
+          float v[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = 0.0f;
-        if (r < nrow && unit_ok) {
-          const uint32_t i = i0 + (uint32_t)r;
-          const bool logn = gen::is_lognormal(la.law, i, half);
-          float z[4];
-          gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2), i, logn, z);
+          for (int e = 0; e < 8; ++e) v[e] = 0.0f;
+          if (r < nrow && unit_ok) {
+            const uint32_t i = i0 + (uint32_t)r;
+            const bool logn = gen::is_lognormal(la.law, i, half);
+            float z[4];
+            gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2), i, logn, z);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) v[e] = (D8 || j0 + e < d) ? z[e] : 0.0f;
-          if (D8 || j0 + 4 < d) {
-            gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2) + 1u, i, logn, z);
+            for (int e = 0; e < 4; ++e) v[e] = (D8 || j0 + e < d) ? z[e] : 0.0f;
+            if (D8 || j0 + 4 < d) {
+              gen::Gen<float>::block(gs, (uint32_t)(j0 >> 2) + 1u, i, logn, z);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) v[4 + e] = (D8 || j0 + 4 + e < d) ? z[e] : 0.0f;
+              for (int e = 0; e < 4; ++e) v[4 + e] = (D8 || j0 + 4 + e < d) ? z[e] : 0.0f;
+            }
+            if (tlaw) {
+              const float sv = sm->s_buf[sb][r];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) v[e] *= sv;
+            }
           }
-          if (tlaw) {
-            const float sv = sm->s_buf[sb][r];
+          uint32_t hi[4], lo[4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] *= sv;
+          for (int e = 0; e < 4; ++e) {
+            const unsigned long long vp = f2_pack(__float_as_uint(v[2 * e]), __float_as_uint(v[2 * e + 1]));
+            hi[e] = pack2<F16>(v[2 * e], v[2 * e + 1]);
+            const float2 h = unpack2<F16>(hi[e]);
+            float l0, l1;
+            f2_unpack(f2_sub(vp, f2_pack(__float_as_uint(h.x), __float_as_uint(h.y))), l0, l1);
+            lo[e] = pack2<F16>(l0, l1);
+            mp[kb][e] = f2_add(mp[kb][e], vp);
           }
+          const uint32_t off = sw_off(r, cu);
+          *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(stage + kM * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-          hi[e / 2] = pack2<F16>(v[e], v[e + 1]);
-          const float2 h = unpack2<F16>(hi[e / 2]);
-          lo[e / 2] = pack2<F16>(v[e] - h.x, v[e + 1] - h.y);
-        }
-        const uint32_t off = sw_off(r, cu);
-        *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(stage + kM * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) vs[e] += v[e];
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&sm->a_full[st]));
+        if (++st == kStages) { st = 0; ph ^= 1u; }
       }
-#pragma unroll
-      for (int b = 0; b < NKB; ++b)
-        if (b == kb)
-#pragma unroll
-          for (int e = 0; e < 8; ++e) macc[b][e] += vs[e];
-      fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sm->a_full[st]));
-      if (++kb == a.nkb) { kb = 0; ++tt; }
-      if (++st == kStages) { st = 0; ph ^= 1u; }
     }
+#pragma unroll
+    for (int b = 0; b < NKB; ++b)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) f2_unpack(mp[b][e], macc[b][2 * e], macc[b][2 * e + 1]);
     // lanes with equal rt & 7 hold the same unit: fold them (lanes 0..7 keep the sums)
 #pragma unroll
     for (int b = 0; b < NKB; ++b)
@@ -592,7 +608,7 @@ __global__ void __launch_bounds__(kThreads1, 1) k_tc_value1(Args a) {
   __syncthreads();   // MMAs drained: the A stages are free for the reductions
   const int dpad = a.nkb * kKB;
   double* red_s2 = reinterpret_cast<double*>(As);      // [kEpiWarps][Kp]
-  float* red_m = reinterpret_cast<float*>(red_s2 + kEpiWarps * a.Kp);   // [kRngWarps][dpad]
+  float* red_m = reinterpret_cast<float*>(red_s2 + kEpiWarps * a.Kp);   // [kRngWarps1][dpad]
   if (warp >= kEpiWarps && lane < 8) {
     const int rw = warp - kEpiWarps;
 #pragma unroll
@@ -609,7 +625,7 @@ __global__ void __launch_bounds__(kThreads1, 1) k_tc_value1(Args a) {
   __syncthreads();
   for (int j = threadIdx.x; j < d; j += blockDim.x) {
     double s = 0.0;
-    for (int rw = 0; rw < kRngWarps; ++rw) s += (double)red_m[rw * dpad + j];
+    for (int rw = 0; rw < kRngWarps1; ++rw) s += (double)red_m[rw * dpad + j];
     if (bc_ok((size_t)blockIdx.x * d + j, SAA_BOUND(a.n_m), a.err)) a.part_m[(size_t)blockIdx.x * d + j] = s;
   }
   for (int k = threadIdx.x; k < a.K; k += blockDim.x) {

@@ -266,6 +266,11 @@ __device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsig
   asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
 }
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
 __device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
   unsigned long long r;
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
@@ -356,6 +361,17 @@ __device__ __forceinline__ void rot_left(float (&a)[N]) {
 #pragma unroll
   for (int i = 0; i + 1 < N; ++i) a[i] = a[i + 1];
   a[N - 1] = t;
+}
+
+// The same by two (a[i] = a[i + 2]), for a group loop that takes two
+// groups per pass.
+template <int N>
+__device__ __forceinline__ void rot_left2(float (&a)[N]) {
+  const float t0 = a[0], t1 = a[1];
+#pragma unroll
+  for (int i = 0; i + 2 < N; ++i) a[i] = a[i + 2];
+  a[N - 2] = t0;
+  a[N - 1] = t1;
 }
 
 // ---------------------------------------------------------------- clusters
