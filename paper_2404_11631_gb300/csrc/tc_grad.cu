@@ -31,22 +31,23 @@
 //   adjoint   with all rows of W in place, the thread issues
 //             G^(r) = A^(r)' W for the tile, reading the same stage as an
 //             MN-major operand (the dimensions of a 64-dimension chunk are
-//             contiguous) against [W_hi; W_lo] and A_lo' W_hi.  The epilogue
-//             adds each tile's block (hi*hi + corrections) into a
-//             Kahan-compensated running sum held in TMEM, so G never leaves
-//             the SM until the end.
+//             contiguous) against [W_hi; W_lo] and A_lo' W_hi, into a block
+//             accumulator that spans two tiles.  The epilogue adds each
+//             block (hi*hi + corrections) into a Kahan-compensated running
+//             sum held in TMEM, so G never leaves the SM until the end.
 // The draw of tile t + 1 overlaps the forward, exchange and adjoint of tile
-// t (two stages), and the fold of tile t overlaps the exchange of tile
-// t + 1; the exchange moves 2 x 28 KB of distributed shared memory per tile
+// t (two stages), and the fold of a block overlaps the exchange of the
+// tile after it; the exchange moves 2 x 28 KB of distributed shared memory per tile
 // and CTA at C = 8.
 //
 // Accuracy.  The tensor core rounds every update of an accumulator with a
 // bias toward zero, so a running sum over T k steps loses about T/2 units in
 // the last place.  The forward's accumulator takes the 16 correction steps
 // while it is still small and then the 8 hi*hi steps per CTA, and the C
-// partials are added with round-to-nearest FP32 additions; the adjoint's blocks run 8 k
-// steps per tile before their compensated fold, so the bias stays near 4
-// units in the last place of a tile's block.  The adjoint's representation
+// partials are added with round-to-nearest FP32 additions; the adjoint's blocks run 16 k
+// steps (two tiles) before their compensated fold, so the bias stays near 8
+// units in the last place of a block (folding every tile, 4 units, took
+// 2.5 % more time).  The adjoint's representation
 // error changes sign and size from scenario to scenario, so it shrinks like
 // sqrt(d / N) relative to G: FP16 hi/lo (2^-22 per product) keeps it below
 // 1e-6 from N ~ d upwards, where BF16 hi/lo (2^-17) would not.
@@ -80,6 +81,7 @@ constexpr int kGThreads = 32 * (kGEpiWarps + 1 + kGRngWarps);
 constexpr int kGRngThreads = 32 * kGRngWarps;
 constexpr int kGKp = 64;                   // decision columns (K <= 64; unused ones are zero)
 constexpr int kGMaxCluster = 8;
+constexpr int kGFoldTiles = 2;             // tiles per block of G between compensated folds
 constexpr int kGMaxDim = kGDims * kGMaxCluster;
 static_assert(kGRngThreads == 512, "stage mapping assumes 512 generator threads");
 
@@ -279,8 +281,9 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
     const uint32_t ida2 = idesc_f16(kGDims, 2 * kGKp, F16) | kIdescAMajorMN | kIdescBMajorMN;
     const uint32_t ida1 = idesc_f16(kGDims, kGKp, F16) | kIdescAMajorMN | kIdescBMajorMN;
     bool adj_issued = false;
-    // Kahan fold of tile tf's block of G (hi*hi + corrections) into the
-    // running sum; then the block's TMEM is free for the next adjoint
+    // Kahan fold of the block of G (hi*hi + corrections) that ends with
+    // tile tf (kGFoldTiles tiles, fewer at the end) into the running sum;
+    // then the block's TMEM is free for the next adjoint
     auto fold = [&](int tf) {
       tc_fence_after();
 #pragma unroll 1
@@ -288,7 +291,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         uint32_t rg[8], rh[8], rs[8], rc[8];
         tmem_ld8(tg1 + lane_base + c0, rg);
         tmem_ld8(tg2 + lane_base + c0, rh);
-        if (tf > 0) {
+        if (tf >= kGFoldTiles) {
           tmem_ld8(tgs + lane_base + c0, rs);
           tmem_ld8(tgc + lane_base + c0, rc);
         }
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const float g = __uint_as_float(rg[q]) + __uint_as_float(rh[q]);
-          if (tf == 0) {
+          if (tf < kGFoldTiles) {
             rc[q] = 0u;
             rg[q] = __float_as_uint(g);
           } else {
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         mbar_expect_tx(smem_u32(&sm->x_full), (uint32_t)(C - 1) * (uint32_t)nr * 64u);
       }
       __syncwarp();
-      if (!VO && tt > 0) fold(tt - 1);
+      if (!VO && tt > 0 && tt % kGFoldTiles == 0) fold(tt - 1);
       // ---- reduce this CTA's rows: the C partials in rank order, S2, and W into every CTA
       if (!warp_wait_cluster(smem_u32(&sm->x_full), (uint32_t)(tt & 1), abort_flag, a.err)) break;
       float s2t[8];
@@ -383,12 +386,14 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         float q[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) q[j] = 0.0f;
-#pragma unroll 1
-        for (int p = 0; p < C; ++p) {   // rank order: the sum does not depend on timing
-          const float4 va = *reinterpret_cast<const float4*>(inbox + inbox_off(p, nr, l, 8 * kq));
-          const float4 vb = *reinterpret_cast<const float4*>(inbox + inbox_off(p, nr, l, 8 * kq + 4));
-          q[0] += va.x; q[1] += va.y; q[2] += va.z; q[3] += va.w;
-          q[4] += vb.x; q[5] += vb.y; q[6] += vb.z; q[7] += vb.w;
+#pragma unroll
+        for (int p = 0; p < kGMaxCluster; ++p) {   // rank order: the sum does not depend on timing
+          if (p < C) {
+            const float4 va = *reinterpret_cast<const float4*>(inbox + inbox_off(p, nr, l, 8 * kq));
+            const float4 vb = *reinterpret_cast<const float4*>(inbox + inbox_off(p, nr, l, 8 * kq + 4));
+            q[0] += va.x; q[1] += va.y; q[2] += va.z; q[3] += va.w;
+            q[4] += vb.x; q[5] += vb.y; q[6] += vb.z; q[7] += vb.w;
+          }
         }
         uint4 hv, lv;
         uint32_t* hp = &hv.x;
@@ -448,7 +453,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
       // contiguous, the hi and lo halves 16 KB apart)
       if (issuer) {
         bool ok = mbar_wait_cluster(smem_u32(&sm->w_full), (uint32_t)(tt & 1), abort_flag, a.err) &&
-                  (tt == 0 || mbar_wait(smem_u32(&sm->g_empty), (uint32_t)((tt - 1) & 1), abort_flag, a.err));
+                  (tt % kGFoldTiles != 0 || tt == 0 ||   // a new block waits for the last one's fold
+                   mbar_wait(smem_u32(&sm->g_empty), (uint32_t)((tt / kGFoldTiles - 1) & 1), abort_flag, a.err));
         if (ok) {
           tc_fence_after();
           const uint32_t stage = sRing + (uint32_t)((tt % kGStages) * kGStageBytes);
@@ -456,7 +462,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
           for (int kk = 0; kk < 8; ++kk) {   // 16 scenarios per k step
             const uint32_t at_hi = stage + (uint32_t)(kk * 2048), at_lo = at_hi + kGChunkBytes;
             const uint64_t bw = desc_mn_sw128(sW + (uint32_t)(kk * 2048), wchunk, 1024);
-            mma_bf16(tg1, desc_mn_sw128(at_hi, 2 * kGChunkBytes, 1024), bw, ida2, kk == 0 ? 0u : 1u);
+            mma_bf16(tg1, desc_mn_sw128(at_hi, 2 * kGChunkBytes, 1024), bw, ida2,
+                     (kk == 0 && tt % kGFoldTiles == 0) ? 0u : 1u);
             mma_bf16(tg2, desc_mn_sw128(at_lo, 2 * kGChunkBytes, 1024), bw, ida1, 1u);
           }
           mma_commit(smem_u32(&sm->a_empty[tt % kGStages]));
