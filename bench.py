@@ -242,7 +242,7 @@ EPI_OPS_TC_GRAD = 8.0   # per pair: chunk fold, D1 + D2, square + reduce, W hi/l
 # (dram__bytes_read.sum + dram__bytes_write.sum) on a small case, scaled to
 # the launch's N where the traffic grows with the number of tiles; absent
 # until taken on the current kernel.
-GRAD_TRAFFIC = {("f16x3", 1024, 64): lambda n: 408832.0}   # N = 2^17 capture; image and partials, not N
+GRAD_TRAFFIC = {("f16x3", 1024, 64): lambda n: 409600.0}   # N = 2^17 capture; image and partials, not N
 
 
 def grad_roofline(prec, d, N, K, law, kern_s, peaks):

@@ -32,7 +32,7 @@
 //             G^(r) = A^(r)' W for the tile, reading the same stage as an
 //             MN-major operand (the dimensions of a 64-dimension chunk are
 //             contiguous) against [W_hi; W_lo] and A_lo' W_hi, into a block
-//             accumulator that spans two tiles.  The epilogue adds each
+//             accumulator that spans four tiles.  The epilogue adds each
 //             block (hi*hi + corrections) into a Kahan-compensated running
 //             sum held in TMEM, so G never leaves the SM until the end.
 // The draw of tile t + 1 overlaps the forward, exchange and adjoint of tile
@@ -44,10 +44,11 @@
 // bias toward zero, so a running sum over T k steps loses about T/2 units in
 // the last place.  The forward's accumulator takes the 16 correction steps
 // while it is still small and then the 8 hi*hi steps per CTA, and the C
-// partials are added with round-to-nearest FP32 additions; the adjoint's blocks run 16 k
-// steps (two tiles) before their compensated fold, so the bias stays near 8
-// units in the last place of a block (folding every tile, 4 units, took
-// 2.5 % more time).  The adjoint's representation
+// partials are added with round-to-nearest FP32 additions; the adjoint's blocks run 32 k
+// steps (four tiles) before their compensated fold, so the bias stays near
+// 16 units in the last place of a block (folding every tile, 4 units, took
+// 3.8 % more time; the blocks' partial sums change sign from block to block,
+// and G moved by 5e-9 relative to its largest entry).  The adjoint's representation
 // error changes sign and size from scenario to scenario, so it shrinks like
 // sqrt(d / N) relative to G: FP16 hi/lo (2^-22 per product) keeps it below
 // 1e-6 from N ~ d upwards, where BF16 hi/lo (2^-17) would not.
@@ -81,7 +82,7 @@ constexpr int kGThreads = 32 * (kGEpiWarps + 1 + kGRngWarps);
 constexpr int kGRngThreads = 32 * kGRngWarps;
 constexpr int kGKp = 64;                   // decision columns (K <= 64; unused ones are zero)
 constexpr int kGMaxCluster = 8;
-constexpr int kGFoldTiles = 2;             // tiles per block of G between compensated folds
+constexpr int kGFoldTiles = 4;             // tiles per block of G between compensated folds
 constexpr int kGMaxDim = kGDims * kGMaxCluster;
 static_assert(kGRngThreads == 512, "stage mapping assumes 512 generator threads");
 
@@ -558,9 +559,9 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
       }
       if (tlaw && !warp_wait(s_bar, (uint32_t)((tt >> 1) & 1), abort_flag, a.err)) break;
       uint8_t* chunk = ring + st * kGStageBytes + ch * 2 * kGChunkBytes;
-      float msum[8];
+      unsigned long long mp[4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) msum[q] = 0.0f;
+      for (int e = 0; e < 4; ++e) mp[e] = 0ull;
 #pragma unroll 1
       for (int r = rbase; r < kGM; r += 32) {
         float v[8];
@@ -586,12 +587,14 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         }
         uint32_t hi[4], lo[4];
 #pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-          msum[q] += v[q];
-          msum[q + 1] += v[q + 1];
-          hi[q / 2] = pack2<F16>(v[q], v[q + 1]);
-          const float2 h = unpack2<F16>(hi[q / 2]);
-          lo[q / 2] = pack2<F16>(v[q] - h.x, v[q + 1] - h.y);
+        for (int e = 0; e < 4; ++e) {
+          const unsigned long long vp = f2_pack(__float_as_uint(v[2 * e]), __float_as_uint(v[2 * e + 1]));
+          hi[e] = pack2<F16>(v[2 * e], v[2 * e + 1]);
+          const float2 h = unpack2<F16>(hi[e]);
+          float l0, l1;
+          f2_unpack(f2_sub(vp, f2_pack(__float_as_uint(h.x), __float_as_uint(h.y))), l0, l1);
+          lo[e] = pack2<F16>(l0, l1);
+          mp[e] = f2_add(mp[e], vp);
         }
         const uint32_t off = sw_off(r, cu);
         if (bc_ok(off + 15u, (size_t)kGChunkBytes, a.err)) {   // one 16-byte unit of each half of the chunk
@@ -600,7 +603,12 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         }
       }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) ff_add(mh[q], ml[q], msum[q]);
+      for (int e = 0; e < 4; ++e) {
+        float m0, m1;
+        f2_unpack(mp[e], m0, m1);
+        ff_add(mh[2 * e], ml[2 * e], m0);
+        ff_add(mh[2 * e + 1], ml[2 * e + 1], m1);
+      }
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sm->a_full[st][ch]));
