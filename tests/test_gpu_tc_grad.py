@@ -52,6 +52,19 @@ def test_tc_grad_lambda(prec, lam):
 
 
 @pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
+@pytest.mark.parametrize("N", [40 * 128 + 5, 76 * 128 - 51, 101 * 128 + 1])
+def test_tc_grad_partial_blocks_of_G(prec, N):
+    # The adjoint accumulates a block of G over four tiles before each
+    # compensated fold.  With 8-CTA clusters at d = 1024 these scenario
+    # counts leave each cluster 2 or 3, 5 or 6, and 6 or 7 tiles at 15
+    # resident clusters (2 to 8 for 13 to 20 clusters), so the last block is
+    # partial, and for 2 or 3 tiles the first block is also the last.
+    out, ref, X, inst = _grad(1024, N, 5, law=oracle.LAW_MIX, seed=N % 97, prec=prec)
+    assert grad_err(out["grad"], ref["grad"]) <= TOL_GRAD[prec]
+    assert est_err(out["f"], ref["f"], ref["var"], X, inst.mu, 0.5) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f16x3", "bf16x3"])
 def test_tc_grad_small_N_edge(prec):
     # N = 2 (one partial tile), a tile-exact N = 128 and one row past it
     for N in (2, 128, 129):
