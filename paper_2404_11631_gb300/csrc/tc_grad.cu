@@ -559,9 +559,9 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
       }
       if (tlaw && !warp_wait(s_bar, (uint32_t)((tt >> 1) & 1), abort_flag, a.err)) break;
       uint8_t* chunk = ring + st * kGStageBytes + ch * 2 * kGChunkBytes;
-      unsigned long long mp[4];
+      float msum[8];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) mp[e] = 0ull;
+      for (int q = 0; q < 8; ++q) msum[q] = 0.0f;
 #pragma unroll 1
       for (int r = rbase; r < kGM; r += 32) {
         float v[8];
@@ -587,14 +587,12 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         }
         uint32_t hi[4], lo[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const unsigned long long vp = f2_pack(__float_as_uint(v[2 * e]), __float_as_uint(v[2 * e + 1]));
-          hi[e] = pack2<F16>(v[2 * e], v[2 * e + 1]);
-          const float2 h = unpack2<F16>(hi[e]);
-          float l0, l1;
-          f2_unpack(f2_sub(vp, f2_pack(__float_as_uint(h.x), __float_as_uint(h.y))), l0, l1);
-          lo[e] = pack2<F16>(l0, l1);
-          mp[e] = f2_add(mp[e], vp);
+        for (int q = 0; q < 8; q += 2) {
+          msum[q] += v[q];
+          msum[q + 1] += v[q + 1];
+          hi[q / 2] = pack2<F16>(v[q], v[q + 1]);
+          const float2 h = unpack2<F16>(hi[q / 2]);
+          lo[q / 2] = pack2<F16>(v[q] - h.x, v[q + 1] - h.y);
         }
         const uint32_t off = sw_off(r, cu);
         if (bc_ok(off + 15u, (size_t)kGChunkBytes, a.err)) {   // one 16-byte unit of each half of the chunk
@@ -603,12 +601,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_tc_grad(GArgs a) {
         }
       }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        float m0, m1;
-        f2_unpack(mp[e], m0, m1);
-        ff_add(mh[2 * e], ml[2 * e], m0);
-        ff_add(mh[2 * e + 1], ml[2 * e + 1], m1);
-      }
+      for (int q = 0; q < 8; ++q) ff_add(mh[q], ml[q], msum[q]);
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sm->a_full[st][ch]));
