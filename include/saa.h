@@ -135,6 +135,12 @@ size_t saa_workspace_size(const saa_ctx* ctx, const saa_problem* prob, int32_t K
  *   f     device [K]: f_hat(w_k)
  *   pbar  device [K] or NULL: w_k'R_bar (Eq. 5)
  *   var   device [K] or NULL: (1/(N-1)) sum_i (w_k'(R_i - R_bar))^2
+ * At SAA_F16X3 / SAA_BF16X3 a K larger than one tensor-core launch takes
+ * (256 up to d = 128, 128 up to d = 256, 64 above it and for gradients)
+ * runs as consecutive chunks of that size in the same workspace (which
+ * saa_workspace_size sizes for one chunk); every chunk draws the same
+ * scenarios, so the time grows with the number of chunks, and a decision's
+ * result does not depend on the other decisions up to FP32 summation order.
  * Errors: SAA_EINVAL for d < 1, N < 2, N >= 2^32, K outside [1, 65535], a bad law/nu, NULL
  * required pointers; SAA_ENOMEM if ws_bytes is too small; SAA_EUNSUPPORTED
  * for d beyond the precision's limit (saa_max_dim). */
@@ -164,6 +170,7 @@ saa_status saa_eval_host(saa_ctx* ctx, const saa_problem* prob, int32_t K, const
  *   grad f_hat(w) = lambda (2/(N-1)) sum_i (R_i - R_bar)(R_i - R_bar)'w - R_bar).
  *   f     device [K] or NULL
  *   grad  device [K*d]: row k is grad f_hat(w_k)
+ * K beyond 64 runs in chunks at the tensor-core precisions, as saa_eval.
  * Errors as saa_eval. */
 saa_status saa_grad(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec,
                     double* f, double* grad, void* ws, size_t ws_bytes, void* stream);
@@ -568,8 +575,10 @@ saa_status saa_plan_info(const saa_ctx* ctx, const saa_problem* prob, int32_t K,
                          int32_t* grid, int32_t* cluster, int64_t* tiles);
 
 /* Largest d that `prec` supports.  For SAA_F16X3 and SAA_BF16X3 that is
- * 1024: up to d = 256 any K <= 256 (k_tc_value), above it K <= 64 (the
- * cluster kernel that splits the dimensions, without its adjoint for values). */
+ * 1024: up to d = 256 one launch takes K <= 256 (k_tc_value, K <= 128 above
+ * d = 128), above it K <= 64 (the cluster kernel that splits the dimensions,
+ * without its adjoint for values); saa_eval and saa_grad run larger K in
+ * chunks of that size, saa_partials does not. */
 int32_t saa_max_dim(saa_prec prec);
 
 const char* saa_status_string(saa_status s);

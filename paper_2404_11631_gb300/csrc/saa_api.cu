@@ -411,9 +411,25 @@ saa_status saa_plan_info(const saa_ctx* ctx, const saa_problem* prob, int32_t K,
   return SAA_OK;
 }
 
+// Decisions per launch when one tensor-core launch cannot take all K (0:
+// one launch, or not a tensor precision): saa_eval and saa_grad then run K
+// as consecutive chunks of that size.  Each decision's estimate depends
+// only on the scenarios, which every chunk redraws identically, and on its
+// own x_k.
+static int tc_chunk(const saa_problem* p, int K, saa_prec prec, int want_grad) {
+  if (!is_tc(prec) || !p->chol) return 0;
+  if (want_grad) return (!tc_grad_supported(p, K) && tc_grad_supported(p, 64)) ? 64 : 0;
+  if (tc_supported(p, K, 0) || tc_grad_supported(p, K)) return 0;
+  for (int k = 256; k >= 32; k /= 2)
+    if (tc_supported(p, k, 0)) return k;
+  return tc_grad_supported(p, 64) ? 64 : 0;
+}
+
 size_t saa_workspace_size(const saa_ctx* ctx, const saa_problem* prob, int32_t K, saa_prec prec, int want_grad) {
   if (!ctx || check_problem(prob) != SAA_OK || K < 1) return 0;
   if (want_grad == 2) K = 1;
+  const int kc = want_grad == 2 ? 0 : tc_chunk(prob, K, prec, want_grad);
+  if (kc > 0) K = kc;
   DeviceGuard g(ctx->device);
   Plan plan;
   if (make_plan(ctx, prob, K, prec, want_grad ? 1 : 0, &plan) != SAA_OK) return 0;
@@ -433,14 +449,30 @@ static saa_status eval_impl(saa_ctx* ctx, const saa_problem* prob, int32_t K, co
   if (((uintptr_t)ws) & 255u) return fail(SAA_EINVAL, "workspace must be 256-byte aligned");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(SAA_ECUDA, "cudaSetDevice failed");
+  const int kc = tc_chunk(prob, K, prec, want_grad);
+  const int Kl = kc > 0 ? kc : K;   // decisions per launch
   Plan plan;
-  s = make_plan(ctx, prob, K, prec, want_grad, &plan);
+  s = make_plan(ctx, prob, Kl, prec, want_grad, &plan);
   if (s != SAA_OK) return s;
   Workspace w;
-  const size_t need = carve(prob, K, plan, want_grad, ws, &w);
+  const size_t need = carve(prob, Kl, plan, want_grad, ws, &w);
   if (ws_bytes < need) return fail(SAA_ENOMEM, "workspace smaller than saa_workspace_size()");
-  return run_estimator(ctx, prob, K, X, prec, want_grad, plan, w, law_args(prob), f, pbar, var, grad,
-                       (cudaStream_t)stream);
+  const size_t d = (size_t)prob->d;
+  for (int k0 = 0; k0 < K; k0 += Kl) {
+    const int n = K - k0 < Kl ? K - k0 : Kl;
+    Plan pc = plan;
+    if (n != Kl) {   // the last, shorter chunk: its own plan in the same workspace
+      s = make_plan(ctx, prob, n, prec, want_grad, &pc);
+      if (s != SAA_OK) return s;
+      if (carve(prob, n, pc, want_grad, ws, &w) > ws_bytes)
+        return fail(SAA_ENOMEM, "workspace smaller than the last decision chunk needs");
+    }
+    s = run_estimator(ctx, prob, n, X + (size_t)k0 * d, prec, want_grad, pc, w, law_args(prob), f ? f + k0 : nullptr,
+                      pbar ? pbar + k0 : nullptr, var ? var + k0 : nullptr, grad ? grad + (size_t)k0 * d : nullptr,
+                      (cudaStream_t)stream);
+    if (s != SAA_OK) return s;
+  }
+  return SAA_OK;
 }
 
 saa_status saa_eval(saa_ctx* ctx, const saa_problem* prob, int32_t K, const double* X, saa_prec prec, double* f,

@@ -5,7 +5,8 @@ not multiples of 32, ragged scenario tails and every law; the full d=128,
 N=2^20, K=256 workload is checked on sampled decisions.  Above d = 256 the
 values run on the cluster kernel without its adjoint (d <= 1024, K <= 64):
 against the oracle, and bit for bit against saa_grad's values, which take
-the same exchange."""
+the same exchange.  More decisions than one launch takes run in chunks:
+against the oracle, and each chunk bit for bit the call on its decisions."""
 import numpy as np
 import pytest
 import torch
@@ -109,12 +110,27 @@ def test_tc_value_large_d_many_tiles_sampled_decisions():
 
 def test_tc_unsupported_shapes_are_rejected():
     from paper_2404_11631_gb300 import saa
-    gp, op, inst = make(1024, 1000)
-    with pytest.raises(saa.SAAError):
-        saa.saa_eval(gp, torch.zeros(65, 1024, dtype=torch.float64, device="cuda"), "f16x3")
     gp, op, inst = make(1025, 1000)
-    with pytest.raises(saa.SAAError):
+    with pytest.raises(saa.SAAError) as e:
         saa.saa_eval(gp, torch.zeros(2, 1025, dtype=torch.float64, device="cuda"), "f16x3")
-    gp, op, inst = make(16, 1000)
-    with pytest.raises(saa.SAAError):
-        saa.saa_eval(gp, torch.zeros(257, 16, dtype=torch.float64, device="cuda"), "f16x3")
+    assert e.value.status in (saa.SAA_EINVAL, saa.SAA_EUNSUPPORTED)   # the workspace query refuses it first
+
+
+@pytest.mark.parametrize("d,K,chunk", [(128, 300, 256), (200, 150, 128), (512, 100, 64)])
+def test_tc_values_in_decision_chunks(d, K, chunk):
+    # more decisions than one launch takes: consecutive chunks in one
+    # workspace; against the oracle, and each chunk bit for bit the call on
+    # its own decisions
+    from paper_2404_11631_gb300 import saa
+    N = 4_001
+    out, ref, X, inst = _tc(d, N, K, law=oracle.LAW_MIX, seed=d, prec="f16x3")
+    assert est_err(out["f"], ref["f"], ref["var"], X, inst.mu, 0.5) <= TOL["f16x3"]
+    assert est_err(out["pbar"], ref["pbar"], ref["var"], X, inst.mu, 0.5) <= TOL["f16x3"]
+    assert np.max(np.abs(out["var"] - ref["var"]) / ref["var"]) <= TOL["f16x3"]
+    gp, op, inst = make(d, N, law=oracle.LAW_MIX, seed=d)
+    Xt = torch.tensor(X, device="cuda")
+    for k0 in range(0, K, chunk):
+        part = saa.saa_eval(gp, Xt[k0:k0 + chunk], "f16x3")
+        saa.saa_ctx_sync()
+        for key in ("f", "pbar", "var"):
+            assert np.array_equal(part[key].cpu().numpy(), out[key][k0:k0 + chunk]), (key, k0)
