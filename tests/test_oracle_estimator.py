@@ -176,3 +176,17 @@ def test_thread_count_does_not_change_results():
         outs.append(subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
                                    check=True).stdout)
     assert outs[0] == outs[1]
+
+
+def test_each_decision_depends_only_on_the_scenarios_and_its_own_w():
+    # Eq. 4 for decision w_k involves only the scenarios and w_k, so any
+    # subset or order of the K decisions gives the same rows, bit for bit:
+    # the property that lets the GPU path run many decisions in chunks.
+    d, N = 9, 4000
+    prob, inst = _gauss_problem(d, N, 11, law=oracle.LAW_MIX)
+    X = inputs.decisions(7, d, seed=4)
+    full = oracle.saa(prob, 32, X, grad=True)
+    for rows in ([0, 1, 2], [6], [5, 3, 4]):
+        part = oracle.saa(prob, 32, X[rows], grad=True)
+        for key in ("f", "pbar", "var", "grad"):
+            assert np.array_equal(part[key], full[key][rows]), (key, rows)
