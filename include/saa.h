@@ -510,9 +510,8 @@ saa_status saa_cholesky(saa_ctx* ctx, int32_t d, const double* Sigma, double* ch
  * SAA_ENOMEM with the needed size in saa_last_error().  The call allocates
  * nothing (no cudaMalloc, cudaFree or allocating library routine).  Its
  * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and keeps it for the process, so make that first
- * call before any stream capture, and do not use this entry point across a
- * cudaDeviceReset.  A diagonal entry of chol that is not positive and
+ * (cudaGetSymbolAddress) and keeps it for the process, so do not use this
+ * entry point across a cudaDeviceReset.  A diagonal entry of chol that is not positive and
  * finite cannot be reported through a context here: the call writes NaN to
  * f (and to pbar, var when given) instead.  All calls share the array:
  * calls whose GPU work overlaps (other streams, other host threads) race on
